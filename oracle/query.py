@@ -1,0 +1,372 @@
+"""Oracle for the encrypted-query circuit: plan (levels, scales, integer
+constants), plain per-block execution, and the FP64 plaintext pipeline the
+decrypted result is judged against.
+
+TEST INFRASTRUCTURE (see oracle/__init__.py).
+
+The circuit is the server side of the paper's exploration (Algorithm 2, the
+local threshold and InnerSum): a linear combination of attribute columns with
+encrypted coefficients (attribute selection, Section 3.3), a private
+polynomial with encrypted coefficients, subtraction of an encrypted threshold
+(Section 4.3.2), a composite odd sign polynomial mapped to step(x) =
+(sign(x)+1)/2 (Section 4.3.2), a sum over ciphertext blocks and InnerSum by
+rotations (Appendix A.1.2 rotation semantics).
+
+Scale discipline (a reading; the paper only says scales multiply and rescale
+divides, Section 2.5): every ciphertext at level l carries the standard scale
+S[l], S[L] = Delta, S[l-1] = S[l]*S[l]/q_l, so the product of two level-l
+ciphertexts rescales exactly onto S[l-1]. A ciphertext is moved to a lower
+level t by adjust(): keep primes q_0..q_{t+1}, multiply by the integer
+floor(a*S[t]*q_{t+1}/scale + 1/2) (which also applies a public factor a), and
+rescale by q_{t+1}.
+"""
+from __future__ import annotations
+
+import math
+from dataclasses import dataclass, field
+
+import numpy as np
+
+import synth
+from . import ckks, rns
+from .ckks import Ct, Params, round_half_up
+
+
+# ---------------------------------------------------------------------------
+# Sign polynomials (Section 4.3.2; the paper composes low-degree polynomials
+# after Lee et al. but prints no coefficients).  Default stage: the odd
+# degree-7 polynomial f3 with f3(1) = 1 and f3'(x) = 35/16 (1-x^2)^3.
+# ---------------------------------------------------------------------------
+F3 = (35.0 / 16.0, -35.0 / 16.0, 21.0 / 16.0, -5.0 / 16.0)   # coefficients of x, x^3, x^5, x^7
+
+
+def odd_poly(coeffs, x):
+    x = np.asarray(x, dtype=np.float64)
+    return sum(a * x ** (2 * k + 1) for k, a in enumerate(coeffs))
+
+
+def composite_sign(stages, x):
+    for c in stages:
+        x = odd_poly(c, x)
+    return x
+
+
+def sign_margin(stages, tol: float, grid: int = 1 << 20) -> float:
+    """Smallest a in (0, 1] such that |composite(x) - sign(x)| <= tol for all
+    a <= |x| <= 1 on a dense grid (brute force over the grid)."""
+    x = np.linspace(0.0, 1.0, grid + 1)[1:]
+    err = np.abs(composite_sign(stages, x) - 1.0)
+    bad = np.nonzero(err > tol)[0]
+    if bad.size == 0:
+        return float(x[0])
+    if bad[-1] + 1 >= x.size:
+        return 1.0
+    return float(x[bad[-1] + 1])
+
+
+# ---------------------------------------------------------------------------
+# Query shape and plan
+# ---------------------------------------------------------------------------
+@dataclass
+class QueryShape:
+    records: int
+    attrs: int
+    degree: int
+    sign_stages: list            # list of (a0, a1, a2, a3) for x, x^3, x^5, x^7
+
+    def blocks(self, n_slots: int) -> int:
+        return -(-self.records // n_slots)
+
+
+def standard_scales(par: Params) -> list:
+    S = [0.0] * (par.L + 1)
+    S[par.L] = float(par.scale)
+    for l in range(par.L, 0, -1):
+        S[l - 1] = (S[l] * S[l]) / float(par.q[l])
+    return S
+
+
+def ceil_log2(k: int) -> int:
+    return (k - 1).bit_length()
+
+
+@dataclass
+class Plan:
+    S: list
+    l_lin: int          # level of the linear combination x
+    l_d: int            # level at which the c_k x^k products are formed
+    l_y: int            # level of y = f(x) and z = y - t
+    l_u: int            # level after the sign stages and step affine
+    l_out: int          # level of the returned ciphertext
+    pt_scale: float     # scale of the database plaintexts
+    mask_scale: float   # scale of the ragged-block mask plaintext (0 if none)
+    ragged: bool
+    stage_coeffs: list = field(default_factory=list)   # folded coefficients per stage
+    step_const: float = 0.0
+
+
+def make_plan(par: Params, shape: QueryShape) -> Plan:
+    if shape.degree < 1 or shape.attrs < 1 or shape.records < 1 or not shape.sign_stages:
+        raise ValueError("empty query")
+    L, S = par.L, standard_scales(par)
+    l_lin = L - 1
+    l_d = l_lin - ceil_log2(shape.degree)
+    l_y = l_d - 1
+    l_u = l_y - 3 * len(shape.sign_stages)
+    n = par.n_slots
+    ragged = shape.records % n != 0
+    l_out = l_u - 1 if ragged else l_u
+    if l_out < 1:
+        raise ValueError(f"circuit needs more levels: ends at level {l_out}")
+    R = float(shape.records)
+    stages = []
+    ns = len(shape.sign_stages)
+    for s, co in enumerate(shape.sign_stages):
+        co = [float(c) for c in co]
+        if len(co) != 4:
+            raise ValueError("sign stages are odd degree-7 polynomials")
+        if s == 0:   # z = (y - t)/2 folded in: a_k -> a_k * 2^-(2k+1)
+            co = [c * (0.5 ** (2 * k + 1)) for k, c in enumerate(co)]
+        if s == ns - 1:   # step = (p + 1) / 2, normalised by 1/records
+            co = [c / (2.0 * R) for c in co]
+        stages.append(co)
+    return Plan(S=S, l_lin=l_lin, l_d=l_d, l_y=l_y, l_u=l_u, l_out=l_out,
+                pt_scale=(S[L - 1] * float(par.q[L])) / S[L],
+                mask_scale=((S[l_u - 1] * float(par.q[l_u])) / S[l_u]) if ragged else 0.0,
+                ragged=ragged, stage_coeffs=stages, step_const=1.0 / (2.0 * R))
+
+
+def adjust_const(plan: Plan, par: Params, lt: int, a: float, scale: float) -> int:
+    return round_half_up(((a * plan.S[lt]) * float(par.q[lt + 1])) / scale)
+
+
+# ---------------------------------------------------------------------------
+# Database encoding (Appendix A.1.2): records fill the N/2 slots of each block
+# in order; slot values are the normalised attribute / attrs.
+# ---------------------------------------------------------------------------
+def normalise(vals_u8: np.ndarray) -> np.ndarray:
+    return (vals_u8.astype(np.float64) - 127.5) / 127.5
+
+
+def block_slots(par: Params, vals_u8: np.ndarray, b: int, j: int) -> np.ndarray:
+    n = par.n_slots
+    rec = vals_u8[b * n:(b + 1) * n, j]
+    z = np.zeros(n)
+    z[: rec.shape[0]] = normalise(rec) / vals_u8.shape[1]
+    return z
+
+
+@dataclass
+class EncodedDB:
+    pts: list           # [blocks][attrs] int64[N] coefficients at plan.pt_scale
+    mask: object        # int64[N] at plan.mask_scale, or None
+
+
+def encode_database(par: Params, plan: Plan, vals_u8: np.ndarray) -> EncodedDB:
+    R, h = vals_u8.shape
+    B = -(-R // par.n_slots)
+    pts = [[ckks.encode_int(par.N, block_slots(par, vals_u8, b, j), plan.pt_scale) for j in range(h)] for b in range(B)]
+    mask = None
+    if plan.ragged:
+        live = R - (B - 1) * par.n_slots
+        z = np.zeros(par.n_slots)
+        z[:live] = 1.0
+        mask = ckks.encode_int(par.N, z, plan.mask_scale)
+    return EncodedDB(pts=pts, mask=mask)
+
+
+# ---------------------------------------------------------------------------
+# Keys and encrypted query (client side, from the seeded draws)
+# ---------------------------------------------------------------------------
+def innersum_galois(par: Params) -> list:
+    return [pow(5, 1 << k, 2 * par.N) for k in range(par.log_n - 1)]
+
+
+@dataclass
+class Keys:
+    alpha: int
+    rlk: np.ndarray
+    rot: dict           # galois element -> key
+
+
+def secret(par: Params, seed: int, h: int) -> np.ndarray:
+    return synth.ternary_secret(synth.stream(seed, "secret"), par.N, h)
+
+
+def make_keys(par: Params, s: np.ndarray, seed: int, alpha: int, galois=()) -> Keys:
+    dnum = ckks.dnum_for(par.L, alpha)
+    d = synth.switch_key_draws(seed, "relin", dnum, par.moduli, par.N)
+    rlk = ckks.relin_key(par, s, d.a, d.e, alpha)
+    rot = {}
+    for g in galois:
+        d = synth.switch_key_draws(seed, f"rot{g}", dnum, par.moduli, par.N)
+        rot[g] = ckks.rotation_key(par, g, s, d.a, d.e, alpha)
+    return Keys(alpha=alpha, rlk=rlk, rot=rot)
+
+
+def encrypt_value(par: Params, s: np.ndarray, v: float, seed: int, name: str, level=None) -> Ct:
+    """Encryption of v in every slot: the constant polynomial round(v * Delta)."""
+    level = par.L if level is None else level
+    m = np.zeros(par.N, dtype=np.int64)
+    m[0] = round_half_up(v * par.scale)
+    d = synth.encryption_draws(seed, name, par.q[: level + 1], par.N)
+    return ckks.encrypt(par, m, s, d.a, d.e, level, par.scale)
+
+
+@dataclass
+class EncQuery:
+    w: list
+    c: list
+    t: Ct
+
+
+def encrypt_query(par: Params, s: np.ndarray, qv: synth.QueryValues, seed: int) -> EncQuery:
+    return EncQuery(w=[encrypt_value(par, s, float(v), seed, f"w{j}") for j, v in enumerate(qv.w)],
+                    c=[encrypt_value(par, s, float(v), seed, f"c{k}") for k, v in enumerate(qv.c)],
+                    t=encrypt_value(par, s, float(qv.t), seed, "t"))
+
+
+# ---------------------------------------------------------------------------
+# Server-side evaluation
+# ---------------------------------------------------------------------------
+class Evaluator:
+    def __init__(self, par: Params, keys: Keys, plan: Plan):
+        self.par, self.keys, self.plan = par, keys, plan
+
+    def adjust(self, ct: Ct, lt: int, a: float = 1.0) -> Ct:
+        par, plan = self.par, self.plan
+        if ct.level == lt:
+            if a != 1.0 or ct.scale != plan.S[lt]:
+                raise ValueError("adjust at the same level")
+            return ct
+        if ct.level < lt:
+            raise ValueError("input ciphertext level too low")
+        c = adjust_const(plan, par, lt, a, ct.scale)
+        out = ckks.rescale(par, ckks.mul_int(par, ckks.drop_to(ct, lt + 1), c))
+        out.scale = plan.S[lt]
+        return out
+
+    def mul(self, a: Ct, b: Ct) -> Ct:
+        assert a.level == b.level
+        par = self.par
+        out = ckks.rescale(par, ckks.relinearize(par, ckks.tensor(par, a, b), self.keys.rlk, self.keys.alpha))
+        out.scale = self.plan.S[a.level - 1]
+        return out
+
+    def add(self, a: Ct, b: Ct) -> Ct:
+        return ckks.add(self.par, a, b)
+
+    def sign_stage(self, u: Ct, co) -> Ct:
+        l = u.level
+        u2 = self.mul(u, u)
+        u4 = self.mul(u2, u2)
+        b1 = self.adjust(u, l - 1, co[1])
+        b3 = self.adjust(u, l - 1, co[3])
+        t3 = self.mul(b1, u2)
+        t7 = self.mul(b3, u2)
+        inner = self.add(t7, self.adjust(u, l - 2, co[2]))
+        t57 = self.mul(inner, u4)
+        t1 = self.adjust(u, l - 3, co[0])
+        return self.add(self.add(t1, self.adjust(t3, l - 3)), t57)
+
+    def per_query(self, q: EncQuery, degree: int):
+        """Bring the encrypted coefficients and threshold to their levels (once per query)."""
+        p = self.plan
+        for w in q.w:
+            if w.level != self.par.L or w.scale != p.S[self.par.L]:
+                raise ValueError("linear-combination coefficients must be fresh top-level ciphertexts")
+        ck = [self.adjust(q.c[0], p.l_y)] + [self.adjust(q.c[k], p.l_d) for k in range(1, degree + 1)]
+        return ck, self.adjust(q.t, p.l_y)
+
+    def block(self, pts: list, q: EncQuery, ck: list, tadj: Ct, degree: int) -> Ct:
+        par, p = self.par, self.plan
+        L = par.L
+        # linear combination: sum_j pt_j * Enc(w_j), rescale
+        acc = None
+        for pt, w in zip(pts, q.w):
+            prod = ckks.mul_plain(par, w, rns.to_rns(pt, par.q), p.pt_scale)
+            acc = prod if acc is None else ckks.add(par, acc, prod)
+        x = ckks.rescale(par, acc)
+        x.scale = p.S[L - 1]
+        # powers x^k, k <= degree
+        P = {1: x}
+        cache = {}
+
+        def lvl(k: int, lt: int) -> Ct:
+            if P[k].level == lt:
+                return P[k]
+            if (k, lt) not in cache:
+                cache[(k, lt)] = self.adjust(P[k], lt)
+            return cache[(k, lt)]
+
+        for k in range(2, degree + 1):
+            a = 1 << (k.bit_length() - 1)
+            if a == k:
+                P[k] = self.mul(P[k // 2], P[k // 2])
+            else:
+                A = P[a]
+                P[k] = self.mul(A, lvl(k - a, A.level))
+        # y = sum_k c_k x^k: degree-2 products summed, one relinearisation
+        T = None
+        for k in range(1, degree + 1):
+            tk = ckks.tensor(par, ck[k], lvl(k, p.l_d))
+            T = tk if T is None else ckks.add(par, T, tk)
+        y = ckks.rescale(par, ckks.relinearize(par, T, self.keys.rlk, self.keys.alpha))
+        y.scale = p.S[p.l_y]
+        y = ckks.add(par, y, ck[0])
+        # z = y - t (the 1/2 is folded into the first sign stage)
+        u = ckks.sub(par, y, tadj)
+        for co in p.stage_coeffs:
+            u = self.sign_stage(u, co)
+        return ckks.add_int_const(par, u, round_half_up(p.step_const * p.S[u.level]))
+
+    def innersum(self, acc: Ct) -> Ct:
+        for g in innersum_galois(self.par):
+            acc = ckks.add(self.par, acc, ckks.rotate(self.par, acc, g, self.keys.rot[g], self.keys.alpha))
+        return acc
+
+
+def evaluate_query(par: Params, keys: Keys, shape: QueryShape, db: EncodedDB, q: EncQuery, blocks=None) -> Ct:
+    """The whole circuit; ``blocks`` restricts the block loop (for timing samples)."""
+    plan = make_plan(par, shape)
+    ev = Evaluator(par, keys, plan)
+    ck, tadj = ev.per_query(q, shape.degree)
+    B = len(db.pts)
+    idx = range(B) if blocks is None else blocks
+    full = None
+    last = None
+    for b in idx:
+        u = ev.block(db.pts[b], q, ck, tadj, shape.degree)
+        if plan.ragged and b == B - 1:
+            last = u
+        else:
+            full = u if full is None else ckks.add(par, full, u)
+    if plan.ragged and last is not None:
+        m = ckks.rescale(par, ckks.mul_plain(par, last, rns.to_rns(db.mask, par.q), plan.mask_scale))
+        m.scale = plan.S[plan.l_out]
+        acc = m if full is None else ckks.add(par, ev.adjust(full, plan.l_out), m)
+    else:
+        acc = full
+    return ev.innersum(acc)
+
+
+# ---------------------------------------------------------------------------
+# FP64 plaintext pipeline
+# ---------------------------------------------------------------------------
+@dataclass
+class Fp64Result:
+    x: np.ndarray
+    y: np.ndarray
+    z: np.ndarray
+    u: np.ndarray        # per-record step approximation
+    count: float         # sum of u
+    exact: int           # number of records with z > 0
+
+
+def fp64_pipeline(vals_u8: np.ndarray, qv: synth.QueryValues, stages) -> Fp64Result:
+    h = vals_u8.shape[1]
+    x = (normalise(vals_u8) / h) @ np.asarray(qv.w, dtype=np.float64)
+    y = sum(c * x ** k for k, c in enumerate(qv.c))
+    z = (y - qv.t) / 2.0
+    u = (composite_sign(stages, z) + 1.0) / 2.0
+    return Fp64Result(x=x, y=y, z=z, u=u, count=float(u.sum()), exact=int((z > 0).sum()))

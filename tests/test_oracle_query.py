@@ -1,0 +1,92 @@
+"""Pins for the oracle's query circuit: the decrypted count matches the FP64
+plaintext pipeline (same polynomials, computed in floating point without
+encryption); with every record outside the sign margin (the epsilon shift of
+Section 4.3.2 keeps records off the threshold) the rounded count is the exact
+integer count; InnerSum leaves the total in every slot."""
+import numpy as np
+import pytest
+
+import synth
+from oracle import ckks, query, rns
+
+
+def chain_params(n_q40: int, log_n: int = 12):
+    """Test-only chain: one 50-bit q_0, n_q40 primes of 40 bits, one 60-bit special prime, Delta = 2^40."""
+    q = rns.gen_primes(50, 1) + rns.gen_primes(40, n_q40)
+    return ckks.Params(log_n, q, rns.gen_primes(60, 1), 2.0 ** 40)
+
+
+def run(par, vals, qv, stages, seed=1, alpha=1):
+    shape = query.QueryShape(vals.shape[0], vals.shape[1], len(qv.c) - 1, stages)
+    plan = query.make_plan(par, shape)
+    s = query.secret(par, seed, 2 * par.N // 3)
+    keys = query.make_keys(par, s, seed, alpha, query.innersum_galois(par))
+    db = query.encode_database(par, plan, vals)
+    eq = query.encrypt_query(par, s, qv, seed)
+    out = query.evaluate_query(par, keys, shape, db, eq)
+    assert out.level == plan.l_out
+    return ckks.decrypt_slots(par, out, s).real, plan
+
+
+def test_plan_levels():
+    par = chain_params(11)
+    p = query.make_plan(par, query.QueryShape(2048, 8, 7, [query.F3]))
+    assert (p.l_lin, p.l_d, p.l_y, p.l_u, p.l_out) == (10, 7, 6, 3, 3)
+    q2 = rns.gen_primes(50, 20)
+    par2 = ckks.Params(16, q2, rns.gen_primes(60, 3), 2.0 ** 50)
+    p2 = query.make_plan(par2, query.QueryShape(131072, 16, 15, [query.F3] * 3))
+    assert (p2.l_lin, p2.l_d, p2.l_y, p2.l_u, p2.l_out) == (18, 14, 13, 4, 4)
+    p3 = query.make_plan(par2, query.QueryShape(1 << 14, 16, 31, [query.F3] * 3))
+    assert p3.ragged and p3.l_out == 2
+    with pytest.raises(ValueError):
+        query.make_plan(par, query.QueryShape(2048, 8, 31, [query.F3] * 3))
+    # exact standard scales: S[l-1] q_l = S[l]^2 up to one rounding
+    for l in range(1, par2.L + 1):
+        assert abs(p2.S[l - 1] * par2.q[l] / p2.S[l] ** 2 - 1) < 1e-15
+
+
+def test_query_matches_fp64_pipeline():
+    par = chain_params(11)
+    vals = synth.database(synth.stream(11, "db"), 2048, 8)
+    qv = synth.query_values(synth.stream(11, "qv"), 8, 7)
+    got, plan = run(par, vals, qv, [query.F3])
+    ref = query.fp64_pipeline(vals, qv, [query.F3])
+    R = vals.shape[0]
+    # InnerSum puts the normalised count in every slot
+    assert np.ptp(got) < 1e-6
+    assert abs(got[0] * R - ref.count) < 0.05
+
+
+def test_query_ragged_mask():
+    par = chain_params(12)
+    vals = synth.database(synth.stream(12, "db"), 1500, 4, "paper")
+    qv = synth.query_values(synth.stream(12, "qv"), 4, 3)
+    got, plan = run(par, vals, qv, [query.F3])
+    assert plan.ragged
+    ref = query.fp64_pipeline(vals, qv, [query.F3])
+    assert abs(got[0] * 1500 - ref.count) < 0.05
+
+
+def margin_dataset(records, attrs, seed, margin):
+    """Records whose z = (x - t)/2 stays at least ``margin`` from 0 (t = 0, f(x) = x)."""
+    g = np.random.default_rng(seed)
+    w = g.choice([-1.0, 1.0], size=attrs)
+    side = g.choice([-1.0, 1.0], size=records)
+    mag = g.uniform(0.75, 1.0, size=(records, attrs))
+    xh = side[:, None] * w[None, :] * mag              # normalised values in [-1, 1]
+    vals = np.clip(np.rint(xh * 127.5 + 127.5), 0, 255).astype(np.uint8)
+    qv = synth.QueryValues(w=w, c=np.array([0.0, 1.0, 0.0, 0.0]), t=0.0)
+    return vals, qv, side
+
+
+def test_exact_count_outside_margin():
+    stages = [query.F3] * 3
+    tol = 2.0 ** -13
+    margin = query.sign_margin(stages, tol)
+    vals, qv, side = margin_dataset(2048, 8, 5, margin)
+    ref = query.fp64_pipeline(vals, qv, stages)
+    assert np.min(np.abs(ref.z)) > margin
+    par = chain_params(15)
+    got, _ = run(par, vals, qv, stages)
+    R = vals.shape[0]
+    assert int(np.rint(got[0] * R)) == ref.exact == int((side > 0).sum())
