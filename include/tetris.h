@@ -1,0 +1,233 @@
+/*
+ * tetris.h -- C ABI of the GB300 library for the server side of the TETRIS
+ * private functional exploration (arXiv 2412.13269): RNS-CKKS evaluation of
+ * an encrypted query over a plaintext database.
+ *
+ * Paper references are to that paper's sections, equations, algorithms and
+ * tables.
+ *
+ * Conventions (every entry point):
+ *   - Returns a tetris_status (0 on success, negative on error); nothing is
+ *     thrown across the ABI.  tetris_last_error() gives a message for the
+ *     calling thread's last failure.  An error leaves the context usable.
+ *   - Host buffers passed in are owned by the caller, read during the call
+ *     and not retained.  Output host buffers are owned by the caller.
+ *   - Polynomials at the boundary are in the coefficient domain: residues in
+ *     [0, q) of the coefficients of X^0 .. X^{N-1}, one limb of N uint64 per
+ *     prime, limbs in prime order.  A ciphertext at level l is
+ *     [ncomp][l+1][N] uint64 (components c0, c1[, c2]), modulo q_0 .. q_l.
+ *   - Device state (keys, databases, work buffers) is owned by the context.
+ *   - Not thread-safe per context: one thread drives a context at a time.
+ */
+#ifndef TETRIS_H
+#define TETRIS_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct tetris_ctx tetris_ctx;
+
+typedef enum {
+    TETRIS_OK = 0,
+    TETRIS_EINVAL = -1,     /* bad argument: size, layout, level, scale */
+    TETRIS_ENOMEM = -2,     /* device allocation failed */
+    TETRIS_ECUDA = -3,      /* CUDA runtime error */
+    TETRIS_ELEVEL = -4,     /* circuit needs more levels than the ciphertexts have */
+    TETRIS_ENOTFOUND = -5,  /* unknown handle or missing key */
+    TETRIS_ETIMEOUT = -6,   /* poll deadline passed */
+    TETRIS_EBUSY = -7       /* admission refused: not enough device memory now */
+} tetris_status;
+
+/* ---------------------------------------------------------------------------
+ * Context.  The ring R_Q = Z_Q[X]/(X^N + 1) of Section 2.2 with
+ * Q = q_0 ... q_{n_q-1} (RNS, q_0 first and dropped last by rescale) and the
+ * special modulus P = p_0 ... p_{n_p-1} of SwitchKey (Section 2.4.1).
+ * Every prime must be below 2^61 and = 1 mod 2N; all distinct.  log_n in
+ * [10, 16].  scale is Delta of fresh ciphertexts (Section 2.5).  device is
+ * the CUDA ordinal.  The context owns its device memory until destroyed.
+ * ------------------------------------------------------------------------- */
+int tetris_ctx_create(tetris_ctx **out, uint32_t log_n,
+                      const uint64_t *q, uint32_t n_q,
+                      const uint64_t *p, uint32_t n_p,
+                      double scale, int device);
+void tetris_ctx_destroy(tetris_ctx *ctx);
+const char *tetris_last_error(void);
+
+typedef struct {
+    uint32_t log_n, n_q, n_p;
+    double scale;         /* Delta */
+    double pt_scale;      /* scale of database plaintexts: S[L-1] * q_L / S[L] */
+    size_t device_bytes;  /* device memory the context holds now */
+} tetris_ctx_info;
+int tetris_get_info(const tetris_ctx *ctx, tetris_ctx_info *out);
+
+/* Standard scale S[level]: S[L] = Delta, S[l-1] = S[l] * S[l] / q_l (double
+ * arithmetic in that order).  Every ciphertext inside a query at level l
+ * carries S[l]; Section 2.5 gives the multiply-then-rescale rule it follows. */
+int tetris_standard_scale(const tetris_ctx *ctx, uint32_t level, double *out);
+
+/* The count largest primes q < 2^bits with q = 1 mod 2^congruence_log2, in
+ * descending order, skipping the n_exclude values of exclude (may be NULL). */
+int tetris_gen_primes(uint32_t bits, uint32_t count, uint32_t congruence_log2,
+                      const uint64_t *exclude, uint32_t n_exclude, uint64_t *out);
+
+/* ---------------------------------------------------------------------------
+ * Keys (Section 2.4.1, SwitchKeyGen; Appendix A.2 for their use).
+ * A switching key is [dnum][2][n_q + n_p][N] uint64, coefficient domain,
+ * limbs q_0..q_{n_q-1}, p_0..p_{n_p-1}; digit j covers the primes
+ * q_{j*alpha} .. q_{j*alpha+alpha-1} (CRT gadget), dnum = ceil(n_q / alpha).
+ * n_words must equal dnum * 2 * (n_q + n_p) * N.  The context copies the key
+ * to device memory (converted to its internal NTT domain); loading a key for
+ * an element that already has one replaces it.  alpha must be the same for
+ * all keys of a context.
+ * ------------------------------------------------------------------------- */
+int tetris_load_relin_key(tetris_ctx *ctx, const uint64_t *evk, size_t n_words, uint32_t alpha);
+int tetris_load_rotation_key(tetris_ctx *ctx, uint32_t galois_elt, const uint64_t *evk,
+                             size_t n_words, uint32_t alpha);
+/* Copy a loaded key back (coefficient domain, same layout); galois_elt 0
+ * selects the relinearisation key. */
+int tetris_get_key(tetris_ctx *ctx, uint32_t galois_elt, uint64_t *out, size_t cap_words);
+
+/* Client-side key generation on the GPU from caller-drawn randomness
+ * (Section 2.3 distributions): s int64[N] ternary secret; a uint64
+ * [dnum][n_q+n_p][N] uniform residues; e int64[dnum][N] errors.  Builds
+ * swk_j = (-a_j s + e_j + w_j P s', a_j) with s' = s^2 (relinearisation) or
+ * s(X^g) (rotation by galois element g) and loads it as above. */
+int tetris_keygen_relin(tetris_ctx *ctx, const int64_t *s, const uint64_t *a, const int64_t *e,
+                        uint32_t alpha);
+int tetris_keygen_rotation(tetris_ctx *ctx, uint32_t galois_elt, const int64_t *s,
+                           const uint64_t *a, const int64_t *e, uint32_t alpha);
+
+/* ---------------------------------------------------------------------------
+ * Ciphertexts at the boundary.
+ * ------------------------------------------------------------------------- */
+typedef struct {
+    uint32_t level;        /* l: data holds l+1 limbs per component */
+    uint32_t ncomp;        /* 2 (or 3 for a degree-2 ciphertext, 1 for a plaintext) */
+    double scale;
+    const uint64_t *data;  /* [ncomp][level+1][N] */
+} tetris_ct_in;
+
+typedef struct {
+    uint32_t level;        /* set by the library */
+    uint32_t ncomp;        /* set by the library */
+    double scale;          /* set by the library */
+    uint64_t *data;        /* caller buffer */
+    size_t cap_words;      /* its capacity in uint64 words */
+} tetris_ct_out;
+
+/* Secret-key encryption (Section 2.3): (c0, c1) = (-a s + e + m, a) mod Q_level.
+ * m int64[N] message coefficients; a uint64[level+1][N]; e int64[N]. */
+int tetris_encrypt(tetris_ctx *ctx, const int64_t *m, const int64_t *s, const uint64_t *a,
+                   const int64_t *e, uint32_t level, double scale, tetris_ct_out *out);
+
+/* ---------------------------------------------------------------------------
+ * Database (the plaintext matrix P, p x h, of Section 3.3): row-major u8
+ * [records][attrs].  Records fill the N/2 slots of consecutive blocks; slot
+ * value = ((v - 127.5) / 127.5) / attrs.  The library encodes each
+ * (block, attribute) column with its FP64 canonical-embedding encoder
+ * (Appendix A.1.2) at the context's pt_scale and keeps the plaintexts resident
+ * on the device (NTT domain, all n_q primes).  *db_out receives a handle.
+ * ------------------------------------------------------------------------- */
+int tetris_upload_database(tetris_ctx *ctx, const uint8_t *vals, uint64_t records, uint32_t attrs,
+                           uint32_t *db_out);
+/* Same, with the encoding done by the caller: coeffs int64 [blocks][attrs][N]
+ * (the integer plaintext polynomials at pt_scale), blocks = ceil(records / (N/2));
+ * mask_real float64[N]: the real coefficients (scale 1) of the encoding of the
+ * live-slot indicator of the last block, required iff records is not a
+ * multiple of N/2 (else NULL). */
+int tetris_upload_database_encoded(tetris_ctx *ctx, const int64_t *coeffs, const double *mask_real,
+                                   uint64_t records, uint32_t attrs, uint32_t *db_out);
+int tetris_free_database(tetris_ctx *ctx, uint32_t db);
+
+/* FP64 encoder alone: slots float64[n_values] (n_values <= N/2, rest zero) ->
+ * coeffs int64[N] = floor(scale * m_i + 1/2), m = canonical-embedding preimage. */
+int tetris_encode(tetris_ctx *ctx, const double *slots, uint32_t n_values, double scale,
+                  int64_t *coeffs);
+/* The real coefficients m (before scaling) of the same map. */
+int tetris_encode_real(tetris_ctx *ctx, const double *slots, uint32_t n_values, double *m_out);
+
+/* ---------------------------------------------------------------------------
+ * Query (server side of Algorithm 2's local threshold and InnerSum):
+ *   x = sum_j P[.,j] * Enc(w_j)                (attribute selection, Sec. 3.3)
+ *   y = sum_{k=0}^{d} Enc(c_k) x^k             (private polynomial)
+ *   z = (y - Enc(t)) / 2                       (private threshold, Sec. 4.3.2)
+ *   u = (p_S(...p_1(z)) + 1) / (2 * records)   (composite sign -> step)
+ *   out = InnerSum(sum over blocks of u)       (Algorithm 2, InnerSum)
+ * Each p_s is odd of degree sign_degree (7): sign_coeffs holds, per stage,
+ * the coefficients of x, x^3, x^5, x^7.  w: n_attrs fresh ciphertexts at the
+ * top level with scale Delta; f_coeffs: f_degree+1 ciphertexts, threshold:
+ * one, each at any level at or above where it is used (the library moves it
+ * down).  Keys needed: relinearisation and rotations by 5^(2^k) mod 2N,
+ * k < log_n - 1.  The result, at the level reported in out, decrypts to
+ * count / records in every slot.
+ * ------------------------------------------------------------------------- */
+typedef struct {
+    uint32_t n_attrs;
+    const tetris_ct_in *w;
+    uint32_t f_degree;
+    const tetris_ct_in *f_coeffs;
+    const tetris_ct_in *threshold;
+    uint32_t sign_stages;
+    uint32_t sign_degree;
+    const double *sign_coeffs;
+} tetris_query;
+
+/* Host buffers in and out; blocks until the result is in out. */
+int tetris_evaluate_query(tetris_ctx *ctx, uint32_t db, const tetris_query *query, tetris_ct_out *out);
+/* Device buffers in and out (every data pointer of query and out is device
+ * memory); enqueued on the CUDA stream `stream` (cudaStream_t, NULL for the
+ * legacy default stream); returns before the work completes. */
+int tetris_evaluate_query_device(tetris_ctx *ctx, uint32_t db, const tetris_query *query,
+                                 tetris_ct_out *out, void *stream);
+
+typedef struct {
+    int32_t l_lin, l_d, l_y, l_u, l_out;
+    uint32_t ragged;
+    uint32_t relins, rescales, rotations, kernel_launches;
+    double pt_scale, mask_scale;
+} tetris_plan_info;
+/* Levels and operation counts of the plan for a query shape on a database. */
+int tetris_plan(tetris_ctx *ctx, uint32_t db, uint32_t f_degree, uint32_t sign_stages,
+                tetris_plan_info *out);
+
+/* Options. */
+enum {
+    TETRIS_OPT_BLOCKS_PER_LAUNCH = 1,  /* 0: all blocks of a database in each launch (batched);
+                                          k: k blocks per launch (1 = plain per-ciphertext form) */
+    TETRIS_OPT_USE_GRAPH = 2,          /* 1: replay the query as a captured CUDA graph */
+    TETRIS_OPT_KS_ALPHA = 3            /* read-only: alpha of the loaded keys */
+};
+int tetris_set_option(tetris_ctx *ctx, int option, int64_t value);
+int tetris_get_option(tetris_ctx *ctx, int option, int64_t *value);
+
+/* ---------------------------------------------------------------------------
+ * Single primitives on caller ciphertexts (host buffers), for parity checks.
+ * ------------------------------------------------------------------------- */
+enum {
+    TETRIS_OP_ADD = 1,          /* a + b */
+    TETRIS_OP_SUB = 2,          /* a - b */
+    TETRIS_OP_TENSOR = 3,       /* (a0 b0, a0 b1 + a1 b0, a1 b1), Appendix A.2 */
+    TETRIS_OP_RELIN = 4,        /* a is degree 2: SwitchKey(a2, swk_{s^2->s}) + (a0, a1) */
+    TETRIS_OP_RESCALE = 5,      /* divide by q_l with rounding, drop q_l (Section 2.5) */
+    TETRIS_OP_MUL_INT = 6,      /* a * arg (signed integer constant) */
+    TETRIS_OP_ADD_INT = 7,      /* a + arg as a constant polynomial */
+    TETRIS_OP_AUTOMORPHISM = 8, /* a(X^arg), no key switch (Section 2.2) */
+    TETRIS_OP_ROTATE = 9,       /* automorphism X -> X^arg then SwitchKey back to s */
+    TETRIS_OP_KEYSWITCH = 10,   /* a has one component d: SwitchKey(d, key arg) (0 = relin key) */
+    TETRIS_OP_MUL_PLAIN = 11,   /* b is a plaintext (ncomp = 1, residues): a * b */
+    TETRIS_OP_NTT = 12,         /* a -> internal evaluation order NTT (bit-reversed order) */
+    TETRIS_OP_INNERSUM = 13,    /* sum of rotations by 2^k, k < log_n - 1 */
+    TETRIS_OP_DROP = 14         /* keep primes q_0..q_arg */
+};
+int tetris_op(tetris_ctx *ctx, int opcode, const tetris_ct_in *a, const tetris_ct_in *b,
+              int64_t arg, tetris_ct_out *out);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* TETRIS_H */

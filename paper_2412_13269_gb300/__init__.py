@@ -1,0 +1,295 @@
+"""Python binding of the GB300 RNS-CKKS query library (include/tetris.h).
+
+Argument marshalling only: every entry point forwards to the CUDA library
+libtetris.so built in-tree by ``build()``; nothing here computes.  Importing
+the package does not load the library; the first call does, and it raises
+if the library has not been built (there is no CPU fallback).
+
+Functions keep the C names (``tetris_ctx_create`` ...).  ``Ctx`` is a small
+convenience wrapper that turns numpy arrays (host) or torch CUDA tensors
+(device) into the C structs.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+from functools import lru_cache
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "_build", "libtetris.so")
+
+TETRIS_OK = 0
+ERRORS = {-1: "EINVAL", -2: "ENOMEM", -3: "ECUDA", -4: "ELEVEL", -5: "ENOTFOUND", -6: "ETIMEOUT", -7: "EBUSY"}
+
+OP_ADD, OP_SUB, OP_TENSOR, OP_RELIN, OP_RESCALE, OP_MUL_INT, OP_ADD_INT = 1, 2, 3, 4, 5, 6, 7
+OP_AUTOMORPHISM, OP_ROTATE, OP_KEYSWITCH, OP_MUL_PLAIN, OP_NTT, OP_INNERSUM, OP_DROP = 8, 9, 10, 11, 12, 13, 14
+OPT_BLOCKS_PER_LAUNCH, OPT_USE_GRAPH, OPT_KS_ALPHA = 1, 2, 3
+
+
+def build(force: bool = False) -> str:
+    from . import buildlib
+    return buildlib.build(force=force)
+
+
+class TetrisError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"{ERRORS.get(code, code)}: {msg}")
+        self.code = code
+
+
+class CtIn(C.Structure):
+    _fields_ = [("level", C.c_uint32), ("ncomp", C.c_uint32), ("scale", C.c_double), ("data", C.c_void_p)]
+
+
+class CtOut(C.Structure):
+    _fields_ = [("level", C.c_uint32), ("ncomp", C.c_uint32), ("scale", C.c_double), ("data", C.c_void_p),
+                ("cap_words", C.c_size_t)]
+
+
+class Query(C.Structure):
+    _fields_ = [("n_attrs", C.c_uint32), ("w", C.POINTER(CtIn)), ("f_degree", C.c_uint32),
+                ("f_coeffs", C.POINTER(CtIn)), ("threshold", C.POINTER(CtIn)), ("sign_stages", C.c_uint32),
+                ("sign_degree", C.c_uint32), ("sign_coeffs", C.POINTER(C.c_double))]
+
+
+class CtxInfo(C.Structure):
+    _fields_ = [("log_n", C.c_uint32), ("n_q", C.c_uint32), ("n_p", C.c_uint32), ("scale", C.c_double),
+                ("pt_scale", C.c_double), ("device_bytes", C.c_size_t)]
+
+
+class PlanInfo(C.Structure):
+    _fields_ = [("l_lin", C.c_int32), ("l_d", C.c_int32), ("l_y", C.c_int32), ("l_u", C.c_int32),
+                ("l_out", C.c_int32), ("ragged", C.c_uint32), ("relins", C.c_uint32), ("rescales", C.c_uint32),
+                ("rotations", C.c_uint32), ("kernel_launches", C.c_uint32), ("pt_scale", C.c_double),
+                ("mask_scale", C.c_double)]
+
+
+_vp, _u32, _u64, _i64, _sz, _d = C.c_void_p, C.c_uint32, C.c_uint64, C.c_int64, C.c_size_t, C.c_double
+SIGNATURES = {
+    "tetris_ctx_create": [C.POINTER(_vp), _u32, _vp, _u32, _vp, _u32, _d, C.c_int],
+    "tetris_ctx_destroy": [_vp],
+    "tetris_last_error": [],
+    "tetris_get_info": [_vp, C.POINTER(CtxInfo)],
+    "tetris_standard_scale": [_vp, _u32, C.POINTER(_d)],
+    "tetris_gen_primes": [_u32, _u32, _u32, _vp, _u32, _vp],
+    "tetris_load_relin_key": [_vp, _vp, _sz, _u32],
+    "tetris_load_rotation_key": [_vp, _u32, _vp, _sz, _u32],
+    "tetris_get_key": [_vp, _u32, _vp, _sz],
+    "tetris_keygen_relin": [_vp, _vp, _vp, _vp, _u32],
+    "tetris_keygen_rotation": [_vp, _u32, _vp, _vp, _vp, _u32],
+    "tetris_encrypt": [_vp, _vp, _vp, _vp, _vp, _u32, _d, C.POINTER(CtOut)],
+    "tetris_upload_database": [_vp, _vp, _u64, _u32, C.POINTER(_u32)],
+    "tetris_upload_database_encoded": [_vp, _vp, _vp, _u64, _u32, C.POINTER(_u32)],
+    "tetris_free_database": [_vp, _u32],
+    "tetris_encode": [_vp, _vp, _u32, _d, _vp],
+    "tetris_encode_real": [_vp, _vp, _u32, _vp],
+    "tetris_evaluate_query": [_vp, _u32, C.POINTER(Query), C.POINTER(CtOut)],
+    "tetris_evaluate_query_device": [_vp, _u32, C.POINTER(Query), C.POINTER(CtOut), _vp],
+    "tetris_plan": [_vp, _u32, _u32, _u32, C.POINTER(PlanInfo)],
+    "tetris_set_option": [_vp, C.c_int, _i64],
+    "tetris_get_option": [_vp, C.c_int, C.POINTER(_i64)],
+    "tetris_op": [_vp, C.c_int, C.POINTER(CtIn), C.POINTER(CtIn), _i64, C.POINTER(CtOut)],
+}
+
+
+@lru_cache(maxsize=1)
+def lib():
+    if not os.path.exists(LIB_PATH):
+        raise ImportError(f"libtetris.so is not built ({LIB_PATH}); run paper_2412_13269_gb300.build()")
+    so = C.CDLL(LIB_PATH)
+    for name, args in SIGNATURES.items():
+        f = getattr(so, name)
+        f.argtypes = args
+        f.restype = C.c_char_p if name == "tetris_last_error" else (None if name == "tetris_ctx_destroy" else C.c_int)
+    return so
+
+
+def check(rc: int):
+    if rc != TETRIS_OK:
+        raise TetrisError(rc, lib().tetris_last_error().decode())
+
+
+def _ptr(a) -> int:
+    """Address of a C-contiguous numpy array or a torch tensor."""
+    if isinstance(a, np.ndarray):
+        assert a.flags["C_CONTIGUOUS"]
+        return a.ctypes.data
+    return a.data_ptr()
+
+
+def _is_device(a) -> bool:
+    return not isinstance(a, np.ndarray)
+
+
+def gen_primes(bits: int, count: int, congruence_log2: int = 17, exclude=()) -> list:
+    out = np.zeros(count, dtype=np.uint64)
+    ex = np.asarray(list(exclude), dtype=np.uint64)
+    check(lib().tetris_gen_primes(bits, count, congruence_log2, ex.ctypes.data if ex.size else None, ex.size, out.ctypes.data))
+    return [int(x) for x in out]
+
+
+def ct_in(data, level: int, scale: float, ncomp: int | None = None) -> CtIn:
+    nc = ncomp if ncomp is not None else data.shape[0]
+    return CtIn(level, nc, float(scale), _ptr(data))
+
+
+class Ctx:
+    """Owns a tetris_ctx; methods marshal numpy/torch buffers into the C calls."""
+
+    def __init__(self, log_n: int, q, p, scale: float, device: int = 0):
+        self.log_n, self.N = log_n, 1 << log_n
+        self.q, self.p = [int(x) for x in q], [int(x) for x in p]
+        self.scale = float(scale)
+        qa, pa = np.asarray(self.q, dtype=np.uint64), np.asarray(self.p, dtype=np.uint64)
+        h = C.c_void_p()
+        check(lib().tetris_ctx_create(C.byref(h), log_n, qa.ctypes.data, len(self.q), pa.ctypes.data, len(self.p),
+                                      self.scale, device))
+        self.h = h
+        self._keep = []
+
+    def close(self):
+        if getattr(self, "h", None):
+            lib().tetris_ctx_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    @property
+    def L(self) -> int:
+        return len(self.q) - 1
+
+    def info(self) -> CtxInfo:
+        i = CtxInfo()
+        check(lib().tetris_get_info(self.h, C.byref(i)))
+        return i
+
+    def standard_scale(self, level: int) -> float:
+        v = C.c_double()
+        check(lib().tetris_standard_scale(self.h, level, C.byref(v)))
+        return v.value
+
+    # keys
+    def load_relin_key(self, evk: np.ndarray, alpha: int):
+        evk = np.ascontiguousarray(evk, dtype=np.uint64)
+        check(lib().tetris_load_relin_key(self.h, evk.ctypes.data, evk.size, alpha))
+
+    def load_rotation_key(self, g: int, evk: np.ndarray, alpha: int):
+        evk = np.ascontiguousarray(evk, dtype=np.uint64)
+        check(lib().tetris_load_rotation_key(self.h, g, evk.ctypes.data, evk.size, alpha))
+
+    def keygen_relin(self, s, a, e, alpha: int):
+        s, a, e = (np.ascontiguousarray(x) for x in (s, a, e))
+        check(lib().tetris_keygen_relin(self.h, s.ctypes.data, a.ctypes.data, e.ctypes.data, alpha))
+
+    def keygen_rotation(self, g: int, s, a, e, alpha: int):
+        s, a, e = (np.ascontiguousarray(x) for x in (s, a, e))
+        check(lib().tetris_keygen_rotation(self.h, g, s.ctypes.data, a.ctypes.data, e.ctypes.data, alpha))
+
+    def get_key(self, g: int, dnum: int) -> np.ndarray:
+        out = np.empty((dnum, 2, len(self.q) + len(self.p), self.N), dtype=np.uint64)
+        check(lib().tetris_get_key(self.h, g, out.ctypes.data, out.size))
+        return out
+
+    def encrypt(self, m, s, a, e, level: int, scale: float) -> np.ndarray:
+        m, s, e = (np.ascontiguousarray(x, dtype=np.int64) for x in (m, s, e))
+        a = np.ascontiguousarray(a[: level + 1], dtype=np.uint64)
+        out = np.empty((2, level + 1, self.N), dtype=np.uint64)
+        o = CtOut(0, 0, 0.0, out.ctypes.data, out.size)
+        check(lib().tetris_encrypt(self.h, m.ctypes.data, s.ctypes.data, a.ctypes.data, e.ctypes.data, level, scale,
+                                   C.byref(o)))
+        return out
+
+    # database
+    def upload_database(self, vals: np.ndarray) -> int:
+        vals = np.ascontiguousarray(vals, dtype=np.uint8)
+        h = C.c_uint32()
+        check(lib().tetris_upload_database(self.h, vals.ctypes.data, vals.shape[0], vals.shape[1], C.byref(h)))
+        return h.value
+
+    def upload_database_encoded(self, coeffs: np.ndarray, mask_real, records: int, attrs: int) -> int:
+        coeffs = np.ascontiguousarray(coeffs, dtype=np.int64)
+        mr = None if mask_real is None else np.ascontiguousarray(mask_real, dtype=np.float64)
+        h = C.c_uint32()
+        check(lib().tetris_upload_database_encoded(self.h, coeffs.ctypes.data, None if mr is None else mr.ctypes.data,
+                                                   records, attrs, C.byref(h)))
+        return h.value
+
+    def free_database(self, db: int):
+        check(lib().tetris_free_database(self.h, db))
+
+    def encode(self, slots, scale: float) -> np.ndarray:
+        z = np.ascontiguousarray(slots, dtype=np.float64)
+        out = np.empty(self.N, dtype=np.int64)
+        check(lib().tetris_encode(self.h, z.ctypes.data, z.size, scale, out.ctypes.data))
+        return out
+
+    def encode_real(self, slots) -> np.ndarray:
+        z = np.ascontiguousarray(slots, dtype=np.float64)
+        out = np.empty(self.N, dtype=np.float64)
+        check(lib().tetris_encode_real(self.h, z.ctypes.data, z.size, out.ctypes.data))
+        return out
+
+    # options / plan
+    def set_option(self, opt: int, value: int):
+        check(lib().tetris_set_option(self.h, opt, value))
+
+    def get_option(self, opt: int) -> int:
+        v = C.c_int64()
+        check(lib().tetris_get_option(self.h, opt, C.byref(v)))
+        return v.value
+
+    def plan(self, db: int, degree: int, stages: int) -> PlanInfo:
+        p = PlanInfo()
+        check(lib().tetris_plan(self.h, db, degree, stages, C.byref(p)))
+        return p
+
+    # query
+    def _query_struct(self, w, w_meta, c, c_meta, t, t_meta, sign_coeffs):
+        W = (CtIn * len(w))(*[CtIn(lv, 2, sc, _ptr(x)) for x, (lv, sc) in zip(w, w_meta)])
+        Cc = (CtIn * len(c))(*[CtIn(lv, 2, sc, _ptr(x)) for x, (lv, sc) in zip(c, c_meta)])
+        T = CtIn(t_meta[0], 2, t_meta[1], _ptr(t))
+        sc = np.ascontiguousarray(np.asarray(sign_coeffs, dtype=np.float64).reshape(-1))
+        q = Query(len(w), W, len(c) - 1, Cc, C.pointer(T), sc.size // 4, 7,
+                  sc.ctypes.data_as(C.POINTER(C.c_double)))
+        return q, (W, Cc, T, sc)
+
+    def evaluate_query(self, db: int, w, w_meta, c, c_meta, t, t_meta, sign_coeffs, out=None):
+        """Host arrays: w/c/t are [2][level+1][N] uint64; metas are (level, scale).
+        Returns (out array, level, scale)."""
+        q, keep = self._query_struct(w, w_meta, c, c_meta, t, t_meta, sign_coeffs)
+        if out is None:
+            out = np.empty(2 * (self.L + 1) * self.N, dtype=np.uint64)
+        o = CtOut(0, 0, 0.0, _ptr(out), out.size if isinstance(out, np.ndarray) else out.numel())
+        check(lib().tetris_evaluate_query(self.h, db, C.byref(q), C.byref(o)))
+        n = 2 * (o.level + 1) * self.N
+        return out[:n].reshape(2, o.level + 1, self.N), o.level, o.scale
+
+    def evaluate_query_device(self, db: int, w, w_meta, c, c_meta, t, t_meta, sign_coeffs, out, stream: int):
+        """torch CUDA tensors in and out; enqueued on ``stream`` (a cudaStream_t as int)."""
+        q, keep = self._query_struct(w, w_meta, c, c_meta, t, t_meta, sign_coeffs)
+        o = CtOut(0, 0, 0.0, _ptr(out), out.numel())
+        check(lib().tetris_evaluate_query_device(self.h, db, C.byref(q), C.byref(o), stream))
+        return o.level, o.scale
+
+    # single operations
+    def op(self, opcode: int, a: np.ndarray, a_level: int, a_scale: float = 1.0, b: np.ndarray | None = None,
+           b_level: int = 0, arg: int = 0, out_comps: int | None = None, out_level: int | None = None):
+        a = np.ascontiguousarray(a, dtype=np.uint64)
+        A = CtIn(a_level, a.shape[0], a_scale, a.ctypes.data)
+        B = None
+        if b is not None:
+            b = np.ascontiguousarray(b, dtype=np.uint64)
+            B = CtIn(b_level, b.shape[0], 1.0, b.ctypes.data)
+        comps = out_comps if out_comps is not None else 3
+        lev = out_level if out_level is not None else a_level
+        out = np.empty((comps, lev + 1, self.N), dtype=np.uint64)
+        o = CtOut(0, 0, 0.0, out.ctypes.data, out.size)
+        check(lib().tetris_op(self.h, opcode, C.byref(A), C.byref(B) if B is not None else None, arg, C.byref(o)))
+        n = o.ncomp * (o.level + 1) * self.N
+        return out.reshape(-1)[:n].reshape(o.ncomp, o.level + 1, self.N), o.level, o.scale

@@ -1,0 +1,777 @@
+// The C ABI (include/tetris.h): argument checks, host<->device copies and
+// dispatch into the recorder.  Every entry point catches library errors and
+// returns a status; the message is kept per thread.
+#include <cmath>
+#include <cstring>
+
+#include "program.h"
+
+struct tetris_ctx {
+    tetris::Ctx c;
+};
+
+namespace tetris {
+
+static thread_local std::string g_last_error;
+void set_last_error(const std::string &m) { g_last_error = m; }
+
+template <class F>
+static int guarded(F &&f) {
+    try {
+        f();
+        return TETRIS_OK;
+    } catch (const Error &e) {
+        set_last_error(e.what());
+        cudaGetLastError();
+        return e.code;
+    } catch (const std::bad_alloc &) {
+        set_last_error("host allocation failed");
+        return TETRIS_ENOMEM;
+    } catch (const std::exception &e) {
+        set_last_error(e.what());
+        return TETRIS_EINVAL;
+    }
+}
+
+static void run_now(Ctx &C, Program &P) {
+    P.finalize();
+    P.run(C.stream);
+    TCHECK_CUDA(cudaStreamSynchronize(C.stream));
+}
+
+static BufPtr upload(Pool &pool, const void *src, size_t bytes, cudaStream_t s) {
+    BufPtr b = pool.alloc((bytes + 7) / 8);
+    TCHECK_CUDA(cudaMemcpyAsync(b->ptr, src, bytes, cudaMemcpyHostToDevice, s));
+    return b;
+}
+
+static void build_tables(Ctx &C) {
+    const size_t N = C.N, np = C.all.size();
+    std::vector<u64> tw(np * N), tws(np * N), itw(np * N), itws(np * N);
+    C.mods_host.resize(np);
+    for (size_t t = 0; t < np; t++) {
+        const u64 q = C.all[t], psi = C.psi[t], ipsi = h_invmod(psi, q);
+        std::vector<u64> pw(N), ipw(N);
+        pw[0] = ipw[0] = 1;
+        for (size_t e = 1; e < N; e++) {
+            pw[e] = h_mulmod(pw[e - 1], psi, q);
+            ipw[e] = h_mulmod(ipw[e - 1], ipsi, q);
+        }
+        for (size_t k = 0; k < N; k++) {
+            const uint32_t r = bitrev((uint32_t)k, C.log_n);
+            tw[t * N + k] = pw[r];
+            tws[t * N + k] = h_shoup(pw[r], q);
+            itw[t * N + k] = ipw[r];
+            itws[t * N + k] = h_shoup(ipw[r], q);
+        }
+        ModInfo &m = C.mods_host[t];
+        m.q = q;
+        m.r64 = (u64)((((u128)1) << 64) % q);
+        m.r64_sh = h_shoup(m.r64, q);
+        m.one_sh = (u64)((((u128)1) << 64) / q);
+        m.ninv = h_invmod(N % q, q);
+        m.ninv_sh = h_shoup(m.ninv, q);
+    }
+    // encoder: [N/2] exp(-2 pi i k/N), [N] exp(-pi i k/N), [N/2] int u_j
+    std::vector<double> enc(2 * (N / 2) + 2 * N + N / 4 + 2, 0.0);
+    for (size_t k = 0; k < N / 2; k++) {
+        const double a = 2.0 * M_PI * (double)k / (double)N;
+        enc[2 * k] = std::cos(a);
+        enc[2 * k + 1] = -std::sin(a);
+    }
+    double *twist = enc.data() + N;
+    for (size_t k = 0; k < N; k++) {
+        const double a = M_PI * (double)k / (double)N;
+        twist[2 * k] = std::cos(a);
+        twist[2 * k + 1] = -std::sin(a);
+    }
+    int *uj = reinterpret_cast<int *>(twist + 2 * N);
+    u64 e = 1;
+    for (size_t j = 0; j < N / 2; j++) {
+        uj[j] = (int)((e - 1) / 2);
+        e = e * 5 % (2 * N);
+    }
+    const size_t w = np * N;
+    const size_t mods_words = (np * sizeof(ModInfo) + 7) / 8;
+    const size_t enc_words = enc.size();
+    C.tables = C.pool.alloc(4 * w + mods_words + enc_words);
+    u64 *base = C.tables->ptr;
+    TCHECK_CUDA(cudaMemcpy(base, tw.data(), w * 8, cudaMemcpyHostToDevice));
+    TCHECK_CUDA(cudaMemcpy(base + w, tws.data(), w * 8, cudaMemcpyHostToDevice));
+    TCHECK_CUDA(cudaMemcpy(base + 2 * w, itw.data(), w * 8, cudaMemcpyHostToDevice));
+    TCHECK_CUDA(cudaMemcpy(base + 3 * w, itws.data(), w * 8, cudaMemcpyHostToDevice));
+    TCHECK_CUDA(cudaMemcpy(base + 4 * w, C.mods_host.data(), np * sizeof(ModInfo), cudaMemcpyHostToDevice));
+    TCHECK_CUDA(cudaMemcpy(base + 4 * w + mods_words, enc.data(), enc_words * 8, cudaMemcpyHostToDevice));
+    C.nt.tw = base;
+    C.nt.tw_sh = base + w;
+    C.nt.itw = base + 2 * w;
+    C.nt.itw_sh = base + 3 * w;
+    C.nt.mods = reinterpret_cast<const ModInfo *>(base + 4 * w);
+    C.enc_tw = reinterpret_cast<const double *>(base + 4 * w + mods_words);
+}
+
+// ---------------------------------------------------------------------------
+// Keys
+// ---------------------------------------------------------------------------
+static void set_alpha(Ctx &C, uint32_t alpha) {
+    TREQUIRE(alpha >= 1 && (int)alpha <= kMaxConvSrc, TETRIS_EINVAL, "alpha must be in [1, 4]");
+    TREQUIRE(C.alpha == 0 || C.alpha == (int)alpha, TETRIS_EINVAL, "all keys of a context share one alpha");
+    const int dnum = (C.L() + 1 + alpha - 1) / alpha;
+    TREQUIRE(dnum <= 32, TETRIS_EINVAL, "too many key digits (at most 32)");
+    C.alpha = alpha;
+}
+
+static Key load_key(Ctx &C, const uint64_t *evk, size_t n_words, uint32_t alpha) {
+    set_alpha(C, alpha);
+    const int dnum = (C.L() + 1 + alpha - 1) / alpha, nqp = C.nqp();
+    const size_t N = C.N;
+    TREQUIRE(evk && n_words == (size_t)dnum * 2 * nqp * N, TETRIS_EINVAL, "key: wrong size");
+    Key k;
+    k.dnum = dnum;
+    k.buf = upload(C.pool, evk, n_words * 8, C.stream);
+    Program P;
+    Rec R(C, P);
+    std::vector<NttJob> jobs;
+    for (int j = 0; j < dnum; j++)
+        for (int c = 0; c < 2; c++)
+            for (int t = 0; t < nqp; t++) {
+                NttJob jb{};
+                jb.src = jb.dst = k.buf->ptr + (((size_t)j * 2 + c) * nqp + t) * N;
+                jb.prime = t;
+                jobs.push_back(jb);
+            }
+    R.ntt(false, jobs, LOAD_PLAIN, STORE_PLAIN);
+    run_now(C, P);
+    return k;
+}
+
+// s (int64, N) -> NTT-domain residues over every prime [nqp][N]
+static BufPtr secret_ntt(Ctx &C, Program &P, Rec &R, const int64_t *s, int nlimbs) {
+    BufPtr sd = upload(P.pool, s, C.N * 8, C.stream);
+    P.hold.push_back(sd);
+    BufPtr out = P.pool.alloc((size_t)nlimbs * C.N);
+    std::vector<NttJob> jobs;
+    for (int t = 0; t < nlimbs; t++) {
+        NttJob j{};
+        j.src = sd->ptr;
+        j.dst = out->ptr + (size_t)t * C.N;
+        j.prime = t;
+        jobs.push_back(j);
+    }
+    R.ntt(false, jobs, LOAD_INT64, STORE_PLAIN);
+    return out;
+}
+
+// swk_j = (-a_j s + e_j + w_j P s_from, a_j) over Q P, NTT domain (Section 2.4.1)
+static Key gen_key(Ctx &C, const int64_t *s, const uint64_t *a, const int64_t *e, uint32_t alpha, uint32_t galois) {
+    set_alpha(C, alpha);
+    const int dnum = (C.L() + 1 + alpha - 1) / alpha, nqp = C.nqp();
+    const size_t N = C.N;
+    TREQUIRE(s && a && e, TETRIS_EINVAL, "keygen: null input");
+    Program P;
+    Rec R(C, P);
+    BufPtr sn = secret_ntt(C, P, R, s, nqp);
+    BufPtr sf = P.pool.alloc((size_t)nqp * N);
+    if (galois == 0) {
+        std::vector<EwJob> jobs;
+        for (int t = 0; t < nqp; t++) {
+            EwJob j{};
+            j.op = EW_MUL;
+            j.prime = t;
+            j.a = j.b = sn->ptr + (size_t)t * N;
+            j.dst = sf->ptr + (size_t)t * N;
+            jobs.push_back(j);
+        }
+        R.ew(jobs);
+    } else {
+        std::vector<AutJob> jobs;
+        for (int t = 0; t < nqp; t++) jobs.push_back({sn->ptr + (size_t)t * N, sf->ptr + (size_t)t * N});
+        R.aut(jobs, galois & (uint32_t)(2 * N - 1));
+    }
+    Key k;
+    k.dnum = dnum;
+    k.buf = C.pool.alloc((size_t)dnum * 2 * nqp * N);
+    BufPtr ad = upload(P.pool, a, (size_t)dnum * nqp * N * 8, C.stream);
+    BufPtr ed = upload(P.pool, e, (size_t)dnum * N * 8, C.stream);
+    P.hold.push_back(ad);
+    P.hold.push_back(ed);
+    auto kl = [&](int j, int c, int t) { return k.buf->ptr + (((size_t)j * 2 + c) * nqp + t) * N; };
+    std::vector<NttJob> ja, je;
+    for (int j = 0; j < dnum; j++)
+        for (int t = 0; t < nqp; t++) {
+            NttJob x{};
+            x.src = ad->ptr + ((size_t)j * nqp + t) * N;
+            x.dst = kl(j, 1, t);
+            x.prime = t;
+            ja.push_back(x);
+            NttJob y{};
+            y.src = ed->ptr + (size_t)j * N;
+            y.dst = kl(j, 0, t);
+            y.prime = t;
+            je.push_back(y);
+        }
+    R.ntt(false, ja, LOAD_PLAIN, STORE_PLAIN);
+    R.ntt(false, je, LOAD_INT64, STORE_PLAIN);
+    BufPtr tmp = P.pool.alloc((size_t)dnum * nqp * N);
+    std::vector<EwJob> m1, m2, m3;
+    for (int j = 0; j < dnum; j++)
+        for (int t = 0; t < nqp; t++) {
+            EwJob x{};
+            x.op = EW_MUL;
+            x.prime = t;
+            x.a = kl(j, 1, t);
+            x.b = sn->ptr + (size_t)t * N;
+            x.dst = tmp->ptr + ((size_t)j * nqp + t) * N;
+            m1.push_back(x);
+            EwJob y{};
+            y.op = EW_SUB;
+            y.prime = t;
+            y.a = kl(j, 0, t);
+            y.b = x.dst;
+            y.dst = kl(j, 0, t);
+            m2.push_back(y);
+            const int lo = j * (int)alpha, hi = std::min(C.L() + 1, (j + 1) * (int)alpha);
+            if (t >= lo && t < hi) {
+                const u64 qt = C.all[t];
+                u64 pm = 1 % qt;
+                for (u64 pk : C.p) pm = h_mulmod(pm, pk % qt, qt);
+                EwJob z{};
+                z.op = EW_ADD_MUL_CONST;
+                z.prime = t;
+                z.a = sf->ptr + (size_t)t * N;
+                z.b = kl(j, 0, t);
+                z.dst = kl(j, 0, t);
+                z.k = pm;
+                z.k_sh = h_shoup(pm, qt);
+                m3.push_back(z);
+            }
+        }
+    R.ew(m1);
+    R.ew(m2);
+    R.ew(m3);
+    run_now(C, P);
+    return k;
+}
+
+// ---------------------------------------------------------------------------
+// Ciphertext upload / download helpers for single operations
+// ---------------------------------------------------------------------------
+static CtH upload_ct(Ctx &C, Program &P, Rec &R, const tetris_ct_in &c, bool to_ntt) {
+    TREQUIRE(c.data && c.ncomp >= 1 && c.ncomp <= 3 && (int)c.level <= C.L(), TETRIS_EINVAL, "ciphertext: bad shape");
+    CtH h = R.new_ct(1, c.ncomp, c.level);
+    h.scale = c.scale;
+    P.hold.push_back(h.buf);
+    TCHECK_CUDA(cudaMemcpyAsync(h.base, c.data, h.bstride * 8, cudaMemcpyHostToDevice, C.stream));
+    if (to_ntt) R.to_ntt(h);
+    return h;
+}
+
+static void download_ct(Ctx &C, Program &P, const CtH &h, tetris_ct_out *out) {
+    TREQUIRE(out && out->data, TETRIS_EINVAL, "null output");
+    const size_t words = (size_t)h.comps * (h.level + 1) * C.N;
+    TREQUIRE(out->cap_words >= words, TETRIS_EINVAL, "output buffer too small");
+    P.finalize();
+    P.run(C.stream);
+    // h may be a view with component stride > (level+1)*N
+    for (int c = 0; c < h.comps; c++)
+        TCHECK_CUDA(cudaMemcpyAsync(out->data + (size_t)c * (h.level + 1) * C.N, h.limb(0, c, 0),
+                                    (size_t)(h.level + 1) * C.N * 8, cudaMemcpyDeviceToHost, C.stream));
+    TCHECK_CUDA(cudaStreamSynchronize(C.stream));
+    out->level = h.level;
+    out->ncomp = h.comps;
+    out->scale = h.scale;
+}
+
+}  // namespace tetris
+
+using namespace tetris;
+
+extern "C" {
+
+const char *tetris_last_error(void) { return g_last_error.c_str(); }
+
+int tetris_gen_primes(uint32_t bits, uint32_t count, uint32_t cong, const uint64_t *exclude, uint32_t n_ex, uint64_t *out) {
+    return guarded([&] {
+        TREQUIRE(out, TETRIS_EINVAL, "null output");
+        std::vector<u64> ex(exclude, exclude + (exclude ? n_ex : 0));
+        auto v = h_gen_primes((int)bits, (int)count, (int)cong, ex);
+        std::memcpy(out, v.data(), v.size() * 8);
+    });
+}
+
+int tetris_ctx_create(tetris_ctx **out, uint32_t log_n, const uint64_t *q, uint32_t n_q, const uint64_t *p, uint32_t n_p,
+                      double scale, int device) {
+    return guarded([&] {
+        TREQUIRE(out && q && p, TETRIS_EINVAL, "ctx_create: null pointer");
+        TREQUIRE(log_n >= 10 && log_n <= 16, TETRIS_EINVAL, "log_n must be in [10, 16]");
+        TREQUIRE(n_q >= 1 && n_p >= 1 && n_p <= (uint32_t)kMaxConvSrc && n_q + n_p <= (uint32_t)kMaxPrimes, TETRIS_EINVAL,
+                 "prime counts out of range");
+        TREQUIRE(scale > 0 && std::isfinite(scale), TETRIS_EINVAL, "scale must be positive");
+        const u64 N = 1ull << log_n;
+        std::vector<u64> all(q, q + n_q);
+        all.insert(all.end(), p, p + n_p);
+        for (size_t i = 0; i < all.size(); i++) {
+            TREQUIRE(all[i] < (1ull << 61) && all[i] > 2 * N && (all[i] - 1) % (2 * N) == 0 && h_is_prime(all[i]),
+                     TETRIS_EINVAL, "every modulus must be a prime below 2^61 with q = 1 mod 2N");
+            for (size_t j = 0; j < i; j++) TREQUIRE(all[i] != all[j], TETRIS_EINVAL, "moduli must be distinct");
+        }
+        int ndev = 0;
+        TCHECK_CUDA(cudaGetDeviceCount(&ndev));
+        TREQUIRE(device >= 0 && device < ndev, TETRIS_EINVAL, "no such CUDA device");
+        TCHECK_CUDA(cudaSetDevice(device));
+        auto *h = new tetris_ctx();
+        Ctx &C = h->c;
+        try {
+            C.device = device;
+            C.log_n = log_n;
+            C.N = N;
+            C.q.assign(q, q + n_q);
+            C.p.assign(p, p + n_p);
+            C.all = all;
+            for (u64 m : all) C.psi.push_back(h_primitive_2n_root(m, N));
+            C.scale = scale;
+            C.S.assign(n_q, 0.0);
+            C.S[n_q - 1] = scale;
+            for (int l = (int)n_q - 1; l > 0; l--) C.S[l - 1] = (C.S[l] * C.S[l]) / (double)C.q[l];
+            const int L = (int)n_q - 1;
+            C.pt_scale = L >= 1 ? (C.S[L - 1] * (double)C.q[L]) / C.S[L] : 0.0;
+            TCHECK_CUDA(cudaStreamCreateWithFlags(&C.stream, cudaStreamNonBlocking));
+            build_tables(C);
+        } catch (...) {
+            if (C.stream) cudaStreamDestroy(C.stream);
+            delete h;
+            throw;
+        }
+        *out = h;
+    });
+}
+
+void tetris_ctx_destroy(tetris_ctx *ctx) {
+    if (!ctx) return;
+    cudaSetDevice(ctx->c.device);
+    cudaStreamSynchronize(ctx->c.stream);
+    cudaStream_t s = ctx->c.stream;
+    delete ctx;
+    cudaStreamDestroy(s);
+}
+
+int tetris_get_info(const tetris_ctx *ctx, tetris_ctx_info *out) {
+    return guarded([&] {
+        TREQUIRE(ctx && out, TETRIS_EINVAL, "null pointer");
+        const Ctx &C = ctx->c;
+        out->log_n = C.log_n;
+        out->n_q = (uint32_t)C.q.size();
+        out->n_p = (uint32_t)C.p.size();
+        out->scale = C.scale;
+        out->pt_scale = C.pt_scale;
+        out->device_bytes = C.bytes_held();
+    });
+}
+
+int tetris_standard_scale(const tetris_ctx *ctx, uint32_t level, double *out) {
+    return guarded([&] {
+        TREQUIRE(ctx && out && level < ctx->c.S.size(), TETRIS_EINVAL, "bad level");
+        *out = ctx->c.S[level];
+    });
+}
+
+int tetris_load_relin_key(tetris_ctx *ctx, const uint64_t *evk, size_t n_words, uint32_t alpha) {
+    return guarded([&] {
+        TREQUIRE(ctx, TETRIS_EINVAL, "null context");
+        cudaSetDevice(ctx->c.device);
+        ctx->c.relin = load_key(ctx->c, evk, n_words, alpha);
+        ctx->c.programs.clear();
+    });
+}
+
+int tetris_load_rotation_key(tetris_ctx *ctx, uint32_t g, const uint64_t *evk, size_t n_words, uint32_t alpha) {
+    return guarded([&] {
+        TREQUIRE(ctx && (g & 1), TETRIS_EINVAL, "galois element must be odd");
+        cudaSetDevice(ctx->c.device);
+        ctx->c.rot[g & (uint32_t)(2 * ctx->c.N - 1)] = load_key(ctx->c, evk, n_words, alpha);
+        ctx->c.programs.clear();
+    });
+}
+
+int tetris_keygen_relin(tetris_ctx *ctx, const int64_t *s, const uint64_t *a, const int64_t *e, uint32_t alpha) {
+    return guarded([&] {
+        TREQUIRE(ctx, TETRIS_EINVAL, "null context");
+        cudaSetDevice(ctx->c.device);
+        ctx->c.relin = gen_key(ctx->c, s, a, e, alpha, 0);
+        ctx->c.programs.clear();
+    });
+}
+
+int tetris_keygen_rotation(tetris_ctx *ctx, uint32_t g, const int64_t *s, const uint64_t *a, const int64_t *e, uint32_t alpha) {
+    return guarded([&] {
+        TREQUIRE(ctx && (g & 1), TETRIS_EINVAL, "galois element must be odd");
+        cudaSetDevice(ctx->c.device);
+        ctx->c.rot[g & (uint32_t)(2 * ctx->c.N - 1)] = gen_key(ctx->c, s, a, e, alpha, g);
+        ctx->c.programs.clear();
+    });
+}
+
+int tetris_get_key(tetris_ctx *ctx, uint32_t g, uint64_t *out, size_t cap) {
+    return guarded([&] {
+        TREQUIRE(ctx && out, TETRIS_EINVAL, "null pointer");
+        Ctx &C = ctx->c;
+        cudaSetDevice(C.device);
+        const Key &k = find_key(C, g & (uint32_t)(2 * C.N - 1));
+        const int nqp = C.nqp();
+        const size_t words = (size_t)k.dnum * 2 * nqp * C.N;
+        TREQUIRE(cap >= words, TETRIS_EINVAL, "output buffer too small");
+        Program P;
+        Rec R(C, P);
+        BufPtr o = P.pool.alloc(words);
+        std::vector<NttJob> jobs;
+        for (size_t l = 0; l < (size_t)k.dnum * 2 * nqp; l++) {
+            NttJob j{};
+            j.src = k.buf->ptr + l * C.N;
+            j.dst = o->ptr + l * C.N;
+            j.prime = (uint32_t)(l % nqp);
+            jobs.push_back(j);
+        }
+        R.ntt(true, jobs, LOAD_PLAIN, STORE_PLAIN);
+        run_now(C, P);
+        TCHECK_CUDA(cudaMemcpy(out, o->ptr, words * 8, cudaMemcpyDeviceToHost));
+    });
+}
+
+int tetris_encrypt(tetris_ctx *ctx, const int64_t *m, const int64_t *s, const uint64_t *a, const int64_t *e,
+                   uint32_t level, double scale, tetris_ct_out *out) {
+    return guarded([&] {
+        TREQUIRE(ctx && m && s && a && e, TETRIS_EINVAL, "null pointer");
+        Ctx &C = ctx->c;
+        cudaSetDevice(C.device);
+        TREQUIRE((int)level <= C.L(), TETRIS_EINVAL, "level out of range");
+        const int nl = level + 1;
+        const size_t N = C.N;
+        Program P;
+        Rec R(C, P);
+        BufPtr sn = secret_ntt(C, P, R, s, nl);
+        CtH ct = R.new_ct(1, 2, level);
+        ct.scale = scale;
+        BufPtr md = upload(P.pool, m, N * 8, C.stream), ed = upload(P.pool, e, N * 8, C.stream);
+        P.hold.push_back(md);
+        P.hold.push_back(ed);
+        TCHECK_CUDA(cudaMemcpyAsync(ct.limb(0, 1, 0), a, (size_t)nl * N * 8, cudaMemcpyHostToDevice, C.stream));
+        BufPtr mn = P.pool.alloc((size_t)nl * N), en = P.pool.alloc((size_t)nl * N), as = P.pool.alloc((size_t)nl * N);
+        std::vector<NttJob> jm, je, ja;
+        for (int i = 0; i < nl; i++) {
+            NttJob x{};
+            x.prime = i;
+            x.src = md->ptr;
+            x.dst = mn->ptr + (size_t)i * N;
+            jm.push_back(x);
+            x.src = ed->ptr;
+            x.dst = en->ptr + (size_t)i * N;
+            je.push_back(x);
+            x.src = x.dst = ct.limb(0, 1, i);
+            ja.push_back(x);
+        }
+        R.ntt(false, jm, LOAD_INT64, STORE_PLAIN);
+        R.ntt(false, je, LOAD_INT64, STORE_PLAIN);
+        R.ntt(false, ja, LOAD_PLAIN, STORE_PLAIN);
+        std::vector<EwJob> j1, j2;
+        for (int i = 0; i < nl; i++) {
+            EwJob x{};
+            x.op = EW_ADD;
+            x.prime = i;
+            x.a = mn->ptr + (size_t)i * N;
+            x.b = en->ptr + (size_t)i * N;
+            x.dst = mn->ptr + (size_t)i * N;
+            j1.push_back(x);
+            EwJob y{};
+            y.op = EW_MUL;
+            y.prime = i;
+            y.a = ct.limb(0, 1, i);
+            y.b = sn->ptr + (size_t)i * N;
+            y.dst = as->ptr + (size_t)i * N;
+            j1.push_back(y);
+            EwJob z{};
+            z.op = EW_SUB;
+            z.prime = i;
+            z.a = mn->ptr + (size_t)i * N;
+            z.b = as->ptr + (size_t)i * N;
+            z.dst = ct.limb(0, 0, i);
+            j2.push_back(z);
+        }
+        // m+e and a*s are independent; the subtraction runs after both
+        R.ew(j1);
+        R.ew(j2);
+        CtH o = R.from_ntt(ct);
+        download_ct(C, P, o, out);
+    });
+}
+
+int tetris_upload_database(tetris_ctx *ctx, const uint8_t *vals, uint64_t records, uint32_t attrs, uint32_t *db_out) {
+    return guarded([&] {
+        TREQUIRE(ctx && vals && db_out && records > 0 && attrs > 0, TETRIS_EINVAL, "upload_database: bad arguments");
+        Ctx &C = ctx->c;
+        cudaSetDevice(C.device);
+        TREQUIRE(C.L() >= 1, TETRIS_ELEVEL, "context has a single prime");
+        const size_t N = C.N, n = N / 2, nq = C.q.size();
+        Database db;
+        db.records = records;
+        db.attrs = attrs;
+        db.blocks = (int)((records + n - 1) / n);
+        db.pts = C.pool.alloc((size_t)db.blocks * attrs * nq * N);
+        Program P;
+        Rec R(C, P);
+        BufPtr vd = upload(P.pool, vals, records * attrs, C.stream);
+        const size_t npt = (size_t)db.blocks * attrs;
+        BufPtr slots = P.pool.alloc(npt * n);
+        db_slots(reinterpret_cast<const uint8_t *>(vd->ptr), records, attrs, db.blocks, C.log_n,
+                 reinterpret_cast<double *>(slots->ptr), C.stream);
+        const size_t chunk = 32;
+        BufPtr m = P.pool.alloc(chunk * N), work = P.pool.alloc(chunk * N * 4), ints = P.pool.alloc(chunk * N);
+        for (size_t c0 = 0; c0 < npt; c0 += chunk) {
+            const size_t cnt = std::min(chunk, npt - c0);
+            encode_real_batch(reinterpret_cast<const double *>(slots->ptr) + c0 * n, reinterpret_cast<double *>(m->ptr),
+                              (int)cnt, C.log_n, C.enc_tw, reinterpret_cast<double *>(work->ptr), C.stream);
+            round_scale(reinterpret_cast<const double *>(m->ptr), reinterpret_cast<int64_t *>(ints->ptr), cnt * N, C.pt_scale,
+                        C.stream);
+            Program Q;
+            Rec RQ(C, Q);
+            std::vector<NttJob> jobs;
+            for (size_t k = 0; k < cnt; k++)
+                for (size_t i = 0; i < nq; i++) {
+                    NttJob j{};
+                    j.src = ints->ptr + k * N;
+                    j.dst = db.pts->ptr + ((c0 + k) * nq + i) * N;
+                    j.prime = (uint32_t)i;
+                    jobs.push_back(j);
+                }
+            RQ.ntt(false, jobs, LOAD_INT64, STORE_PLAIN);
+            run_now(C, Q);
+        }
+        if (records % n) {
+            const uint64_t live = records - (uint64_t)(db.blocks - 1) * n;
+            std::vector<double> z(n, 0.0);
+            for (uint64_t i = 0; i < live; i++) z[i] = 1.0;
+            BufPtr zs = upload(P.pool, z.data(), n * 8, C.stream);
+            db.mask_real = C.pool.alloc(N);
+            encode_real_batch(reinterpret_cast<const double *>(zs->ptr), reinterpret_cast<double *>(db.mask_real->ptr), 1,
+                              C.log_n, C.enc_tw, reinterpret_cast<double *>(work->ptr), C.stream);
+            TCHECK_CUDA(cudaStreamSynchronize(C.stream));
+        }
+        TCHECK_CUDA(cudaStreamSynchronize(C.stream));
+        TCHECK_CUDA(cudaGetLastError());
+        const uint32_t h = C.next_db++;
+        C.dbs[h] = db;
+        *db_out = h;
+    });
+}
+
+int tetris_upload_database_encoded(tetris_ctx *ctx, const int64_t *coeffs, const double *mask_real, uint64_t records,
+                                   uint32_t attrs, uint32_t *db_out) {
+    return guarded([&] {
+        TREQUIRE(ctx && coeffs && db_out && records > 0 && attrs > 0, TETRIS_EINVAL, "upload_database_encoded: bad arguments");
+        Ctx &C = ctx->c;
+        cudaSetDevice(C.device);
+        const size_t N = C.N, n = N / 2, nq = C.q.size();
+        TREQUIRE((records % n == 0) == (mask_real == nullptr), TETRIS_EINVAL,
+                 "mask_real is required exactly when the last block is partly filled");
+        Database db;
+        db.records = records;
+        db.attrs = attrs;
+        db.blocks = (int)((records + n - 1) / n);
+        db.pts = C.pool.alloc((size_t)db.blocks * attrs * nq * N);
+        const size_t npt = (size_t)db.blocks * attrs;
+        const size_t chunk = 64;
+        for (size_t c0 = 0; c0 < npt; c0 += chunk) {
+            const size_t cnt = std::min(chunk, npt - c0);
+            Program P;
+            Rec R(C, P);
+            BufPtr cd = upload(P.pool, coeffs + c0 * N, cnt * N * 8, C.stream);
+            std::vector<NttJob> jobs;
+            for (size_t k = 0; k < cnt; k++)
+                for (size_t i = 0; i < nq; i++) {
+                    NttJob j{};
+                    j.src = cd->ptr + k * N;
+                    j.dst = db.pts->ptr + ((c0 + k) * nq + i) * N;
+                    j.prime = (uint32_t)i;
+                    jobs.push_back(j);
+                }
+            R.ntt(false, jobs, LOAD_INT64, STORE_PLAIN);
+            run_now(C, P);
+        }
+        if (mask_real) db.mask_real = upload(C.pool, mask_real, N * 8, C.stream);
+        TCHECK_CUDA(cudaStreamSynchronize(C.stream));
+        const uint32_t h = C.next_db++;
+        C.dbs[h] = db;
+        *db_out = h;
+    });
+}
+
+int tetris_free_database(tetris_ctx *ctx, uint32_t db) {
+    return guarded([&] {
+        TREQUIRE(ctx, TETRIS_EINVAL, "null context");
+        auto it = ctx->c.dbs.find(db);
+        TREQUIRE(it != ctx->c.dbs.end(), TETRIS_ENOTFOUND, "unknown database handle");
+        cudaSetDevice(ctx->c.device);
+        cudaStreamSynchronize(ctx->c.stream);
+        drop_programs_of_db(ctx->c, db);
+        ctx->c.dbs.erase(it);
+    });
+}
+
+static void encode_common(Ctx &C, const double *slots, uint32_t nv, double *m_host, int64_t *ints_host, double scale) {
+    const size_t N = C.N, n = N / 2;
+    TREQUIRE(slots && nv <= n, TETRIS_EINVAL, "encode: too many slot values");
+    Pool pool;
+    std::vector<double> z(n, 0.0);
+    std::memcpy(z.data(), slots, nv * 8);
+    BufPtr zs = upload(pool, z.data(), n * 8, C.stream);
+    BufPtr m = pool.alloc(N), work = pool.alloc(4 * N), ints = pool.alloc(N);
+    encode_real_batch(reinterpret_cast<const double *>(zs->ptr), reinterpret_cast<double *>(m->ptr), 1, C.log_n, C.enc_tw,
+                      reinterpret_cast<double *>(work->ptr), C.stream);
+    if (ints_host) round_scale(reinterpret_cast<const double *>(m->ptr), reinterpret_cast<int64_t *>(ints->ptr), N, scale, C.stream);
+    TCHECK_CUDA(cudaStreamSynchronize(C.stream));
+    TCHECK_CUDA(cudaGetLastError());
+    if (m_host) TCHECK_CUDA(cudaMemcpy(m_host, m->ptr, N * 8, cudaMemcpyDeviceToHost));
+    if (ints_host) TCHECK_CUDA(cudaMemcpy(ints_host, ints->ptr, N * 8, cudaMemcpyDeviceToHost));
+}
+
+int tetris_encode(tetris_ctx *ctx, const double *slots, uint32_t nv, double scale, int64_t *coeffs) {
+    return guarded([&] {
+        TREQUIRE(ctx && coeffs, TETRIS_EINVAL, "null pointer");
+        cudaSetDevice(ctx->c.device);
+        encode_common(ctx->c, slots, nv, nullptr, coeffs, scale);
+    });
+}
+
+int tetris_encode_real(tetris_ctx *ctx, const double *slots, uint32_t nv, double *m_out) {
+    return guarded([&] {
+        TREQUIRE(ctx && m_out, TETRIS_EINVAL, "null pointer");
+        cudaSetDevice(ctx->c.device);
+        encode_common(ctx->c, slots, nv, m_out, nullptr, 1.0);
+    });
+}
+
+int tetris_evaluate_query(tetris_ctx *ctx, uint32_t db, const tetris_query *q, tetris_ct_out *out) {
+    return guarded([&] {
+        TREQUIRE(ctx, TETRIS_EINVAL, "null context");
+        cudaSetDevice(ctx->c.device);
+        evaluate_query(ctx->c, db, q, out, ctx->c.stream, false);
+    });
+}
+
+int tetris_evaluate_query_device(tetris_ctx *ctx, uint32_t db, const tetris_query *q, tetris_ct_out *out, void *stream) {
+    return guarded([&] {
+        TREQUIRE(ctx, TETRIS_EINVAL, "null context");
+        cudaSetDevice(ctx->c.device);
+        evaluate_query(ctx->c, db, q, out, reinterpret_cast<cudaStream_t>(stream), true);
+    });
+}
+
+int tetris_plan(tetris_ctx *ctx, uint32_t db, uint32_t f_degree, uint32_t sign_stages, tetris_plan_info *out) {
+    return guarded([&] {
+        TREQUIRE(ctx && out, TETRIS_EINVAL, "null pointer");
+        cudaSetDevice(ctx->c.device);
+        plan_info(ctx->c, db, f_degree, sign_stages, out);
+    });
+}
+
+int tetris_set_option(tetris_ctx *ctx, int option, int64_t value) {
+    return guarded([&] {
+        TREQUIRE(ctx, TETRIS_EINVAL, "null context");
+        Ctx &C = ctx->c;
+        switch (option) {
+            case TETRIS_OPT_BLOCKS_PER_LAUNCH:
+                TREQUIRE(value >= 0 && value < (1 << 20), TETRIS_EINVAL, "bad value");
+                if (C.blocks_per_launch != (int)value) C.blocks_per_launch = (int)value;
+                break;
+            case TETRIS_OPT_USE_GRAPH:
+                C.use_graph = value ? 1 : 0;
+                break;
+            default:
+                throw Error(TETRIS_EINVAL, "unknown or read-only option");
+        }
+    });
+}
+
+int tetris_get_option(tetris_ctx *ctx, int option, int64_t *value) {
+    return guarded([&] {
+        TREQUIRE(ctx && value, TETRIS_EINVAL, "null pointer");
+        Ctx &C = ctx->c;
+        switch (option) {
+            case TETRIS_OPT_BLOCKS_PER_LAUNCH: *value = C.blocks_per_launch; break;
+            case TETRIS_OPT_USE_GRAPH: *value = C.use_graph; break;
+            case TETRIS_OPT_KS_ALPHA: *value = C.alpha; break;
+            default: throw Error(TETRIS_EINVAL, "unknown option");
+        }
+    });
+}
+
+int tetris_op(tetris_ctx *ctx, int op, const tetris_ct_in *a, const tetris_ct_in *b, int64_t arg, tetris_ct_out *out) {
+    return guarded([&] {
+        TREQUIRE(ctx && a, TETRIS_EINVAL, "null pointer");
+        Ctx &C = ctx->c;
+        cudaSetDevice(C.device);
+        Program P;
+        Rec R(C, P);
+        CtH x = upload_ct(C, P, R, *a, true);
+        CtH r;
+        switch (op) {
+            case TETRIS_OP_ADD:
+            case TETRIS_OP_SUB: {
+                TREQUIRE(b, TETRIS_EINVAL, "needs b");
+                CtH y = upload_ct(C, P, R, *b, true);
+                r = op == TETRIS_OP_ADD ? R.add(x, y) : R.sub(x, y);
+                break;
+            }
+            case TETRIS_OP_TENSOR: {
+                TREQUIRE(b, TETRIS_EINVAL, "needs b");
+                r = R.tensor(x, upload_ct(C, P, R, *b, true));
+                break;
+            }
+            case TETRIS_OP_RELIN: r = R.relin(x); break;
+            case TETRIS_OP_RESCALE: r = R.rescale(x); break;
+            case TETRIS_OP_MUL_INT: r = R.mul_int(x, arg); break;
+            case TETRIS_OP_ADD_INT: r = R.add_int(x, arg); break;
+            case TETRIS_OP_AUTOMORPHISM: r = R.automorphism(x, (uint32_t)arg); break;
+            case TETRIS_OP_ROTATE: r = R.rotate(x, (uint32_t)arg); break;
+            case TETRIS_OP_KEYSWITCH: {
+                TREQUIRE(x.comps == 1, TETRIS_EINVAL, "keyswitch takes one polynomial");
+                const Key &k = find_key(C, (uint32_t)arg & (uint32_t)(2 * C.N - 1));
+                r = R.keyswitch(1, x.level, [&](int, int i) { return (const u64 *)x.limb(0, 0, i); }, k,
+                                [](int, int, int) { return (const u64 *)nullptr; });
+                break;
+            }
+            case TETRIS_OP_MUL_PLAIN: {
+                TREQUIRE(b && b->ncomp == 1 && b->level >= a->level, TETRIS_EINVAL, "plaintext must have one component");
+                CtH y = upload_ct(C, P, R, *b, true);
+                r = R.mul_plain(x, y.base, 0);
+                break;
+            }
+            case TETRIS_OP_NTT: {
+                TREQUIRE(out && out->data && out->cap_words >= x.bstride, TETRIS_EINVAL, "output buffer too small");
+                P.finalize();
+                P.run(C.stream);
+                for (int c = 0; c < x.comps; c++)
+                    TCHECK_CUDA(cudaMemcpyAsync(out->data + (size_t)c * (x.level + 1) * C.N, x.limb(0, c, 0),
+                                                (size_t)(x.level + 1) * C.N * 8, cudaMemcpyDeviceToHost, C.stream));
+                TCHECK_CUDA(cudaStreamSynchronize(C.stream));
+                out->level = x.level;
+                out->ncomp = x.comps;
+                out->scale = x.scale;
+                return;
+            }
+            case TETRIS_OP_INNERSUM: {
+                r = x;
+                for (int k = 0; k + 1 < C.log_n; k++) {
+                    const uint32_t g = (uint32_t)h_powmod(5, 1ull << k, 2 * C.N);
+                    r = R.add(r, R.rotate(r, g));
+                }
+                break;
+            }
+            case TETRIS_OP_DROP: r = R.drop(x, (int)arg); break;
+            default: throw Error(TETRIS_EINVAL, "unknown opcode");
+        }
+        CtH o = R.from_ntt(r);
+        download_ct(C, P, o, out);
+    });
+}
+
+}  // extern "C"

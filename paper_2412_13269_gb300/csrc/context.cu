@@ -1,0 +1,634 @@
+// Context creation, memory pool, recorded programs and the ciphertext-level
+// recorder.  Paper references: Section 2.2 (ring), 2.4.1 (SwitchKey), 2.5
+// (rescale), Appendix A.2 (relinearisation, automorphism + key switch).
+#include <algorithm>
+#include <cstring>
+
+#include "program.h"
+
+namespace tetris {
+
+// ---------------------------------------------------------------------------
+// Pool
+// ---------------------------------------------------------------------------
+Pool::~Pool() {
+    *alive_ = 0;
+    for (auto &a : all_) cudaFree(a.first);
+}
+
+BufPtr Pool::alloc(size_t words) {
+    words = std::max<size_t>(words, 2);
+    u64 *ptr = nullptr;
+    auto it = free_.find(words);
+    if (it != free_.end()) {
+        ptr = it->second;
+        free_.erase(it);
+    } else {
+        cudaError_t e = cudaMalloc(&ptr, words * 8);
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            trim();
+            e = cudaMalloc(&ptr, words * 8);
+            if (e != cudaSuccess) {
+                cudaGetLastError();
+                throw Error(TETRIS_ENOMEM, "device allocation of " + std::to_string(words * 8) + " bytes failed");
+            }
+        }
+        all_.push_back({ptr, words});
+        held_ += words * 8;
+    }
+    std::weak_ptr<int> alive = alive_;
+    auto *fl = &free_;
+    return BufPtr(new DevBuf{ptr, words}, [alive, fl](DevBuf *b) {
+        if (auto a = alive.lock())
+            if (*a) fl->insert({b->words, b->ptr});
+        delete b;
+    });
+}
+
+void Pool::trim() {
+    for (auto &f : free_) {
+        cudaFree(f.second);
+        auto it = std::find_if(all_.begin(), all_.end(), [&](auto &a) { return a.first == f.second; });
+        if (it != all_.end()) {
+            held_ -= it->second * 8;
+            all_.erase(it);
+        }
+    }
+    free_.clear();
+}
+
+size_t Ctx::bytes_held() const {
+    size_t b = pool.bytes_held();
+    for (auto &kv : programs) b += kv.second->pool.bytes_held();
+    return b;
+}
+
+int64_t round_half_up(double x) { return (int64_t)std::floor(x + 0.5); }
+
+const Key &find_key(const Ctx &c, uint32_t galois) {
+    if (galois == 0) {
+        TREQUIRE(c.relin.buf, TETRIS_ENOTFOUND, "relinearisation key not loaded");
+        return c.relin;
+    }
+    auto it = c.rot.find(galois);
+    TREQUIRE(it != c.rot.end(), TETRIS_ENOTFOUND, "rotation key for galois element " + std::to_string(galois) + " not loaded");
+    return it->second;
+}
+
+// ---------------------------------------------------------------------------
+// Program
+// ---------------------------------------------------------------------------
+Program::~Program() {
+    if (exec) cudaGraphExecDestroy(exec);
+    if (graph) cudaGraphDestroy(graph);
+}
+
+size_t Program::add_jobs(const void *p, size_t bytes) {
+    size_t off = (arena.size() + 255) & ~(size_t)255;
+    arena.resize(off + bytes);
+    std::memcpy(arena.data() + off, p, bytes);
+    return off;
+}
+
+void Program::finalize() {
+    if (arena.empty()) arena.resize(256);
+    arena_dev = pool.alloc((arena.size() + 7) / 8);
+    TCHECK_CUDA(cudaMemcpy(arena_dev->ptr, arena.data(), arena.size(), cudaMemcpyHostToDevice));
+}
+
+void Program::run(cudaStream_t s) {
+    const uint8_t *a = reinterpret_cast<const uint8_t *>(arena_dev->ptr);
+    for (auto &f : launches) f(s, a);
+    TCHECK_CUDA(cudaGetLastError());
+}
+
+void Program::run_graph(cudaStream_t s) {
+    if (!exec) {
+        cudaStream_t cs;
+        TCHECK_CUDA(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
+        TCHECK_CUDA(cudaStreamBeginCapture(cs, cudaStreamCaptureModeRelaxed));
+        const uint8_t *a = reinterpret_cast<const uint8_t *>(arena_dev->ptr);
+        for (auto &f : launches) f(cs, a);
+        cudaError_t e = cudaStreamEndCapture(cs, &graph);
+        cudaStreamDestroy(cs);
+        TCHECK_CUDA(e);
+        TCHECK_CUDA(cudaGraphInstantiate(&exec, graph, 0));
+    }
+    TCHECK_CUDA(cudaGraphLaunch(exec, s));
+}
+
+// ---------------------------------------------------------------------------
+// Recorder primitives
+// ---------------------------------------------------------------------------
+CtH Rec::new_ct(int B, int comps, int level) {
+    CtH c;
+    c.N = C.N;
+    c.B = B;
+    c.comps = comps;
+    c.level = level;
+    c.cstride = (size_t)(level + 1) * C.N;
+    c.bstride = c.cstride * comps;
+    c.buf = P.pool.alloc(c.bstride * B);
+    c.base = c.buf->ptr;
+    return c;
+}
+
+CtH Rec::view(const BufPtr &buf, u64 *base, int B, int comps, int level, size_t bstride, size_t cstride, double scale) {
+    CtH c;
+    c.N = C.N;
+    c.buf = buf;
+    c.base = base;
+    c.B = B;
+    c.comps = comps;
+    c.level = level;
+    c.bstride = bstride;
+    c.cstride = cstride;
+    c.scale = scale;
+    return c;
+}
+
+void Rec::ntt(bool inverse, const std::vector<NttJob> &jobs, int load_mode, int store_mode) {
+    if (jobs.empty()) return;
+    size_t off = P.add_jobs(jobs.data(), jobs.size() * sizeof(NttJob));
+    int n = (int)jobs.size(), logn = C.log_n;
+    NttTables t = C.nt;
+    P.launches.push_back([=](cudaStream_t s, const uint8_t *a) {
+        launch_ntt(inverse, logn, t, reinterpret_cast<const NttJob *>(a + off), n, load_mode, store_mode, s);
+    });
+    P.kernel_launches += ntt_launch_count(logn);
+}
+
+void Rec::ew(const std::vector<EwJob> &jobs) {
+    if (jobs.empty()) return;
+    size_t off = P.add_jobs(jobs.data(), jobs.size() * sizeof(EwJob));
+    int n = (int)jobs.size(), logn = C.log_n;
+    const ModInfo *m = C.nt.mods;
+    P.launches.push_back([=](cudaStream_t s, const uint8_t *a) {
+        launch_ew(reinterpret_cast<const EwJob *>(a + off), n, logn, m, s);
+    });
+    P.kernel_launches += 1;
+}
+
+void Rec::aut(const std::vector<AutJob> &jobs, uint32_t g) {
+    if (jobs.empty()) return;
+    size_t off = P.add_jobs(jobs.data(), jobs.size() * sizeof(AutJob));
+    int n = (int)jobs.size(), logn = C.log_n;
+    P.launches.push_back([=](cudaStream_t s, const uint8_t *a) {
+        launch_automorphism(reinterpret_cast<const AutJob *>(a + off), n, logn, g, s);
+    });
+    P.kernel_launches += 1;
+}
+
+void Rec::kip(const std::vector<KipJob> &jobs) {
+    if (jobs.empty()) return;
+    size_t off = P.add_jobs(jobs.data(), jobs.size() * sizeof(KipJob));
+    int n = (int)jobs.size(), logn = C.log_n;
+    const ModInfo *m = C.nt.mods;
+    P.launches.push_back([=](cudaStream_t s, const uint8_t *a) {
+        launch_keyip(reinterpret_cast<const KipJob *>(a + off), n, logn, m, s);
+    });
+    P.kernel_launches += 1;
+}
+
+void Rec::lin(const std::vector<LinJob> &jobs) {
+    if (jobs.empty()) return;
+    size_t off = P.add_jobs(jobs.data(), jobs.size() * sizeof(LinJob));
+    int n = (int)jobs.size(), logn = C.log_n;
+    const ModInfo *m = C.nt.mods;
+    P.launches.push_back([=](cudaStream_t s, const uint8_t *a) {
+        launch_lincomb(reinterpret_cast<const LinJob *>(a + off), n, logn, m, s);
+    });
+    P.kernel_launches += 1;
+}
+
+void Rec::red(const std::vector<RedJob> &jobs) {
+    if (jobs.empty()) return;
+    size_t off = P.add_jobs(jobs.data(), jobs.size() * sizeof(RedJob));
+    int n = (int)jobs.size(), logn = C.log_n;
+    const ModInfo *m = C.nt.mods;
+    P.launches.push_back([=](cudaStream_t s, const uint8_t *a) {
+        launch_reduce_i64(reinterpret_cast<const RedJob *>(a + off), n, logn, m, s);
+    });
+    P.kernel_launches += 1;
+}
+
+static EwJob ewj(EwOp op, uint32_t prime, u64 *dst, const u64 *a, const u64 *b = nullptr) {
+    EwJob j{};
+    j.op = op;
+    j.prime = prime;
+    j.dst = dst;
+    j.a = a;
+    j.b = b;
+    return j;
+}
+
+// ---------------------------------------------------------------------------
+// Ciphertext operations
+// ---------------------------------------------------------------------------
+void Rec::to_ntt(const CtH &a) {
+    std::vector<NttJob> jobs;
+    for (int b = 0; b < a.B; b++)
+        for (int c = 0; c < a.comps; c++)
+            for (int i = 0; i <= a.level; i++) {
+                NttJob j{};
+                j.src = j.dst = a.limb(b, c, i);
+                j.prime = i;
+                jobs.push_back(j);
+            }
+    ntt(false, jobs, LOAD_PLAIN, STORE_PLAIN);
+}
+
+CtH Rec::from_ntt(const CtH &a) {
+    CtH o = new_ct(a.B, a.comps, a.level);
+    o.scale = a.scale;
+    std::vector<NttJob> jobs;
+    for (int b = 0; b < a.B; b++)
+        for (int c = 0; c < a.comps; c++)
+            for (int i = 0; i <= a.level; i++) {
+                NttJob j{};
+                j.src = a.limb(b, c, i);
+                j.dst = o.limb(b, c, i);
+                j.prime = i;
+                jobs.push_back(j);
+            }
+    ntt(true, jobs, LOAD_PLAIN, STORE_PLAIN);
+    return o;
+}
+
+CtH Rec::add(const CtH &a, const CtH &b) {
+    TREQUIRE(a.level == b.level && a.comps == b.comps, TETRIS_EINVAL, "add: level/components differ");
+    TREQUIRE(a.B == b.B || a.B == 1 || b.B == 1, TETRIS_EINVAL, "add: batch sizes differ");
+    int B = std::max(a.B, b.B);
+    CtH o = new_ct(B, a.comps, a.level);
+    o.scale = a.scale;
+    std::vector<EwJob> jobs;
+    for (int k = 0; k < B; k++)
+        for (int c = 0; c < a.comps; c++)
+            for (int i = 0; i <= a.level; i++) jobs.push_back(ewj(EW_ADD, i, o.limb(k, c, i), a.limb(k, c, i), b.limb(k, c, i)));
+    ew(jobs);
+    return o;
+}
+
+CtH Rec::sub(const CtH &a, const CtH &b) {
+    TREQUIRE(a.level == b.level && a.comps == b.comps, TETRIS_EINVAL, "sub: level/components differ");
+    TREQUIRE(a.B == b.B || a.B == 1 || b.B == 1, TETRIS_EINVAL, "sub: batch sizes differ");
+    int B = std::max(a.B, b.B);
+    CtH o = new_ct(B, a.comps, a.level);
+    o.scale = a.scale;
+    std::vector<EwJob> jobs;
+    for (int k = 0; k < B; k++)
+        for (int c = 0; c < a.comps; c++)
+            for (int i = 0; i <= a.level; i++) jobs.push_back(ewj(EW_SUB, i, o.limb(k, c, i), a.limb(k, c, i), b.limb(k, c, i)));
+    ew(jobs);
+    return o;
+}
+
+static u64 signed_mod(int64_t c, u64 q) {
+    if (c >= 0) return (u64)c % q;
+    u64 r = (u64)(-(c + 1)) % q;
+    return q - 1 - r;
+}
+
+CtH Rec::mul_int(const CtH &a, int64_t cst) {
+    CtH o = new_ct(a.B, a.comps, a.level);
+    o.scale = a.scale;
+    std::vector<EwJob> jobs;
+    for (int k = 0; k < a.B; k++)
+        for (int c = 0; c < a.comps; c++)
+            for (int i = 0; i <= a.level; i++) {
+                EwJob j = ewj(EW_MUL_CONST, i, o.limb(k, c, i), a.limb(k, c, i));
+                j.k = signed_mod(cst, C.q[i]);
+                j.k_sh = h_shoup(j.k, C.q[i]);
+                jobs.push_back(j);
+            }
+    ew(jobs);
+    return o;
+}
+
+CtH Rec::add_int(const CtH &a, int64_t cst) {
+    CtH o = new_ct(a.B, a.comps, a.level);
+    o.scale = a.scale;
+    std::vector<EwJob> jobs;
+    for (int k = 0; k < a.B; k++)
+        for (int c = 0; c < a.comps; c++)
+            for (int i = 0; i <= a.level; i++) {
+                if (c == 0) {
+                    // the constant polynomial is the same constant at every evaluation point
+                    EwJob j = ewj(EW_ADD_CONST, i, o.limb(k, c, i), a.limb(k, c, i));
+                    j.k = signed_mod(cst, C.q[i]);
+                    jobs.push_back(j);
+                } else {
+                    jobs.push_back(ewj(EW_COPY, i, o.limb(k, c, i), a.limb(k, c, i)));
+                }
+            }
+    ew(jobs);
+    return o;
+}
+
+CtH Rec::mul_plain(const CtH &a, const u64 *pt, size_t pt_bstride) {
+    CtH o = new_ct(a.B, a.comps, a.level);
+    std::vector<EwJob> jobs;
+    for (int k = 0; k < a.B; k++)
+        for (int c = 0; c < a.comps; c++)
+            for (int i = 0; i <= a.level; i++)
+                jobs.push_back(ewj(EW_MUL, i, o.limb(k, c, i), a.limb(k, c, i), pt + k * pt_bstride + (size_t)i * C.N));
+    ew(jobs);
+    return o;
+}
+
+CtH Rec::tensor(const CtH &a, const CtH &b) {
+    TREQUIRE(a.level == b.level && a.comps == 2 && b.comps == 2, TETRIS_EINVAL, "tensor: operands differ");
+    TREQUIRE(a.B == b.B || a.B == 1 || b.B == 1, TETRIS_EINVAL, "tensor: batch sizes differ");
+    int B = std::max(a.B, b.B);
+    CtH o = new_ct(B, 3, a.level);
+    o.scale = a.scale * b.scale;
+    std::vector<EwJob> jobs;
+    for (int k = 0; k < B; k++)
+        for (int i = 0; i <= a.level; i++) {
+            EwJob j = ewj(EW_TENSOR, i, o.limb(k, 0, i), a.limb(k, 0, i), b.limb(k, 0, i));
+            j.a1 = a.limb(k, 1, i);
+            j.b1 = b.limb(k, 1, i);
+            j.d1 = o.limb(k, 1, i);
+            j.d2 = o.limb(k, 2, i);
+            jobs.push_back(j);
+        }
+    ew(jobs);
+    return o;
+}
+
+// Fast base conversion from the consecutive primes first..first+nsrc-1 to
+// dst_prime: x -> sum_s [(x_s + add_s) * (Qs/q_s)^-1]_{q_s} * (Qs/q_s mod q_dst).
+NttJob Rec::conv_job(uint32_t dst_prime, const u64 *src, uint32_t first, int nsrc, const u64 *adds) {
+    NttJob j{};
+    j.src = src;
+    j.src_stride = C.N;
+    j.nsrc = nsrc;
+    j.prime = dst_prime;
+    const u64 qd = C.all[dst_prime];
+    for (int s = 0; s < nsrc; s++) {
+        const u64 qs = C.all[first + s];
+        u64 hat_s = 1 % qs, hat_d = 1 % qd;
+        for (int r = 0; r < nsrc; r++)
+            if (r != s) {
+                hat_s = h_mulmod(hat_s, C.all[first + r] % qs, qs);
+                hat_d = h_mulmod(hat_d, C.all[first + r] % qd, qd);
+            }
+        j.src_prime[s] = first + s;
+        j.add_s[s] = adds ? adds[s] : 0;
+        j.c1[s] = h_invmod(hat_s, qs);
+        j.c1_sh[s] = h_shoup(j.c1[s], qs);
+        j.c2[s] = hat_d;
+    }
+    return j;
+}
+
+// Hybrid SwitchKey (Section 2.4.1) on B polynomials d(b, i), i <= l, NTT domain:
+// ModUp each CRT digit to Q_l P, inner product with the key, ModDown by P.
+// extra(b, c, i) (may return null) is added to component c of the result.
+CtH Rec::keyswitch(int B, int l, const std::function<const u64 *(int, int)> &d, const Key &key,
+                   const std::function<const u64 *(int, int, int)> &extra) {
+    const int nl = l + 1, K = C.K(), ntg = nl + K, alpha = C.alpha;
+    const int dnum = (nl + alpha - 1) / alpha;
+    const size_t N = C.N;
+    TREQUIRE(K >= 1 && K <= kMaxConvSrc && alpha <= kMaxConvSrc, TETRIS_EINVAL, "keyswitch: K or alpha too large");
+    TREQUIRE(dnum <= key.dnum && dnum <= 32, TETRIS_EINVAL, "keyswitch: key has too few digits");
+    const int nQP = C.nqp();
+    // 1. d -> coefficient domain
+    BufPtr dcoef = P.pool.alloc((size_t)B * nl * N);
+    {
+        std::vector<NttJob> jobs;
+        for (int b = 0; b < B; b++)
+            for (int i = 0; i < nl; i++) {
+                NttJob j{};
+                j.src = d(b, i);
+                j.dst = dcoef->ptr + ((size_t)b * nl + i) * N;
+                j.prime = i;
+                jobs.push_back(j);
+            }
+        ntt(true, jobs, LOAD_PLAIN, STORE_PLAIN);
+    }
+    // 2. ModUp: digit j -> every prime outside it, then NTT (conversion fused into the load)
+    BufPtr mu = P.pool.alloc((size_t)B * dnum * ntg * N);
+    auto mul = [&](int b, int j, int t) { return mu->ptr + (((size_t)b * dnum + j) * ntg + t) * N; };
+    {
+        std::vector<NttJob> jobs;
+        for (int j = 0; j < dnum; j++) {
+            const int lo = j * alpha, hi = std::min(nl, (j + 1) * alpha);
+            for (int t = 0; t < ntg; t++) {
+                if (t >= lo && t < hi) continue;
+                NttJob proto = conv_job(C.qp_prime(l, t), nullptr, lo, hi - lo, nullptr);
+                for (int b = 0; b < B; b++) {
+                    NttJob jb = proto;
+                    jb.src = dcoef->ptr + ((size_t)b * nl + lo) * N;
+                    jb.dst = mul(b, j, t);
+                    jobs.push_back(jb);
+                }
+            }
+        }
+        ntt(false, jobs, LOAD_CONV, STORE_PLAIN);
+    }
+    // 3. key inner product over Q_l P
+    BufPtr acc = P.pool.alloc((size_t)B * 2 * ntg * N);
+    auto accl = [&](int b, int c, int t) { return acc->ptr + (((size_t)b * 2 + c) * ntg + t) * N; };
+    {
+        std::vector<KipJob> jobs;
+        for (int b = 0; b < B; b++)
+            for (int t = 0; t < ntg; t++) {
+                KipJob k{};
+                const uint32_t gp = C.qp_prime(l, t);
+                for (int j = 0; j < dnum; j++) {
+                    const int lo = j * alpha, hi = std::min(nl, (j + 1) * alpha);
+                    k.src[j] = (t >= lo && t < hi) ? d(b, t) : mul(b, j, t);
+                    k.key0[j] = key.buf->ptr + (((size_t)j * 2 + 0) * nQP + gp) * N;
+                    k.key1[j] = key.buf->ptr + (((size_t)j * 2 + 1) * nQP + gp) * N;
+                }
+                k.acc0 = accl(b, 0, t);
+                k.acc1 = accl(b, 1, t);
+                k.prime = gp;
+                k.ndig = dnum;
+                jobs.push_back(k);
+            }
+        kip(jobs);
+    }
+    mu.reset();
+    dcoef.reset();
+    // 4. ModDown: special limbs to the coefficient domain
+    BufPtr pc = P.pool.alloc((size_t)B * 2 * K * N);
+    {
+        std::vector<NttJob> jobs;
+        for (int b = 0; b < B; b++)
+            for (int c = 0; c < 2; c++)
+                for (int k = 0; k < K; k++) {
+                    NttJob j{};
+                    j.src = accl(b, c, nl + k);
+                    j.dst = pc->ptr + (((size_t)b * 2 + c) * K + k) * N;
+                    j.prime = C.L() + 1 + k;
+                    jobs.push_back(j);
+                }
+        ntt(true, jobs, LOAD_PLAIN, STORE_PLAIN);
+    }
+    // 5. convert (c_P + floor(P/2)) to each q_i, NTT, and combine:
+    //    out_i = extra + (acc_i + [floor(P/2)]_{q_i} - conv) * P^-1
+    CtH out = new_ct(B, 2, l);
+    {
+        u64 adds[kMaxConvSrc];
+        for (int k = 0; k < K; k++) adds[k] = (C.p[k] - 1) / 2;  // floor(P/2) = (P-1)/2 is (p_k-1)/2 mod p_k
+        std::vector<NttJob> jobs;
+        for (int i = 0; i < nl; i++) {
+            const u64 qi = C.q[i];
+            u64 pm = 1 % qi;
+            for (int k = 0; k < K; k++) pm = h_mulmod(pm, C.p[k] % qi, qi);
+            const u64 half = h_mulmod((pm + qi - 1) % qi, h_invmod(2, qi), qi);
+            const u64 pinv = h_invmod(pm, qi);
+            NttJob proto = conv_job(i, nullptr, C.L() + 1, K, adds);
+            proto.addt = half;
+            proto.mul = pinv;
+            proto.mul_sh = h_shoup(pinv, qi);
+            for (int b = 0; b < B; b++)
+                for (int c = 0; c < 2; c++) {
+                    NttJob jb = proto;
+                    jb.src = pc->ptr + (((size_t)b * 2 + c) * K) * N;
+                    jb.base = accl(b, c, i);
+                    jb.extra = extra ? extra(b, c, i) : nullptr;
+                    jb.dst = out.limb(b, c, i);
+                    jobs.push_back(jb);
+                }
+        }
+        ntt(false, jobs, LOAD_CONV, STORE_COMBINE);
+    }
+    return out;
+}
+
+CtH Rec::relin(const CtH &t) {
+    TREQUIRE(t.comps == 3, TETRIS_EINVAL, "relin: needs a degree-2 ciphertext");
+    const Key &k = find_key(C, 0);
+    CtH o = keyswitch(t.B, t.level, [&](int b, int i) { return (const u64 *)t.limb(b, 2, i); }, k,
+                      [&](int b, int c, int i) { return (const u64 *)t.limb(b, c, i); });
+    o.scale = t.scale;
+    P.relins++;
+    return o;
+}
+
+// Rescale (Section 2.5): out_i = (a_i + [floor(q_l/2)]_{q_i} - [[a_l + floor(q_l/2)]_{q_l}]_{q_i}) * q_l^-1.
+CtH Rec::rescale(const CtH &a) {
+    const int l = a.level;
+    TREQUIRE(l >= 1, TETRIS_ELEVEL, "rescale at level 0");
+    const size_t N = C.N;
+    BufPtr tmp = P.pool.alloc((size_t)a.B * a.comps * N);
+    {
+        std::vector<NttJob> jobs;
+        for (int b = 0; b < a.B; b++)
+            for (int c = 0; c < a.comps; c++) {
+                NttJob j{};
+                j.src = a.limb(b, c, l);
+                j.dst = tmp->ptr + ((size_t)b * a.comps + c) * N;
+                j.prime = l;
+                jobs.push_back(j);
+            }
+        ntt(true, jobs, LOAD_PLAIN, STORE_PLAIN);
+    }
+    CtH o = new_ct(a.B, a.comps, l - 1);
+    o.scale = a.scale / (double)C.q[l];
+    const u64 ql = C.q[l], half = (ql - 1) / 2;
+    std::vector<NttJob> jobs;
+    for (int i = 0; i < l; i++) {
+        const u64 qi = C.q[i];
+        NttJob proto = conv_job(i, nullptr, l, 1, &half);
+        proto.addt = half % qi;
+        proto.mul = h_invmod(ql % qi, qi);
+        proto.mul_sh = h_shoup(proto.mul, qi);
+        for (int b = 0; b < a.B; b++)
+            for (int c = 0; c < a.comps; c++) {
+                NttJob jb = proto;
+                jb.src = tmp->ptr + ((size_t)b * a.comps + c) * N;
+                jb.base = a.limb(b, c, i);
+                jb.dst = o.limb(b, c, i);
+                jobs.push_back(jb);
+            }
+    }
+    ntt(false, jobs, LOAD_CONV, STORE_COMBINE);
+    P.rescales++;
+    return o;
+}
+
+CtH Rec::drop(const CtH &a, int level) {
+    TREQUIRE(level <= a.level && level >= 0, TETRIS_ELEVEL, "drop: bad level");
+    CtH o = a;
+    o.level = level;
+    return o;
+}
+
+CtH Rec::automorphism(const CtH &a, uint32_t g) {
+    TREQUIRE(g & 1, TETRIS_EINVAL, "galois element must be odd");
+    g &= (uint32_t)(2 * C.N - 1);
+    CtH o = new_ct(a.B, a.comps, a.level);
+    o.scale = a.scale;
+    std::vector<AutJob> jobs;
+    for (int b = 0; b < a.B; b++)
+        for (int c = 0; c < a.comps; c++)
+            for (int i = 0; i <= a.level; i++) jobs.push_back({a.limb(b, c, i), o.limb(b, c, i)});
+    aut(jobs, g);
+    return o;
+}
+
+// Automorphism then SwitchKey(phi(c1), swk_{phi(s)->s}) + (phi(c0), 0) (Appendix A.2).
+CtH Rec::rotate(const CtH &a, uint32_t g) {
+    TREQUIRE(a.comps == 2, TETRIS_EINVAL, "rotate: needs a degree-1 ciphertext");
+    const Key &k = find_key(C, g & (uint32_t)(2 * C.N - 1));
+    CtH t = automorphism(a, g);
+    CtH o = keyswitch(t.B, t.level, [&](int b, int i) { return (const u64 *)t.limb(b, 1, i); }, k,
+                      [&](int b, int c, int i) { return c == 0 ? (const u64 *)t.limb(b, 0, i) : (const u64 *)nullptr; });
+    o.scale = a.scale;
+    P.rotations++;
+    return o;
+}
+
+CtH Rec::sum_batch(const CtH &a) {
+    if (a.B == 1) return a;
+    // pairwise tree of additions over the batch entries
+    CtH cur = a;
+    int n = a.B;
+    while (n > 1) {
+        int h = n / 2;
+        CtH nx = new_ct((n + 1) / 2, a.comps, a.level);
+        std::vector<EwJob> jobs;
+        for (int k = 0; k < (n + 1) / 2; k++)
+            for (int c = 0; c < a.comps; c++)
+                for (int i = 0; i <= a.level; i++) {
+                    if (k < h)
+                        jobs.push_back(ewj(EW_ADD, i, nx.limb(k, c, i), cur.limb(k, c, i), cur.limb(k + h, c, i)));
+                    else
+                        jobs.push_back(ewj(EW_COPY, i, nx.limb(k, c, i), cur.limb(n - 1, c, i)));
+                }
+        ew(jobs);
+        cur = nx;
+        n = (n + 1) / 2;
+    }
+    cur.scale = a.scale;
+    return cur;
+}
+
+// Move to level lt with the standard scale S[lt], applying a public factor:
+// keep q_0..q_{lt+1}, multiply by floor(factor * S[lt] * q_{lt+1} / scale + 1/2), rescale.
+CtH Rec::adjust(const CtH &a, int lt, double factor) {
+    if (a.level == lt) {
+        TREQUIRE(factor == 1.0 && a.scale == C.S[lt], TETRIS_EINVAL, "adjust at the same level");
+        return a;
+    }
+    TREQUIRE(a.level > lt, TETRIS_ELEVEL, "input ciphertext level too low");
+    CtH v = drop(a, lt + 1);
+    const int64_t cst = round_half_up(((factor * C.S[lt]) * (double)C.q[lt + 1]) / a.scale);
+    CtH o = rescale(mul_int(v, cst));
+    o.scale = C.S[lt];
+    return o;
+}
+
+CtH Rec::mul(const CtH &a, const CtH &b) {
+    TREQUIRE(a.level == b.level, TETRIS_EINVAL, "mul: levels differ");
+    CtH o = rescale(relin(tensor(a, b)));
+    o.scale = C.S[a.level - 1];
+    return o;
+}
+
+}  // namespace tetris

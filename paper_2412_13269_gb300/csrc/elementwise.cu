@@ -1,0 +1,214 @@
+// Elementwise kernels over lists of limbs (each limb = N residues of one
+// prime).  All of them stream HBM: a grid-stride loop over (limb, position)
+// with 16-byte vector accesses where the operands allow it.
+#include "internal.h"
+
+namespace tetris {
+
+namespace {
+
+constexpr int kEwThreads = 256;
+
+int sm_count() {
+    static int sms = 0;
+    if (!sms) {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms <= 0) sms = 148;
+    }
+    return sms;
+}
+
+// grid-stride kernels: a few resident CTAs per SM
+int grid_for(size_t work_items) {
+    const int sms = sm_count();
+    size_t want = (work_items + kEwThreads - 1) / kEwThreads;
+    size_t cap = (size_t)sms * 8;
+    return (int)std::max<size_t>(1, std::min(want, cap));
+}
+
+// one thread handles two consecutive positions (a 16-byte pair)
+__global__ void __launch_bounds__(kEwThreads) ew_kernel(const EwJob *jobs, int njobs, int log_n, const ModInfo *mods) {
+    const size_t half = (size_t)1 << (log_n - 1);
+    const size_t total = half * njobs;
+    for (size_t it = blockIdx.x * (size_t)blockDim.x + threadIdx.x; it < total; it += (size_t)gridDim.x * blockDim.x) {
+        const int j = (int)(it >> (log_n - 1));
+        const size_t p = (it & (half - 1)) * 2;
+        const EwJob &J = jobs[j];
+        const ModInfo m = mods[J.prime];
+        const u64 q = m.q;
+        u64 r[2];
+        switch (J.op) {
+            case EW_ADD: {
+                ulonglong2 a = *reinterpret_cast<const ulonglong2 *>(J.a + p);
+                ulonglong2 b = *reinterpret_cast<const ulonglong2 *>(J.b + p);
+                r[0] = add_mod(a.x, b.x, q); r[1] = add_mod(a.y, b.y, q);
+                break;
+            }
+            case EW_SUB: {
+                ulonglong2 a = *reinterpret_cast<const ulonglong2 *>(J.a + p);
+                ulonglong2 b = *reinterpret_cast<const ulonglong2 *>(J.b + p);
+                r[0] = sub_mod(a.x, b.x, q); r[1] = sub_mod(a.y, b.y, q);
+                break;
+            }
+            case EW_MUL: {
+                ulonglong2 a = *reinterpret_cast<const ulonglong2 *>(J.a + p);
+                ulonglong2 b = *reinterpret_cast<const ulonglong2 *>(J.b + p);
+                r[0] = mul_mod(a.x, b.x, m); r[1] = mul_mod(a.y, b.y, m);
+                break;
+            }
+            case EW_MUL_CONST: {
+                ulonglong2 a = *reinterpret_cast<const ulonglong2 *>(J.a + p);
+                r[0] = shoup(a.x, J.k, J.k_sh, q); r[1] = shoup(a.y, J.k, J.k_sh, q);
+                break;
+            }
+            case EW_ADD_CONST: {
+                ulonglong2 a = *reinterpret_cast<const ulonglong2 *>(J.a + p);
+                r[0] = add_mod(a.x, J.k, q); r[1] = add_mod(a.y, J.k, q);
+                break;
+            }
+            case EW_NEG: {
+                ulonglong2 a = *reinterpret_cast<const ulonglong2 *>(J.a + p);
+                r[0] = a.x ? q - a.x : 0; r[1] = a.y ? q - a.y : 0;
+                break;
+            }
+            case EW_COPY: {
+                ulonglong2 a = *reinterpret_cast<const ulonglong2 *>(J.a + p);
+                r[0] = a.x; r[1] = a.y;
+                break;
+            }
+            case EW_FMA: {
+                ulonglong2 a = *reinterpret_cast<const ulonglong2 *>(J.a + p);
+                ulonglong2 b = *reinterpret_cast<const ulonglong2 *>(J.b + p);
+                ulonglong2 c = *reinterpret_cast<const ulonglong2 *>(J.c + p);
+                r[0] = add_mod(mul_mod(a.x, b.x, m), c.x, q); r[1] = add_mod(mul_mod(a.y, b.y, m), c.y, q);
+                break;
+            }
+            case EW_ADD_MUL_CONST: {  // b + k * a
+                ulonglong2 a = *reinterpret_cast<const ulonglong2 *>(J.a + p);
+                ulonglong2 b = *reinterpret_cast<const ulonglong2 *>(J.b + p);
+                r[0] = add_mod(b.x, shoup(a.x, J.k, J.k_sh, q), q);
+                r[1] = add_mod(b.y, shoup(a.y, J.k, J.k_sh, q), q);
+                break;
+            }
+            case EW_TENSOR: {
+                ulonglong2 a0 = *reinterpret_cast<const ulonglong2 *>(J.a + p);
+                ulonglong2 a1 = *reinterpret_cast<const ulonglong2 *>(J.a1 + p);
+                ulonglong2 b0 = *reinterpret_cast<const ulonglong2 *>(J.b + p);
+                ulonglong2 b1 = *reinterpret_cast<const ulonglong2 *>(J.b1 + p);
+                ulonglong2 d0, d1, d2;
+                d0.x = mul_mod(a0.x, b0.x, m); d0.y = mul_mod(a0.y, b0.y, m);
+                d2.x = mul_mod(a1.x, b1.x, m); d2.y = mul_mod(a1.y, b1.y, m);
+                {
+                    Acc128 c = {0, 0};
+                    acc_mad(c, a0.x, b1.x); acc_mad(c, a1.x, b0.x);
+                    d1.x = reduce128(c.hi, c.lo, m);
+                    Acc128 e = {0, 0};
+                    acc_mad(e, a0.y, b1.y); acc_mad(e, a1.y, b0.y);
+                    d1.y = reduce128(e.hi, e.lo, m);
+                }
+                *reinterpret_cast<ulonglong2 *>(J.dst + p) = d0;
+                *reinterpret_cast<ulonglong2 *>(J.d1 + p) = d1;
+                *reinterpret_cast<ulonglong2 *>(J.d2 + p) = d2;
+                continue;
+            }
+            default:
+                r[0] = r[1] = 0;
+        }
+        *reinterpret_cast<ulonglong2 *>(J.dst + p) = make_ulonglong2(r[0], r[1]);
+    }
+}
+
+__global__ void __launch_bounds__(kEwThreads) aut_kernel(const AutJob *jobs, int njobs, int log_n, uint32_t g) {
+    const size_t n = (size_t)1 << log_n;
+    const size_t total = n * njobs;
+    const uint32_t mask2n = (uint32_t)(2 * n - 1);
+    for (size_t it = blockIdx.x * (size_t)blockDim.x + threadIdx.x; it < total; it += (size_t)gridDim.x * blockDim.x) {
+        const int j = (int)(it >> log_n);
+        const uint32_t k = (uint32_t)(it & (n - 1));
+        // index k holds A(psi^(2 brv(k) + 1)); the image at k is A(psi^(g (2 brv(k) + 1)))
+        const uint32_t e = 2 * (__brev(k) >> (32 - log_n)) + 1;
+        const uint32_t ge = (uint32_t)(((uint64_t)g * e) & mask2n);
+        const uint32_t src = __brev((ge - 1) >> 1) >> (32 - log_n);
+        jobs[j].dst[k] = jobs[j].src[src];
+    }
+}
+
+__global__ void __launch_bounds__(kEwThreads) keyip_kernel(const KipJob *jobs, int njobs, int log_n, const ModInfo *mods) {
+    const size_t n = (size_t)1 << log_n;
+    const size_t total = n * njobs;
+    for (size_t it = blockIdx.x * (size_t)blockDim.x + threadIdx.x; it < total; it += (size_t)gridDim.x * blockDim.x) {
+        const int j = (int)(it >> log_n);
+        const size_t p = it & (n - 1);
+        const KipJob &J = jobs[j];
+        const ModInfo m = mods[J.prime];
+        Acc128 a0 = {0, 0}, a1 = {0, 0};
+        for (uint32_t d = 0; d < J.ndig; d++) {
+            const u64 x = J.src[d][p];
+            acc_mad(a0, x, __ldg(J.key0[d] + p));
+            acc_mad(a1, x, __ldg(J.key1[d] + p));
+        }
+        J.acc0[p] = reduce128(a0.hi, a0.lo, m);
+        J.acc1[p] = reduce128(a1.hi, a1.lo, m);
+    }
+}
+
+__global__ void __launch_bounds__(kEwThreads) lincomb_kernel(const LinJob *jobs, int njobs, int log_n, const ModInfo *mods) {
+    const size_t n = (size_t)1 << log_n;
+    const size_t total = n * njobs;
+    for (size_t it = blockIdx.x * (size_t)blockDim.x + threadIdx.x; it < total; it += (size_t)gridDim.x * blockDim.x) {
+        const int j = (int)(it >> log_n);
+        const size_t p = it & (n - 1);
+        const LinJob &J = jobs[j];
+        const ModInfo m = mods[J.prime];
+        Acc128 a0 = {0, 0}, a1 = {0, 0};
+        for (uint32_t a = 0; a < J.nattr; a++) {
+            const u64 pt = J.pt[a * J.pt_stride + p];
+            acc_mad(a0, pt, J.w0[a * J.w_stride + p]);
+            acc_mad(a1, pt, J.w1[a * J.w_stride + p]);
+        }
+        J.d0[p] = reduce128(a0.hi, a0.lo, m);
+        J.d1[p] = reduce128(a1.hi, a1.lo, m);
+    }
+}
+
+__global__ void __launch_bounds__(kEwThreads) reduce_i64_kernel(const RedJob *jobs, int njobs, int log_n, const ModInfo *mods) {
+    const size_t n = (size_t)1 << log_n;
+    const size_t total = n * njobs;
+    for (size_t it = blockIdx.x * (size_t)blockDim.x + threadIdx.x; it < total; it += (size_t)gridDim.x * blockDim.x) {
+        const int j = (int)(it >> log_n);
+        const size_t p = it & (n - 1);
+        const RedJob &J = jobs[j];
+        const u64 q = mods[J.prime].q;
+        const int64_t x = J.src[p];
+        u64 v;
+        if (x >= 0) v = (u64)x % q;
+        else v = q - 1 - ((u64)(-(x + 1)) % q);
+        J.dst[p] = v;
+    }
+}
+
+}  // namespace
+
+void launch_ew(const EwJob *jobs, int njobs, int log_n, const ModInfo *mods, cudaStream_t s) {
+    if (njobs <= 0) return;
+    ew_kernel<<<grid_for(((size_t)njobs << log_n) / 2), kEwThreads, 0, s>>>(jobs, njobs, log_n, mods);
+}
+void launch_automorphism(const AutJob *jobs, int njobs, int log_n, uint32_t galois, cudaStream_t s) {
+    if (njobs <= 0) return;
+    aut_kernel<<<grid_for((size_t)njobs << log_n), kEwThreads, 0, s>>>(jobs, njobs, log_n, galois);
+}
+void launch_keyip(const KipJob *jobs, int njobs, int log_n, const ModInfo *mods, cudaStream_t s) {
+    if (njobs <= 0) return;
+    keyip_kernel<<<grid_for((size_t)njobs << log_n), kEwThreads, 0, s>>>(jobs, njobs, log_n, mods);
+}
+void launch_lincomb(const LinJob *jobs, int njobs, int log_n, const ModInfo *mods, cudaStream_t s) {
+    if (njobs <= 0) return;
+    lincomb_kernel<<<grid_for((size_t)njobs << log_n), kEwThreads, 0, s>>>(jobs, njobs, log_n, mods);
+}
+void launch_reduce_i64(const RedJob *jobs, int njobs, int log_n, const ModInfo *mods, cudaStream_t s) {
+    if (njobs <= 0) return;
+    reduce_i64_kernel<<<grid_for((size_t)njobs << log_n), kEwThreads, 0, s>>>(jobs, njobs, log_n, mods);
+}
+
+}  // namespace tetris

@@ -1,0 +1,192 @@
+// Internal declarations shared by the library's translation units.
+#pragma once
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <functional>
+#include <map>
+#include <memory>
+#include <stdexcept>
+#include <string>
+#include <vector>
+
+#include "modarith.cuh"
+
+namespace tetris {
+
+constexpr int kMaxPrimes = 64;
+constexpr int kMaxConvSrc = 4;   // primes per digit (alpha) and special primes (K) at most
+
+// ---------------------------------------------------------------------------
+// Errors: thrown inside the library, converted to a status at the C ABI.
+// ---------------------------------------------------------------------------
+struct Error : std::runtime_error {
+    int code;
+    Error(int c, const std::string &m) : std::runtime_error(m), code(c) {}
+};
+void set_last_error(const std::string &msg);
+#define TCHECK_CUDA(x)                                                                        \
+    do {                                                                                      \
+        cudaError_t e_ = (x);                                                                 \
+        if (e_ != cudaSuccess)                                                                \
+            throw ::tetris::Error(-3, std::string(#x) + ": " + cudaGetErrorString(e_));        \
+    } while (0)
+#define TREQUIRE(cond, code, msg)                              \
+    do {                                                       \
+        if (!(cond)) throw ::tetris::Error((code), (msg));     \
+    } while (0)
+
+// ---------------------------------------------------------------------------
+// Host modular arithmetic (hostmath.cu)
+// ---------------------------------------------------------------------------
+u64 h_mulmod(u64 a, u64 b, u64 q);
+u64 h_powmod(u64 a, u64 e, u64 q);
+u64 h_invmod(u64 a, u64 q);
+u64 h_shoup(u64 w, u64 q);  // floor(w * 2^64 / q)
+bool h_is_prime(u64 n);
+u64 h_primitive_2n_root(u64 q, u64 n);
+std::vector<u64> h_gen_primes(int bits, int count, int cong_log2, const std::vector<u64> &exclude);
+uint32_t bitrev(uint32_t x, int bits);
+
+// ---------------------------------------------------------------------------
+// Device memory: buffers owned through shared_ptr; a size-keyed free list
+// lets a recorded program reuse memory after a buffer's last use.
+// ---------------------------------------------------------------------------
+struct DevBuf {
+    u64 *ptr = nullptr;
+    size_t words = 0;
+};
+using BufPtr = std::shared_ptr<DevBuf>;
+
+class Pool {
+  public:
+    ~Pool();
+    BufPtr alloc(size_t words);
+    size_t bytes_held() const { return held_; }
+    void trim();
+
+  private:
+    std::multimap<size_t, u64 *> free_;
+    std::vector<std::pair<u64 *, size_t>> all_;
+    size_t held_ = 0;
+    std::shared_ptr<int> alive_ = std::make_shared<int>(1);
+};
+
+// ---------------------------------------------------------------------------
+// Kernel job descriptors
+// ---------------------------------------------------------------------------
+enum LoadMode { LOAD_PLAIN = 0, LOAD_CONV = 1, LOAD_INT64 = 2 };
+enum StoreMode { STORE_PLAIN = 0, STORE_COMBINE = 1 };
+
+// One limb transform.  LOAD_CONV computes, per coefficient,
+//   sum_s [ (src_s + add_s) * c1_s ]_{q_s} * c2_s  mod q_dst
+// from nsrc source limbs src + s*src_stride (coefficient domain).
+// STORE_COMBINE writes (extra ? extra : 0) + (base + addt - x) * mul mod q_dst.
+struct NttJob {
+    const u64 *src;
+    u64 *dst;
+    const u64 *base;
+    const u64 *extra;
+    uint32_t prime;
+    uint32_t nsrc;
+    uint64_t src_stride;
+    uint32_t src_prime[kMaxConvSrc];
+    u64 add_s[kMaxConvSrc];
+    u64 c1[kMaxConvSrc], c1_sh[kMaxConvSrc];
+    u64 c2[kMaxConvSrc];
+    u64 addt, mul, mul_sh;
+};
+
+struct NttTables {
+    const u64 *tw;      // [nprimes][N] psi^brv(k)
+    const u64 *tw_sh;
+    const u64 *itw;     // [nprimes][N] psi^-brv(k)
+    const u64 *itw_sh;
+    const ModInfo *mods;
+};
+
+// launchers (ntt.cu)
+void launch_ntt(bool inverse, int log_n, const NttTables &t, const NttJob *jobs_dev, int njobs, int load_mode,
+                int store_mode, cudaStream_t s);
+int ntt_launch_count(int log_n);
+
+// ---------------------------------------------------------------------------
+// Elementwise kernels (elementwise.cu).  A "limb list" kernel walks njobs
+// limbs of N words; per-limb pointers and constants come from a job table.
+// ---------------------------------------------------------------------------
+enum EwOp {
+    EW_ADD = 0,       // dst = a + b
+    EW_SUB = 1,       // dst = a - b
+    EW_MUL = 2,       // dst = a * b (variable)
+    EW_MUL_CONST = 3, // dst = a * k (k, k_sh per limb)
+    EW_ADD_CONST = 4, // dst = a + k
+    EW_NEG = 5,       // dst = -a
+    EW_COPY = 6,      // dst = a
+    EW_FMA = 7,       // dst = a * b + c
+    EW_TENSOR = 8,    // a0,a1,b0,b1 -> d0,d1,d2 (pointers a,b,c,d with strides)
+    EW_ADD_MUL_CONST = 9  // dst = b + k * a  (used by key generation)
+};
+struct EwJob {
+    const u64 *a, *b, *c;
+    u64 *dst;
+    uint32_t prime;
+    uint32_t op;
+    u64 k, k_sh;
+    // tensor: second components
+    const u64 *a1, *b1;
+    u64 *d1, *d2;
+};
+void launch_ew(const EwJob *jobs_dev, int njobs, int log_n, const ModInfo *mods, cudaStream_t s);
+
+// automorphism in the NTT domain: dst[k] = src[perm_g(k)]
+struct AutJob {
+    const u64 *src;
+    u64 *dst;
+};
+void launch_automorphism(const AutJob *jobs_dev, int njobs, int log_n, uint32_t galois, cudaStream_t s);
+
+// key inner product: for each (batch, target limb t):
+//   acc_c[t] = sum_j src_j[t] * key_j[c][t]  (c = 0, 1)
+struct KipJob {
+    const u64 *src[32];   // per digit source limb (NTT domain)
+    const u64 *key0[32];  // per digit key limb for component 0
+    const u64 *key1[32];
+    u64 *acc0, *acc1;
+    uint32_t prime;
+    uint32_t ndig;
+};
+void launch_keyip(const KipJob *jobs_dev, int njobs, int log_n, const ModInfo *mods, cudaStream_t s);
+
+// linear combination: dst_c[limb] = sum_j pt_j[limb] * w_j[c][limb], c = 0,1
+struct LinJob {
+    const u64 *pt;      // first attribute's plaintext limb
+    uint64_t pt_stride; // words between attributes
+    const u64 *w0, *w1; // first attribute's ciphertext limbs
+    uint64_t w_stride;  // words between attributes
+    u64 *d0, *d1;
+    uint32_t prime;
+    uint32_t nattr;
+};
+void launch_lincomb(const LinJob *jobs_dev, int njobs, int log_n, const ModInfo *mods, cudaStream_t s);
+
+// int64 coefficients -> residues modulo a prime
+struct RedJob {
+    const int64_t *src;
+    u64 *dst;
+    uint32_t prime;
+};
+void launch_reduce_i64(const RedJob *jobs_dev, int njobs, int log_n, const ModInfo *mods, cudaStream_t s);
+
+// ---------------------------------------------------------------------------
+// FP64 encoder (encode.cu)
+// ---------------------------------------------------------------------------
+// slots [batch][n_slots] (real) -> m [batch][N] real coefficients
+void encode_real_batch(const double *slots, double *m, int batch, int log_n, const double *twid_dev,
+                       double *work, cudaStream_t s);
+// database columns: vals u8 [records][attrs] -> slots [blocks][attrs][n_slots]
+void db_slots(const uint8_t *vals, uint64_t records, int attrs, int blocks, int log_n, double *slots,
+              cudaStream_t s);
+// m [batch][N] -> int64 floor(scale * m + 1/2)
+void round_scale(const double *m, int64_t *out, size_t count, double scale, cudaStream_t s);
+
+}  // namespace tetris

@@ -1,0 +1,153 @@
+// Context, recorded programs and the ciphertext-level recorder.
+//
+// Work is recorded once as a list of kernel launches whose per-limb job
+// tables live in one device arena; the list is then replayed on a stream (or
+// captured once into a CUDA graph and replayed).  Buffers are shared_ptrs
+// into a pool: when the recorder drops the last handle, the memory returns to
+// the pool's free list and later operations of the same program reuse it
+// (launches run in program order on one stream, so reuse after the last use
+// is safe).
+#pragma once
+#include <array>
+#include <cmath>
+#include <mutex>
+
+#include "internal.h"
+#include "../../include/tetris.h"
+
+namespace tetris {
+
+struct Key {
+    BufPtr buf;  // NTT domain [dnum][2][nQP][N]
+    int dnum = 0;
+};
+
+struct Database {
+    uint64_t records = 0;
+    int attrs = 0;
+    int blocks = 0;
+    BufPtr pts;        // NTT domain [blocks][attrs][n_q][N]
+    BufPtr mask_real;  // double[N] on device (bytes in words), or null
+};
+
+struct Program;
+
+struct Ctx {
+    int device = 0;
+    int log_n = 0;
+    size_t N = 0;
+    std::vector<u64> q, p, all, psi;
+    double scale = 0;
+    std::vector<double> S;  // standard scales
+    double pt_scale = 0;
+    std::vector<ModInfo> mods_host;
+    BufPtr tables;          // tw, tw_sh, itw, itw_sh, mods, encoder tables
+    NttTables nt{};
+    const double *enc_tw = nullptr;
+    Pool pool;
+    int alpha = 0;
+    Key relin;
+    std::map<uint32_t, Key> rot;
+    std::map<uint32_t, Database> dbs;
+    uint32_t next_db = 1;
+    cudaStream_t stream = nullptr;
+    int blocks_per_launch = 0;
+    int use_graph = 1;
+    std::map<std::string, std::unique_ptr<Program>> programs;
+
+    int L() const { return (int)q.size() - 1; }
+    int K() const { return (int)p.size(); }
+    int nqp() const { return (int)all.size(); }
+    // prime index of limb t of a buffer over q_0..q_l, p_0..p_{K-1}
+    uint32_t qp_prime(int l, int t) const { return t <= l ? (uint32_t)t : (uint32_t)(L() + 1 + (t - l - 1)); }
+    size_t bytes_held() const;
+};
+
+struct CtH {
+    BufPtr buf;
+    u64 *base = nullptr;
+    int level = -1, comps = 0, B = 0;
+    size_t bstride = 0, cstride = 0;
+    double scale = 0;
+    size_t N = 0;
+    u64 *limb(int b, int c, int i) const {
+        return base + (size_t)(B == 1 ? 0 : b) * bstride + (size_t)c * cstride + (size_t)i * N;
+    }
+};
+
+struct Program {
+    Ctx *ctx = nullptr;
+    Pool pool;
+    std::vector<uint8_t> arena;
+    BufPtr arena_dev;
+    std::vector<std::function<void(cudaStream_t, const uint8_t *)>> launches;
+    int kernel_launches = 0;
+    std::vector<BufPtr> hold;
+    // query programs: input staging slots (device pointer, words) and output
+    std::vector<std::pair<u64 *, size_t>> in_slots;
+    BufPtr out_buf;
+    u64 *out_base = nullptr;
+    size_t out_words = 0;
+    int out_level = 0, out_comps = 0;
+    double out_scale = 0;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    // counters
+    int relins = 0, rescales = 0, rotations = 0;
+
+    ~Program();
+    size_t add_jobs(const void *p, size_t bytes);
+    void finalize();
+    void run(cudaStream_t s);
+    void run_graph(cudaStream_t s);
+};
+
+class Rec {
+  public:
+    Rec(Ctx &c, Program &p) : C(c), P(p) {}
+    Ctx &C;
+    Program &P;
+
+    CtH new_ct(int B, int comps, int level);
+    CtH view(const BufPtr &buf, u64 *base, int B, int comps, int level, size_t bstride, size_t cstride, double scale);
+
+    void ntt(bool inverse, const std::vector<NttJob> &jobs, int load_mode, int store_mode);
+    void ew(const std::vector<EwJob> &jobs);
+    void aut(const std::vector<AutJob> &jobs, uint32_t g);
+    void kip(const std::vector<KipJob> &jobs);
+    void lin(const std::vector<LinJob> &jobs);
+    void red(const std::vector<RedJob> &jobs);
+
+    // ciphertext operations (NTT domain)
+    void to_ntt(const CtH &a);           // in place, coefficient -> NTT
+    CtH from_ntt(const CtH &a);          // new buffer, NTT -> coefficient
+    CtH add(const CtH &a, const CtH &b);
+    CtH sub(const CtH &a, const CtH &b);
+    CtH mul_int(const CtH &a, int64_t c);
+    CtH add_int(const CtH &a, int64_t c);
+    CtH mul_plain(const CtH &a, const u64 *pt_limb0, size_t pt_bstride);
+    CtH tensor(const CtH &a, const CtH &b);
+    CtH keyswitch(int B, int l, const std::function<const u64 *(int, int)> &d, const Key &key,
+                  const std::function<const u64 *(int, int, int)> &extra);
+    CtH relin(const CtH &t3);
+    CtH rescale(const CtH &a);
+    CtH drop(const CtH &a, int level);
+    CtH automorphism(const CtH &a, uint32_t g);
+    CtH rotate(const CtH &a, uint32_t g);
+    CtH sum_batch(const CtH &a);
+    CtH adjust(const CtH &a, int lt, double factor);
+    CtH mul(const CtH &a, const CtH &b);
+
+  private:
+    NttJob conv_job(uint32_t dst_prime, const u64 *src, uint32_t first_src_prime, int nsrc, const u64 *adds);
+};
+
+int64_t round_half_up(double x);
+const Key &find_key(const Ctx &c, uint32_t galois);
+
+// query.cu
+void evaluate_query(Ctx &C, uint32_t db, const tetris_query *q, tetris_ct_out *out, cudaStream_t s, bool device);
+void plan_info(Ctx &C, uint32_t db, uint32_t degree, uint32_t stages, tetris_plan_info *out);
+void drop_programs_of_db(Ctx &C, uint32_t db);
+
+}  // namespace tetris

@@ -1,0 +1,385 @@
+// Query planner and executor: the server side of the paper's Algorithm 2
+// for the local threshold and InnerSum, with the attribute-selection product
+// (Section 3.3), a private polynomial with encrypted coefficients, the
+// encrypted threshold (Section 4.3.2), a composite odd sign polynomial mapped
+// to step(x) = (sign(x) + 1)/2, the block sum and InnerSum (Appendix A.1.2
+// rotations).
+//
+// Scale discipline: a ciphertext at level l carries S[l] (S[L] = Delta,
+// S[l-1] = S[l]^2 / q_l), so a product of two level-l ciphertexts rescales
+// exactly onto S[l-1].  adjust() moves a ciphertext to a lower level t with
+// scale S[t] and applies a public factor a in one rescale: keep q_0..q_{t+1},
+// multiply by floor(a * S[t] * q_{t+1} / scale + 1/2), rescale by q_{t+1}.
+//
+// A block group of nb blocks is evaluated with every launch covering all nb
+// blocks (nb = all blocks: batched form; nb = 1: plain per-ciphertext form).
+#include <cstring>
+#include <sstream>
+
+#include "program.h"
+
+namespace tetris {
+
+struct QPlan {
+    int l_lin, l_d, l_y, l_u, l_out;
+    bool ragged;
+    double mask_scale;
+    std::vector<std::array<double, 4>> co;
+    double step_const;
+};
+
+static int ceil_log2(int k) {
+    int r = 0;
+    while ((1 << r) < k) r++;
+    return r;
+}
+
+QPlan make_plan(const Ctx &C, uint64_t records, int degree, const std::vector<std::array<double, 4>> &stages) {
+    TREQUIRE(degree >= 1 && !stages.empty() && records >= 1, TETRIS_EINVAL, "empty query");
+    QPlan p;
+    const int L = C.L();
+    p.l_lin = L - 1;
+    p.l_d = p.l_lin - ceil_log2(degree);
+    p.l_y = p.l_d - 1;
+    p.l_u = p.l_y - 3 * (int)stages.size();
+    const uint64_t n = C.N / 2;
+    p.ragged = records % n != 0;
+    p.l_out = p.ragged ? p.l_u - 1 : p.l_u;
+    TREQUIRE(p.l_out >= 1, TETRIS_ELEVEL, "circuit needs more levels: it would end at level " + std::to_string(p.l_out));
+    const double R = (double)records;
+    const size_t ns = stages.size();
+    for (size_t s = 0; s < ns; s++) {
+        std::array<double, 4> c = stages[s];
+        if (s == 0)  // z = (y - t)/2 folded into the first stage
+            for (int k = 0; k < 4; k++) c[k] = c[k] * std::ldexp(1.0, -(2 * k + 1));
+        if (s == ns - 1)  // step = (p + 1)/2, normalised by 1/records
+            for (int k = 0; k < 4; k++) c[k] = c[k] / (2.0 * R);
+        p.co.push_back(c);
+    }
+    p.step_const = 1.0 / (2.0 * R);
+    p.mask_scale = p.ragged ? (C.S[p.l_u - 1] * (double)C.q[p.l_u]) / C.S[p.l_u] : 0.0;
+    return p;
+}
+
+// p(u) = a0 u + a1 u^3 + a2 u^5 + a3 u^7 in depth 3:
+//   a0 u + (a1 u) u^2 + ((a3 u) u^2 + a2 u) u^4
+static CtH sign_stage(Rec &R, const CtH &u, const std::array<double, 4> &co) {
+    const int l = u.level;
+    CtH u2 = R.mul(u, u);
+    CtH u4 = R.mul(u2, u2);
+    CtH b1 = R.adjust(u, l - 1, co[1]);
+    CtH b3 = R.adjust(u, l - 1, co[3]);
+    CtH t3 = R.mul(b1, u2);
+    CtH t7 = R.mul(b3, u2);
+    CtH inner = R.add(t7, R.adjust(u, l - 2, co[2]));
+    CtH t57 = R.mul(inner, u4);
+    CtH t1 = R.adjust(u, l - 3, co[0]);
+    return R.add(R.add(t1, R.adjust(t3, l - 3, 1.0)), t57);
+}
+
+static CtH eval_blocks(Rec &R, const Database &db, const QPlan &pl, int b0, int nb, const u64 *wbase,
+                       const std::vector<CtH> &ck, const CtH &tadj, int degree) {
+    Ctx &C = R.C;
+    const int L = C.L();
+    const size_t N = C.N, nq = C.q.size();
+    // x = sum_j pt_j * Enc(w_j), then rescale
+    CtH x0 = R.new_ct(nb, 2, L);
+    {
+        std::vector<LinJob> jobs;
+        for (int b = 0; b < nb; b++)
+            for (int i = 0; i <= L; i++) {
+                LinJob j{};
+                j.pt = db.pts->ptr + (((size_t)(b0 + b) * db.attrs) * nq + i) * N;
+                j.pt_stride = nq * N;
+                j.w0 = wbase + (size_t)i * N;
+                j.w1 = wbase + (size_t)(L + 1) * N + (size_t)i * N;
+                j.w_stride = 2 * (size_t)(L + 1) * N;
+                j.d0 = x0.limb(b, 0, i);
+                j.d1 = x0.limb(b, 1, i);
+                j.prime = i;
+                j.nattr = db.attrs;
+                jobs.push_back(j);
+            }
+        R.lin(jobs);
+    }
+    CtH x = R.rescale(x0);
+    x.scale = C.S[L - 1];
+    x0 = CtH();
+    // powers x^k
+    std::map<int, CtH> Pw;
+    std::map<std::pair<int, int>, CtH> cache;
+    Pw[1] = x;
+    auto lvl = [&](int k, int lt) -> CtH {
+        if (Pw[k].level == lt) return Pw[k];
+        auto key = std::make_pair(k, lt);
+        auto it = cache.find(key);
+        if (it != cache.end()) return it->second;
+        CtH a = R.adjust(Pw[k], lt, 1.0);
+        cache[key] = a;
+        return a;
+    };
+    for (int k = 2; k <= degree; k++) {
+        int a = 1;
+        while (a * 2 <= k) a *= 2;
+        if (a == k) Pw[k] = R.mul(Pw[k / 2], Pw[k / 2]);
+        else Pw[k] = R.mul(Pw[a], lvl(k - a, Pw[a].level));
+    }
+    // y = sum_k c_k x^k with one relinearisation
+    CtH T;
+    for (int k = 1; k <= degree; k++) {
+        CtH tk = R.tensor(ck[k], lvl(k, pl.l_d));
+        T = (k == 1) ? tk : R.add(T, tk);
+    }
+    Pw.clear();
+    cache.clear();
+    CtH y = R.rescale(R.relin(T));
+    T = CtH();
+    y.scale = C.S[pl.l_y];
+    y = R.add(y, ck[0]);
+    CtH u = R.sub(y, tadj);
+    for (auto &co : pl.co) u = sign_stage(R, u, co);
+    return R.add_int(u, round_half_up(pl.step_const * C.S[u.level]));
+}
+
+struct QuerySpec {
+    int attrs = 0, degree = 0;
+    std::vector<int> c_level;
+    std::vector<double> c_scale;
+    int t_level = 0;
+    double t_scale = 0;
+    std::vector<std::array<double, 4>> stages;
+    int bpl = 0;
+    std::string key(uint32_t db) const {
+        std::ostringstream o;
+        o << "q" << db << ":" << attrs << ":" << degree << ":" << bpl << ":" << t_level << ":";
+        auto bits = [&](double v) {
+            uint64_t b;
+            std::memcpy(&b, &v, 8);
+            o << std::hex << b << std::dec << ",";
+        };
+        bits(t_scale);
+        for (size_t i = 0; i < c_level.size(); i++) {
+            o << c_level[i] << "/";
+            bits(c_scale[i]);
+        }
+        for (auto &s : stages)
+            for (double v : s) bits(v);
+        return o.str();
+    }
+};
+
+static std::unique_ptr<Program> record_query(Ctx &C, const Database &db, const QuerySpec &q) {
+    auto P = std::make_unique<Program>();
+    P->ctx = &C;
+    Rec R(C, *P);
+    const QPlan pl = make_plan(C, db.records, q.degree, q.stages);
+    const int L = C.L();
+    const size_t N = C.N;
+    // staging buffers for the inputs (coefficient domain on arrival, NTT in place)
+    const size_t wwords = (size_t)2 * (L + 1) * N;
+    BufPtr wbuf = P->pool.alloc(wwords * q.attrs);
+    P->hold.push_back(wbuf);
+    for (int j = 0; j < q.attrs; j++) P->in_slots.push_back({wbuf->ptr + j * wwords, wwords});
+    std::vector<CtH> cin;
+    for (int k = 0; k <= q.degree; k++) {
+        CtH c = R.new_ct(1, 2, q.c_level[k]);
+        c.scale = q.c_scale[k];
+        P->hold.push_back(c.buf);
+        P->in_slots.push_back({c.base, c.bstride});
+        cin.push_back(c);
+    }
+    CtH tin = R.new_ct(1, 2, q.t_level);
+    tin.scale = q.t_scale;
+    P->hold.push_back(tin.buf);
+    P->in_slots.push_back({tin.base, tin.bstride});
+    {
+        std::vector<NttJob> jobs;
+        auto add_limbs = [&](u64 *base, int level) {
+            for (int c = 0; c < 2; c++)
+                for (int i = 0; i <= level; i++) {
+                    NttJob j{};
+                    j.src = j.dst = base + ((size_t)c * (level + 1) + i) * N;
+                    j.prime = i;
+                    jobs.push_back(j);
+                }
+        };
+        for (int j = 0; j < q.attrs; j++) add_limbs(wbuf->ptr + j * wwords, L);
+        for (auto &c : cin) add_limbs(c.base, c.level);
+        add_limbs(tin.base, tin.level);
+        R.ntt(false, jobs, LOAD_PLAIN, STORE_PLAIN);
+    }
+    // per-query: coefficients and threshold moved to their levels
+    std::vector<CtH> ck;
+    ck.push_back(R.adjust(cin[0], pl.l_y, 1.0));
+    for (int k = 1; k <= q.degree; k++) ck.push_back(R.adjust(cin[k], pl.l_d, 1.0));
+    CtH tadj = R.adjust(tin, pl.l_y, 1.0);
+    // block groups
+    const int B = db.blocks;
+    const int bpl = q.bpl <= 0 ? B : std::min(q.bpl, B);
+    CtH full, last;
+    bool have_full = false, have_last = false;
+    for (int b0 = 0; b0 < B; b0 += bpl) {
+        const int nb = std::min(bpl, B - b0);
+        CtH u = eval_blocks(R, db, pl, b0, nb, wbuf->ptr, ck, tadj, q.degree);
+        int nfull = nb;
+        if (pl.ragged && b0 + nb == B) {
+            last = R.view(u.buf, u.limb(nb - 1, 0, 0), 1, u.comps, u.level, u.bstride, u.cstride, u.scale);
+            have_last = true;
+            nfull = nb - 1;
+        }
+        if (nfull > 0) {
+            CtH part = R.sum_batch(R.view(u.buf, u.base, nfull, u.comps, u.level, u.bstride, u.cstride, u.scale));
+            full = have_full ? R.add(full, part) : part;
+            have_full = true;
+        }
+    }
+    CtH acc;
+    if (pl.ragged) {
+        TREQUIRE(db.mask_real && have_last, TETRIS_EINVAL, "database has no mask for its ragged last block");
+        BufPtr mi = P->pool.alloc(N);
+        BufPtr mpt = P->pool.alloc((size_t)(pl.l_u + 1) * N);
+        const double *mr = reinterpret_cast<const double *>(db.mask_real->ptr);
+        int64_t *mip = reinterpret_cast<int64_t *>(mi->ptr);
+        const double ms = pl.mask_scale;
+        P->launches.push_back([=](cudaStream_t s, const uint8_t *) { round_scale(mr, mip, N, ms, s); });
+        P->kernel_launches += 1;
+        std::vector<NttJob> jobs;
+        for (int i = 0; i <= pl.l_u; i++) {
+            NttJob j{};
+            j.src = mi->ptr;
+            j.dst = mpt->ptr + (size_t)i * N;
+            j.prime = i;
+            jobs.push_back(j);
+        }
+        R.ntt(false, jobs, LOAD_INT64, STORE_PLAIN);
+        CtH m = R.rescale(R.mul_plain(last, mpt->ptr, 0));
+        m.scale = C.S[pl.l_out];
+        acc = have_full ? R.add(R.adjust(full, pl.l_out, 1.0), m) : m;
+    } else {
+        acc = full;
+    }
+    // InnerSum: acc += Rot_{2^k}(acc)
+    for (int k = 0; k + 1 < C.log_n; k++) {
+        const uint32_t g = (uint32_t)h_powmod(5, 1ull << k, 2 * C.N);
+        acc = R.add(acc, R.rotate(acc, g));
+    }
+    CtH o = R.from_ntt(acc);
+    P->out_buf = o.buf;
+    P->out_base = o.base;
+    P->out_words = o.bstride;
+    P->out_level = acc.level;
+    P->out_comps = 2;
+    P->out_scale = C.S[acc.level];
+    P->finalize();
+    return P;
+}
+
+static QuerySpec spec_of(const Ctx &C, const Database &db, const tetris_query *q) {
+    TREQUIRE(q && q->w && q->f_coeffs && q->threshold && q->sign_coeffs, TETRIS_EINVAL, "query: null pointer");
+    TREQUIRE((int)q->n_attrs == db.attrs, TETRIS_EINVAL, "query: attribute count differs from the database");
+    TREQUIRE(q->sign_degree == 7, TETRIS_EINVAL, "query: sign stages must be odd degree-7 polynomials");
+    TREQUIRE(q->sign_stages >= 1 && q->f_degree >= 1, TETRIS_EINVAL, "query: empty polynomial");
+    QuerySpec s;
+    s.attrs = q->n_attrs;
+    s.degree = q->f_degree;
+    const int L = C.L();
+    for (uint32_t j = 0; j < q->n_attrs; j++) {
+        TREQUIRE(q->w[j].level == (uint32_t)L && q->w[j].ncomp == 2 && q->w[j].scale == C.S[L] && q->w[j].data,
+                 TETRIS_EINVAL, "query: linear-combination coefficients must be fresh top-level ciphertexts");
+    }
+    for (uint32_t k = 0; k <= q->f_degree; k++) {
+        TREQUIRE(q->f_coeffs[k].ncomp == 2 && (int)q->f_coeffs[k].level <= L && q->f_coeffs[k].data && q->f_coeffs[k].scale > 0,
+                 TETRIS_EINVAL, "query: bad polynomial coefficient ciphertext");
+        s.c_level.push_back(q->f_coeffs[k].level);
+        s.c_scale.push_back(q->f_coeffs[k].scale);
+    }
+    TREQUIRE(q->threshold->ncomp == 2 && (int)q->threshold->level <= L && q->threshold->data && q->threshold->scale > 0,
+             TETRIS_EINVAL, "query: bad threshold ciphertext");
+    s.t_level = q->threshold->level;
+    s.t_scale = q->threshold->scale;
+    for (uint32_t st = 0; st < q->sign_stages; st++) {
+        std::array<double, 4> a;
+        for (int k = 0; k < 4; k++) a[k] = q->sign_coeffs[st * 4 + k];
+        s.stages.push_back(a);
+    }
+    s.bpl = C.blocks_per_launch;
+    return s;
+}
+
+static Program &get_program(Ctx &C, uint32_t dbh, const QuerySpec &s) {
+    auto it = C.dbs.find(dbh);
+    TREQUIRE(it != C.dbs.end(), TETRIS_ENOTFOUND, "unknown database handle");
+    const std::string key = s.key(dbh);
+    auto pit = C.programs.find(key);
+    if (pit == C.programs.end()) {
+        auto prog = record_query(C, it->second, s);
+        pit = C.programs.emplace(key, std::move(prog)).first;
+    }
+    return *pit->second;
+}
+
+void drop_programs_of_db(Ctx &C, uint32_t dbh) {
+    const std::string pre = "q" + std::to_string(dbh) + ":";
+    for (auto it = C.programs.begin(); it != C.programs.end();) {
+        if (it->first.compare(0, pre.size(), pre) == 0) it = C.programs.erase(it);
+        else ++it;
+    }
+}
+
+void evaluate_query(Ctx &C, uint32_t dbh, const tetris_query *q, tetris_ct_out *out, cudaStream_t s, bool device) {
+    auto it = C.dbs.find(dbh);
+    TREQUIRE(it != C.dbs.end(), TETRIS_ENOTFOUND, "unknown database handle");
+    TREQUIRE(out && out->data, TETRIS_EINVAL, "query: null output");
+    QuerySpec spec = spec_of(C, it->second, q);
+    Program &P = get_program(C, dbh, spec);
+    TREQUIRE(out->cap_words >= P.out_words, TETRIS_EINVAL, "query: output buffer too small");
+    const cudaMemcpyKind in_kind = device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+    size_t slot = 0;
+    auto put = [&](const tetris_ct_in &c) {
+        TCHECK_CUDA(cudaMemcpyAsync(P.in_slots[slot].first, c.data, P.in_slots[slot].second * 8, in_kind, s));
+        slot++;
+    };
+    for (uint32_t j = 0; j < q->n_attrs; j++) put(q->w[j]);
+    for (uint32_t k = 0; k <= q->f_degree; k++) put(q->f_coeffs[k]);
+    put(*q->threshold);
+    if (C.use_graph) P.run_graph(s);
+    else P.run(s);
+    TCHECK_CUDA(cudaMemcpyAsync(out->data, P.out_base, P.out_words * 8,
+                                device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, s));
+    out->level = P.out_level;
+    out->ncomp = P.out_comps;
+    out->scale = P.out_scale;
+    if (!device) TCHECK_CUDA(cudaStreamSynchronize(s));
+}
+
+void plan_info(Ctx &C, uint32_t dbh, uint32_t degree, uint32_t stages, tetris_plan_info *out) {
+    auto it = C.dbs.find(dbh);
+    TREQUIRE(it != C.dbs.end(), TETRIS_ENOTFOUND, "unknown database handle");
+    QuerySpec s;
+    s.attrs = it->second.attrs;
+    s.degree = degree;
+    for (uint32_t k = 0; k <= degree; k++) {
+        s.c_level.push_back(C.L());
+        s.c_scale.push_back(C.scale);
+    }
+    s.t_level = C.L();
+    s.t_scale = C.scale;
+    for (uint32_t i = 0; i < stages; i++) s.stages.push_back({35.0 / 16, -35.0 / 16, 21.0 / 16, -5.0 / 16});
+    s.bpl = C.blocks_per_launch;
+    QPlan pl = make_plan(C, it->second.records, degree, s.stages);
+    Program &P = get_program(C, dbh, s);
+    out->l_lin = pl.l_lin;
+    out->l_d = pl.l_d;
+    out->l_y = pl.l_y;
+    out->l_u = pl.l_u;
+    out->l_out = pl.l_out;
+    out->ragged = pl.ragged;
+    out->relins = P.relins;
+    out->rescales = P.rescales;
+    out->rotations = P.rotations;
+    out->kernel_launches = P.kernel_launches;
+    out->pt_scale = C.pt_scale;
+    out->mask_scale = pl.mask_scale;
+}
+
+}  // namespace tetris

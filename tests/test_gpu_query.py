@@ -1,0 +1,180 @@
+"""GPU parity for the whole encrypted query: the CUDA path's output ciphertext
+equals the oracle's residue for residue (given the oracle's encoded database),
+in batched and plain forms, replayed as a CUDA graph or launched directly,
+through host or device buffers; and the decrypted count matches the FP64
+plaintext pipeline at the full benchmark size."""
+import numpy as np
+import pytest
+
+import synth
+from oracle import ckks, query, rns
+
+pytestmark = pytest.mark.gpu
+
+T = pytest.importorskip("paper_2412_13269_gb300")
+
+
+class Chain:
+    """Test-only chain at N = 2^12: a 50-bit q_0, n40 primes of 40 bits, one
+    60-bit special prime, Delta = 2^40, one-prime digits."""
+
+    def __init__(self, n40=11, seed=5):
+        T.build()
+        q = rns.gen_primes(50, 1) + rns.gen_primes(40, n40)
+        p = rns.gen_primes(60, 1)
+        self.par = ckks.Params(12, q, p, 2.0 ** 40)
+        self.ctx = T.Ctx(12, q, p, 2.0 ** 40)
+        self.alpha = 1
+        self.s = query.secret(self.par, seed, 2 * self.par.N // 3)
+        self.keys = query.make_keys(self.par, self.s, seed, 1, query.innersum_galois(self.par))
+        self.ctx.load_relin_key(self.keys.rlk, 1)
+        for g, k in self.keys.rot.items():
+            self.ctx.load_rotation_key(g, k, 1)
+
+
+@pytest.fixture(scope="module")
+def chain():
+    return Chain()
+
+
+def make_case(par, s, records, attrs, degree, nst, seed, dist="uniform"):
+    vals = synth.database(synth.stream(seed, "db"), records, attrs, dist)
+    qv = synth.query_values(synth.stream(seed, "qv"), attrs, degree)
+    stages = [query.F3] * nst
+    shape = query.QueryShape(records, attrs, degree, stages)
+    plan = query.make_plan(par, shape)
+    db = query.encode_database(par, plan, vals)
+    eq = query.encrypt_query(par, s, qv, seed)
+    return vals, qv, stages, shape, plan, db, eq
+
+
+def upload_encoded(ctx, par, plan, db, records, attrs):
+    coeffs = np.stack([np.stack(blk) for blk in db.pts])
+    mask = None
+    if plan.ragged:
+        live = records - (len(db.pts) - 1) * par.n_slots
+        z = np.zeros(par.n_slots)
+        z[:live] = 1.0
+        mask = ckks.encode_real(par.N, z, 1.0)
+    return ctx.upload_database_encoded(coeffs, mask, records, attrs)
+
+
+def gpu_query(ctx, dbh, eq, stages):
+    w = [c.data for c in eq.w]
+    c = [x.data for x in eq.c]
+    return ctx.evaluate_query(dbh, w, [(x.level, x.scale) for x in eq.w], c, [(x.level, x.scale) for x in eq.c],
+                              eq.t.data, (eq.t.level, eq.t.scale), np.array(stages))
+
+
+@pytest.mark.parametrize("records,attrs,degree,nst", [(2048, 8, 7, 1), (1500, 4, 3, 1), (3000, 3, 2, 1)])
+def test_query_bit_exact(chain, records, attrs, degree, nst):
+    par, ctx = chain.par, chain.ctx
+    vals, qv, stages, shape, plan, db, eq = make_case(par, chain.s, records, attrs, degree, nst, records)
+    want = query.evaluate_query(par, chain.keys, shape, db, eq)
+    dbh = upload_encoded(ctx, par, plan, db, records, attrs)
+    for bpl, graph in [(0, 1), (1, 0), (0, 0), (1, 1)]:
+        ctx.set_option(T.OPT_BLOCKS_PER_LAUNCH, bpl)
+        ctx.set_option(T.OPT_USE_GRAPH, graph)
+        got, lev, sc = gpu_query(ctx, dbh, eq, stages)
+        assert lev == want.level == plan.l_out
+        assert np.array_equal(got, want.data), (bpl, graph)
+        assert sc == plan.S[plan.l_out]
+    ctx.set_option(T.OPT_BLOCKS_PER_LAUNCH, 0)
+    ctx.set_option(T.OPT_USE_GRAPH, 1)
+    # decrypts to the FP64 pipeline's normalised count in every slot
+    z = ckks.decrypt_slots(par, ckks.Ct(got.copy(), lev, sc), chain.s).real
+    ref = query.fp64_pipeline(vals, qv, stages)
+    assert np.ptp(z) < 1e-6 and abs(z[0] * records - ref.count) < 0.05
+    ctx.free_database(dbh)
+
+
+def test_device_buffers_match_host(chain):
+    torch = pytest.importorskip("torch")
+    par, ctx = chain.par, chain.ctx
+    vals, qv, stages, shape, plan, db, eq = make_case(par, chain.s, 2048, 8, 7, 1, 77)
+    dbh = upload_encoded(ctx, par, plan, db, 2048, 8)
+    host, lev, sc = gpu_query(ctx, dbh, eq, stages)
+    dev = lambda a: torch.from_numpy(a.view(np.int64).copy()).cuda()
+    w = [dev(c.data) for c in eq.w]
+    c = [dev(x.data) for x in eq.c]
+    t = dev(eq.t.data)
+    out = torch.empty(2 * (par.L + 1) * par.N, dtype=torch.int64, device="cuda")
+    stream = torch.cuda.current_stream()
+    lev2, sc2 = ctx.evaluate_query_device(dbh, w, [(x.level, x.scale) for x in eq.w], c, [(x.level, x.scale) for x in eq.c],
+                                          t, (eq.t.level, eq.t.scale), np.array(stages), out, stream.cuda_stream)
+    stream.synchronize()
+    got = out.cpu().numpy().view(np.uint64)[: host.size].reshape(host.shape)
+    assert lev2 == lev and np.array_equal(got, host)
+    ctx.free_database(dbh)
+
+
+def test_gpu_encoded_database_decrypts_to_fp64(chain):
+    par, ctx = chain.par, chain.ctx
+    vals, qv, stages, shape, plan, db, eq = make_case(par, chain.s, 1800, 6, 5, 1, 31, "paper")
+    dbh = ctx.upload_database(vals)
+    got, lev, sc = gpu_query(ctx, dbh, eq, stages)
+    z = ckks.decrypt_slots(par, ckks.Ct(got.copy(), lev, sc), chain.s).real
+    ref = query.fp64_pipeline(vals, qv, stages)
+    assert abs(z[0] * 1800 - ref.count) < 0.05
+    ctx.free_database(dbh)
+
+
+def test_plan_counts(chain):
+    par, ctx = chain.par, chain.ctx
+    vals = synth.database(synth.stream(1, "db"), 2048, 8)
+    dbh = ctx.upload_database(vals)
+    info = ctx.plan(dbh, 7, 1)
+    p = query.make_plan(par, query.QueryShape(2048, 8, 7, [query.F3]))
+    assert (info.l_lin, info.l_d, info.l_y, info.l_u, info.l_out) == (p.l_lin, p.l_d, p.l_y, p.l_u, p.l_out)
+    assert info.rotations == par.log_n - 1 and info.relins > 0 and info.kernel_launches > 0
+    assert info.pt_scale == p.pt_scale
+    ctx.free_database(dbh)
+
+
+def test_errors_leave_context_usable(chain):
+    ctx = chain.ctx
+    with pytest.raises(T.TetrisError):
+        ctx.free_database(12345)
+    with pytest.raises(T.TetrisError):
+        ctx.op(T.OP_ROTATE, np.zeros((2, 1, ctx.N), dtype=np.uint64), 0, arg=7)   # no key for 7
+    a = np.zeros((2, 1, ctx.N), dtype=np.uint64)
+    got = ctx.op(T.OP_ADD, a, 0, b=a, b_level=0, out_comps=2)[0]
+    assert not got.any()
+
+
+@pytest.fixture(scope="module")
+def full():
+    """The benchmark's parameters: N = 2^16, twenty 50-bit primes, three 60-bit special primes, Delta = 2^50, alpha = 3."""
+    T.build()
+    q, p = rns.gen_primes(50, 20), rns.gen_primes(60, 3)
+    par = ckks.Params(16, q, p, 2.0 ** 50)
+    ctx = T.Ctx(16, q, p, 2.0 ** 50)
+    s = query.secret(par, 8, 192)
+    keys = query.make_keys(par, s, 8, 3, query.innersum_galois(par))
+    ctx.load_relin_key(keys.rlk, 3)
+    for g, k in keys.rot.items():
+        ctx.load_rotation_key(g, k, 3)
+    return par, ctx, s, keys
+
+
+def test_full_size_one_block_bit_exact(full):
+    par, ctx, s, keys = full
+    vals, qv, stages, shape, plan, db, eq = make_case(par, s, 32768, 16, 15, 3, 4, "mixed")
+    want = query.evaluate_query(par, keys, shape, db, eq)
+    dbh = upload_encoded(ctx, par, plan, db, 32768, 16)
+    got, lev, sc = gpu_query(ctx, dbh, eq, stages)
+    assert lev == want.level and np.array_equal(got, want.data)
+    ctx.free_database(dbh)
+
+
+def test_full_size_benchmark_workload_decrypts(full):
+    """131072 records x 16 attributes (four blocks, as timed by the benchmark): decrypted count vs FP64."""
+    par, ctx, s, keys = full
+    vals, qv, stages, shape, plan, db, eq = make_case(par, s, 131072, 16, 15, 3, 6, "mixed")
+    dbh = ctx.upload_database(vals)
+    got, lev, sc = gpu_query(ctx, dbh, eq, stages)
+    z = ckks.decrypt_slots(par, ckks.Ct(got.copy(), lev, sc), s).real
+    ref = query.fp64_pipeline(vals, qv, stages)
+    assert np.ptp(z) < 1e-6
+    assert abs(z[0] * 131072 - ref.count) < 0.5
+    ctx.free_database(dbh)
