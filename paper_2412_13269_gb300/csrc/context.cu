@@ -468,8 +468,8 @@ CtH Rec::keyswitch(int B, int l, const std::function<const u64 *(int, int)> &d, 
                 }
         ntt(true, jobs, LOAD_PLAIN, STORE_PLAIN);
     }
-    // 5. convert (c_P + floor(P/2)) to each q_i, NTT, and combine:
-    //    out_i = extra + (acc_i + [floor(P/2)]_{q_i} - conv) * P^-1
+    // 5. convert (c_P + floor(P/2)) to each q_i, subtract [floor(P/2)]_{q_i} from
+    //    every coefficient, NTT, and combine: out_i = extra + (acc_i - x) * P^-1
     CtH out = new_ct(B, 2, l);
     {
         u64 adds[kMaxConvSrc];
@@ -482,7 +482,7 @@ CtH Rec::keyswitch(int B, int l, const std::function<const u64 *(int, int)> &d, 
             const u64 half = h_mulmod((pm + qi - 1) % qi, h_invmod(2, qi), qi);
             const u64 pinv = h_invmod(pm, qi);
             NttJob proto = conv_job(i, nullptr, C.L() + 1, K, adds);
-            proto.addt = half;
+            proto.conv_sub = half;
             proto.mul = pinv;
             proto.mul_sh = h_shoup(pinv, qi);
             for (int b = 0; b < B; b++)
@@ -510,7 +510,9 @@ CtH Rec::relin(const CtH &t) {
     return o;
 }
 
-// Rescale (Section 2.5): out_i = (a_i + [floor(q_l/2)]_{q_i} - [[a_l + floor(q_l/2)]_{q_l}]_{q_i}) * q_l^-1.
+// Rescale (Section 2.5), per coefficient:
+//   out_i = (a_i + [floor(q_l/2)]_{q_i} - [[a_l + floor(q_l/2)]_{q_l}]_{q_i}) * q_l^-1;
+// the two constants are folded into the converted top limb before its NTT.
 CtH Rec::rescale(const CtH &a) {
     const int l = a.level;
     TREQUIRE(l >= 1, TETRIS_ELEVEL, "rescale at level 0");
@@ -535,7 +537,7 @@ CtH Rec::rescale(const CtH &a) {
     for (int i = 0; i < l; i++) {
         const u64 qi = C.q[i];
         NttJob proto = conv_job(i, nullptr, l, 1, &half);
-        proto.addt = half % qi;
+        proto.conv_sub = half % qi;
         proto.mul = h_invmod(ql % qi, qi);
         proto.mul_sh = h_shoup(proto.mul, qi);
         for (int b = 0; b < a.B; b++)

@@ -79,9 +79,9 @@ enum LoadMode { LOAD_PLAIN = 0, LOAD_CONV = 1, LOAD_INT64 = 2 };
 enum StoreMode { STORE_PLAIN = 0, STORE_COMBINE = 1 };
 
 // One limb transform.  LOAD_CONV computes, per coefficient,
-//   sum_s [ (src_s + add_s) * c1_s ]_{q_s} * c2_s  mod q_dst
+//   sum_s [ (src_s + add_s) * c1_s ]_{q_s} * c2_s - conv_sub  mod q_dst
 // from nsrc source limbs src + s*src_stride (coefficient domain).
-// STORE_COMBINE writes (extra ? extra : 0) + (base + addt - x) * mul mod q_dst.
+// STORE_COMBINE writes (extra ? extra : 0) + (base - x) * mul mod q_dst.
 struct NttJob {
     const u64 *src;
     u64 *dst;
@@ -94,7 +94,7 @@ struct NttJob {
     u64 add_s[kMaxConvSrc];
     u64 c1[kMaxConvSrc], c1_sh[kMaxConvSrc];
     u64 c2[kMaxConvSrc];
-    u64 addt, mul, mul_sh;
+    u64 conv_sub, mul, mul_sh;
 };
 
 struct NttTables {

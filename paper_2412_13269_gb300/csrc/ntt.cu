@@ -17,8 +17,9 @@
 // column pass and o = N1 + row in the row pass.
 //
 // Load modes fuse the producer: plain, int64 -> residue, or a fast base
-// conversion from up to four source limbs (ModUp / ModDown / rescale).  The
-// combine store fuses the consumer: (extra) + (base + addt - x) * mul.
+// conversion from up to four source limbs (ModUp / ModDown / rescale), less a
+// per-coefficient constant.  The combine store fuses the consumer:
+// (extra) + (base - x) * mul.
 #include "internal.h"
 
 namespace tetris {
@@ -53,7 +54,7 @@ __device__ __forceinline__ u64 load_elem(const NttJob &J, const PassParams &P, s
         y = shoup(y, J.c1[s], J.c1_sh[s], qs);
         acc_mad(acc, y, J.c2[s]);
     }
-    return reduce128(acc.hi, acc.lo, P.t.mods[J.prime]);
+    return sub_mod(reduce128(acc.hi, acc.lo, P.t.mods[J.prime]), J.conv_sub, q);
 }
 
 template <int LOGM, bool INV, bool COL>
@@ -163,7 +164,7 @@ __global__ void __launch_bounds__(kThreads) ntt_pass_kernel(PassParams P) {
         u64 v = sm[smidx(r, ss)];
         if (P.scale_out) v = shoup(v, mi.ninv, mi.ninv_sh, q);
         if (P.store_mode == STORE_COMBINE) {
-            v = shoup(sub_mod(add_mod(J.base[gi], J.addt, q), v, q), J.mul, J.mul_sh, q);
+            v = shoup(sub_mod(J.base[gi], v, q), J.mul, J.mul_sh, q);
             if (J.extra) v = add_mod(v, J.extra[gi], q);
         }
         J.dst[gi] = v;
