@@ -1,0 +1,376 @@
+#!/usr/bin/env python
+"""Benchmark of the encrypted-query hot path on GB300.
+
+One step = one whole encrypted query over the resident database: input
+ciphertexts to the NTT domain, linear combination with encrypted
+coefficients, degree-15 polynomial with encrypted coefficients, encrypted
+threshold, three composite-sign stages, block sum, InnerSum, output back to
+the coefficient domain.  Workload: N = 2^16, twenty 50-bit ciphertext primes,
+three 60-bit special primes, Delta = 2^50, 131072 records x 16 attributes
+(four 32768-slot blocks), alpha = 3 (seven key digits at the top level).
+
+Metric: amortised microseconds per record per query (lower is better),
+batched form (every launch covers all blocks, CUDA-graph replay) as `value`,
+the plain per-block form beside it, keyswitch GB/s against the measured HBM
+peak.  `--impl reference` times the CPU oracle on the same workload.
+
+Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+Multi-GPU (one process per GPU under torch.distributed.run): each rank holds
+its own shard of records (weak scaling); the per-rank count ciphertexts are
+summed residue-wise across ranks (the one exchange of the method).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import synth  # noqa: E402
+
+METRIC = "amortized µs/record/query (batched vs plain on GB300); keyswitch GB/s vs HBM peak"
+WL = dict(log_n=16, n_q=20, q_bits=50, n_p=3, p_bits=60, scale=2.0 ** 50, records=131072, attrs=16, degree=15,
+          stages=3, alpha=3, dist="mixed", hw=192)
+WL_NAME = "query N=2^16 L=20x50b K=3x60b alpha=3; 131072 records x 16 attrs; f deg 15 enc coeffs; 3 x deg-7 sign; InnerSum"
+F3 = (35.0 / 16.0, -35.0 / 16.0, 21.0 / 16.0, -5.0 / 16.0)
+
+
+def dist_env():
+    return int(os.environ.get("RANK", 0)), int(os.environ.get("WORLD_SIZE", 1)), int(os.environ.get("LOCAL_RANK", 0))
+
+
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f), "measured"
+    except Exception:
+        return {"hbm_gbs": 6800.0}, "fallback"
+
+
+class Clocks:
+    """nvidia-smi sampling during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu: int):
+        self.gpu = gpu
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                                          "-lms", "50", "-i", str(self.gpu)], stdout=self.f, stderr=subprocess.DEVNULL)
+            time.sleep(0.15)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if not self.proc:
+            return None
+        time.sleep(0.1)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.f.close()
+        sm, mx, reasons = [], 0.0, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx = max(mx, float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        os.unlink(self.path)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def primes():
+    import paper_2412_13269_gb300 as T
+    q = T.gen_primes(WL["q_bits"], WL["n_q"])
+    p = T.gen_primes(WL["p_bits"], WL["n_p"], exclude=q)
+    return q, p
+
+
+def galois_elements(n):
+    return [pow(5, 1 << k, 2 * n) for k in range(int(math.log2(n)) - 1)]
+
+
+def setup_gpu(rank: int, local_rank: int):
+    """Context, keys (generated on the GPU from seeded draws), database (GPU encoder), encrypted query."""
+    import paper_2412_13269_gb300 as T
+    T.build()
+    q, p = primes()
+    N = 1 << WL["log_n"]
+    ctx = T.Ctx(WL["log_n"], q, p, WL["scale"], device=local_rank)
+    seed = 1000 + rank
+    s = synth.ternary_secret(synth.stream(seed, "secret"), N, WL["hw"])
+    dnum = -(-WL["n_q"] // WL["alpha"])
+    mods = q + p
+    d = synth.switch_key_draws(seed, "relin", dnum, mods, N)
+    ctx.keygen_relin(s, d.a, d.e, WL["alpha"])
+    for g in galois_elements(N):
+        d = synth.switch_key_draws(seed, f"rot{g}", dnum, mods, N)
+        ctx.keygen_rotation(g, s, d.a, d.e, WL["alpha"])
+    vals = synth.database(synth.stream(seed, "db"), WL["records"], WL["attrs"], WL["dist"])
+    dbh = ctx.upload_database(vals)
+    qv = synth.query_values(synth.stream(seed, "qv"), WL["attrs"], WL["degree"])
+    L = WL["n_q"] - 1
+
+    def enc(v, name):
+        m = ctx.encode(np.full(N // 2, float(v)), WL["scale"])
+        dr = synth.encryption_draws(seed, name, q, N)
+        return ctx.encrypt(m, s, dr.a, dr.e, L, WL["scale"])
+
+    w = [enc(v, f"w{j}") for j, v in enumerate(qv.w)]
+    c = [enc(v, f"c{k}") for k, v in enumerate(qv.c)]
+    t = enc(qv.t, "t")
+    return ctx, dbh, w, c, t, s, vals, qv
+
+
+def oracle_sample(rank: int, nblocks_full: int, seed_offset: int = 0):
+    """The CPU oracle on a bounded sample of the same workload: per-query work,
+    one of the four blocks, and InnerSum; the block time is counted once per
+    block of the full workload.  Returns (us per record per query, seconds of
+    CPU work, threads, description)."""
+    from oracle import ckks, query, rns
+    q = rns.gen_primes(WL["q_bits"], WL["n_q"])
+    p = rns.gen_primes(WL["p_bits"], WL["n_p"], exclude=q)
+    par = ckks.Params(WL["log_n"], q, p, WL["scale"])
+    seed = 1000 + rank + seed_offset
+    s = synth.ternary_secret(synth.stream(seed, "secret"), par.N, WL["hw"])
+    keys = query.make_keys(par, s, seed, WL["alpha"], query.innersum_galois(par))
+    vals = synth.database(synth.stream(seed, "db"), par.n_slots, WL["attrs"], WL["dist"])
+    qv = synth.query_values(synth.stream(seed, "qv"), WL["attrs"], WL["degree"])
+    shape = query.QueryShape(WL["records"], WL["attrs"], WL["degree"], [F3] * WL["stages"])
+    plan = query.make_plan(par, shape)
+    db = query.encode_database(par, plan, vals)
+    eq = query.encrypt_query(par, s, qv, seed)
+    ev = query.Evaluator(par, keys, plan)
+    t0 = time.perf_counter()
+    ck, tadj = ev.per_query(eq, WL["degree"])
+    t1 = time.perf_counter()
+    u = ev.block(db.pts[0], eq, ck, tadj, WL["degree"])
+    t2 = time.perf_counter()
+    ev.innersum(u)
+    t3 = time.perf_counter()
+    total = (t1 - t0) + nblocks_full * (t2 - t1) + (t3 - t2)
+    threads = int(rns.lib().or_num_threads())
+    desc = (f"oracle: per-query work + 1 of {nblocks_full} blocks ({par.n_slots} of {WL['records']} records) + InnerSum "
+            f"timed ({t3 - t0:.1f} s), block time x{nblocks_full}")
+    return total * 1e6 / WL["records"], t3 - t0, threads, desc
+
+
+def run_reference(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return
+    blocks = WL["records"] // (1 << (WL["log_n"] - 1))
+    for _ in range(args.warmup):
+        oracle_sample(rank, blocks)
+    vals, secs = [], 0.0
+    for _ in range(args.steps):
+        v, t, threads, desc = oracle_sample(rank, blocks)
+        vals.append(v)
+        secs += t
+    value = statistics.mean(vals)
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "us/record/query", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": value * WL["records"] / 1e3,
+            "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "u64",
+            "data": "synthetic (seeded)", "config": {"workload": WL_NAME},
+            "cpu_baseline": {"value": value, "unit": "us/record/query", "cores": threads, "kind": "oracle", "sample": desc},
+            "e2e": {"value": value, "unit": "us/record/query", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-plain", action="store_true")
+    ap.add_argument("--ncu", action="store_true", help="profile exactly one query between cudaProfilerStart/Stop")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+
+    import torch
+    rank, world, local_rank = dist_env()
+    torch.cuda.set_device(local_rank)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    import paper_2412_13269_gb300 as T
+
+    ctx, dbh, w, c, t, s, vals, qv = setup_gpu(rank, local_rank)
+    N, L = 1 << WL["log_n"], WL["n_q"] - 1
+    Delta = WL["scale"]
+    sign = np.array([F3] * WL["stages"])
+    meta_w = [(L, Delta)] * len(w)
+    meta_c = [(L, Delta)] * len(c)
+    dev = lambda a: torch.from_numpy(np.ascontiguousarray(a).view(np.int64)).cuda()
+    dw, dc, dt = [dev(x) for x in w], [dev(x) for x in c], dev(t)
+    out = torch.empty(2 * (L + 1) * N, dtype=torch.int64, device="cuda")
+    stream = torch.cuda.Stream()
+
+    def step():
+        return ctx.evaluate_query_device(dbh, dw, meta_w, dc, meta_c, dt, (L, Delta), sign, out, stream.cuda_stream)
+
+    def barrier():
+        if world > 1:
+            torch.distributed.barrier()
+        torch.cuda.synchronize()
+
+    def timed(k):
+        barrier()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(k):
+            step()
+        e1.record(stream)
+        e1.synchronize()
+        barrier()
+        ms = e0.elapsed_time(e1) / k
+        if world > 1:
+            tt = torch.tensor([ms], device="cuda")
+            torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
+            ms = float(tt.item())
+        return ms
+
+    if args.ncu:
+        ctx.set_option(T.OPT_USE_GRAPH, 0)
+        step()
+        stream.synchronize()
+        torch.cuda.profiler.start()
+        step()
+        stream.synchronize()
+        torch.cuda.profiler.stop()
+        print(json.dumps({"ncu_profiled_query": True}))
+        return
+
+    # batched form (all blocks per launch), CUDA graph replay
+    for _ in range(args.warmup):
+        step()
+    stream.synchronize()
+    clocks = Clocks(local_rank)
+    clocks.start()
+    ms = timed(args.steps)
+    clk = clocks.stop()
+    out_level = None
+    records_total = WL["records"] * world
+    value = ms * 1e3 / WL["records"]  # per-rank records per rank time == all records / all time (weak scaling)
+
+    # plain per-block form
+    plain = None
+    if not args.no_plain:
+        ctx.set_option(T.OPT_BLOCKS_PER_LAUNCH, 1)
+        step()
+        stream.synchronize()
+        k2 = max(3, args.steps // 4)
+        pms = timed(k2)
+        plain = {"value": pms * 1e3 / WL["records"], "unit": "us/record/query", "ms_per_step": pms, "steps": k2,
+                 "form": "one block per launch, CUDA graph replay"}
+        ctx.set_option(T.OPT_BLOCKS_PER_LAUNCH, 0)
+
+    # end to end through the public API with host buffers (pinned), copies inside the timed region
+    pin = lambda a: torch.from_numpy(np.ascontiguousarray(a).view(np.int64)).pin_memory().numpy().view(np.uint64)
+    hw, hc, ht = [pin(x) for x in w], [pin(x) for x in c], pin(t)
+    hout = torch.empty(2 * (L + 1) * N, dtype=torch.int64).pin_memory().numpy().view(np.uint64)
+    ctx.evaluate_query(dbh, hw, meta_w, hc, meta_c, ht, (L, Delta), sign, out=hout)
+    barrier()
+    k3 = max(3, args.steps // 4)
+    t0 = time.perf_counter()
+    for _ in range(k3):
+        res, out_level, out_scale = ctx.evaluate_query(dbh, hw, meta_w, hc, meta_c, ht, (L, Delta), sign, out=hout)
+    e2e_ms = (time.perf_counter() - t0) * 1e3 / k3
+    h2d = sum(x.nbytes for x in hw) + sum(x.nbytes for x in hc) + ht.nbytes
+    d2h = res.nbytes
+
+    # per-kernel profile of one query (eager, CUDA event pair around every launch on its stream)
+    ctx.set_option(T.OPT_PROFILE, 1)
+    step()
+    stream.synchronize()
+    ctx.set_option(T.OPT_PROFILE, 0)
+    stats = ctx.kernel_stats()
+    info = ctx.plan(dbh, WL["degree"], WL["stages"])
+    peaks, peak_kind = measured_peaks()
+    hbm = float(peaks.get("hbm_gbs", 6800.0))
+    kern = {k: v for k, v in stats.items() if k != "keyswitch(total)"}
+    tot_ms = sum(v[1] for v in kern.values())
+    dom = max(kern, key=lambda k: kern[k][1])
+    n_l, dom_ms, dom_b = kern[dom]
+    achieved = (dom_b / n_l) / (dom_ms / n_l * 1e-3) / 1e9
+    roofline = {"kernel": dom, "bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
+                "frac": achieved / hbm, "traffic": None, "share": dom_ms / tot_ms, "launches_per_query": n_l,
+                "avg_launch_us": dom_ms / n_l * 1e3, "peak_source": f"{peak_kind} hbm_gbs"}
+    ks = stats.get("keyswitch(total)")
+    keyswitch = None
+    if ks:
+        gbs = ks[2] / (ks[1] * 1e-3) / 1e9
+        keyswitch = {"count_per_query": ks[0], "gbs": gbs, "frac_of_hbm": gbs / hbm, "ms_per_query": ks[1],
+                     "share_of_query": ks[1] / tot_ms,
+                     "bytes": "per keyswitch: input limbs + key limbs used + output limbs (the key read once per batched launch)"}
+    top = sorted(kern.items(), key=lambda kv: -kv[1][1])[:8]
+    kernels = [{"kind": k, "launches": v[0], "ms": round(v[1], 4), "share": round(v[1] / tot_ms, 4),
+                "alg_gbs": round(v[2] / (v[1] * 1e-3) / 1e9, 1)} for k, v in top]
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        v, secs, threads, desc = oracle_sample(rank, WL["records"] // (N // 2))
+        cpu = {"value": v, "unit": "us/record/query", "cores": threads, "kind": "oracle", "sample": desc}
+
+    line = {
+        "metric": METRIC, "value": value, "unit": "us/record/query", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": False, "scaling": "weak",
+        "vs_baseline": None, "dtype": "u64",
+        "data": "synthetic, seeded: u8 attributes, half uniform and half the paper's clipped-normal features",
+        "config": {"workload": WL_NAME, "records_per_gpu": WL["records"], "records_total": records_total,
+                   "form": "batched: every launch covers all 4 blocks; CUDA graph replay; device-resident inputs",
+                   "l2": "inputs larger than L2 (2.6 GB of keys, 640 MiB database per query)",
+                   "parallelism": f"records sharded over {world} GPU(s)"},
+        "plain": plain,
+        "e2e": {"value": e2e_ms * 1e3 / WL["records"], "unit": "us/record/query", "ms_per_step": e2e_ms,
+                "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+                "api": "tetris_evaluate_query, pinned host buffers, copies and sync inside"},
+        "roofline": roofline, "keyswitch": keyswitch, "kernels": kernels,
+        "cpu_baseline": cpu, "clocks": clk,
+        "gpu_launches": info.kernel_launches * args.steps,
+        "plan": {"relins": info.relins, "rescales": info.rescales, "rotations": info.rotations,
+                 "launches_per_query": info.kernel_launches, "l_out": info.l_out},
+    }
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    ctx.close()
+    if world > 1:
+        torch.distributed.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -200,10 +200,24 @@ enum {
     TETRIS_OPT_BLOCKS_PER_LAUNCH = 1,  /* 0: all blocks of a database in each launch (batched);
                                           k: k blocks per launch (1 = plain per-ciphertext form) */
     TETRIS_OPT_USE_GRAPH = 2,          /* 1: replay the query as a captured CUDA graph */
-    TETRIS_OPT_KS_ALPHA = 3            /* read-only: alpha of the loaded keys */
+    TETRIS_OPT_KS_ALPHA = 3,           /* read-only: alpha of the loaded keys */
+    TETRIS_OPT_PROFILE = 4             /* 1: run queries eagerly with a CUDA event pair around
+                                          every launch, accumulating per-kernel statistics */
 };
 int tetris_set_option(tetris_ctx *ctx, int option, int64_t value);
 int tetris_get_option(tetris_ctx *ctx, int option, int64_t *value);
+
+/* Per-kernel statistics gathered while TETRIS_OPT_PROFILE is on: for each
+ * kernel kind, its launches, their summed event-timed duration and the
+ * algorithmic bytes they move (distinct inputs read once plus outputs
+ * written once).  Writes up to cap entries and *n_out; clears the tally. */
+typedef struct {
+    char kind[48];
+    uint32_t launches;
+    double total_ms;
+    double alg_bytes;
+} tetris_kernel_stat;
+int tetris_get_kernel_stats(tetris_ctx *ctx, tetris_kernel_stat *out, uint32_t cap, uint32_t *n_out);
 
 /* ---------------------------------------------------------------------------
  * Single primitives on caller ciphertexts (host buffers), for parity checks.

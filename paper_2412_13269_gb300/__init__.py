@@ -25,7 +25,7 @@ ERRORS = {-1: "EINVAL", -2: "ENOMEM", -3: "ECUDA", -4: "ELEVEL", -5: "ENOTFOUND"
 
 OP_ADD, OP_SUB, OP_TENSOR, OP_RELIN, OP_RESCALE, OP_MUL_INT, OP_ADD_INT = 1, 2, 3, 4, 5, 6, 7
 OP_AUTOMORPHISM, OP_ROTATE, OP_KEYSWITCH, OP_MUL_PLAIN, OP_NTT, OP_INNERSUM, OP_DROP = 8, 9, 10, 11, 12, 13, 14
-OPT_BLOCKS_PER_LAUNCH, OPT_USE_GRAPH, OPT_KS_ALPHA = 1, 2, 3
+OPT_BLOCKS_PER_LAUNCH, OPT_USE_GRAPH, OPT_KS_ALPHA, OPT_PROFILE = 1, 2, 3, 4
 
 
 def build(force: bool = False) -> str:
@@ -66,6 +66,10 @@ class PlanInfo(C.Structure):
                 ("mask_scale", C.c_double)]
 
 
+class KernelStat(C.Structure):
+    _fields_ = [("kind", C.c_char * 48), ("launches", C.c_uint32), ("total_ms", C.c_double), ("alg_bytes", C.c_double)]
+
+
 _vp, _u32, _u64, _i64, _sz, _d = C.c_void_p, C.c_uint32, C.c_uint64, C.c_int64, C.c_size_t, C.c_double
 SIGNATURES = {
     "tetris_ctx_create": [C.POINTER(_vp), _u32, _vp, _u32, _vp, _u32, _d, C.c_int],
@@ -91,6 +95,7 @@ SIGNATURES = {
     "tetris_set_option": [_vp, C.c_int, _i64],
     "tetris_get_option": [_vp, C.c_int, C.POINTER(_i64)],
     "tetris_op": [_vp, C.c_int, C.POINTER(CtIn), C.POINTER(CtIn), _i64, C.POINTER(CtOut)],
+    "tetris_get_kernel_stats": [_vp, C.POINTER(KernelStat), _u32, C.POINTER(_u32)],
 }
 
 
@@ -243,6 +248,13 @@ class Ctx:
         v = C.c_int64()
         check(lib().tetris_get_option(self.h, opt, C.byref(v)))
         return v.value
+
+    def kernel_stats(self) -> dict:
+        """{kind: (launches, total_ms, alg_bytes)} gathered while OPT_PROFILE is on (clears them)."""
+        buf = (KernelStat * 256)()
+        n = C.c_uint32()
+        check(lib().tetris_get_kernel_stats(self.h, buf, 256, C.byref(n)))
+        return {buf[i].kind.decode(): (buf[i].launches, buf[i].total_ms, buf[i].alg_bytes) for i in range(n.value)}
 
     def plan(self, db: int, degree: int, stages: int) -> PlanInfo:
         p = PlanInfo()

@@ -685,6 +685,9 @@ int tetris_set_option(tetris_ctx *ctx, int option, int64_t value) {
             case TETRIS_OPT_USE_GRAPH:
                 C.use_graph = value ? 1 : 0;
                 break;
+            case TETRIS_OPT_PROFILE:
+                C.profile = value ? 1 : 0;
+                break;
             default:
                 throw Error(TETRIS_EINVAL, "unknown or read-only option");
         }
@@ -699,8 +702,29 @@ int tetris_get_option(tetris_ctx *ctx, int option, int64_t *value) {
             case TETRIS_OPT_BLOCKS_PER_LAUNCH: *value = C.blocks_per_launch; break;
             case TETRIS_OPT_USE_GRAPH: *value = C.use_graph; break;
             case TETRIS_OPT_KS_ALPHA: *value = C.alpha; break;
+            case TETRIS_OPT_PROFILE: *value = C.profile; break;
             default: throw Error(TETRIS_EINVAL, "unknown option");
         }
+    });
+}
+
+int tetris_get_kernel_stats(tetris_ctx *ctx, tetris_kernel_stat *out, uint32_t cap, uint32_t *n_out) {
+    return guarded([&] {
+        TREQUIRE(ctx && n_out && (out || cap == 0), TETRIS_EINVAL, "null pointer");
+        uint32_t n = 0;
+        for (auto &kv : ctx->c.stats) {
+            if (n < cap) {
+                tetris_kernel_stat &o = out[n];
+                std::memset(o.kind, 0, sizeof(o.kind));
+                std::strncpy(o.kind, kv.first.c_str(), sizeof(o.kind) - 1);
+                o.launches = kv.second.launches;
+                o.total_ms = kv.second.ms;
+                o.alg_bytes = kv.second.bytes;
+            }
+            n++;
+        }
+        *n_out = std::min(n, cap);
+        ctx->c.stats.clear();
     });
 }
 

@@ -97,10 +97,46 @@ void Program::finalize() {
     TCHECK_CUDA(cudaMemcpy(arena_dev->ptr, arena.data(), arena.size(), cudaMemcpyHostToDevice));
 }
 
+void Program::add_launch(std::function<void(cudaStream_t, const uint8_t *)> fn, const std::string &kind, double bytes) {
+    launches.push_back({std::move(fn), kind, bytes});
+    kernel_launches += 1;
+}
+
 void Program::run(cudaStream_t s) {
     const uint8_t *a = reinterpret_cast<const uint8_t *>(arena_dev->ptr);
-    for (auto &f : launches) f(s, a);
+    for (auto &l : launches) l.fn(s, a);
     TCHECK_CUDA(cudaGetLastError());
+}
+
+// Eager replay with a CUDA event pair around every launch on the same stream.
+void Program::run_profiled(cudaStream_t s, std::map<std::string, KernelStat> &stats) {
+    const uint8_t *a = reinterpret_cast<const uint8_t *>(arena_dev->ptr);
+    std::vector<cudaEvent_t> ev(2 * launches.size());
+    for (auto &e : ev) TCHECK_CUDA(cudaEventCreate(&e));
+    for (size_t i = 0; i < launches.size(); i++) {
+        TCHECK_CUDA(cudaEventRecord(ev[2 * i], s));
+        launches[i].fn(s, a);
+        TCHECK_CUDA(cudaEventRecord(ev[2 * i + 1], s));
+    }
+    TCHECK_CUDA(cudaStreamSynchronize(s));
+    TCHECK_CUDA(cudaGetLastError());
+    double ks_ms = 0;
+    for (size_t i = 0; i < launches.size(); i++) {
+        float ms = 0;
+        TCHECK_CUDA(cudaEventElapsedTime(&ms, ev[2 * i], ev[2 * i + 1]));
+        KernelStat &k = stats[launches[i].kind];
+        k.launches += 1;
+        k.ms += ms;
+        k.bytes += launches[i].bytes;
+        if (launches[i].kind.compare(0, 3, "ks.") == 0) ks_ms += ms;
+    }
+    if (ks_count) {
+        KernelStat &k = stats["keyswitch(total)"];
+        k.launches += ks_count;
+        k.ms += ks_ms;
+        k.bytes += ks_bytes;
+    }
+    for (auto &e : ev) cudaEventDestroy(e);
 }
 
 void Program::run_graph(cudaStream_t s) {
@@ -109,7 +145,7 @@ void Program::run_graph(cudaStream_t s) {
         TCHECK_CUDA(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
         TCHECK_CUDA(cudaStreamBeginCapture(cs, cudaStreamCaptureModeRelaxed));
         const uint8_t *a = reinterpret_cast<const uint8_t *>(arena_dev->ptr);
-        for (auto &f : launches) f(cs, a);
+        for (auto &l : launches) l.fn(cs, a);
         cudaError_t e = cudaStreamEndCapture(cs, &graph);
         cudaStreamDestroy(cs);
         TCHECK_CUDA(e);
@@ -148,15 +184,59 @@ CtH Rec::view(const BufPtr &buf, u64 *base, int B, int comps, int level, size_t 
     return c;
 }
 
+namespace {
+// distinct limbs among a set of pointers, in bytes of N words each
+double distinct_bytes(const std::vector<const void *> &ptrs, size_t N) {
+    std::vector<const void *> v;
+    for (auto p : ptrs)
+        if (p) v.push_back(p);
+    std::sort(v.begin(), v.end());
+    v.erase(std::unique(v.begin(), v.end()), v.end());
+    return (double)v.size() * N * 8;
+}
+const char *load_name(int m) { return m == LOAD_CONV ? "conv" : m == LOAD_INT64 ? "int64" : "plain"; }
+const char *ew_name(int op) {
+    switch (op) {
+        case EW_ADD: return "add";
+        case EW_SUB: return "sub";
+        case EW_MUL: return "mul";
+        case EW_MUL_CONST: return "mulc";
+        case EW_ADD_CONST: return "addc";
+        case EW_NEG: return "neg";
+        case EW_COPY: return "copy";
+        case EW_FMA: return "fma";
+        case EW_TENSOR: return "tensor";
+        case EW_ADD_MUL_CONST: return "addmulc";
+    }
+    return "?";
+}
+}  // namespace
+
 void Rec::ntt(bool inverse, const std::vector<NttJob> &jobs, int load_mode, int store_mode) {
     if (jobs.empty()) return;
     size_t off = P.add_jobs(jobs.data(), jobs.size() * sizeof(NttJob));
     int n = (int)jobs.size(), logn = C.log_n;
     NttTables t = C.nt;
-    P.launches.push_back([=](cudaStream_t s, const uint8_t *a) {
-        launch_ntt(inverse, logn, t, reinterpret_cast<const NttJob *>(a + off), n, load_mode, store_mode, s);
-    });
-    P.kernel_launches += ntt_launch_count(logn);
+    const size_t N = C.N;
+    std::vector<const void *> srcs, bases, extras;
+    for (auto &j : jobs) {
+        if (load_mode == LOAD_CONV)
+            for (uint32_t s = 0; s < j.nsrc; s++) srcs.push_back(j.src + s * j.src_stride);
+        else
+            srcs.push_back(j.src);
+        bases.push_back(j.base);
+        extras.push_back(j.extra);
+    }
+    const double limb = (double)N * 8, w = n * limb;
+    const std::string dir = inverse ? "ntt_inv" : "ntt_fwd";
+    P.add_launch([=](cudaStream_t s, const uint8_t *a) {
+        launch_ntt(inverse, logn, t, reinterpret_cast<const NttJob *>(a + off), n, load_mode, store_mode, s, 0);
+    }, prefix + dir + "_p1_" + load_name(load_mode), distinct_bytes(srcs, N) + w);
+    double b2 = 2 * w;
+    if (store_mode == STORE_COMBINE) b2 += distinct_bytes(bases, N) + distinct_bytes(extras, N);
+    P.add_launch([=](cudaStream_t s, const uint8_t *a) {
+        launch_ntt(inverse, logn, t, reinterpret_cast<const NttJob *>(a + off), n, load_mode, store_mode, s, 1);
+    }, prefix + dir + "_p2_" + (store_mode == STORE_COMBINE ? "combine" : "plain"), b2);
 }
 
 void Rec::ew(const std::vector<EwJob> &jobs) {
@@ -164,20 +244,28 @@ void Rec::ew(const std::vector<EwJob> &jobs) {
     size_t off = P.add_jobs(jobs.data(), jobs.size() * sizeof(EwJob));
     int n = (int)jobs.size(), logn = C.log_n;
     const ModInfo *m = C.nt.mods;
-    P.launches.push_back([=](cudaStream_t s, const uint8_t *a) {
+    std::vector<const void *> rd;
+    double writes = 0;
+    for (auto &j : jobs) {
+        rd.push_back(j.a);
+        rd.push_back(j.b);
+        rd.push_back(j.c);
+        rd.push_back(j.a1);
+        rd.push_back(j.b1);
+        writes += j.op == EW_TENSOR ? 3 : 1;
+    }
+    P.add_launch([=](cudaStream_t s, const uint8_t *a) {
         launch_ew(reinterpret_cast<const EwJob *>(a + off), n, logn, m, s);
-    });
-    P.kernel_launches += 1;
+    }, prefix + "ew_" + ew_name(jobs[0].op), distinct_bytes(rd, C.N) + writes * C.N * 8);
 }
 
 void Rec::aut(const std::vector<AutJob> &jobs, uint32_t g) {
     if (jobs.empty()) return;
     size_t off = P.add_jobs(jobs.data(), jobs.size() * sizeof(AutJob));
     int n = (int)jobs.size(), logn = C.log_n;
-    P.launches.push_back([=](cudaStream_t s, const uint8_t *a) {
+    P.add_launch([=](cudaStream_t s, const uint8_t *a) {
         launch_automorphism(reinterpret_cast<const AutJob *>(a + off), n, logn, g, s);
-    });
-    P.kernel_launches += 1;
+    }, prefix + "automorphism", 2.0 * n * C.N * 8);
 }
 
 void Rec::kip(const std::vector<KipJob> &jobs) {
@@ -185,10 +273,16 @@ void Rec::kip(const std::vector<KipJob> &jobs) {
     size_t off = P.add_jobs(jobs.data(), jobs.size() * sizeof(KipJob));
     int n = (int)jobs.size(), logn = C.log_n;
     const ModInfo *m = C.nt.mods;
-    P.launches.push_back([=](cudaStream_t s, const uint8_t *a) {
+    std::vector<const void *> rd;
+    for (auto &j : jobs)
+        for (uint32_t d = 0; d < j.ndig; d++) {
+            rd.push_back(j.src[d]);
+            rd.push_back(j.key0[d]);
+            rd.push_back(j.key1[d]);
+        }
+    P.add_launch([=](cudaStream_t s, const uint8_t *a) {
         launch_keyip(reinterpret_cast<const KipJob *>(a + off), n, logn, m, s);
-    });
-    P.kernel_launches += 1;
+    }, prefix + "keyip", distinct_bytes(rd, C.N) + 2.0 * n * C.N * 8);
 }
 
 void Rec::lin(const std::vector<LinJob> &jobs) {
@@ -196,10 +290,16 @@ void Rec::lin(const std::vector<LinJob> &jobs) {
     size_t off = P.add_jobs(jobs.data(), jobs.size() * sizeof(LinJob));
     int n = (int)jobs.size(), logn = C.log_n;
     const ModInfo *m = C.nt.mods;
-    P.launches.push_back([=](cudaStream_t s, const uint8_t *a) {
+    std::vector<const void *> rd;
+    for (auto &j : jobs)
+        for (uint32_t a = 0; a < j.nattr; a++) {
+            rd.push_back(j.pt + a * j.pt_stride);
+            rd.push_back(j.w0 + a * j.w_stride);
+            rd.push_back(j.w1 + a * j.w_stride);
+        }
+    P.add_launch([=](cudaStream_t s, const uint8_t *a) {
         launch_lincomb(reinterpret_cast<const LinJob *>(a + off), n, logn, m, s);
-    });
-    P.kernel_launches += 1;
+    }, prefix + "lincomb", distinct_bytes(rd, C.N) + 2.0 * n * C.N * 8);
 }
 
 void Rec::red(const std::vector<RedJob> &jobs) {
@@ -207,10 +307,9 @@ void Rec::red(const std::vector<RedJob> &jobs) {
     size_t off = P.add_jobs(jobs.data(), jobs.size() * sizeof(RedJob));
     int n = (int)jobs.size(), logn = C.log_n;
     const ModInfo *m = C.nt.mods;
-    P.launches.push_back([=](cudaStream_t s, const uint8_t *a) {
+    P.add_launch([=](cudaStream_t s, const uint8_t *a) {
         launch_reduce_i64(reinterpret_cast<const RedJob *>(a + off), n, logn, m, s);
-    });
-    P.kernel_launches += 1;
+    }, prefix + "reduce_i64", 2.0 * n * C.N * 8);
 }
 
 static EwJob ewj(EwOp op, uint32_t prime, u64 *dst, const u64 *a, const u64 *b = nullptr) {
@@ -394,6 +493,11 @@ CtH Rec::keyswitch(int B, int l, const std::function<const u64 *(int, int)> &d, 
     TREQUIRE(K >= 1 && K <= kMaxConvSrc && alpha <= kMaxConvSrc, TETRIS_EINVAL, "keyswitch: K or alpha too large");
     TREQUIRE(dnum <= key.dnum && dnum <= 32, TETRIS_EINVAL, "keyswitch: key has too few digits");
     const int nQP = C.nqp();
+    const std::string saved_prefix = prefix;
+    prefix = "ks." + prefix;
+    P.ks_count += 1;
+    // algorithmic bytes of one batched keyswitch: B inputs, the key limbs it uses once, 2B outputs
+    P.ks_bytes += ((double)B * nl + 2.0 * dnum * ntg + 2.0 * B * nl) * N * 8;
     // 1. d -> coefficient domain
     BufPtr dcoef = P.pool.alloc((size_t)B * nl * N);
     {
@@ -497,6 +601,7 @@ CtH Rec::keyswitch(int B, int l, const std::function<const u64 *(int, int)> &d, 
         }
         ntt(false, jobs, LOAD_CONV, STORE_COMBINE);
     }
+    prefix = saved_prefix;
     return out;
 }
 

@@ -106,9 +106,9 @@ struct NttTables {
 };
 
 // launchers (ntt.cu)
+// pass: 0 = first pass only, 1 = second pass only, -1 = both
 void launch_ntt(bool inverse, int log_n, const NttTables &t, const NttJob *jobs_dev, int njobs, int load_mode,
-                int store_mode, cudaStream_t s);
-int ntt_launch_count(int log_n);
+                int store_mode, cudaStream_t s, int pass = -1);
 
 // ---------------------------------------------------------------------------
 // Elementwise kernels (elementwise.cu).  A "limb list" kernel walks njobs

@@ -205,26 +205,23 @@ void dispatch(int logm, const PassParams &P, int njobs, cudaStream_t st) {
 
 }  // namespace
 
-int ntt_launch_count(int) { return 2; }
-
 void launch_ntt(bool inverse, int log_n, const NttTables &t, const NttJob *jobs_dev, int njobs, int load_mode,
-                int store_mode, cudaStream_t s) {
+                int store_mode, cudaStream_t s, int pass) {
     if (njobs <= 0) return;
     PassParams P;
     P.t = t;
     P.jobs = jobs_dev;
     P.log1 = (log_n + 1) / 2;  // rows: N1 >= N2
     P.log2 = log_n / 2;
-    if (!inverse) {
+    if (pass != 1) {
         P.first = 1; P.load_mode = load_mode; P.store_mode = STORE_PLAIN; P.scale_out = 0;
-        dispatch<false, true>(P.log1, P, njobs, s);
-        P.first = 0; P.load_mode = LOAD_PLAIN; P.store_mode = store_mode;
-        dispatch<false, false>(P.log2, P, njobs, s);
-    } else {
-        P.first = 1; P.load_mode = load_mode; P.store_mode = STORE_PLAIN; P.scale_out = 0;
-        dispatch<true, false>(P.log2, P, njobs, s);
-        P.first = 0; P.load_mode = LOAD_PLAIN; P.store_mode = store_mode; P.scale_out = 1;
-        dispatch<true, true>(P.log1, P, njobs, s);
+        if (!inverse) dispatch<false, true>(P.log1, P, njobs, s);
+        else dispatch<true, false>(P.log2, P, njobs, s);
+    }
+    if (pass != 0) {
+        P.first = 0; P.load_mode = LOAD_PLAIN; P.store_mode = store_mode; P.scale_out = inverse ? 1 : 0;
+        if (!inverse) dispatch<false, false>(P.log2, P, njobs, s);
+        else dispatch<true, true>(P.log1, P, njobs, s);
     }
 }
 

@@ -32,6 +32,11 @@ struct Database {
 
 struct Program;
 
+struct KernelStat {
+    uint32_t launches = 0;
+    double ms = 0, bytes = 0;
+};
+
 struct Ctx {
     int device = 0;
     int log_n = 0;
@@ -53,6 +58,8 @@ struct Ctx {
     cudaStream_t stream = nullptr;
     int blocks_per_launch = 0;
     int use_graph = 1;
+    int profile = 0;
+    std::map<std::string, KernelStat> stats;
     std::map<std::string, std::unique_ptr<Program>> programs;
 
     int L() const { return (int)q.size() - 1; }
@@ -75,12 +82,20 @@ struct CtH {
     }
 };
 
+// One recorded kernel launch: the launcher, a kind tag for profiling and the
+// algorithmic bytes it must move (distinct inputs read once + outputs written).
+struct Launch {
+    std::function<void(cudaStream_t, const uint8_t *)> fn;
+    std::string kind;
+    double bytes = 0;
+};
+
 struct Program {
     Ctx *ctx = nullptr;
     Pool pool;
     std::vector<uint8_t> arena;
     BufPtr arena_dev;
-    std::vector<std::function<void(cudaStream_t, const uint8_t *)>> launches;
+    std::vector<Launch> launches;
     int kernel_launches = 0;
     std::vector<BufPtr> hold;
     // query programs: input staging slots (device pointer, words) and output
@@ -94,12 +109,16 @@ struct Program {
     cudaGraphExec_t exec = nullptr;
     // counters
     int relins = 0, rescales = 0, rotations = 0;
+    int ks_count = 0;
+    double ks_bytes = 0;  // per keyswitch: input d + key limbs used + output, summed
 
     ~Program();
     size_t add_jobs(const void *p, size_t bytes);
     void finalize();
     void run(cudaStream_t s);
     void run_graph(cudaStream_t s);
+    void run_profiled(cudaStream_t s, std::map<std::string, KernelStat> &stats);
+    void add_launch(std::function<void(cudaStream_t, const uint8_t *)> fn, const std::string &kind, double bytes);
 };
 
 class Rec {
@@ -107,6 +126,7 @@ class Rec {
     Rec(Ctx &c, Program &p) : C(c), P(p) {}
     Ctx &C;
     Program &P;
+    std::string prefix;  // prepended to the kind of every launch recorded (profiling scopes)
 
     CtH new_ct(int B, int comps, int level);
     CtH view(const BufPtr &buf, u64 *base, int B, int comps, int level, size_t bstride, size_t cstride, double scale);

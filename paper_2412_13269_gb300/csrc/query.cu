@@ -241,8 +241,7 @@ static std::unique_ptr<Program> record_query(Ctx &C, const Database &db, const Q
         const double *mr = reinterpret_cast<const double *>(db.mask_real->ptr);
         int64_t *mip = reinterpret_cast<int64_t *>(mi->ptr);
         const double ms = pl.mask_scale;
-        P->launches.push_back([=](cudaStream_t s, const uint8_t *) { round_scale(mr, mip, N, ms, s); });
-        P->kernel_launches += 1;
+        P->add_launch([=](cudaStream_t s, const uint8_t *) { round_scale(mr, mip, N, ms, s); }, "round_scale", 16.0 * N);
         std::vector<NttJob> jobs;
         for (int i = 0; i <= pl.l_u; i++) {
             NttJob j{};
@@ -342,7 +341,8 @@ void evaluate_query(Ctx &C, uint32_t dbh, const tetris_query *q, tetris_ct_out *
     for (uint32_t j = 0; j < q->n_attrs; j++) put(q->w[j]);
     for (uint32_t k = 0; k <= q->f_degree; k++) put(q->f_coeffs[k]);
     put(*q->threshold);
-    if (C.use_graph) P.run_graph(s);
+    if (C.profile) P.run_profiled(s, C.stats);
+    else if (C.use_graph) P.run_graph(s);
     else P.run(s);
     TCHECK_CUDA(cudaMemcpyAsync(out->data, P.out_base, P.out_words * 8,
                                 device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, s));
