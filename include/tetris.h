@@ -241,6 +241,36 @@ enum {
 int tetris_op(tetris_ctx *ctx, int opcode, const tetris_ct_in *a, const tetris_ct_in *b,
               int64_t arg, tetris_ct_out *out);
 
+/* ---------------------------------------------------------------------------
+ * Allocation-free rescale (the paper has no counterpart; this is an
+ * interface for callers that cannot let the library allocate).
+ *
+ * cudaFree synchronises the whole device and cudaMalloc fails or fragments
+ * once a serving process or another framework's caching allocator has
+ * reserved the GPU, so a caller that drives the GPU that way may not let a
+ * library allocate behind its back.  This call allocates nothing: in and out
+ * are caller-owned device buffers and its scratch is one fixed device array
+ * inside the library (tetris_noalloc_scratch_bytes() bytes: the top limb of
+ * up to 3 components at N <= 2^16 plus the job tables of two transforms),
+ * which every GPU that loads the library holds until the process exits.
+ *
+ * in:  device pointer, [ncomp][level+1][N] uint64 in the library's NTT order
+ *      (the order TETRIS_OP_NTT returns), 1 <= level <= n_q - 1, ncomp <= 3.
+ * out: device pointer, [ncomp][level][N], same order; must not overlap in.
+ * stream: cudaStream_t (NULL = legacy default stream); the call enqueues the
+ *      work and returns; it may wait for earlier work in that stream while
+ *      it copies its job tables from host memory.
+ * The first call on each device resolves the scratch array's address there
+ * (with that device current).  All calls share the array and it keeps the
+ * last call's contents (nothing in it needs to start at zero); calls whose
+ * work overlaps on the GPU race on it, so callers serialise them.
+ * Errors: TETRIS_EINVAL for sizes beyond the maximum, overlap or null
+ * buffers, TETRIS_ELEVEL for a level outside [1, n_q - 1].
+ * ------------------------------------------------------------------------- */
+int tetris_rescale_ntt_noalloc(tetris_ctx *ctx, const uint64_t *in, uint64_t *out, uint32_t level,
+                               uint32_t ncomp, void *stream);
+size_t tetris_noalloc_scratch_bytes(void);
+
 #ifdef __cplusplus
 }
 #endif

@@ -96,6 +96,8 @@ SIGNATURES = {
     "tetris_get_option": [_vp, C.c_int, C.POINTER(_i64)],
     "tetris_op": [_vp, C.c_int, C.POINTER(CtIn), C.POINTER(CtIn), _i64, C.POINTER(CtOut)],
     "tetris_get_kernel_stats": [_vp, C.POINTER(KernelStat), _u32, C.POINTER(_u32)],
+    "tetris_rescale_ntt_noalloc": [_vp, _vp, _vp, _u32, _u32, _vp],
+    "tetris_noalloc_scratch_bytes": [],
 }
 
 
@@ -107,7 +109,8 @@ def lib():
     for name, args in SIGNATURES.items():
         f = getattr(so, name)
         f.argtypes = args
-        f.restype = C.c_char_p if name == "tetris_last_error" else (None if name == "tetris_ctx_destroy" else C.c_int)
+        f.restype = {"tetris_last_error": C.c_char_p, "tetris_ctx_destroy": None,
+                     "tetris_noalloc_scratch_bytes": C.c_size_t}.get(name, C.c_int)
     return so
 
 
@@ -255,6 +258,11 @@ class Ctx:
         n = C.c_uint32()
         check(lib().tetris_get_kernel_stats(self.h, buf, 256, C.byref(n)))
         return {buf[i].kind.decode(): (buf[i].launches, buf[i].total_ms, buf[i].alg_bytes) for i in range(n.value)}
+
+    def rescale_ntt_noalloc(self, src, dst, level: int, ncomp: int, stream: int = 0):
+        """Allocation-free rescale of a device-resident NTT-order ciphertext
+        (torch CUDA tensors); enqueued on ``stream``."""
+        check(lib().tetris_rescale_ntt_noalloc(self.h, _ptr(src), _ptr(dst), level, ncomp, stream))
 
     def plan(self, db: int, degree: int, stages: int) -> PlanInfo:
         p = PlanInfo()

@@ -708,6 +708,17 @@ int tetris_get_option(tetris_ctx *ctx, int option, int64_t *value) {
     });
 }
 
+int tetris_rescale_ntt_noalloc(tetris_ctx *ctx, const uint64_t *in, uint64_t *out, uint32_t level, uint32_t ncomp,
+                               void *stream) {
+    return guarded([&] {
+        TREQUIRE(ctx, TETRIS_EINVAL, "null context");
+        cudaSetDevice(ctx->c.device);
+        rescale_ntt_noalloc(ctx->c, in, out, (int)level, (int)ncomp, reinterpret_cast<cudaStream_t>(stream));
+    });
+}
+
+size_t tetris_noalloc_scratch_bytes(void) { return noalloc_scratch_bytes(); }
+
 int tetris_get_kernel_stats(tetris_ctx *ctx, tetris_kernel_stat *out, uint32_t cap, uint32_t *n_out) {
     return guarded([&] {
         TREQUIRE(ctx && n_out && (out || cap == 0), TETRIS_EINVAL, "null pointer");

@@ -170,4 +170,8 @@ void evaluate_query(Ctx &C, uint32_t db, const tetris_query *q, tetris_ct_out *o
 void plan_info(Ctx &C, uint32_t db, uint32_t degree, uint32_t stages, tetris_plan_info *out);
 void drop_programs_of_db(Ctx &C, uint32_t db);
 
+// noalloc.cu
+void rescale_ntt_noalloc(Ctx &C, const u64 *in, u64 *out, int level, int ncomp, cudaStream_t s);
+size_t noalloc_scratch_bytes();
+
 }  // namespace tetris
