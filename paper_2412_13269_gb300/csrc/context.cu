@@ -194,7 +194,15 @@ double distinct_bytes(const std::vector<const void *> &ptrs, size_t N) {
     v.erase(std::unique(v.begin(), v.end()), v.end());
     return (double)v.size() * N * 8;
 }
-const char *load_name(int m) { return m == LOAD_CONV ? "conv" : m == LOAD_INT64 ? "int64" : "plain"; }
+const char *load_name(int m) {
+    switch (m) {
+        case LOAD_CONV: return "conv";
+        case LOAD_CONV_PRE: return "convpre";
+        case LOAD_REDUCE: return "reduce";
+        case LOAD_INT64: return "int64";
+    }
+    return "plain";
+}
 const char *ew_name(int op) {
     switch (op) {
         case EW_ADD: return "add";
@@ -220,7 +228,7 @@ void Rec::ntt(bool inverse, const std::vector<NttJob> &jobs, int load_mode, int 
     const size_t N = C.N;
     std::vector<const void *> srcs, bases, extras;
     for (auto &j : jobs) {
-        if (load_mode == LOAD_CONV)
+        if (load_mode == LOAD_CONV || load_mode == LOAD_CONV_PRE)
             for (uint32_t s = 0; s < j.nsrc; s++) srcs.push_back(j.src + s * j.src_stride);
         else
             srcs.push_back(j.src);
@@ -236,7 +244,7 @@ void Rec::ntt(bool inverse, const std::vector<NttJob> &jobs, int load_mode, int 
     if (store_mode == STORE_COMBINE) b2 += distinct_bytes(bases, N) + distinct_bytes(extras, N);
     P.add_launch([=](cudaStream_t s, const uint8_t *a) {
         launch_ntt(inverse, logn, t, reinterpret_cast<const NttJob *>(a + off), n, load_mode, store_mode, s, 1);
-    }, prefix + dir + "_p2_" + (store_mode == STORE_COMBINE ? "combine" : "plain"), b2);
+    }, prefix + dir + "_p2_" + (store_mode == STORE_COMBINE ? "combine" : store_mode == STORE_SCALED ? "scaled" : "plain"), b2);
 }
 
 void Rec::ew(const std::vector<EwJob> &jobs) {
@@ -458,6 +466,9 @@ CtH Rec::tensor(const CtH &a, const CtH &b) {
 
 // Fast base conversion from the consecutive primes first..first+nsrc-1 to
 // dst_prime: x -> sum_s [(x_s + add_s) * (Qs/q_s)^-1]_{q_s} * (Qs/q_s mod q_dst).
+// The recorded transforms fold the first factor into the inverse NTT that
+// produces the sources (STORE_SCALED) and load with LOAD_CONV_PRE, which only
+// uses c2 = Qs/q_s mod q_dst.
 NttJob Rec::conv_job(uint32_t dst_prime, const u64 *src, uint32_t first, int nsrc, const u64 *adds) {
     NttJob j{};
     j.src = src;
@@ -498,19 +509,30 @@ CtH Rec::keyswitch(int B, int l, const std::function<const u64 *(int, int)> &d, 
     P.ks_count += 1;
     // algorithmic bytes of one batched keyswitch: B inputs, the key limbs it uses once, 2B outputs
     P.ks_bytes += ((double)B * nl + 2.0 * dnum * ntg + 2.0 * B * nl) * N * 8;
-    // 1. d -> coefficient domain
+    // 1. d -> coefficient domain, each limb already multiplied by its digit's
+    //    [(Q_j/q_i)^-1]_{q_i} (folded with N^-1 into the transform's last store)
     BufPtr dcoef = P.pool.alloc((size_t)B * nl * N);
     {
         std::vector<NttJob> jobs;
-        for (int b = 0; b < B; b++)
-            for (int i = 0; i < nl; i++) {
-                NttJob j{};
+        for (int i = 0; i < nl; i++) {
+            const int lo = (i / alpha) * alpha, hi = std::min(nl, lo + alpha);
+            const u64 qi = C.q[i];
+            u64 hat = 1 % qi;
+            for (int r = lo; r < hi; r++)
+                if (r != i) hat = h_mulmod(hat, C.q[r] % qi, qi);
+            NttJob proto{};
+            proto.prime = i;
+            proto.mul = h_mulmod(C.mods_host[i].ninv, h_invmod(hat, qi), qi);
+            proto.mul_sh = h_shoup(proto.mul, qi);
+            proto.conv_sub = 0;
+            for (int b = 0; b < B; b++) {
+                NttJob j = proto;
                 j.src = d(b, i);
                 j.dst = dcoef->ptr + ((size_t)b * nl + i) * N;
-                j.prime = i;
                 jobs.push_back(j);
             }
-        ntt(true, jobs, LOAD_PLAIN, STORE_PLAIN);
+        }
+        ntt(true, jobs, LOAD_PLAIN, STORE_SCALED);
     }
     // 2. ModUp: digit j -> every prime outside it, then NTT (conversion fused into the load)
     BufPtr mu = P.pool.alloc((size_t)B * dnum * ntg * N);
@@ -530,7 +552,7 @@ CtH Rec::keyswitch(int B, int l, const std::function<const u64 *(int, int)> &d, 
                 }
             }
         }
-        ntt(false, jobs, LOAD_CONV, STORE_PLAIN);
+        ntt(false, jobs, LOAD_CONV_PRE, STORE_PLAIN);
     }
     // 3. key inner product over Q_l P
     BufPtr acc = P.pool.alloc((size_t)B * 2 * ntg * N);
@@ -557,27 +579,37 @@ CtH Rec::keyswitch(int B, int l, const std::function<const u64 *(int, int)> &d, 
     }
     mu.reset();
     dcoef.reset();
-    // 4. ModDown: special limbs to the coefficient domain
+    // 4. ModDown: special limbs to the coefficient domain, stored as
+    //    [(c_k + floor(P/2)) * (P/p_k)^-1]_{p_k} (floor(P/2) = (p_k - 1)/2 mod p_k)
     BufPtr pc = P.pool.alloc((size_t)B * 2 * K * N);
     {
         std::vector<NttJob> jobs;
-        for (int b = 0; b < B; b++)
-            for (int c = 0; c < 2; c++)
-                for (int k = 0; k < K; k++) {
-                    NttJob j{};
+        for (int k = 0; k < K; k++) {
+            const uint32_t gp = C.L() + 1 + k;
+            const u64 pk = C.p[k];
+            u64 hat = 1 % pk;
+            for (int r = 0; r < K; r++)
+                if (r != k) hat = h_mulmod(hat, C.p[r] % pk, pk);
+            const u64 c1 = h_invmod(hat, pk);
+            NttJob proto{};
+            proto.prime = gp;
+            proto.mul = h_mulmod(C.mods_host[gp].ninv, c1, pk);
+            proto.mul_sh = h_shoup(proto.mul, pk);
+            proto.conv_sub = h_mulmod((pk - 1) / 2, c1, pk);
+            for (int b = 0; b < B; b++)
+                for (int c = 0; c < 2; c++) {
+                    NttJob j = proto;
                     j.src = accl(b, c, nl + k);
                     j.dst = pc->ptr + (((size_t)b * 2 + c) * K + k) * N;
-                    j.prime = C.L() + 1 + k;
                     jobs.push_back(j);
                 }
-        ntt(true, jobs, LOAD_PLAIN, STORE_PLAIN);
+        }
+        ntt(true, jobs, LOAD_PLAIN, STORE_SCALED);
     }
     // 5. convert (c_P + floor(P/2)) to each q_i, subtract [floor(P/2)]_{q_i} from
     //    every coefficient, NTT, and combine: out_i = extra + (acc_i - x) * P^-1
     CtH out = new_ct(B, 2, l);
     {
-        u64 adds[kMaxConvSrc];
-        for (int k = 0; k < K; k++) adds[k] = (C.p[k] - 1) / 2;  // floor(P/2) = (P-1)/2 is (p_k-1)/2 mod p_k
         std::vector<NttJob> jobs;
         for (int i = 0; i < nl; i++) {
             const u64 qi = C.q[i];
@@ -585,7 +617,7 @@ CtH Rec::keyswitch(int B, int l, const std::function<const u64 *(int, int)> &d, 
             for (int k = 0; k < K; k++) pm = h_mulmod(pm, C.p[k] % qi, qi);
             const u64 half = h_mulmod((pm + qi - 1) % qi, h_invmod(2, qi), qi);
             const u64 pinv = h_invmod(pm, qi);
-            NttJob proto = conv_job(i, nullptr, C.L() + 1, K, adds);
+            NttJob proto = conv_job(i, nullptr, C.L() + 1, K, nullptr);
             proto.conv_sub = half;
             proto.mul = pinv;
             proto.mul_sh = h_shoup(pinv, qi);
@@ -599,7 +631,7 @@ CtH Rec::keyswitch(int B, int l, const std::function<const u64 *(int, int)> &d, 
                     jobs.push_back(jb);
                 }
         }
-        ntt(false, jobs, LOAD_CONV, STORE_COMBINE);
+        ntt(false, jobs, LOAD_CONV_PRE, STORE_COMBINE);
     }
     prefix = saved_prefix;
     return out;
@@ -622,6 +654,8 @@ CtH Rec::rescale(const CtH &a) {
     const int l = a.level;
     TREQUIRE(l >= 1, TETRIS_ELEVEL, "rescale at level 0");
     const size_t N = C.N;
+    const u64 ql = C.q[l], half = (ql - 1) / 2;
+    // top limb to the coefficient domain, stored as [a_l + floor(q_l/2)]_{q_l}
     BufPtr tmp = P.pool.alloc((size_t)a.B * a.comps * N);
     {
         std::vector<NttJob> jobs;
@@ -631,17 +665,20 @@ CtH Rec::rescale(const CtH &a) {
                 j.src = a.limb(b, c, l);
                 j.dst = tmp->ptr + ((size_t)b * a.comps + c) * N;
                 j.prime = l;
+                j.mul = C.mods_host[l].ninv;
+                j.mul_sh = C.mods_host[l].ninv_sh;
+                j.conv_sub = half;
                 jobs.push_back(j);
             }
-        ntt(true, jobs, LOAD_PLAIN, STORE_PLAIN);
+        ntt(true, jobs, LOAD_PLAIN, STORE_SCALED);
     }
     CtH o = new_ct(a.B, a.comps, l - 1);
     o.scale = a.scale / (double)C.q[l];
-    const u64 ql = C.q[l], half = (ql - 1) / 2;
     std::vector<NttJob> jobs;
     for (int i = 0; i < l; i++) {
         const u64 qi = C.q[i];
-        NttJob proto = conv_job(i, nullptr, l, 1, &half);
+        NttJob proto{};
+        proto.prime = i;
         proto.conv_sub = half % qi;
         proto.mul = h_invmod(ql % qi, qi);
         proto.mul_sh = h_shoup(proto.mul, qi);
@@ -654,7 +691,7 @@ CtH Rec::rescale(const CtH &a) {
                 jobs.push_back(jb);
             }
     }
-    ntt(false, jobs, LOAD_CONV, STORE_COMBINE);
+    ntt(false, jobs, LOAD_REDUCE, STORE_COMBINE);
     P.rescales++;
     return o;
 }

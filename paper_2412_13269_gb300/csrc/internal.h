@@ -75,8 +75,13 @@ class Pool {
 // ---------------------------------------------------------------------------
 // Kernel job descriptors
 // ---------------------------------------------------------------------------
-enum LoadMode { LOAD_PLAIN = 0, LOAD_CONV = 1, LOAD_INT64 = 2 };
-enum StoreMode { STORE_PLAIN = 0, STORE_COMBINE = 1 };
+// LOAD_CONV:     sum_s [(src_s + add_s) * c1_s]_{q_s} * c2_s - conv_sub
+// LOAD_CONV_PRE: sum_s src_s * c2_s - conv_sub (sources already scaled by c1_s, see STORE_SCALED)
+// LOAD_REDUCE:   [src]_{q_dst} - conv_sub (a single source of another prime)
+enum LoadMode { LOAD_PLAIN = 0, LOAD_CONV = 1, LOAD_INT64 = 2, LOAD_CONV_PRE = 3, LOAD_REDUCE = 4 };
+// STORE_SCALED (inverse transforms only): x * mul + conv_sub, where mul already
+// carries N^-1; it precomputes the per-source factor of a following conversion.
+enum StoreMode { STORE_PLAIN = 0, STORE_COMBINE = 1, STORE_SCALED = 2 };
 
 // One limb transform.  LOAD_CONV computes, per coefficient,
 //   sum_s [ (src_s + add_s) * c1_s ]_{q_s} * c2_s - conv_sub  mod q_dst

@@ -76,24 +76,20 @@ void rescale_ntt_noalloc(Ctx &C, const u64 *in, u64 *out, int level, int ncomp, 
 
     const u64 ql = C.q[level], half = (ql - 1) / 2;
     std::vector<NttJob> ji, jf;
-    for (int c = 0; c < ncomp; c++) {
+    for (int c = 0; c < ncomp; c++) {  // top limb -> [a_l + floor(q_l/2)]_{q_l}, coefficient domain
         NttJob j{};
         j.src = in + ((size_t)c * (level + 1) + level) * N;
         j.dst = top + (size_t)c * N;
         j.prime = level;
+        j.mul = C.mods_host[level].ninv;
+        j.mul_sh = C.mods_host[level].ninv_sh;
+        j.conv_sub = half;
         ji.push_back(j);
     }
     for (int i = 0; i < level; i++) {
         const u64 qi = C.q[i];
         NttJob j{};
-        j.nsrc = 1;
-        j.src_stride = N;
         j.prime = i;
-        j.src_prime[0] = level;
-        j.add_s[0] = half;
-        j.c1[0] = 1;
-        j.c1_sh[0] = h_shoup(1, ql);
-        j.c2[0] = 1;
         j.conv_sub = half % qi;
         j.mul = h_invmod(ql % qi, qi);
         j.mul_sh = h_shoup(j.mul, qi);
@@ -108,8 +104,8 @@ void rescale_ntt_noalloc(Ctx &C, const u64 *in, u64 *out, int level, int ncomp, 
     // job tables: copied from pageable host memory (staged before return)
     TCHECK_CUDA(cudaMemcpyAsync(jobs_inv, ji.data(), ji.size() * sizeof(NttJob), cudaMemcpyHostToDevice, s));
     TCHECK_CUDA(cudaMemcpyAsync(jobs_fwd, jf.data(), jf.size() * sizeof(NttJob), cudaMemcpyHostToDevice, s));
-    launch_ntt(true, C.log_n, C.nt, jobs_inv, (int)ji.size(), LOAD_PLAIN, STORE_PLAIN, s);
-    launch_ntt(false, C.log_n, C.nt, jobs_fwd, (int)jf.size(), LOAD_CONV, STORE_COMBINE, s);
+    launch_ntt(true, C.log_n, C.nt, jobs_inv, (int)ji.size(), LOAD_PLAIN, STORE_SCALED, s);
+    launch_ntt(false, C.log_n, C.nt, jobs_fwd, (int)jf.size(), LOAD_REDUCE, STORE_COMBINE, s);
     TCHECK_CUDA(cudaGetLastError());
 }
 

@@ -11,15 +11,19 @@
 // N1-point sub-problem) and a row pass (the remaining log N2 stages within
 // each contiguous row).  Inside a pass a CTA stages its tile in shared
 // memory; each thread holds E = 16 elements in registers and runs four
-// butterfly stages per visit (radix-16 groups), so a 256-point sub-problem
-// takes two shared-memory round trips.  Stage bit b of a sub-problem of size
+// butterfly stages per visit (radix-16 groups).  A thread loads its first
+// group straight from global memory and stores its last group straight back
+// (both coalesced across the warp), so a 256-point sub-problem needs a single
+// shared-memory exchange.  Stage bit b of a sub-problem of size
 // M uses twiddle index (M >> (b+1)) * o + (r >> (b+1)), with o = 1 in the
 // column pass and o = N1 + row in the row pass.
 //
 // Load modes fuse the producer: plain, int64 -> residue, or a fast base
 // conversion from up to four source limbs (ModUp / ModDown / rescale), less a
 // per-coefficient constant.  The combine store fuses the consumer:
-// (extra) + (base - x) * mul.
+// (extra) + (base - x) * mul.  Butterflies are lazy (Harvey): values stay in
+// [0, 4q) (forward) or [0, 2q) (inverse) between stages and between the two
+// passes, and are reduced once when the second pass stores them.
 #include "internal.h"
 
 namespace tetris {
@@ -37,170 +41,279 @@ struct PassParams {
     int first;
 };
 
-__device__ __forceinline__ u64 load_elem(const NttJob &J, const PassParams &P, size_t g, u64 q) {
-    if (!P.first) return J.dst[g];
-    if (P.load_mode == LOAD_PLAIN) return J.src[g];
-    if (P.load_mode == LOAD_INT64) {
-        int64_t x = reinterpret_cast<const int64_t *>(J.src)[g];
-        if (x >= 0) return (u64)x % q;
-        u64 r = (u64)(-(x + 1)) % q;  // -(x+1) >= 0 avoids overflow at INT64_MIN
-        return q - 1 - r;
-    }
-    // LOAD_CONV
-    Acc128 acc = {0, 0};
-    for (uint32_t s = 0; s < J.nsrc; s++) {
-        const u64 qs = P.t.mods[J.src_prime[s]].q;
-        u64 y = add_mod(J.src[s * J.src_stride + g], J.add_s[s], qs);
-        y = shoup(y, J.c1[s], J.c1_sh[s], qs);
-        acc_mad(acc, y, J.c2[s]);
-    }
-    return sub_mod(reduce128(acc.hi, acc.lo, P.t.mods[J.prime]), J.conv_sub, q);
+// Harvey's lazy butterflies.  Forward (Cooley-Tukey): inputs in [0, 4q),
+// outputs in [0, 4q).  Inverse (Gentleman-Sande): inputs and outputs in [0, 2q).
+__device__ __forceinline__ void ct_bfly(u64 &x, u64 &y, u64 w, u64 wsh, u64 q, u64 q2) {
+    u64 X = x >= q2 ? x - q2 : x;
+    u64 T = shoup_lazy(y, w, wsh, q);
+    x = X + T;
+    y = X - T + q2;
+}
+__device__ __forceinline__ void gs_bfly(u64 &x, u64 &y, u64 w, u64 wsh, u64 q, u64 q2) {
+    u64 S = x + y;
+    S = S >= q2 ? S - q2 : S;
+    u64 D = x - y + q2;
+    x = S;
+    y = shoup_lazy(D, w, wsh, q);
 }
 
-template <int LOGM, bool INV, bool COL>
-__global__ void __launch_bounds__(kThreads) ntt_pass_kernel(PassParams P) {
+// Register window of butterfly group g: the thread holds the E elements whose
+// row index differs only in bits [lo, lo + LOGE); stages run on bits [blo, bhi].
+template <int LOGM, int LOGE, bool INV>
+struct Group {
+    __host__ __device__ static constexpr int bhi(int g) {
+        return INV ? ((g * LOGE + LOGE - 1) > LOGM - 1 ? LOGM - 1 : g * LOGE + LOGE - 1) : LOGM - 1 - g * LOGE;
+    }
+    __host__ __device__ static constexpr int blo(int g) {
+        return INV ? g * LOGE : ((LOGM - 1 - g * LOGE - LOGE + 1) < 0 ? 0 : LOGM - 1 - g * LOGE - LOGE + 1);
+    }
+    __host__ __device__ static constexpr int lo(int g) {
+        return INV ? (g * LOGE < LOGM - LOGE ? g * LOGE : LOGM - LOGE) : blo(g);
+    }
+};
+
+// MODE: 0/1/2 = first pass loading plain / int64 / base conversion;
+//       3/4 = second pass storing plain / combined.
+//       5/6 = first pass loading pre-scaled conversion sources / a reduction;
+//       7 = second pass of an inverse transform storing x * mul + add.
+enum { M_PLAIN = 0, M_INT64 = 1, M_CONV = 2, M_STORE = 3, M_COMBINE = 4, M_CONVPRE = 5, M_REDUCE = 6, M_SCALED = 7 };
+constexpr bool is_second(int m) { return m == M_STORE || m == M_COMBINE || m == M_SCALED; }
+
+template <int LOGM, bool INV, bool COL, int MODE>
+__global__ void __launch_bounds__(kThreads, (MODE == M_CONV || MODE == M_CONVPRE) ? 2 : 3) ntt_pass_kernel(PassParams P) {
     constexpr int M = 1 << LOGM;
     constexpr int LOGE = LOGM >= 4 ? 4 : LOGM;
     constexpr int E = 1 << LOGE;
     constexpr int T = M / E;
     constexpr int NG = (LOGM + LOGE - 1) / LOGE;
+    using G = Group<LOGM, LOGE, INV>;
     extern __shared__ u64 sm[];
+    __shared__ NttJob J;
 
-    const NttJob &J = P.jobs[blockIdx.y];
+    {   // the job descriptor, once per CTA
+        const u64 *gj = reinterpret_cast<const u64 *>(P.jobs + blockIdx.y);
+        u64 *dj = reinterpret_cast<u64 *>(&J);
+        for (int i = threadIdx.x; i < (int)(sizeof(NttJob) / 8); i += blockDim.x) dj[i] = gj[i];
+    }
+    __syncthreads();
     const int N1 = 1 << P.log1, N2 = 1 << P.log2;
     const int nsub = COL ? N2 : N1;
     const int sub_cta = min(kThreads / T, nsub);
     const int sub0 = blockIdx.x * sub_cta;
-    const int nthr = sub_cta * T;
     const int tid = threadIdx.x;
-    if (tid >= nthr) return;  // never taken for the supported sizes; keeps syncs uniform
     const ModInfo mi = P.t.mods[J.prime];
-    const u64 q = mi.q;
+    const u64 q = mi.q, q2 = 2 * q;
     const size_t N = (size_t)N1 * N2;
     const u64 *tw = (INV ? P.t.itw : P.t.tw) + (size_t)J.prime * N;
     const u64 *twsh = (INV ? P.t.itw_sh : P.t.tw_sh) + (size_t)J.prime * N;
 
-    // shared layout: column pass [r][sub], row pass [sub][r] padded every 16 words
-    auto smidx = [&](int r, int s) -> int {
-        return COL ? r * sub_cta + s : s * (M + M / 16) + r + (r >> 4);
-    };
-    auto gidx = [&](int r, int s) -> size_t {
-        return COL ? (size_t)r * N2 + sub0 + s : (size_t)(sub0 + s) * N2 + r;
-    };
-
-    // 1. load the tile
-    for (int l = tid; l < M * sub_cta; l += nthr) {
-        int r, s;
-        if (COL) {
-            r = l / sub_cta;
-            s = l - r * sub_cta;
-        } else {
-            s = l >> LOGM;
-            r = l & (M - 1);
-        }
-        sm[smidx(r, s)] = load_elem(J, P, gidx(r, s), q);
-    }
-    __syncthreads();
-
-    // 2. butterfly groups
+    // thread -> (sub-problem s, lane t): consecutive threads take consecutive
+    // columns in the column pass and consecutive lanes of a row in the row pass
     const int s = COL ? tid % sub_cta : tid / T;
     const int t = COL ? tid / sub_cta : tid % T;
     const u64 o = COL ? 1 : (u64)(N1 + sub0 + s);
+    auto smidx = [&](int r) -> int { return COL ? r * sub_cta + s : s * (M + M / 16) + r + (r >> 4); };
+    auto gidx = [&](int r) -> size_t { return COL ? (size_t)r * N2 + sub0 + s : (size_t)(sub0 + s) * N2 + r; };
+    auto row = [&](int g, int k) -> int {
+        const int l = G::lo(g);
+        return (t & ((1 << l) - 1)) | (k << l) | ((t >> l) << (l + LOGE));
+    };
+
+    u64 x[E];
+    // 1. load straight into the first group's registers, through the producer's load mode
+    if (is_second(MODE)) {
+#pragma unroll
+        for (int k = 0; k < E; k++) x[k] = J.dst[gidx(row(0, k))];
+    } else if (MODE == M_REDUCE) {
+        const u64 *src = J.src;
+        const u64 sub = J.conv_sub;
+#pragma unroll
+        for (int k = 0; k < E; k++) {
+            u64 v = src[gidx(row(0, k))];
+            v = v - __umul64hi(v, mi.one_sh) * q;  // Shoup product with w = 1: [0, 2q)
+            v = v >= q ? v - q : v;
+            x[k] = sub_mod(v, sub, q);
+        }
+    } else if (MODE == M_CONVPRE) {
+        const u64 *src = J.src;
+        const u64 stride = J.src_stride;
+        const int ns = (int)J.nsrc;
+        const u64 sub = J.conv_sub;
+        constexpr int C8 = E < 8 ? E : 8;
+#pragma unroll
+        for (int k0 = 0; k0 < E; k0 += C8) {
+            Acc128 acc[C8];
+#pragma unroll
+            for (int k = 0; k < C8; k++) acc[k] = {0, 0};
+#pragma unroll
+            for (int sidx = 0; sidx < kMaxConvSrc; sidx++) {
+                if (sidx < ns) {
+                    const u64 c2 = J.c2[sidx];
+                    const u64 *sp = src + sidx * stride;
+#pragma unroll
+                    for (int k = 0; k < C8; k++) acc_mad(acc[k], sp[gidx(row(0, k0 + k))], c2);
+                }
+            }
+#pragma unroll
+            for (int k = 0; k < C8; k++) x[k0 + k] = sub_mod(reduce128(acc[k].hi, acc[k].lo, mi), sub, q);
+        }
+    } else if (MODE == M_PLAIN) {
+        const u64 *src = J.src;
+#pragma unroll
+        for (int k = 0; k < E; k++) x[k] = src[gidx(row(0, k))];
+    } else if (MODE == M_INT64) {
+        const int64_t *src = reinterpret_cast<const int64_t *>(J.src);
+#pragma unroll
+        for (int k = 0; k < E; k++) {
+            const int64_t v = src[gidx(row(0, k))];
+            x[k] = v >= 0 ? (u64)v % q : q - 1 - ((u64)(-(v + 1)) % q);
+        }
+    } else {  // LOAD_CONV: sum_s [(src_s + add_s) c1_s]_{q_s} c2_s - conv_sub, four elements at a time
+        const u64 *src = J.src;
+        const u64 stride = J.src_stride;
+        const int ns = (int)J.nsrc;
+        const u64 sub = J.conv_sub;
+        constexpr int C4 = E < 4 ? E : 4;
+#pragma unroll
+        for (int k0 = 0; k0 < E; k0 += C4) {
+            Acc128 acc[C4];
+#pragma unroll
+            for (int k = 0; k < C4; k++) acc[k] = {0, 0};
+#pragma unroll
+            for (int sidx = 0; sidx < kMaxConvSrc; sidx++) {
+                if (sidx < ns) {
+                    const u64 qs = P.t.mods[J.src_prime[sidx]].q;
+                    const u64 add = J.add_s[sidx], c1 = J.c1[sidx], c1sh = J.c1_sh[sidx], c2 = J.c2[sidx];
+                    const u64 *sp = src + sidx * stride;
+                    u64 v[C4];
+#pragma unroll
+                    for (int k = 0; k < C4; k++) v[k] = sp[gidx(row(0, k0 + k))];
+#pragma unroll
+                    for (int k = 0; k < C4; k++) acc_mad(acc[k], shoup(add_mod(v[k], add, qs), c1, c1sh, qs), c2);
+                }
+            }
+#pragma unroll
+            for (int k = 0; k < C4; k++) x[k0 + k] = sub_mod(reduce128(acc[k].hi, acc[k].lo, mi), sub, q);
+        }
+    }
+
+    // 2. butterfly groups; one shared-memory exchange between consecutive groups
 #pragma unroll
     for (int g = 0; g < NG; g++) {
-        int blo, bhi, lo;
-        if (!INV) {
-            bhi = LOGM - 1 - g * LOGE;
-            blo = bhi - LOGE + 1 < 0 ? 0 : bhi - LOGE + 1;
-            lo = blo;
-        } else {
-            blo = g * LOGE;
-            bhi = blo + LOGE - 1 > LOGM - 1 ? LOGM - 1 : blo + LOGE - 1;
-            lo = blo < LOGM - LOGE ? blo : LOGM - LOGE;
+        if (g > 0) {
+            __syncthreads();  // (g > 1) every thread has read the previous exchange
+#pragma unroll
+            for (int k = 0; k < E; k++) sm[smidx(row(g - 1, k))] = x[k];
+            __syncthreads();
+#pragma unroll
+            for (int k = 0; k < E; k++) x[k] = sm[smidx(row(g, k))];
         }
+        const int blo = G::blo(g), bhi = G::bhi(g), lo = G::lo(g);
         const int tlow = t & ((1 << lo) - 1);
         const int thigh = (t >> lo) << (lo + LOGE);
-        u64 x[E];
-#pragma unroll
-        for (int k = 0; k < E; k++) x[k] = sm[smidx(tlow | (k << lo) | thigh, s)];
 #pragma unroll
         for (int st = 0; st < LOGE; st++) {
             const int b = INV ? blo + st : bhi - st;
-            if (INV ? (b > bhi) : (b < blo)) break;
-            const int half = 1 << (b - lo);
+            if (b >= blo && b <= bhi) {
+                const int bb = b - lo;
 #pragma unroll
-            for (int k = 0; k < E; k++) {
-                if (k & half) continue;
-                const int r0 = tlow | (k << lo) | thigh;
-                const u64 widx = (u64)(M >> (b + 1)) * o + (u64)(r0 >> (b + 1));
-                const u64 w = __ldg(tw + widx), wsh = __ldg(twsh + widx);
-                const u64 u = x[k], v = x[k | half];
-                if (!INV) {
-                    const u64 vw = shoup(v, w, wsh, q);
-                    x[k] = add_mod(u, vw, q);
-                    x[k | half] = sub_mod(u, vw, q);
-                } else {
-                    x[k] = add_mod(u, v, q);
-                    x[k | half] = shoup(sub_mod(u, v, q), w, wsh, q);
+                for (int k = 0; k < E; k++) {
+                    if (k & (1 << bb)) continue;
+                    // pairs that agree above bit bb share a twiddle; load it once
+                    if (k & ((1 << bb) - 1)) continue;
+                    const int r0 = tlow | (k << lo) | thigh;
+                    const u64 widx = (u64)(M >> (b + 1)) * o + (u64)(r0 >> (b + 1));
+                    const u64 w = __ldg(tw + widx), wsh = __ldg(twsh + widx);
+#pragma unroll
+                    for (int j = 0; j < E; j++) {
+                        if (j >= (1 << bb)) continue;
+                        if (!INV) ct_bfly(x[k + j], x[k + j + (1 << bb)], w, wsh, q, q2);
+                        else gs_bfly(x[k + j], x[k + j + (1 << bb)], w, wsh, q, q2);
+                    }
                 }
             }
         }
-#pragma unroll
-        for (int k = 0; k < E; k++) sm[smidx(tlow | (k << lo) | thigh, s)] = x[k];
-        __syncthreads();
     }
 
-    // 3. store
-    for (int l = tid; l < M * sub_cta; l += nthr) {
-        int r, ss;
-        if (COL) {
-            r = l / sub_cta;
-            ss = l - r * sub_cta;
-        } else {
-            ss = l >> LOGM;
-            r = l & (M - 1);
+    // 3. store straight from the last group's registers; the first pass keeps
+    //    lazy values, the second reduces them and fuses the consumer
+    u64 *dst = J.dst;
+    if (!is_second(MODE)) {
+#pragma unroll
+        for (int k = 0; k < E; k++) dst[gidx(row(NG - 1, k))] = x[k];
+    } else {
+        const u64 *base = J.base, *extra = J.extra;
+        const u64 mul = J.mul, mulsh = J.mul_sh, addk = J.conv_sub;
+#pragma unroll
+        for (int k = 0; k < E; k++) {
+            const size_t gi = gidx(row(NG - 1, k));
+            u64 v = x[k];
+            if (MODE == M_SCALED) v = add_mod(shoup(v, mul, mulsh, q), addk, q);
+            else if (INV) v = shoup(v, mi.ninv, mi.ninv_sh, q);
+            else {
+                v = v >= q2 ? v - q2 : v;
+                v = v >= q ? v - q : v;
+            }
+            if (MODE == M_COMBINE) {
+                v = shoup(sub_mod(base[gi], v, q), mul, mulsh, q);
+                if (extra) v = add_mod(v, extra[gi], q);
+            }
+            dst[gi] = v;
         }
-        const size_t gi = gidx(r, ss);
-        u64 v = sm[smidx(r, ss)];
-        if (P.scale_out) v = shoup(v, mi.ninv, mi.ninv_sh, q);
-        if (P.store_mode == STORE_COMBINE) {
-            v = shoup(sub_mod(J.base[gi], v, q), J.mul, J.mul_sh, q);
-            if (J.extra) v = add_mod(v, J.extra[gi], q);
-        }
-        J.dst[gi] = v;
     }
 }
 
-template <int LOGM, bool INV, bool COL>
+template <int LOGM, bool INV, bool COL, int MODE>
 void run_pass(const PassParams &P, int njobs, cudaStream_t st) {
     constexpr int M = 1 << LOGM;
     constexpr int T = M / (M >= 16 ? 16 : M);
     const int nsub = COL ? (1 << P.log2) : (1 << P.log1);
     const int sub_cta = std::min(kThreads / T, nsub);
     const int threads = sub_cta * T;
-    const size_t smem = COL ? (size_t)M * sub_cta * 8 : (size_t)sub_cta * (M + M / 16) * 8;
-    static bool attr_set = false;
-    if (!attr_set) {
-        cudaFuncSetAttribute(ntt_pass_kernel<LOGM, INV, COL>, cudaFuncAttributeMaxDynamicSharedMemorySize, 96 * 1024);
-        attr_set = true;
-    }
+    constexpr int NG = (LOGM + 3) / 4;
+    const size_t smem = NG < 2 ? 0 : COL ? (size_t)M * sub_cta * 8 : (size_t)sub_cta * (M + M / 16) * 8;
     for (int j0 = 0; j0 < njobs; j0 += 65535) {
         PassParams Q = P;
         Q.jobs = P.jobs + j0;
         dim3 grid(nsub / sub_cta, std::min(65535, njobs - j0));
-        ntt_pass_kernel<LOGM, INV, COL><<<grid, threads, smem, st>>>(Q);
+        ntt_pass_kernel<LOGM, INV, COL, MODE><<<grid, threads, smem, st>>>(Q);
     }
 }
 
-template <bool INV, bool COL>
-void dispatch(int logm, const PassParams &P, int njobs, cudaStream_t st) {
+template <bool INV, bool COL, int MODE>
+void by_size(int logm, const PassParams &P, int njobs, cudaStream_t st) {
     switch (logm) {
-        case 5: run_pass<5, INV, COL>(P, njobs, st); break;
-        case 6: run_pass<6, INV, COL>(P, njobs, st); break;
-        case 7: run_pass<7, INV, COL>(P, njobs, st); break;
-        case 8: run_pass<8, INV, COL>(P, njobs, st); break;
+        case 5: run_pass<5, INV, COL, MODE>(P, njobs, st); break;
+        case 6: run_pass<6, INV, COL, MODE>(P, njobs, st); break;
+        case 7: run_pass<7, INV, COL, MODE>(P, njobs, st); break;
+        case 8: run_pass<8, INV, COL, MODE>(P, njobs, st); break;
         default: throw Error(-1, "unsupported NTT pass size");
     }
+}
+
+// first pass: forward = column pass, inverse = row pass
+template <bool INV>
+void first_pass(int load_mode, int logm, const PassParams &P, int njobs, cudaStream_t st) {
+    if (load_mode == LOAD_CONV) by_size<INV, !INV, M_CONV>(logm, P, njobs, st);
+    else if (load_mode == LOAD_CONV_PRE) by_size<INV, !INV, M_CONVPRE>(logm, P, njobs, st);
+    else if (load_mode == LOAD_REDUCE) by_size<INV, !INV, M_REDUCE>(logm, P, njobs, st);
+    else if (load_mode == LOAD_INT64) by_size<INV, !INV, M_INT64>(logm, P, njobs, st);
+    else by_size<INV, !INV, M_PLAIN>(logm, P, njobs, st);
+}
+
+template <bool INV>
+void second_pass(int store_mode, int logm, const PassParams &P, int njobs, cudaStream_t st) {
+    if (store_mode == STORE_COMBINE) {
+        by_size<INV, INV, M_COMBINE>(logm, P, njobs, st);
+        return;
+    }
+    if constexpr (INV) {
+        if (store_mode == STORE_SCALED) {
+            by_size<INV, INV, M_SCALED>(logm, P, njobs, st);
+            return;
+        }
+    }
+    by_size<INV, INV, M_STORE>(logm, P, njobs, st);
 }
 
 }  // namespace
@@ -215,13 +328,13 @@ void launch_ntt(bool inverse, int log_n, const NttTables &t, const NttJob *jobs_
     P.log2 = log_n / 2;
     if (pass != 1) {
         P.first = 1; P.load_mode = load_mode; P.store_mode = STORE_PLAIN; P.scale_out = 0;
-        if (!inverse) dispatch<false, true>(P.log1, P, njobs, s);
-        else dispatch<true, false>(P.log2, P, njobs, s);
+        if (!inverse) first_pass<false>(load_mode, P.log1, P, njobs, s);
+        else first_pass<true>(load_mode, P.log2, P, njobs, s);
     }
     if (pass != 0) {
         P.first = 0; P.load_mode = LOAD_PLAIN; P.store_mode = store_mode; P.scale_out = inverse ? 1 : 0;
-        if (!inverse) dispatch<false, false>(P.log2, P, njobs, s);
-        else dispatch<true, true>(P.log1, P, njobs, s);
+        if (!inverse) second_pass<false>(store_mode, P.log2, P, njobs, s);
+        else second_pass<true>(store_mode, P.log1, P, njobs, s);
     }
 }
 
