@@ -118,18 +118,25 @@ __global__ void __launch_bounds__(kThreads, (MODE == M_CONV || MODE == M_CONVPRE
         const int l = G::lo(g);
         return (t & ((1 << l) - 1)) | (k << l) | ((t >> l) << (l + LOGE));
     };
+    // In the row pass a group whose register window is the low bits holds
+    // contiguous words per thread; those ends go through shared memory so the
+    // global accesses stay coalesced (lane t takes words t, t + T, t + 2T, ...).
+    constexpr bool IN_STAGE = !COL && G::lo(0) != LOGM - LOGE;
+    constexpr bool OUT_STAGE = !COL && G::lo(NG - 1) != LOGM - LOGE;
+    auto lrow = [&](int k) -> int { return IN_STAGE ? t + T * k : row(0, k); };
+    auto srow = [&](int k) -> int { return OUT_STAGE ? t + T * k : row(NG - 1, k); };
 
     u64 x[E];
     // 1. load straight into the first group's registers, through the producer's load mode
     if (is_second(MODE)) {
 #pragma unroll
-        for (int k = 0; k < E; k++) x[k] = J.dst[gidx(row(0, k))];
+        for (int k = 0; k < E; k++) x[k] = J.dst[gidx(lrow(k))];
     } else if (MODE == M_REDUCE) {
         const u64 *src = J.src;
         const u64 sub = J.conv_sub;
 #pragma unroll
         for (int k = 0; k < E; k++) {
-            u64 v = src[gidx(row(0, k))];
+            u64 v = src[gidx(lrow(k))];
             v = v - __umul64hi(v, mi.one_sh) * q;  // Shoup product with w = 1: [0, 2q)
             v = v >= q ? v - q : v;
             x[k] = sub_mod(v, sub, q);
@@ -151,7 +158,7 @@ __global__ void __launch_bounds__(kThreads, (MODE == M_CONV || MODE == M_CONVPRE
                     const u64 c2 = J.c2[sidx];
                     const u64 *sp = src + sidx * stride;
 #pragma unroll
-                    for (int k = 0; k < C8; k++) acc_mad(acc[k], sp[gidx(row(0, k0 + k))], c2);
+                    for (int k = 0; k < C8; k++) acc_mad(acc[k], sp[gidx(lrow(k0 + k))], c2);
                 }
             }
 #pragma unroll
@@ -160,12 +167,12 @@ __global__ void __launch_bounds__(kThreads, (MODE == M_CONV || MODE == M_CONVPRE
     } else if (MODE == M_PLAIN) {
         const u64 *src = J.src;
 #pragma unroll
-        for (int k = 0; k < E; k++) x[k] = src[gidx(row(0, k))];
+        for (int k = 0; k < E; k++) x[k] = src[gidx(lrow(k))];
     } else if (MODE == M_INT64) {
         const int64_t *src = reinterpret_cast<const int64_t *>(J.src);
 #pragma unroll
         for (int k = 0; k < E; k++) {
-            const int64_t v = src[gidx(row(0, k))];
+            const int64_t v = src[gidx(lrow(k))];
             x[k] = v >= 0 ? (u64)v % q : q - 1 - ((u64)(-(v + 1)) % q);
         }
     } else {  // LOAD_CONV: sum_s [(src_s + add_s) c1_s]_{q_s} c2_s - conv_sub, four elements at a time
@@ -187,7 +194,7 @@ __global__ void __launch_bounds__(kThreads, (MODE == M_CONV || MODE == M_CONVPRE
                     const u64 *sp = src + sidx * stride;
                     u64 v[C4];
 #pragma unroll
-                    for (int k = 0; k < C4; k++) v[k] = sp[gidx(row(0, k0 + k))];
+                    for (int k = 0; k < C4; k++) v[k] = sp[gidx(lrow(k0 + k))];
 #pragma unroll
                     for (int k = 0; k < C4; k++) acc_mad(acc[k], shoup(add_mod(v[k], add, qs), c1, c1sh, qs), c2);
                 }
@@ -195,6 +202,14 @@ __global__ void __launch_bounds__(kThreads, (MODE == M_CONV || MODE == M_CONVPRE
 #pragma unroll
             for (int k = 0; k < C4; k++) x[k0 + k] = sub_mod(reduce128(acc[k].hi, acc[k].lo, mi), sub, q);
         }
+    }
+
+    if (IN_STAGE) {
+#pragma unroll
+        for (int k = 0; k < E; k++) sm[smidx(lrow(k))] = x[k];
+        __syncthreads();
+#pragma unroll
+        for (int k = 0; k < E; k++) x[k] = sm[smidx(row(0, k))];
     }
 
     // 2. butterfly groups; one shared-memory exchange between consecutive groups
@@ -238,15 +253,23 @@ __global__ void __launch_bounds__(kThreads, (MODE == M_CONV || MODE == M_CONVPRE
     // 3. store straight from the last group's registers; the first pass keeps
     //    lazy values, the second reduces them and fuses the consumer
     u64 *dst = J.dst;
+    if (OUT_STAGE) {
+        __syncthreads();
+#pragma unroll
+        for (int k = 0; k < E; k++) sm[smidx(row(NG - 1, k))] = x[k];
+        __syncthreads();
+#pragma unroll
+        for (int k = 0; k < E; k++) x[k] = sm[smidx(srow(k))];
+    }
     if (!is_second(MODE)) {
 #pragma unroll
-        for (int k = 0; k < E; k++) dst[gidx(row(NG - 1, k))] = x[k];
+        for (int k = 0; k < E; k++) dst[gidx(srow(k))] = x[k];
     } else {
         const u64 *base = J.base, *extra = J.extra;
         const u64 mul = J.mul, mulsh = J.mul_sh, addk = J.conv_sub;
 #pragma unroll
         for (int k = 0; k < E; k++) {
-            const size_t gi = gidx(row(NG - 1, k));
+            const size_t gi = gidx(srow(k));
             u64 v = x[k];
             if (MODE == M_SCALED) v = add_mod(shoup(v, mul, mulsh, q), addk, q);
             else if (INV) v = shoup(v, mi.ninv, mi.ninv_sh, q);
@@ -271,7 +294,7 @@ void run_pass(const PassParams &P, int njobs, cudaStream_t st) {
     const int sub_cta = std::min(kThreads / T, nsub);
     const int threads = sub_cta * T;
     constexpr int NG = (LOGM + 3) / 4;
-    const size_t smem = NG < 2 ? 0 : COL ? (size_t)M * sub_cta * 8 : (size_t)sub_cta * (M + M / 16) * 8;
+    const size_t smem = COL ? (NG < 2 ? 0 : (size_t)M * sub_cta * 8) : (size_t)sub_cta * (M + M / 16) * 8;
     for (int j0 = 0; j0 < njobs; j0 += 65535) {
         PassParams Q = P;
         Q.jobs = P.jobs + j0;
