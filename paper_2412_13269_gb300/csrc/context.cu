@@ -489,6 +489,7 @@ NttJob Rec::conv_job(uint32_t dst_prime, const u64 *src, uint32_t first, int nsr
         j.c1[s] = h_invmod(hat_s, qs);
         j.c1_sh[s] = h_shoup(j.c1[s], qs);
         j.c2[s] = hat_d;
+        j.c2_sh[s] = h_shoup(hat_d, qd);
     }
     return j;
 }

@@ -76,7 +76,8 @@ class Pool {
 // Kernel job descriptors
 // ---------------------------------------------------------------------------
 // LOAD_CONV:     sum_s [(src_s + add_s) * c1_s]_{q_s} * c2_s - conv_sub
-// LOAD_CONV_PRE: sum_s src_s * c2_s - conv_sub (sources already scaled by c1_s, see STORE_SCALED)
+// LOAD_CONV_PRE: sum_s src_s * c2_s - conv_sub (sources already scaled by c1_s, see STORE_SCALED;
+//                each product a lazy Shoup product, so nsrc * 2q < 2^64)
 // LOAD_REDUCE:   [src]_{q_dst} - conv_sub (a single source of another prime)
 enum LoadMode { LOAD_PLAIN = 0, LOAD_CONV = 1, LOAD_INT64 = 2, LOAD_CONV_PRE = 3, LOAD_REDUCE = 4 };
 // STORE_SCALED (inverse transforms only): x * mul + conv_sub, where mul already
@@ -98,7 +99,7 @@ struct NttJob {
     uint32_t src_prime[kMaxConvSrc];
     u64 add_s[kMaxConvSrc];
     u64 c1[kMaxConvSrc], c1_sh[kMaxConvSrc];
-    u64 c2[kMaxConvSrc];
+    u64 c2[kMaxConvSrc], c2_sh[kMaxConvSrc];  // c2_sh: Shoup companions of c2 modulo q_dst
     u64 conv_sub, mul, mul_sh;
 };
 

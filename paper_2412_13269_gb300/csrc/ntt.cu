@@ -80,7 +80,7 @@ enum { M_PLAIN = 0, M_INT64 = 1, M_CONV = 2, M_STORE = 3, M_COMBINE = 4, M_CONVP
 constexpr bool is_second(int m) { return m == M_STORE || m == M_COMBINE || m == M_SCALED; }
 
 template <int LOGM, bool INV, bool COL, int MODE>
-__global__ void __launch_bounds__(kThreads, (MODE == M_CONV || MODE == M_CONVPRE) ? 2 : 3) ntt_pass_kernel(PassParams P) {
+__global__ void __launch_bounds__(kThreads, MODE == M_CONV ? 2 : 3) ntt_pass_kernel(PassParams P) {
     constexpr int M = 1 << LOGM;
     constexpr int LOGE = LOGM >= 4 ? 4 : LOGM;
     constexpr int E = 1 << LOGE;
@@ -142,27 +142,29 @@ __global__ void __launch_bounds__(kThreads, (MODE == M_CONV || MODE == M_CONVPRE
             x[k] = sub_mod(v, sub, q);
         }
     } else if (MODE == M_CONVPRE) {
+        // sum_s y_s * c2_s with lazy Shoup products: each term < 2q, the sum < 8q
         const u64 *src = J.src;
         const u64 stride = J.src_stride;
         const int ns = (int)J.nsrc;
-        const u64 sub = J.conv_sub;
-        constexpr int C8 = E < 8 ? E : 8;
+        const u64 sub = J.conv_sub, q4 = 4 * q;
 #pragma unroll
-        for (int k0 = 0; k0 < E; k0 += C8) {
-            Acc128 acc[C8];
+        for (int k = 0; k < E; k++) x[k] = 0;
 #pragma unroll
-            for (int k = 0; k < C8; k++) acc[k] = {0, 0};
+        for (int sidx = 0; sidx < kMaxConvSrc; sidx++) {
+            if (sidx < ns) {
+                const u64 c2 = J.c2[sidx], c2sh = J.c2_sh[sidx];
+                const u64 *sp = src + sidx * stride;
 #pragma unroll
-            for (int sidx = 0; sidx < kMaxConvSrc; sidx++) {
-                if (sidx < ns) {
-                    const u64 c2 = J.c2[sidx];
-                    const u64 *sp = src + sidx * stride;
-#pragma unroll
-                    for (int k = 0; k < C8; k++) acc_mad(acc[k], sp[gidx(lrow(k0 + k))], c2);
-                }
+                for (int k = 0; k < E; k++) x[k] += shoup_lazy(sp[gidx(lrow(k))], c2, c2sh, q);
             }
+        }
 #pragma unroll
-            for (int k = 0; k < C8; k++) x[k0 + k] = sub_mod(reduce128(acc[k].hi, acc[k].lo, mi), sub, q);
+        for (int k = 0; k < E; k++) {
+            u64 v = x[k];
+            v = v >= q4 ? v - q4 : v;
+            v = v >= q2 ? v - q2 : v;
+            v = v >= q ? v - q : v;
+            x[k] = sub_mod(v, sub, q);
         }
     } else if (MODE == M_PLAIN) {
         const u64 *src = J.src;
