@@ -35,6 +35,7 @@ def _stale(obj: str, src: str) -> bool:
 
 
 def build(force: bool = False, verbose: bool = False, extra=()) -> str:
+    extra = tuple(extra) + tuple(os.environ.get("TETRIS_NVCC_FLAGS", "").split())
     os.makedirs(OUT, exist_ok=True)
     objs, jobs = [], []
     for s in SOURCES:

@@ -10,11 +10,11 @@
 // first log N1 stages; each column of the N1 x N2 row-major view is an
 // N1-point sub-problem) and a row pass (the remaining log N2 stages within
 // each contiguous row).  Inside a pass a CTA stages its tile in shared
-// memory; each thread holds E = 16 elements in registers and runs four
-// butterfly stages per visit (radix-16 groups).  A thread loads its first
+// memory; each thread holds E = 8 elements in registers and runs three
+// butterfly stages per visit (radix-8 groups; 64 registers, four CTAs per SM).  A thread loads its first
 // group straight from global memory and stores its last group straight back
-// (both coalesced across the warp), so a 256-point sub-problem needs a single
-// shared-memory exchange.  Stage bit b of a sub-problem of size
+// (both coalesced across the warp), so a 256-point sub-problem needs two
+// shared-memory exchanges.  Stage bit b of a sub-problem of size
 // M uses twiddle index (M >> (b+1)) * o + (r >> (b+1)), with o = 1 in the
 // column pass and o = N1 + row in the row pass.
 //
@@ -31,6 +31,10 @@ namespace tetris {
 namespace {
 
 constexpr int kThreads = 256;
+#ifndef TETRIS_NTT_LOGE
+#define TETRIS_NTT_LOGE 3
+#endif
+constexpr int kLogE = TETRIS_NTT_LOGE;  // log2 of the elements a thread holds in registers
 
 struct PassParams {
     NttTables t;
@@ -80,9 +84,9 @@ enum { M_PLAIN = 0, M_INT64 = 1, M_CONV = 2, M_STORE = 3, M_COMBINE = 4, M_CONVP
 constexpr bool is_second(int m) { return m == M_STORE || m == M_COMBINE || m == M_SCALED; }
 
 template <int LOGM, bool INV, bool COL, int MODE>
-__global__ void __launch_bounds__(kThreads, MODE == M_CONV ? 2 : 3) ntt_pass_kernel(PassParams P) {
+__global__ void __launch_bounds__(kThreads, MODE == M_CONV ? 2 : (kLogE >= 4 ? 3 : 4)) ntt_pass_kernel(PassParams P) {
     constexpr int M = 1 << LOGM;
-    constexpr int LOGE = LOGM >= 4 ? 4 : LOGM;
+    constexpr int LOGE = LOGM >= kLogE ? kLogE : LOGM;
     constexpr int E = 1 << LOGE;
     constexpr int T = M / E;
     constexpr int NG = (LOGM + LOGE - 1) / LOGE;
@@ -291,11 +295,12 @@ __global__ void __launch_bounds__(kThreads, MODE == M_CONV ? 2 : 3) ntt_pass_ker
 template <int LOGM, bool INV, bool COL, int MODE>
 void run_pass(const PassParams &P, int njobs, cudaStream_t st) {
     constexpr int M = 1 << LOGM;
-    constexpr int T = M / (M >= 16 ? 16 : M);
+    constexpr int LOGE = LOGM >= kLogE ? kLogE : LOGM;
+    constexpr int T = M >> LOGE;
     const int nsub = COL ? (1 << P.log2) : (1 << P.log1);
     const int sub_cta = std::min(kThreads / T, nsub);
     const int threads = sub_cta * T;
-    constexpr int NG = (LOGM + 3) / 4;
+    constexpr int NG = (LOGM + LOGE - 1) / LOGE;
     const size_t smem = COL ? (NG < 2 ? 0 : (size_t)M * sub_cta * 8) : (size_t)sub_cta * (M + M / 16) * 8;
     for (int j0 = 0; j0 < njobs; j0 += 65535) {
         PassParams Q = P;
