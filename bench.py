@@ -208,6 +208,83 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
+SERVE_DBS = [(1 << 14, 8), (1 << 16, 16), (1 << 18, 24), (1 << 19, 32)]
+SERVE_TYPES = [("linear+threshold", 1), ("degree-15 poly+threshold", 15), ("degree-31 poly+composite sign", 31)]
+
+
+def run_serve(args):
+    """Poisson arrivals of queries drawn uniformly from the three types over
+    four resident databases (N = 2^16), served by the library's request loop
+    with memory-based admission; one JSON line per arrival rate."""
+    import threading
+    import torch
+    import paper_2412_13269_gb300 as T
+    rank, world, local_rank = dist_env()
+    torch.cuda.set_device(local_rank)
+    T.build()
+    q, p = primes()
+    N, L, Delta = 1 << WL["log_n"], WL["n_q"] - 1, WL["scale"]
+    ctx = T.Ctx(WL["log_n"], q, p, Delta, device=local_rank)
+    seed = 2000 + rank
+    s = synth.ternary_secret(synth.stream(seed, "secret"), N, WL["hw"])
+    dnum = -(-WL["n_q"] // WL["alpha"])
+    d = synth.switch_key_draws(seed, "relin", dnum, q + p, N)
+    ctx.keygen_relin(s, d.a, d.e, WL["alpha"])
+    for g in galois_elements(N):
+        d = synth.switch_key_draws(seed, f"rot{g}", dnum, q + p, N)
+        ctx.keygen_rotation(g, s, d.a, d.e, WL["alpha"])
+    dbs = [ctx.upload_database(synth.database(synth.stream(seed, f"db{i}"), r, a, WL["dist"]))
+           for i, (r, a) in enumerate(SERVE_DBS)]
+
+    def enc(v, name):
+        m = ctx.encode(np.full(N // 2, float(v)), Delta)
+        dr = synth.encryption_draws(seed, name, q, N)
+        return ctx.encrypt(m, s, dr.a, dr.e, L, Delta)
+
+    sign = np.array([F3] * WL["stages"])
+    shapes = {}
+    for di, (r, a) in enumerate(SERVE_DBS):
+        for ti, (tname, deg) in enumerate(SERVE_TYPES):
+            qv = synth.query_values(synth.stream(seed, f"qv{di}.{ti}"), a, deg)
+            w = [enc(v, f"w{di}.{ti}.{j}") for j, v in enumerate(qv.w)]
+            c = [enc(v, f"c{di}.{ti}.{k}") for k, v in enumerate(qv.c)]
+            t = enc(qv.t, f"t{di}.{ti}")
+            shapes[(di, ti)] = (dbs[di], w, [(L, Delta)] * len(w), c, [(L, Delta)] * len(c), t, (L, Delta), sign)
+    budget = 96 << 30
+    ctx.serve_start(budget, 8)
+    for key in shapes:  # size and capture every shape once before timing
+        ctx.poll(ctx.submit(*shapes[key]), 600000)
+    ctx.serve_stats(reset=True)
+    rnd = np.random.default_rng(seed)
+    keys = list(shapes)
+    for rate in [float(x) for x in args.rates.split(",")]:
+        gaps = rnd.exponential(1.0 / rate, size=args.serve_queries)
+        picks = [keys[i] for i in rnd.integers(0, len(keys), size=args.serve_queries)]
+        tickets = []
+        t0 = time.perf_counter()
+        t_next = t0
+        for gap, key in zip(gaps, picks):
+            t_next += gap
+            delay = t_next - time.perf_counter()
+            if delay > 0:
+                time.sleep(delay)
+            tickets.append(ctx.submit(*shapes[key]))
+        for tk in tickets:
+            ctx.poll(tk, 600000)
+        elapsed = time.perf_counter() - t0
+        st = ctx.serve_stats(reset=True)
+        rec = sum(SERVE_DBS[k[0]][0] for k in picks)
+        print(json.dumps({"metric": "serving: queries/s and p50/p99 latency", "impl": "ours", "rate_qps": rate,
+                          "queries": len(tickets), "qps": len(tickets) / elapsed, "records_per_s": rec / elapsed,
+                          "p50_ms": st.p50_ms, "p99_ms": st.p99_ms, "completed": st.completed,
+                          "rejected": st.rejected, "peak_device_gb": st.peak_device_bytes / 1e9,
+                          "budget_gb": budget / 1e9, "max_inflight": 8,
+                          "config": {"workload": "N=2^16 L=20x50b K=3x60b; databases " + ", ".join(f"{r}x{a}" for r, a in SERVE_DBS)
+                                     + "; types " + ", ".join(t for t, _ in SERVE_TYPES)}}), flush=True)
+    ctx.serve_stop()
+    ctx.close()
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -217,9 +294,14 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-plain", action="store_true")
     ap.add_argument("--ncu", action="store_true", help="profile exactly one query between cudaProfilerStart/Stop")
+    ap.add_argument("--serve", action="store_true", help="serving workload: Poisson arrivals, mixed queries")
+    ap.add_argument("--rates", default="5,10,20,40", help="arrival rates (queries/s) for --serve")
+    ap.add_argument("--serve-queries", type=int, default=40, help="queries per rate for --serve")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
+    if args.serve:
+        return run_serve(args)
 
     import torch
     rank, world, local_rank = dist_env()

@@ -242,6 +242,36 @@ int tetris_op(tetris_ctx *ctx, int opcode, const tetris_ct_in *a, const tetris_c
               int64_t arg, tetris_ct_out *out);
 
 /* ---------------------------------------------------------------------------
+ * Serving.  tetris_serve_start starts a server thread that owns the GPU work
+ * of the context until tetris_serve_stop; in between, only tetris_submit,
+ * tetris_poll, tetris_serve_stats and tetris_serve_stop may be called on the
+ * context (from any thread).  tetris_submit copies the query's inputs
+ * (host buffers, as for tetris_evaluate_query) into pinned memory and returns
+ * a ticket at once.  The server admits queued queries in arrival order while
+ * fewer than max_inflight are running and the device memory of the program
+ * instance a query needs fits memory_budget_bytes (idle instances of other
+ * query shapes are released first; the first instance of a shape is sized by
+ * recording it).  Each running query has its own buffers and stream, so
+ * queries admitted while others run overlap on the device.  tetris_poll
+ * waits up to timeout_ms for the ticket (TETRIS_ETIMEOUT if still running)
+ * and copies the result into out, exactly as tetris_evaluate_query would
+ * have returned it; a query that cannot fit the budget even alone fails
+ * with TETRIS_EBUSY.  Latency is measured from submit to completion.
+ * ------------------------------------------------------------------------- */
+typedef struct {
+    uint64_t submitted, completed, rejected;
+    double p50_ms, p99_ms;
+    size_t device_bytes, peak_device_bytes;
+} tetris_serve_stats;
+int tetris_serve_start(tetris_ctx *ctx, size_t memory_budget_bytes, uint32_t max_inflight);
+int tetris_submit(tetris_ctx *ctx, uint32_t db, const tetris_query *query, uint64_t *ticket);
+int tetris_poll(tetris_ctx *ctx, uint64_t ticket, tetris_ct_out *out, uint32_t timeout_ms);
+/* Counters and submit-to-completion latency percentiles since the start (or
+ * the last reset); reset != 0 clears them after reading. */
+int tetris_serve_stats_get(tetris_ctx *ctx, tetris_serve_stats *out, int reset);
+int tetris_serve_stop(tetris_ctx *ctx);
+
+/* ---------------------------------------------------------------------------
  * Allocation-free rescale (the paper has no counterpart; this is an
  * interface for callers that cannot let the library allocate).
  *

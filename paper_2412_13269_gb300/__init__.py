@@ -66,6 +66,11 @@ class PlanInfo(C.Structure):
                 ("mask_scale", C.c_double)]
 
 
+class ServeStats(C.Structure):
+    _fields_ = [("submitted", C.c_uint64), ("completed", C.c_uint64), ("rejected", C.c_uint64), ("p50_ms", C.c_double),
+                ("p99_ms", C.c_double), ("device_bytes", C.c_size_t), ("peak_device_bytes", C.c_size_t)]
+
+
 class KernelStat(C.Structure):
     _fields_ = [("kind", C.c_char * 48), ("launches", C.c_uint32), ("total_ms", C.c_double), ("alg_bytes", C.c_double)]
 
@@ -97,6 +102,11 @@ SIGNATURES = {
     "tetris_op": [_vp, C.c_int, C.POINTER(CtIn), C.POINTER(CtIn), _i64, C.POINTER(CtOut)],
     "tetris_get_kernel_stats": [_vp, C.POINTER(KernelStat), _u32, C.POINTER(_u32)],
     "tetris_rescale_ntt_noalloc": [_vp, _vp, _vp, _u32, _u32, _vp],
+    "tetris_serve_start": [_vp, _sz, _u32],
+    "tetris_submit": [_vp, _u32, C.POINTER(Query), C.POINTER(_u64)],
+    "tetris_poll": [_vp, _u64, C.POINTER(CtOut), _u32],
+    "tetris_serve_stats_get": [_vp, C.POINTER(ServeStats), C.c_int],
+    "tetris_serve_stop": [_vp],
     "tetris_noalloc_scratch_bytes": [],
 }
 
@@ -296,6 +306,35 @@ class Ctx:
         o = CtOut(0, 0, 0.0, _ptr(out), out.numel())
         check(lib().tetris_evaluate_query_device(self.h, db, C.byref(q), C.byref(o), stream))
         return o.level, o.scale
+
+    # serving
+    def serve_start(self, budget_bytes: int, max_inflight: int):
+        check(lib().tetris_serve_start(self.h, budget_bytes, max_inflight))
+
+    def submit(self, db: int, w, w_meta, c, c_meta, t, t_meta, sign_coeffs) -> int:
+        q, keep = self._query_struct(w, w_meta, c, c_meta, t, t_meta, sign_coeffs)
+        tk = C.c_uint64()
+        check(lib().tetris_submit(self.h, db, C.byref(q), C.byref(tk)))
+        return tk.value
+
+    def poll(self, ticket: int, timeout_ms: int = 60000):
+        """Returns (out array, level, scale), or None if the ticket is still running."""
+        out = np.empty(2 * (self.L + 1) * self.N, dtype=np.uint64)
+        o = CtOut(0, 0, 0.0, out.ctypes.data, out.size)
+        rc = lib().tetris_poll(self.h, ticket, C.byref(o), timeout_ms)
+        if rc == -6:
+            return None
+        check(rc)
+        n = 2 * (o.level + 1) * self.N
+        return out[:n].reshape(2, o.level + 1, self.N), o.level, o.scale
+
+    def serve_stats(self, reset: bool = False) -> ServeStats:
+        st = ServeStats()
+        check(lib().tetris_serve_stats_get(self.h, C.byref(st), 1 if reset else 0))
+        return st
+
+    def serve_stop(self):
+        check(lib().tetris_serve_stop(self.h))
 
     # single operations
     def op(self, opcode: int, a: np.ndarray, a_level: int, a_scale: float = 1.0, b: np.ndarray | None = None,

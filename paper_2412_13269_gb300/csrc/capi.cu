@@ -349,6 +349,10 @@ int tetris_ctx_create(tetris_ctx **out, uint32_t log_n, const uint64_t *q, uint3
 void tetris_ctx_destroy(tetris_ctx *ctx) {
     if (!ctx) return;
     cudaSetDevice(ctx->c.device);
+    try {
+        serve_stop(ctx->c);
+    } catch (...) {
+    }
     cudaStreamSynchronize(ctx->c.stream);
     cudaStream_t s = ctx->c.stream;
     delete ctx;
@@ -705,6 +709,48 @@ int tetris_get_option(tetris_ctx *ctx, int option, int64_t *value) {
             case TETRIS_OPT_PROFILE: *value = C.profile; break;
             default: throw Error(TETRIS_EINVAL, "unknown option");
         }
+    });
+}
+
+int tetris_serve_start(tetris_ctx *ctx, size_t budget, uint32_t max_inflight) {
+    return guarded([&] {
+        TREQUIRE(ctx, TETRIS_EINVAL, "null context");
+        cudaSetDevice(ctx->c.device);
+        cudaStreamSynchronize(ctx->c.stream);
+        serve_start(ctx->c, budget, max_inflight);
+    });
+}
+
+int tetris_submit(tetris_ctx *ctx, uint32_t db, const tetris_query *q, uint64_t *ticket) {
+    return guarded([&] {
+        TREQUIRE(ctx && ticket, TETRIS_EINVAL, "null pointer");
+        cudaSetDevice(ctx->c.device);
+        *ticket = serve_submit(ctx->c, db, q);
+    });
+}
+
+int tetris_poll(tetris_ctx *ctx, uint64_t ticket, tetris_ct_out *out, uint32_t timeout_ms) {
+    int rc = TETRIS_OK;
+    int g = guarded([&] {
+        TREQUIRE(ctx, TETRIS_EINVAL, "null context");
+        rc = serve_poll(ctx->c, ticket, out, timeout_ms);
+        if (rc == TETRIS_ETIMEOUT) set_last_error("poll: ticket still running");
+    });
+    return g != TETRIS_OK ? g : rc;
+}
+
+int tetris_serve_stats_get(tetris_ctx *ctx, tetris_serve_stats *out, int reset) {
+    return guarded([&] {
+        TREQUIRE(ctx && out, TETRIS_EINVAL, "null pointer");
+        serve_stats(ctx->c, out, reset != 0);
+    });
+}
+
+int tetris_serve_stop(tetris_ctx *ctx) {
+    return guarded([&] {
+        TREQUIRE(ctx, TETRIS_EINVAL, "null context");
+        cudaSetDevice(ctx->c.device);
+        serve_stop(ctx->c);
     });
 }
 

@@ -10,7 +10,9 @@
 #pragma once
 #include <array>
 #include <cmath>
+#include <cstring>
 #include <mutex>
+#include <sstream>
 
 #include "internal.h"
 #include "../../include/tetris.h"
@@ -60,6 +62,7 @@ struct Ctx {
     int use_graph = 1;
     int profile = 0;
     std::map<std::string, KernelStat> stats;
+    void *server = nullptr;  // serve.cu
     std::map<std::string, std::unique_ptr<Program>> programs;
 
     int L() const { return (int)q.size() - 1; }
@@ -165,10 +168,47 @@ class Rec {
 int64_t round_half_up(double x);
 const Key &find_key(const Ctx &c, uint32_t galois);
 
+// Shape of a query: what a recorded program depends on.
+struct QuerySpec {
+    int attrs = 0, degree = 0;
+    std::vector<int> c_level;
+    std::vector<double> c_scale;
+    int t_level = 0;
+    double t_scale = 0;
+    std::vector<std::array<double, 4>> stages;
+    int bpl = 0;
+    std::string key(uint32_t db) const {
+        std::ostringstream o;
+        o << "q" << db << ":" << attrs << ":" << degree << ":" << bpl << ":" << t_level << ":";
+        auto bits = [&](double v) {
+            uint64_t b;
+            std::memcpy(&b, &v, 8);
+            o << std::hex << b << std::dec << ",";
+        };
+        bits(t_scale);
+        for (size_t i = 0; i < c_level.size(); i++) {
+            o << c_level[i] << "/";
+            bits(c_scale[i]);
+        }
+        for (auto &s : stages)
+            for (double v : s) bits(v);
+        return o.str();
+    }
+};
+
 // query.cu
+std::unique_ptr<Program> record_query(Ctx &C, const Database &db, const QuerySpec &q);
+QuerySpec spec_of(const Ctx &C, const Database &db, const tetris_query *q);
 void evaluate_query(Ctx &C, uint32_t db, const tetris_query *q, tetris_ct_out *out, cudaStream_t s, bool device);
 void plan_info(Ctx &C, uint32_t db, uint32_t degree, uint32_t stages, tetris_plan_info *out);
 void drop_programs_of_db(Ctx &C, uint32_t db);
+
+// serve.cu
+void serve_start(Ctx &C, size_t budget, uint32_t max_inflight);
+uint64_t serve_submit(Ctx &C, uint32_t db, const tetris_query *q);
+int serve_poll(Ctx &C, uint64_t ticket, tetris_ct_out *out, uint32_t timeout_ms);
+void serve_stats(Ctx &C, tetris_serve_stats *st, bool reset);
+void serve_stop(Ctx &C);
 
 // noalloc.cu
 void rescale_ntt_noalloc(Ctx &C, const u64 *in, u64 *out, int level, int ncomp, cudaStream_t s);

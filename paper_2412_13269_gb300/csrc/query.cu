@@ -141,34 +141,7 @@ static CtH eval_blocks(Rec &R, const Database &db, const QPlan &pl, int b0, int 
     return R.add_int(u, round_half_up(pl.step_const * C.S[u.level]));
 }
 
-struct QuerySpec {
-    int attrs = 0, degree = 0;
-    std::vector<int> c_level;
-    std::vector<double> c_scale;
-    int t_level = 0;
-    double t_scale = 0;
-    std::vector<std::array<double, 4>> stages;
-    int bpl = 0;
-    std::string key(uint32_t db) const {
-        std::ostringstream o;
-        o << "q" << db << ":" << attrs << ":" << degree << ":" << bpl << ":" << t_level << ":";
-        auto bits = [&](double v) {
-            uint64_t b;
-            std::memcpy(&b, &v, 8);
-            o << std::hex << b << std::dec << ",";
-        };
-        bits(t_scale);
-        for (size_t i = 0; i < c_level.size(); i++) {
-            o << c_level[i] << "/";
-            bits(c_scale[i]);
-        }
-        for (auto &s : stages)
-            for (double v : s) bits(v);
-        return o.str();
-    }
-};
-
-static std::unique_ptr<Program> record_query(Ctx &C, const Database &db, const QuerySpec &q) {
+std::unique_ptr<Program> record_query(Ctx &C, const Database &db, const QuerySpec &q) {
     auto P = std::make_unique<Program>();
     P->ctx = &C;
     Rec R(C, *P);
@@ -273,7 +246,7 @@ static std::unique_ptr<Program> record_query(Ctx &C, const Database &db, const Q
     return P;
 }
 
-static QuerySpec spec_of(const Ctx &C, const Database &db, const tetris_query *q) {
+QuerySpec spec_of(const Ctx &C, const Database &db, const tetris_query *q) {
     TREQUIRE(q && q->w && q->f_coeffs && q->threshold && q->sign_coeffs, TETRIS_EINVAL, "query: null pointer");
     TREQUIRE((int)q->n_attrs == db.attrs, TETRIS_EINVAL, "query: attribute count differs from the database");
     TREQUIRE(q->sign_degree == 7, TETRIS_EINVAL, "query: sign stages must be odd degree-7 polynomials");

@@ -1,0 +1,401 @@
+// Serving: a request loop inside the library.
+//
+// Clients submit encrypted queries from any thread; each submission copies
+// its input ciphertexts into pinned host memory and returns a ticket.  One
+// server thread owns the GPU work of the context: it admits queued requests
+// while an in-flight slot is free and the device memory of the program
+// instance the request needs fits the budget (idle instances of other query
+// shapes are released first), replays that instance's captured graph on the
+// instance's own stream, and moves on without waiting.  Requests admitted
+// while others run therefore overlap on the device (continuous admission at
+// request granularity; within a request every launch already covers all of
+// its database's blocks).  A host callback enqueued after each request's
+// device-to-host copy marks its ticket done.  Results are bit-identical to
+// the same query evaluated alone: every kernel is deterministic and requests
+// share no buffers.
+//
+// No CUDA call is made while the server's mutex is held: host callbacks of
+// running requests take that mutex, and a CUDA call that synchronises the
+// device (freeing memory does) would otherwise wait for them forever.
+// Pinned input buffers are pooled for that reason, and instances released
+// to make room are destroyed after the mutex is dropped.
+#include <algorithm>
+#include <chrono>
+#include <condition_variable>
+#include <deque>
+#include <thread>
+
+#include "program.h"
+
+namespace tetris {
+
+namespace {
+
+using Clock = std::chrono::steady_clock;
+
+struct Request {
+    uint64_t ticket = 0;
+    uint32_t db = 0;
+    QuerySpec spec;
+    std::string key;
+    u64 *pinned_in = nullptr;      // all input ciphertexts, slot order
+    std::vector<size_t> in_words;  // words per slot
+    size_t total_in = 0;
+    Clock::time_point t_submit, t_done;
+    // result
+    bool done = false;
+    int status = TETRIS_OK;
+    std::string error;
+    std::vector<u64> out;
+    int level = 0, ncomp = 0;
+    double scale = 0;
+};
+
+struct Instance {
+    std::unique_ptr<Program> prog;
+    std::string key;
+    size_t bytes = 0;
+    cudaStream_t stream = nullptr;
+    u64 *pinned_out = nullptr;
+    std::shared_ptr<Request> req;
+    bool busy = false;
+    uint64_t last_use = 0;
+    ~Instance() {
+        if (stream) {
+            cudaStreamSynchronize(stream);
+            cudaStreamDestroy(stream);
+        }
+        if (pinned_out) cudaFreeHost(pinned_out);
+    }
+};
+
+}  // namespace
+
+struct Server {
+    Ctx *C = nullptr;
+    size_t budget = 0;
+    uint32_t max_inflight = 0;
+    std::thread th;
+    std::mutex mu;
+    std::condition_variable cv_work, cv_done;
+    std::deque<std::shared_ptr<Request>> queue;
+    std::map<uint64_t, std::shared_ptr<Request>> tickets;
+    std::vector<std::unique_ptr<Instance>> instances;
+    std::map<std::string, size_t> bytes_of;  // measured device bytes per instance of a query shape
+    std::vector<Instance *> finished;        // set by host callbacks, drained by the server thread
+    std::vector<std::unique_ptr<Instance>> graveyard;  // released instances, destroyed outside the mutex
+    std::multimap<size_t, u64 *> pinned_free;          // reusable pinned input buffers, by words
+    uint64_t next_ticket = 1, use_clock = 0;
+    bool stopping = false;
+    size_t used = 0, peak = 0;
+    std::vector<double> latencies_ms;
+    uint64_t submitted = 0, completed = 0, rejected = 0;
+
+    void loop();
+    bool admit_one(std::unique_lock<std::mutex> &lk);
+    void retire(Instance *in);
+};
+
+namespace {
+
+void CUDART_CB on_done(void *arg) {
+    auto *pr = static_cast<std::pair<Server *, Instance *> *>(arg);
+    Server *S = pr->first;
+    Instance *in = pr->second;
+    delete pr;
+    {
+        std::lock_guard<std::mutex> lk(S->mu);
+        S->finished.push_back(in);
+    }
+    S->cv_work.notify_one();
+}
+
+}  // namespace
+
+void Server::retire(Instance *in) {
+    auto r = in->req;
+    r->out.assign(in->pinned_out, in->pinned_out + in->prog->out_words);
+    r->level = in->prog->out_level;
+    r->ncomp = in->prog->out_comps;
+    r->scale = in->prog->out_scale;
+    r->t_done = Clock::now();
+    r->done = true;
+    pinned_free.insert({r->total_in, r->pinned_in});
+    r->pinned_in = nullptr;
+    latencies_ms.push_back(std::chrono::duration<double, std::milli>(r->t_done - r->t_submit).count());
+    completed++;
+    in->req.reset();
+    in->busy = false;
+    in->last_use = ++use_clock;
+}
+
+// Called with the lock held; may release it around GPU calls.
+bool Server::admit_one(std::unique_lock<std::mutex> &lk) {
+    if (queue.empty()) return false;
+    uint32_t inflight = 0;
+    for (auto &i : instances) inflight += i->busy;
+    if (inflight >= max_inflight) return false;
+    auto req = queue.front();
+    Instance *in = nullptr;
+    for (auto &i : instances)
+        if (!i->busy && i->key == req->key) {
+            in = i.get();
+            break;
+        }
+    if (!in) {
+        auto evict_one = [&]() -> bool {  // release the least recently used idle instance
+            Instance *victim = nullptr;
+            for (auto &i : instances)
+                if (!i->busy && (!victim || i->last_use < victim->last_use)) victim = i.get();
+            if (!victim) return false;
+            used -= victim->bytes;
+            for (auto it = instances.begin(); it != instances.end(); ++it)
+                if (it->get() == victim) {
+                    graveyard.push_back(std::move(*it));
+                    instances.erase(it);
+                    break;
+                }
+            return true;
+        };
+        auto reject = [&](int code, const std::string &msg) {
+            queue.pop_front();
+            req->status = code;
+            req->error = msg;
+            req->done = true;
+            rejected++;
+            cv_done.notify_all();
+        };
+        auto est = bytes_of.find(req->key);
+        if (est != bytes_of.end()) {
+            while (used + est->second > budget && evict_one()) {
+            }
+            if (used + est->second > budget) {
+                if (inflight > 0) return false;  // wait for running queries to free memory
+                reject(TETRIS_EBUSY, "query needs more device memory than the serving budget");
+                return true;
+            }
+        } else {
+            // first query of this shape: size it by recording it while nothing else runs
+            if (inflight > 0) return false;
+            while (evict_one()) {
+            }
+        }
+        auto db_it = C->dbs.find(req->db);
+        std::unique_ptr<Instance> ni(new Instance);
+        ni->key = req->key;
+        lk.unlock();
+        int code = TETRIS_OK;
+        std::string msg;
+        try {
+            TREQUIRE(db_it != C->dbs.end(), TETRIS_ENOTFOUND, "unknown database handle");
+            ni->prog = record_query(*C, db_it->second, req->spec);
+            ni->bytes = ni->prog->pool.bytes_held();
+            TCHECK_CUDA(cudaStreamCreateWithFlags(&ni->stream, cudaStreamNonBlocking));
+            TCHECK_CUDA(cudaMallocHost(&ni->pinned_out, ni->prog->out_words * 8));
+        } catch (const Error &e) {
+            code = e.code;
+            msg = e.what();
+        }
+        lk.lock();
+        if (code != TETRIS_OK) {
+            graveyard.push_back(std::move(ni));
+            reject(code, msg);
+            return true;
+        }
+        bytes_of[req->key] = ni->bytes;
+        if (used + ni->bytes > budget) {
+            graveyard.push_back(std::move(ni));
+            reject(TETRIS_EBUSY, "query needs more device memory than the serving budget");
+            return true;
+        }
+        used += ni->bytes;
+        peak = std::max(peak, used);
+        in = ni.get();
+        instances.push_back(std::move(ni));
+    }
+    queue.pop_front();
+    in->busy = true;
+    in->req = req;
+    Program &P = *in->prog;
+    lk.unlock();
+    try {
+        size_t off = 0;
+        for (size_t s = 0; s < P.in_slots.size(); s++) {
+            TCHECK_CUDA(cudaMemcpyAsync(P.in_slots[s].first, req->pinned_in + off, P.in_slots[s].second * 8,
+                                        cudaMemcpyHostToDevice, in->stream));
+            off += P.in_slots[s].second;
+        }
+        P.run_graph(in->stream);
+        TCHECK_CUDA(cudaMemcpyAsync(in->pinned_out, P.out_base, P.out_words * 8, cudaMemcpyDeviceToHost, in->stream));
+        TCHECK_CUDA(cudaLaunchHostFunc(in->stream, on_done, new std::pair<Server *, Instance *>(this, in)));
+    } catch (const Error &e) {
+        lk.lock();
+        req->status = e.code;
+        req->error = e.what();
+        req->done = true;
+        in->busy = false;
+        in->req.reset();
+        cv_done.notify_all();
+        return true;
+    }
+    lk.lock();
+    return true;
+}
+
+void Server::loop() {
+    cudaSetDevice(C->device);
+    std::unique_lock<std::mutex> lk(mu);
+    bool blocked = false;  // the head of the queue waits for running queries (memory or sizing)
+    for (;;) {
+        if (!finished.empty()) {
+            for (Instance *in : finished) retire(in);
+            finished.clear();
+            blocked = false;
+            cv_done.notify_all();
+        }
+        while (admit_one(lk)) {
+        }
+        if (!graveyard.empty()) {
+            std::vector<std::unique_ptr<Instance>> dead;
+            dead.swap(graveyard);
+            lk.unlock();
+            dead.clear();  // stream sync + cudaFree/cudaFreeHost, without the mutex
+            lk.lock();
+            continue;  // memory came back: try admitting again
+        }
+        {
+            uint32_t n = 0;
+            for (auto &i : instances) n += i->busy;
+            blocked = !queue.empty() && n < max_inflight;
+        }
+        bool busy = false;
+        for (auto &i : instances) busy |= i->busy;
+        if (stopping && queue.empty() && !busy) break;
+        cv_work.wait(lk, [&] {
+            if (!finished.empty() || stopping) return true;
+            if (queue.empty() || blocked) return false;
+            uint32_t n = 0;
+            for (auto &i : instances) n += i->busy;
+            return n < max_inflight;
+        });
+    }
+}
+
+static Server *server_of(Ctx &C) { return reinterpret_cast<Server *>(C.server); }
+
+void serve_start(Ctx &C, size_t budget, uint32_t max_inflight) {
+    TREQUIRE(!C.server, TETRIS_EINVAL, "serving already started");
+    TREQUIRE(budget > 0 && max_inflight > 0, TETRIS_EINVAL, "serving needs a memory budget and at least one slot");
+    auto *S = new Server;
+    S->C = &C;
+    S->budget = budget;
+    S->max_inflight = max_inflight;
+    C.server = S;
+    S->th = std::thread([S] { S->loop(); });
+}
+
+uint64_t serve_submit(Ctx &C, uint32_t db, const tetris_query *q) {
+    Server *S = server_of(C);
+    TREQUIRE(S, TETRIS_EINVAL, "serving not started");
+    auto it = C.dbs.find(db);
+    TREQUIRE(it != C.dbs.end(), TETRIS_ENOTFOUND, "unknown database handle");
+    auto req = std::make_shared<Request>();
+    req->db = db;
+    req->spec = spec_of(C, it->second, q);
+    req->spec.bpl = 0;
+    req->key = req->spec.key(db);
+    const size_t N = C.N;
+    auto words = [&](const tetris_ct_in &c) { return (size_t)2 * (c.level + 1) * N; };
+    std::vector<const tetris_ct_in *> ins;
+    for (uint32_t j = 0; j < q->n_attrs; j++) ins.push_back(&q->w[j]);
+    for (uint32_t k = 0; k <= q->f_degree; k++) ins.push_back(&q->f_coeffs[k]);
+    ins.push_back(q->threshold);
+    for (auto c : ins) {
+        req->in_words.push_back(words(*c));
+        req->total_in += words(*c);
+    }
+    {
+        std::lock_guard<std::mutex> lk(S->mu);
+        auto it = S->pinned_free.find(req->total_in);
+        if (it != S->pinned_free.end()) {
+            req->pinned_in = it->second;
+            S->pinned_free.erase(it);
+        }
+    }
+    if (!req->pinned_in) TCHECK_CUDA(cudaMallocHost(&req->pinned_in, req->total_in * 8));
+    size_t off = 0;
+    for (size_t i = 0; i < ins.size(); i++) {
+        std::memcpy(req->pinned_in + off, ins[i]->data, req->in_words[i] * 8);
+        off += req->in_words[i];
+    }
+    req->t_submit = Clock::now();
+    {
+        std::lock_guard<std::mutex> lk(S->mu);
+        req->ticket = S->next_ticket++;
+        S->tickets[req->ticket] = req;
+        S->queue.push_back(req);
+        S->submitted++;
+    }
+    S->cv_work.notify_one();
+    return req->ticket;
+}
+
+int serve_poll(Ctx &C, uint64_t ticket, tetris_ct_out *out, uint32_t timeout_ms) {
+    Server *S = server_of(C);
+    TREQUIRE(S, TETRIS_EINVAL, "serving not started");
+    std::unique_lock<std::mutex> lk(S->mu);
+    auto it = S->tickets.find(ticket);
+    TREQUIRE(it != S->tickets.end(), TETRIS_ENOTFOUND, "unknown ticket");
+    auto req = it->second;
+    if (!S->cv_done.wait_for(lk, std::chrono::milliseconds(timeout_ms), [&] { return req->done; }))
+        return TETRIS_ETIMEOUT;
+    S->tickets.erase(it);
+    if (req->status != TETRIS_OK) throw Error(req->status, req->error);
+    TREQUIRE(out && out->data && out->cap_words >= req->out.size(), TETRIS_EINVAL, "output buffer too small");
+    std::memcpy(out->data, req->out.data(), req->out.size() * 8);
+    out->level = req->level;
+    out->ncomp = req->ncomp;
+    out->scale = req->scale;
+    return TETRIS_OK;
+}
+
+void serve_stats(Ctx &C, tetris_serve_stats *st, bool reset) {
+    Server *S = server_of(C);
+    TREQUIRE(S && st, TETRIS_EINVAL, "serving not started");
+    std::lock_guard<std::mutex> lk(S->mu);
+    std::vector<double> l = S->latencies_ms;
+    std::sort(l.begin(), l.end());
+    auto pct = [&](double p) { return l.empty() ? 0.0 : l[std::min(l.size() - 1, (size_t)(p * (l.size() - 1) + 0.5))]; };
+    st->submitted = S->submitted;
+    st->completed = S->completed;
+    st->rejected = S->rejected;
+    st->p50_ms = pct(0.50);
+    st->p99_ms = pct(0.99);
+    st->device_bytes = S->used;
+    st->peak_device_bytes = S->peak;
+    if (reset) {
+        S->latencies_ms.clear();
+        S->submitted = S->completed = S->rejected = 0;
+        S->peak = S->used;
+    }
+}
+
+void serve_stop(Ctx &C) {
+    Server *S = server_of(C);
+    if (!S) return;
+    {
+        std::lock_guard<std::mutex> lk(S->mu);
+        S->stopping = true;
+    }
+    S->cv_work.notify_all();
+    S->th.join();
+    S->instances.clear();
+    S->graveyard.clear();
+    for (auto &kv : S->pinned_free) cudaFreeHost(kv.second);
+    for (auto &kv : S->tickets)
+        if (kv.second->pinned_in) cudaFreeHost(kv.second->pinned_in);
+    delete S;
+    C.server = nullptr;
+}
+
+}  // namespace tetris
