@@ -208,6 +208,35 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
+def run_micro_keyswitch(calls: int):
+    """One-block keyswitch at the top level (the unit ncu captures of the
+    keyswitch kernels are taken on)."""
+    import torch
+    import paper_2412_13269_gb300 as T
+    T.build()
+    q, p = primes()
+    N = 1 << WL["log_n"]
+    ctx = T.Ctx(WL["log_n"], q, p, WL["scale"])
+    s = synth.ternary_secret(synth.stream(1, "s"), N, WL["hw"])
+    dnum = -(-WL["n_q"] // WL["alpha"])
+    d = synth.switch_key_draws(1, "relin", dnum, q + p, N)
+    ctx.keygen_relin(s, d.a, d.e, WL["alpha"])
+    g = np.random.default_rng(0)
+    a = np.stack([g.integers(0, m, N, dtype=np.uint64) for m in q])[None]
+    for i in range(calls):
+        last = i == calls - 1
+        if last:
+            torch.cuda.synchronize()
+            torch.cuda.profiler.start()
+        t0 = time.perf_counter()
+        ctx.op(T.OP_KEYSWITCH, a, WL["n_q"] - 1, arg=0, out_comps=2)
+        if last:
+            torch.cuda.synchronize()
+            torch.cuda.profiler.stop()
+        print(json.dumps({"keyswitch_call": i, "ms_with_transfers": (time.perf_counter() - t0) * 1e3}))
+    ctx.close()
+
+
 SERVE_DBS = [(1 << 14, 8), (1 << 16, 16), (1 << 18, 24), (1 << 19, 32)]
 SERVE_TYPES = [("linear+threshold", 1), ("degree-15 poly+threshold", 15), ("degree-31 poly+composite sign", 31)]
 
@@ -295,6 +324,8 @@ def main():
     ap.add_argument("--no-plain", action="store_true")
     ap.add_argument("--ncu", action="store_true", help="profile exactly one query between cudaProfilerStart/Stop")
     ap.add_argument("--serve", action="store_true", help="serving workload: Poisson arrivals, mixed queries")
+    ap.add_argument("--micro-keyswitch", type=int, default=0, metavar="CALLS",
+                    help="top-level keyswitch via tetris_op, CALLS times; the last call between cudaProfilerStart/Stop")
     ap.add_argument("--rates", default="5,10,20,40", help="arrival rates (queries/s) for --serve")
     ap.add_argument("--serve-queries", type=int, default=40, help="queries per rate for --serve")
     args = ap.parse_args()
@@ -302,6 +333,8 @@ def main():
         return run_reference(args)
     if args.serve:
         return run_serve(args)
+    if args.micro_keyswitch:
+        return run_micro_keyswitch(args.micro_keyswitch)
 
     import torch
     rank, world, local_rank = dist_env()
