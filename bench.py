@@ -237,6 +237,65 @@ def run_micro_keyswitch(calls: int):
     ctx.close()
 
 
+def run_c3(args):
+    """Batching workload: 524288 records x 32 attributes (16 blocks of 32768
+    slots) at the benchmark parameters.  For each keyswitch digit size alpha in
+    {3, 2, 1} (dnum = 7, 10, 20 at 20 primes; larger digits need more special
+    primes than the three the parameters give), keys are generated and the
+    library's autotuner times the query under every schedule it knows (blocks
+    per launch x NTT register-group width).  Reports the tuned best against
+    the fixed plain schedule (one block per launch, radix-8 groups, alpha 3)."""
+    import torch
+    import paper_2412_13269_gb300 as T
+    rank, world, local_rank = dist_env()
+    torch.cuda.set_device(local_rank)
+    T.build()
+    q, p = primes()
+    N, L, Delta = 1 << WL["log_n"], WL["n_q"] - 1, WL["scale"]
+    records, attrs = 524288, 32
+    ctx = T.Ctx(WL["log_n"], q, p, Delta, device=local_rank)
+    seed = 3000 + rank
+    s = synth.ternary_secret(synth.stream(seed, "secret"), N, WL["hw"])
+    dbh = ctx.upload_database(synth.database(synth.stream(seed, "db"), records, attrs, WL["dist"]))
+    qv = synth.query_values(synth.stream(seed, "qv"), attrs, WL["degree"])
+
+    def enc(v, name):
+        m = ctx.encode(np.full(N // 2, float(v)), Delta)
+        dr = synth.encryption_draws(seed, name, q, N)
+        return ctx.encrypt(m, s, dr.a, dr.e, L, Delta)
+
+    w = [enc(v, f"w{j}") for j, v in enumerate(qv.w)]
+    c = [enc(v, f"c{k}") for k, v in enumerate(qv.c)]
+    t = enc(qv.t, "t")
+    qargs = (w, [(L, Delta)] * len(w), c, [(L, Delta)] * len(c), t, (L, Delta), np.array([F3] * WL["stages"]))
+    per_alpha = []
+    for alpha in (3, 2, 1):
+        dnum = -(-WL["n_q"] // alpha)
+        d = synth.switch_key_draws(seed, f"relin.a{alpha}", dnum, q + p, N)
+        ctx.keygen_relin(s, d.a, d.e, alpha)
+        for g in galois_elements(N):
+            d = synth.switch_key_draws(seed, f"rot{g}.a{alpha}", dnum, q + p, N)
+            ctx.keygen_rotation(g, s, d.a, d.e, alpha)
+        table = ctx.autotune(dbh, *qargs, reps=max(2, args.steps // 5))
+        best = min(table, key=lambda e: e[2])
+        per_alpha.append({"alpha": alpha, "dnum": dnum, "best": {"blocks_per_launch": best[0], "ntt_group_log2": best[1],
+                                                                   "ms": best[2]},
+                          "table": [{"blocks_per_launch": b, "ntt_group_log2": g, "ms": round(m, 3)} for b, g, m in table]})
+        if alpha == 3:
+            fixed = next(m for b, g, m in table if b == 1 and g == 3)
+    top = min(per_alpha, key=lambda r: r["best"]["ms"])
+    ms = top["best"]["ms"]
+    line = {"metric": METRIC, "workload": "c3", "value": ms * 1e3 / records, "unit": "us/record/query",
+            "ms_per_step": ms, "higher_is_better": False, "dtype": "u64", "data": "synthetic (seeded)",
+            "config": {"workload": f"batching: N=2^16 L=20x50b K=3x60b; {records} records x {attrs} attrs (16 blocks); "
+                                   "f deg 15; 3 sign stages; autotuned", "tuned": top["best"], "alpha": top["alpha"]},
+            "fixed_schedule": {"value": fixed * 1e3 / records, "ms_per_step": fixed,
+                               "schedule": "one block per launch, radix-8 NTT groups, alpha 3"},
+            "per_alpha": per_alpha}
+    print(json.dumps(line), flush=True)
+    ctx.close()
+
+
 SERVE_DBS = [(1 << 14, 8), (1 << 16, 16), (1 << 18, 24), (1 << 19, 32)]
 SERVE_TYPES = [("linear+threshold", 1), ("degree-15 poly+threshold", 15), ("degree-31 poly+composite sign", 31)]
 
@@ -324,6 +383,8 @@ def main():
     ap.add_argument("--no-plain", action="store_true")
     ap.add_argument("--ncu", action="store_true", help="profile exactly one query between cudaProfilerStart/Stop")
     ap.add_argument("--serve", action="store_true", help="serving workload: Poisson arrivals, mixed queries")
+    ap.add_argument("--workload", default="c2", choices=["c2", "c3"],
+                    help="c2: 131072 x 16 (the default line); c3: batching, 524288 x 32 with the autotuner")
     ap.add_argument("--micro-keyswitch", type=int, default=0, metavar="CALLS",
                     help="top-level keyswitch via tetris_op, CALLS times; the last call between cudaProfilerStart/Stop")
     ap.add_argument("--rates", default="5,10,20,40", help="arrival rates (queries/s) for --serve")
@@ -335,6 +396,8 @@ def main():
         return run_serve(args)
     if args.micro_keyswitch:
         return run_micro_keyswitch(args.micro_keyswitch)
+    if args.workload == "c3":
+        return run_c3(args)
 
     import torch
     rank, world, local_rank = dist_env()
@@ -355,8 +418,18 @@ def main():
     out = torch.empty(2 * (L + 1) * N, dtype=torch.int64, device="cuda")
     stream = torch.cuda.Stream()
 
+    total_records = WL["records"] * world
+
     def step():
-        return ctx.evaluate_query_device(dbh, dw, meta_w, dc, meta_c, dt, (L, Delta), sign, out, stream.cuda_stream)
+        lev, _ = ctx.evaluate_query_device(dbh, dw, meta_w, dc, meta_c, dt, (L, Delta), sign, out, stream.cuda_stream,
+                                           total_records=total_records if world > 1 else 0)
+        if world > 1:
+            # the method's one exchange: residue-wise sum of the ranks' count ciphertexts
+            # (horizontally partitioned database), then reduction mod q in a library kernel
+            with torch.cuda.stream(stream):
+                n = 2 * (lev + 1) * N
+                torch.distributed.all_reduce(out[:n])
+            ctx.reduce_sum_device(out, lev, 2, stream.cuda_stream)
 
     def barrier():
         if world > 1:
@@ -400,7 +473,7 @@ def main():
     clk = clocks.stop()
     out_level = None
     records_total = WL["records"] * world
-    value = ms * 1e3 / WL["records"]  # per-rank records per rank time == all records / all time (weak scaling)
+    value = ms * 1e3 / records_total  # all ranks' records in the slowest rank's time (weak scaling)
 
     # plain per-block form
     plain = None
@@ -467,7 +540,8 @@ def main():
         "vs_baseline": None, "dtype": "u64",
         "data": "synthetic, seeded: u8 attributes, half uniform and half the paper's clipped-normal features",
         "config": {"workload": WL_NAME, "records_per_gpu": WL["records"], "records_total": records_total,
-                   "form": "batched: every launch covers all 4 blocks; CUDA graph replay; device-resident inputs",
+                   "form": "batched: every launch covers all 4 blocks; CUDA graph replay; device-resident inputs"
+                           + ("; per step: NCCL all-reduce of the ranks' result residues + reduction mod q" if world > 1 else ""),
                    "l2": "inputs larger than L2 (2.6 GB of keys, 640 MiB database per query)",
                    "parallelism": f"records sharded over {world} GPU(s)"},
         "plain": plain,

@@ -82,8 +82,8 @@ int tetris_gen_primes(uint32_t bits, uint32_t count, uint32_t congruence_log2,
  * q_{j*alpha} .. q_{j*alpha+alpha-1} (CRT gadget), dnum = ceil(n_q / alpha).
  * n_words must equal dnum * 2 * (n_q + n_p) * N.  The context copies the key
  * to device memory (converted to its internal NTT domain); loading a key for
- * an element that already has one replaces it.  alpha must be the same for
- * all keys of a context.
+ * an element that already has one replaces it.  All keys of a context share
+ * one alpha: loading a key with a different alpha drops every loaded key.
  * ------------------------------------------------------------------------- */
 int tetris_load_relin_key(tetris_ctx *ctx, const uint64_t *evk, size_t n_words, uint32_t alpha);
 int tetris_load_rotation_key(tetris_ctx *ctx, uint32_t galois_elt, const uint64_t *evk,
@@ -175,6 +175,11 @@ typedef struct {
     uint32_t sign_stages;
     uint32_t sign_degree;
     const double *sign_coeffs;
+    uint64_t total_records;   /* the count is normalised by this many records (0: the
+                                 database's own); set it to the total over the partitions
+                                 when a database is split across GPUs or owners (the
+                                 horizontally partitioned database of Section 4.4): the
+                                 partitions' results then add up residue-wise */
 } tetris_query;
 
 /* Host buffers in and out; blocks until the result is in out. */
@@ -184,6 +189,12 @@ int tetris_evaluate_query(tetris_ctx *ctx, uint32_t db, const tetris_query *quer
  * legacy default stream); returns before the work completes. */
 int tetris_evaluate_query_device(tetris_ctx *ctx, uint32_t db, const tetris_query *query,
                                  tetris_ct_out *out, void *stream);
+
+/* Residue-wise sum of partition results: data (device, [ncomp][level+1][N])
+ * holds, per residue, the plain integer sum of at most 8 residues of the same
+ * prime (< 2^63, e.g. after an all-reduce over ranks); reduces it mod q_i in
+ * place, on the given CUDA stream. */
+int tetris_reduce_sum_device(tetris_ctx *ctx, uint64_t *data, uint32_t level, uint32_t ncomp, void *stream);
 
 typedef struct {
     int32_t l_lin, l_d, l_y, l_u, l_out;
@@ -195,14 +206,30 @@ typedef struct {
 int tetris_plan(tetris_ctx *ctx, uint32_t db, uint32_t f_degree, uint32_t sign_stages,
                 tetris_plan_info *out);
 
+/* Autotuner: times the query's recorded program (device time, CUDA events,
+ * reps replays after one warm-up) under each candidate schedule -- blocks per
+ * launch in {all, 8, 4, 2, 1} (those below the database's block count) and
+ * NTT register groups of 8 or 16 elements per thread -- keeps the fastest as
+ * the context's options (TETRIS_OPT_BLOCKS_PER_LAUNCH, TETRIS_OPT_NTT_GROUP)
+ * and writes up to cap timings.  The keyswitch digit size is fixed by the
+ * loaded keys (chosen by the client at key generation). */
+typedef struct {
+    int32_t blocks_per_launch;  /* 0 = all */
+    int32_t ntt_group_log2;     /* 3 or 4 */
+    double ms;                  /* device time per query */
+} tetris_tune_entry;
+int tetris_autotune(tetris_ctx *ctx, uint32_t db, const tetris_query *query, uint32_t reps,
+                    tetris_tune_entry *out, uint32_t cap, uint32_t *n_out);
+
 /* Options. */
 enum {
     TETRIS_OPT_BLOCKS_PER_LAUNCH = 1,  /* 0: all blocks of a database in each launch (batched);
                                           k: k blocks per launch (1 = plain per-ciphertext form) */
     TETRIS_OPT_USE_GRAPH = 2,          /* 1: replay the query as a captured CUDA graph */
     TETRIS_OPT_KS_ALPHA = 3,           /* read-only: alpha of the loaded keys */
-    TETRIS_OPT_PROFILE = 4             /* 1: run queries eagerly with a CUDA event pair around
+    TETRIS_OPT_PROFILE = 4,            /* 1: run queries eagerly with a CUDA event pair around
                                           every launch, accumulating per-kernel statistics */
+    TETRIS_OPT_NTT_GROUP = 5           /* log2 of the NTT elements a thread holds: 3 or 4 */
 };
 int tetris_set_option(tetris_ctx *ctx, int option, int64_t value);
 int tetris_get_option(tetris_ctx *ctx, int option, int64_t *value);

@@ -73,6 +73,8 @@ class QueryShape:
     attrs: int
     degree: int
     sign_stages: list            # list of (a0, a1, a2, a3) for x, x^3, x^5, x^7
+    norm_records: int = 0        # records the count is normalised by (0: this database's own);
+                                 # the total over partitions for a horizontally split database (Section 4.4)
 
     def blocks(self, n_slots: int) -> int:
         return -(-self.records // n_slots)
@@ -118,7 +120,7 @@ def make_plan(par: Params, shape: QueryShape) -> Plan:
     l_out = l_u - 1 if ragged else l_u
     if l_out < 1:
         raise ValueError(f"circuit needs more levels: ends at level {l_out}")
-    R = float(shape.records)
+    R = float(shape.norm_records if shape.norm_records else shape.records)
     stages = []
     ns = len(shape.sign_stages)
     for s, co in enumerate(shape.sign_stages):

@@ -25,7 +25,7 @@ ERRORS = {-1: "EINVAL", -2: "ENOMEM", -3: "ECUDA", -4: "ELEVEL", -5: "ENOTFOUND"
 
 OP_ADD, OP_SUB, OP_TENSOR, OP_RELIN, OP_RESCALE, OP_MUL_INT, OP_ADD_INT = 1, 2, 3, 4, 5, 6, 7
 OP_AUTOMORPHISM, OP_ROTATE, OP_KEYSWITCH, OP_MUL_PLAIN, OP_NTT, OP_INNERSUM, OP_DROP = 8, 9, 10, 11, 12, 13, 14
-OPT_BLOCKS_PER_LAUNCH, OPT_USE_GRAPH, OPT_KS_ALPHA, OPT_PROFILE = 1, 2, 3, 4
+OPT_BLOCKS_PER_LAUNCH, OPT_USE_GRAPH, OPT_KS_ALPHA, OPT_PROFILE, OPT_NTT_GROUP = 1, 2, 3, 4, 5
 
 
 def build(force: bool = False) -> str:
@@ -51,7 +51,7 @@ class CtOut(C.Structure):
 class Query(C.Structure):
     _fields_ = [("n_attrs", C.c_uint32), ("w", C.POINTER(CtIn)), ("f_degree", C.c_uint32),
                 ("f_coeffs", C.POINTER(CtIn)), ("threshold", C.POINTER(CtIn)), ("sign_stages", C.c_uint32),
-                ("sign_degree", C.c_uint32), ("sign_coeffs", C.POINTER(C.c_double))]
+                ("sign_degree", C.c_uint32), ("sign_coeffs", C.POINTER(C.c_double)), ("total_records", C.c_uint64)]
 
 
 class CtxInfo(C.Structure):
@@ -69,6 +69,10 @@ class PlanInfo(C.Structure):
 class ServeStats(C.Structure):
     _fields_ = [("submitted", C.c_uint64), ("completed", C.c_uint64), ("rejected", C.c_uint64), ("p50_ms", C.c_double),
                 ("p99_ms", C.c_double), ("device_bytes", C.c_size_t), ("peak_device_bytes", C.c_size_t)]
+
+
+class TuneEntry(C.Structure):
+    _fields_ = [("blocks_per_launch", C.c_int32), ("ntt_group_log2", C.c_int32), ("ms", C.c_double)]
 
 
 class KernelStat(C.Structure):
@@ -97,6 +101,8 @@ SIGNATURES = {
     "tetris_evaluate_query": [_vp, _u32, C.POINTER(Query), C.POINTER(CtOut)],
     "tetris_evaluate_query_device": [_vp, _u32, C.POINTER(Query), C.POINTER(CtOut), _vp],
     "tetris_plan": [_vp, _u32, _u32, _u32, C.POINTER(PlanInfo)],
+    "tetris_reduce_sum_device": [_vp, _vp, _u32, _u32, _vp],
+    "tetris_autotune": [_vp, _u32, C.POINTER(Query), _u32, C.POINTER(TuneEntry), _u32, C.POINTER(_u32)],
     "tetris_set_option": [_vp, C.c_int, _i64],
     "tetris_get_option": [_vp, C.c_int, C.POINTER(_i64)],
     "tetris_op": [_vp, C.c_int, C.POINTER(CtIn), C.POINTER(CtIn), _i64, C.POINTER(CtOut)],
@@ -274,25 +280,38 @@ class Ctx:
         (torch CUDA tensors); enqueued on ``stream``."""
         check(lib().tetris_rescale_ntt_noalloc(self.h, _ptr(src), _ptr(dst), level, ncomp, stream))
 
+    def autotune(self, db: int, w, w_meta, c, c_meta, t, t_meta, sign_coeffs, reps: int = 3):
+        """Times the query under each candidate schedule, keeps the fastest;
+        returns [(blocks_per_launch, ntt_group_log2, ms)]."""
+        q, keep = self._query_struct(w, w_meta, c, c_meta, t, t_meta, sign_coeffs)
+        buf = (TuneEntry * 32)()
+        n = C.c_uint32()
+        check(lib().tetris_autotune(self.h, db, C.byref(q), reps, buf, 32, C.byref(n)))
+        return [(buf[i].blocks_per_launch, buf[i].ntt_group_log2, buf[i].ms) for i in range(n.value)]
+
+    def reduce_sum_device(self, data, level: int, ncomp: int = 2, stream: int = 0):
+        """In place: residue sums over partitions (torch CUDA int64 tensor) -> residues mod q_i."""
+        check(lib().tetris_reduce_sum_device(self.h, _ptr(data), level, ncomp, stream))
+
     def plan(self, db: int, degree: int, stages: int) -> PlanInfo:
         p = PlanInfo()
         check(lib().tetris_plan(self.h, db, degree, stages, C.byref(p)))
         return p
 
     # query
-    def _query_struct(self, w, w_meta, c, c_meta, t, t_meta, sign_coeffs):
+    def _query_struct(self, w, w_meta, c, c_meta, t, t_meta, sign_coeffs, total_records=0):
         W = (CtIn * len(w))(*[CtIn(lv, 2, sc, _ptr(x)) for x, (lv, sc) in zip(w, w_meta)])
         Cc = (CtIn * len(c))(*[CtIn(lv, 2, sc, _ptr(x)) for x, (lv, sc) in zip(c, c_meta)])
         T = CtIn(t_meta[0], 2, t_meta[1], _ptr(t))
         sc = np.ascontiguousarray(np.asarray(sign_coeffs, dtype=np.float64).reshape(-1))
         q = Query(len(w), W, len(c) - 1, Cc, C.pointer(T), sc.size // 4, 7,
-                  sc.ctypes.data_as(C.POINTER(C.c_double)))
+                  sc.ctypes.data_as(C.POINTER(C.c_double)), int(total_records))
         return q, (W, Cc, T, sc)
 
-    def evaluate_query(self, db: int, w, w_meta, c, c_meta, t, t_meta, sign_coeffs, out=None):
+    def evaluate_query(self, db: int, w, w_meta, c, c_meta, t, t_meta, sign_coeffs, out=None, total_records=0):
         """Host arrays: w/c/t are [2][level+1][N] uint64; metas are (level, scale).
         Returns (out array, level, scale)."""
-        q, keep = self._query_struct(w, w_meta, c, c_meta, t, t_meta, sign_coeffs)
+        q, keep = self._query_struct(w, w_meta, c, c_meta, t, t_meta, sign_coeffs, total_records)
         if out is None:
             out = np.empty(2 * (self.L + 1) * self.N, dtype=np.uint64)
         o = CtOut(0, 0, 0.0, _ptr(out), out.size if isinstance(out, np.ndarray) else out.numel())
@@ -300,9 +319,10 @@ class Ctx:
         n = 2 * (o.level + 1) * self.N
         return out[:n].reshape(2, o.level + 1, self.N), o.level, o.scale
 
-    def evaluate_query_device(self, db: int, w, w_meta, c, c_meta, t, t_meta, sign_coeffs, out, stream: int):
+    def evaluate_query_device(self, db: int, w, w_meta, c, c_meta, t, t_meta, sign_coeffs, out, stream: int,
+                              total_records=0):
         """torch CUDA tensors in and out; enqueued on ``stream`` (a cudaStream_t as int)."""
-        q, keep = self._query_struct(w, w_meta, c, c_meta, t, t_meta, sign_coeffs)
+        q, keep = self._query_struct(w, w_meta, c, c_meta, t, t_meta, sign_coeffs, total_records)
         o = CtOut(0, 0, 0.0, _ptr(out), out.numel())
         check(lib().tetris_evaluate_query_device(self.h, db, C.byref(q), C.byref(o), stream))
         return o.level, o.scale

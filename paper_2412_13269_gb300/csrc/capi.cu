@@ -115,9 +115,14 @@ static void build_tables(Ctx &C) {
 // ---------------------------------------------------------------------------
 static void set_alpha(Ctx &C, uint32_t alpha) {
     TREQUIRE(alpha >= 1 && (int)alpha <= kMaxConvSrc, TETRIS_EINVAL, "alpha must be in [1, 4]");
-    TREQUIRE(C.alpha == 0 || C.alpha == (int)alpha, TETRIS_EINVAL, "all keys of a context share one alpha");
     const int dnum = (C.L() + 1 + alpha - 1) / alpha;
     TREQUIRE(dnum <= 32, TETRIS_EINVAL, "too many key digits (at most 32)");
+    if (C.alpha != 0 && C.alpha != (int)alpha) {  // a new digit size: the old keys are unusable with it
+        cudaStreamSynchronize(C.stream);
+        C.programs.clear();
+        C.relin = Key();
+        C.rot.clear();
+    }
     C.alpha = alpha;
 }
 
@@ -669,6 +674,26 @@ int tetris_evaluate_query_device(tetris_ctx *ctx, uint32_t db, const tetris_quer
     });
 }
 
+int tetris_autotune(tetris_ctx *ctx, uint32_t db, const tetris_query *q, uint32_t reps, tetris_tune_entry *out,
+                    uint32_t cap, uint32_t *n_out) {
+    return guarded([&] {
+        TREQUIRE(ctx && n_out && (out || cap == 0), TETRIS_EINVAL, "null pointer");
+        cudaSetDevice(ctx->c.device);
+        std::vector<tetris_tune_entry> v;
+        autotune(ctx->c, db, q, (int)std::max(1u, reps), v);
+        *n_out = (uint32_t)std::min<size_t>(v.size(), cap);
+        for (uint32_t i = 0; i < *n_out; i++) out[i] = v[i];
+    });
+}
+
+int tetris_reduce_sum_device(tetris_ctx *ctx, uint64_t *data, uint32_t level, uint32_t ncomp, void *stream) {
+    return guarded([&] {
+        TREQUIRE(ctx, TETRIS_EINVAL, "null context");
+        cudaSetDevice(ctx->c.device);
+        reduce_sum(ctx->c, data, (int)level, (int)ncomp, reinterpret_cast<cudaStream_t>(stream));
+    });
+}
+
 int tetris_plan(tetris_ctx *ctx, uint32_t db, uint32_t f_degree, uint32_t sign_stages, tetris_plan_info *out) {
     return guarded([&] {
         TREQUIRE(ctx && out, TETRIS_EINVAL, "null pointer");
@@ -692,6 +717,10 @@ int tetris_set_option(tetris_ctx *ctx, int option, int64_t value) {
             case TETRIS_OPT_PROFILE:
                 C.profile = value ? 1 : 0;
                 break;
+            case TETRIS_OPT_NTT_GROUP:
+                TREQUIRE(value == 3 || value == 4, TETRIS_EINVAL, "NTT group must be 3 or 4");
+                C.nt.loge = (int)value;
+                break;
             default:
                 throw Error(TETRIS_EINVAL, "unknown or read-only option");
         }
@@ -707,6 +736,7 @@ int tetris_get_option(tetris_ctx *ctx, int option, int64_t *value) {
             case TETRIS_OPT_USE_GRAPH: *value = C.use_graph; break;
             case TETRIS_OPT_KS_ALPHA: *value = C.alpha; break;
             case TETRIS_OPT_PROFILE: *value = C.profile; break;
+            case TETRIS_OPT_NTT_GROUP: *value = C.nt.loge; break;
             default: throw Error(TETRIS_EINVAL, "unknown option");
         }
     });

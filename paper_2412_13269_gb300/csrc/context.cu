@@ -215,6 +215,7 @@ const char *ew_name(int op) {
         case EW_FMA: return "fma";
         case EW_TENSOR: return "tensor";
         case EW_ADD_MUL_CONST: return "addmulc";
+        case EW_REDUCE: return "reduce";
     }
     return "?";
 }

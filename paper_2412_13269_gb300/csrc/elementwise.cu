@@ -91,6 +91,13 @@ __global__ void __launch_bounds__(kEwThreads) ew_kernel(const EwJob *jobs, int n
                 r[1] = add_mod(b.y, shoup(a.y, J.k, J.k_sh, q), q);
                 break;
             }
+            case EW_REDUCE: {
+                ulonglong2 a = *reinterpret_cast<const ulonglong2 *>(J.a + p);
+                u64 x = a.x - __umul64hi(a.x, m.one_sh) * q, y = a.y - __umul64hi(a.y, m.one_sh) * q;
+                r[0] = x >= q ? x - q : x;
+                r[1] = y >= q ? y - q : y;
+                break;
+            }
             case EW_TENSOR: {
                 ulonglong2 a0 = *reinterpret_cast<const ulonglong2 *>(J.a + p);
                 ulonglong2 a1 = *reinterpret_cast<const ulonglong2 *>(J.a1 + p);

@@ -109,6 +109,7 @@ struct NttTables {
     const u64 *itw;     // [nprimes][N] psi^-brv(k)
     const u64 *itw_sh;
     const ModInfo *mods;
+    int loge = 3;       // log2 of the elements a thread holds (3 or 4)
 };
 
 // launchers (ntt.cu)
@@ -130,7 +131,8 @@ enum EwOp {
     EW_COPY = 6,      // dst = a
     EW_FMA = 7,       // dst = a * b + c
     EW_TENSOR = 8,    // a0,a1,b0,b1 -> d0,d1,d2 (pointers a,b,c,d with strides)
-    EW_ADD_MUL_CONST = 9  // dst = b + k * a  (used by key generation)
+    EW_ADD_MUL_CONST = 9, // dst = b + k * a  (used by key generation)
+    EW_REDUCE = 10        // dst = a mod q for any 64-bit a
 };
 struct EwJob {
     const u64 *a, *b, *c;

@@ -10,8 +10,9 @@
 // first log N1 stages; each column of the N1 x N2 row-major view is an
 // N1-point sub-problem) and a row pass (the remaining log N2 stages within
 // each contiguous row).  Inside a pass a CTA stages its tile in shared
-// memory; each thread holds E = 8 elements in registers and runs three
-// butterfly stages per visit (radix-8 groups; 64 registers, four CTAs per SM).  A thread loads its first
+// memory; each thread holds E = 8 (or 16) elements in registers and runs
+// three (four) butterfly stages per visit: radix-8 groups use 64 registers
+// and four CTAs per SM, radix-16 groups 80 registers and three.  A thread loads its first
 // group straight from global memory and stores its last group straight back
 // (both coalesced across the warp), so a 256-point sub-problem needs two
 // shared-memory exchanges.  Stage bit b of a sub-problem of size
@@ -31,10 +32,8 @@ namespace tetris {
 namespace {
 
 constexpr int kThreads = 256;
-#ifndef TETRIS_NTT_LOGE
-#define TETRIS_NTT_LOGE 3
-#endif
-constexpr int kLogE = TETRIS_NTT_LOGE;  // log2 of the elements a thread holds in registers
+// Register-group width: a thread holds 2^LOGEV elements.  Both widths are
+// compiled; NttTables::loge picks one per context (the autotuner's knob).
 
 struct PassParams {
     NttTables t;
@@ -83,10 +82,10 @@ struct Group {
 enum { M_PLAIN = 0, M_INT64 = 1, M_CONV = 2, M_STORE = 3, M_COMBINE = 4, M_CONVPRE = 5, M_REDUCE = 6, M_SCALED = 7 };
 constexpr bool is_second(int m) { return m == M_STORE || m == M_COMBINE || m == M_SCALED; }
 
-template <int LOGM, bool INV, bool COL, int MODE>
-__global__ void __launch_bounds__(kThreads, MODE == M_CONV ? 2 : (kLogE >= 4 ? 3 : 4)) ntt_pass_kernel(PassParams P) {
+template <int LOGM, bool INV, bool COL, int MODE, int LOGEV>
+__global__ void __launch_bounds__(kThreads, MODE == M_CONV ? 2 : (LOGEV >= 4 ? 3 : 4)) ntt_pass_kernel(PassParams P) {
     constexpr int M = 1 << LOGM;
-    constexpr int LOGE = LOGM >= kLogE ? kLogE : LOGM;
+    constexpr int LOGE = LOGM >= LOGEV ? LOGEV : LOGM;
     constexpr int E = 1 << LOGE;
     constexpr int T = M / E;
     constexpr int NG = (LOGM + LOGE - 1) / LOGE;
@@ -292,10 +291,10 @@ __global__ void __launch_bounds__(kThreads, MODE == M_CONV ? 2 : (kLogE >= 4 ? 3
     }
 }
 
-template <int LOGM, bool INV, bool COL, int MODE>
+template <int LOGM, bool INV, bool COL, int MODE, int LOGEV>
 void run_pass(const PassParams &P, int njobs, cudaStream_t st) {
     constexpr int M = 1 << LOGM;
-    constexpr int LOGE = LOGM >= kLogE ? kLogE : LOGM;
+    constexpr int LOGE = LOGM >= LOGEV ? LOGEV : LOGM;
     constexpr int T = M >> LOGE;
     const int nsub = COL ? (1 << P.log2) : (1 << P.log1);
     const int sub_cta = std::min(kThreads / T, nsub);
@@ -306,19 +305,25 @@ void run_pass(const PassParams &P, int njobs, cudaStream_t st) {
         PassParams Q = P;
         Q.jobs = P.jobs + j0;
         dim3 grid(nsub / sub_cta, std::min(65535, njobs - j0));
-        ntt_pass_kernel<LOGM, INV, COL, MODE><<<grid, threads, smem, st>>>(Q);
+        ntt_pass_kernel<LOGM, INV, COL, MODE, LOGEV><<<grid, threads, smem, st>>>(Q);
+    }
+}
+
+template <bool INV, bool COL, int MODE, int LOGEV>
+void by_size_v(int logm, const PassParams &P, int njobs, cudaStream_t st) {
+    switch (logm) {
+        case 5: run_pass<5, INV, COL, MODE, LOGEV>(P, njobs, st); break;
+        case 6: run_pass<6, INV, COL, MODE, LOGEV>(P, njobs, st); break;
+        case 7: run_pass<7, INV, COL, MODE, LOGEV>(P, njobs, st); break;
+        case 8: run_pass<8, INV, COL, MODE, LOGEV>(P, njobs, st); break;
+        default: throw Error(-1, "unsupported NTT pass size");
     }
 }
 
 template <bool INV, bool COL, int MODE>
 void by_size(int logm, const PassParams &P, int njobs, cudaStream_t st) {
-    switch (logm) {
-        case 5: run_pass<5, INV, COL, MODE>(P, njobs, st); break;
-        case 6: run_pass<6, INV, COL, MODE>(P, njobs, st); break;
-        case 7: run_pass<7, INV, COL, MODE>(P, njobs, st); break;
-        case 8: run_pass<8, INV, COL, MODE>(P, njobs, st); break;
-        default: throw Error(-1, "unsupported NTT pass size");
-    }
+    if (P.t.loge == 4) by_size_v<INV, COL, MODE, 4>(logm, P, njobs, st);
+    else by_size_v<INV, COL, MODE, 3>(logm, P, njobs, st);
 }
 
 // first pass: forward = column pass, inverse = row pass

@@ -177,9 +177,12 @@ struct QuerySpec {
     double t_scale = 0;
     std::vector<std::array<double, 4>> stages;
     int bpl = 0;
+    int loge = 3;                // NTT register-group width (log2 elements per thread)
+    uint64_t total_records = 0;  // 0: the database's own record count
     std::string key(uint32_t db) const {
         std::ostringstream o;
-        o << "q" << db << ":" << attrs << ":" << degree << ":" << bpl << ":" << t_level << ":";
+        o << "q" << db << ":" << attrs << ":" << degree << ":" << bpl << ":" << loge << ":" << t_level << ":"
+          << total_records << ":";
         auto bits = [&](double v) {
             uint64_t b;
             std::memcpy(&b, &v, 8);
@@ -202,6 +205,8 @@ QuerySpec spec_of(const Ctx &C, const Database &db, const tetris_query *q);
 void evaluate_query(Ctx &C, uint32_t db, const tetris_query *q, tetris_ct_out *out, cudaStream_t s, bool device);
 void plan_info(Ctx &C, uint32_t db, uint32_t degree, uint32_t stages, tetris_plan_info *out);
 void drop_programs_of_db(Ctx &C, uint32_t db);
+void reduce_sum(Ctx &C, u64 *data, int level, int ncomp, cudaStream_t s);
+void autotune(Ctx &C, uint32_t db, const tetris_query *q, int reps, std::vector<tetris_tune_entry> &out);
 
 // serve.cu
 void serve_start(Ctx &C, size_t budget, uint32_t max_inflight);

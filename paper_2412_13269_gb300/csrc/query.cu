@@ -34,7 +34,8 @@ static int ceil_log2(int k) {
     return r;
 }
 
-QPlan make_plan(const Ctx &C, uint64_t records, int degree, const std::vector<std::array<double, 4>> &stages) {
+QPlan make_plan(const Ctx &C, uint64_t records, int degree, const std::vector<std::array<double, 4>> &stages,
+                uint64_t norm_records = 0) {
     TREQUIRE(degree >= 1 && !stages.empty() && records >= 1, TETRIS_EINVAL, "empty query");
     QPlan p;
     const int L = C.L();
@@ -46,7 +47,7 @@ QPlan make_plan(const Ctx &C, uint64_t records, int degree, const std::vector<st
     p.ragged = records % n != 0;
     p.l_out = p.ragged ? p.l_u - 1 : p.l_u;
     TREQUIRE(p.l_out >= 1, TETRIS_ELEVEL, "circuit needs more levels: it would end at level " + std::to_string(p.l_out));
-    const double R = (double)records;
+    const double R = (double)(norm_records ? norm_records : records);
     const size_t ns = stages.size();
     for (size_t s = 0; s < ns; s++) {
         std::array<double, 4> c = stages[s];
@@ -145,7 +146,7 @@ std::unique_ptr<Program> record_query(Ctx &C, const Database &db, const QuerySpe
     auto P = std::make_unique<Program>();
     P->ctx = &C;
     Rec R(C, *P);
-    const QPlan pl = make_plan(C, db.records, q.degree, q.stages);
+    const QPlan pl = make_plan(C, db.records, q.degree, q.stages, q.total_records);
     const int L = C.L();
     const size_t N = C.N;
     // staging buffers for the inputs (coefficient domain on arrival, NTT in place)
@@ -275,6 +276,10 @@ QuerySpec spec_of(const Ctx &C, const Database &db, const tetris_query *q) {
         s.stages.push_back(a);
     }
     s.bpl = C.blocks_per_launch;
+    s.loge = C.nt.loge;
+    TREQUIRE(q->total_records == 0 || q->total_records >= db.records, TETRIS_EINVAL,
+             "query: total_records is smaller than the database");
+    s.total_records = q->total_records;
     return s;
 }
 
@@ -325,6 +330,81 @@ void evaluate_query(Ctx &C, uint32_t dbh, const tetris_query *q, tetris_ct_out *
     if (!device) TCHECK_CUDA(cudaStreamSynchronize(s));
 }
 
+// the residues of a sum over partitions, reduced: x mod q_i (x < 2^63)
+void reduce_sum(Ctx &C, u64 *data, int level, int ncomp, cudaStream_t s) {
+    TREQUIRE(data && level >= 0 && level <= C.L() && ncomp >= 1 && ncomp <= 3, TETRIS_EINVAL, "reduce_sum: bad shape");
+    Program P;
+    Rec R(C, P);
+    std::vector<EwJob> jobs;
+    for (int c = 0; c < ncomp; c++)
+        for (int i = 0; i <= level; i++) {
+            EwJob j{};
+            j.op = EW_REDUCE;
+            j.prime = i;
+            j.a = j.dst = data + ((size_t)c * (level + 1) + i) * C.N;
+            jobs.push_back(j);
+        }
+    R.ew(jobs);
+    P.finalize();
+    P.run(s);
+    TCHECK_CUDA(cudaStreamSynchronize(s));
+}
+
+// Time the recorded query under each candidate schedule; keep the fastest.
+void autotune(Ctx &C, uint32_t dbh, const tetris_query *q, int reps, std::vector<tetris_tune_entry> &out) {
+    auto it = C.dbs.find(dbh);
+    TREQUIRE(it != C.dbs.end(), TETRIS_ENOTFOUND, "unknown database handle");
+    const int blocks = it->second.blocks;
+    std::vector<int> bpls = {0};
+    for (int b : {8, 4, 2, 1})
+        if (b < blocks) bpls.push_back(b);
+    const int saved_bpl = C.blocks_per_launch, saved_loge = C.nt.loge;
+    double best = 1e300;
+    int best_bpl = saved_bpl, best_loge = saved_loge;
+    std::string best_key;
+    cudaEvent_t e0, e1;
+    TCHECK_CUDA(cudaEventCreate(&e0));
+    TCHECK_CUDA(cudaEventCreate(&e1));
+    for (int loge : {3, 4})
+        for (int bpl : bpls) {
+            C.blocks_per_launch = bpl;
+            C.nt.loge = loge;
+            QuerySpec spec = spec_of(C, it->second, q);
+            const std::string key = spec.key(dbh);
+            Program &P = get_program(C, dbh, spec);
+            size_t slot = 0;
+            auto put = [&](const tetris_ct_in &c) {
+                TCHECK_CUDA(cudaMemcpyAsync(P.in_slots[slot].first, c.data, P.in_slots[slot].second * 8,
+                                            cudaMemcpyHostToDevice, C.stream));
+                slot++;
+            };
+            for (uint32_t j = 0; j < q->n_attrs; j++) put(q->w[j]);
+            for (uint32_t k = 0; k <= q->f_degree; k++) put(q->f_coeffs[k]);
+            put(*q->threshold);
+            P.run_graph(C.stream);
+            TCHECK_CUDA(cudaEventRecord(e0, C.stream));
+            for (int r = 0; r < reps; r++) P.run_graph(C.stream);
+            TCHECK_CUDA(cudaEventRecord(e1, C.stream));
+            TCHECK_CUDA(cudaEventSynchronize(e1));
+            float ms = 0;
+            TCHECK_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+            out.push_back({bpl, loge, ms / reps});
+            if (ms / reps < best) {
+                if (!best_key.empty()) C.programs.erase(best_key);
+                best = ms / reps;
+                best_bpl = bpl;
+                best_loge = loge;
+                best_key = key;
+            } else {
+                C.programs.erase(key);  // keep only the winner's buffers
+            }
+        }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    C.blocks_per_launch = best_bpl;
+    C.nt.loge = best_loge;
+}
+
 void plan_info(Ctx &C, uint32_t dbh, uint32_t degree, uint32_t stages, tetris_plan_info *out) {
     auto it = C.dbs.find(dbh);
     TREQUIRE(it != C.dbs.end(), TETRIS_ENOTFOUND, "unknown database handle");
@@ -339,6 +419,7 @@ void plan_info(Ctx &C, uint32_t dbh, uint32_t degree, uint32_t stages, tetris_pl
     s.t_scale = C.scale;
     for (uint32_t i = 0; i < stages; i++) s.stages.push_back({35.0 / 16, -35.0 / 16, 21.0 / 16, -5.0 / 16});
     s.bpl = C.blocks_per_launch;
+    s.loge = C.nt.loge;
     QPlan pl = make_plan(C, it->second.records, degree, s.stages);
     Program &P = get_program(C, dbh, s);
     out->l_lin = pl.l_lin;

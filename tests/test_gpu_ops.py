@@ -189,3 +189,19 @@ def test_full_size_primitives():
     got, lev, _ = ctx.op(T.OP_RESCALE, a, l)
     assert np.array_equal(got, ckks.rescale(par, ckks.Ct(a, l, 1.0)).data)
     ctx.close()
+
+
+def test_reduce_sum_device(small):
+    torch = pytest.importorskip("torch")
+    par, ctx = small.par, small.ctx
+    l = par.L
+    parts = [rand_ct(par, 2, l, 70 + r) for r in range(4)]
+    sums = sum(p.astype(object) for p in parts)
+    dev = torch.from_numpy(np.array(sums, dtype=np.uint64).view(np.int64)).cuda()
+    ctx.reduce_sum_device(dev, l, 2, 0)
+    torch.cuda.synchronize()
+    got = dev.cpu().numpy().view(np.uint64)
+    acc = ckks.Ct(parts[0], l, 1.0)
+    for p_ in parts[1:]:
+        acc = ckks.add(par, acc, ckks.Ct(p_, l, 1.0))
+    assert np.array_equal(got, acc.data)

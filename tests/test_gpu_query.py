@@ -88,6 +88,45 @@ def test_query_bit_exact(chain, records, attrs, degree, nst):
     ctx.free_database(dbh)
 
 
+def test_autotune_keeps_results(chain):
+    par, ctx = chain.par, chain.ctx
+    vals, qv, stages, shape, plan, db, eq = make_case(par, chain.s, 3000, 3, 2, 1, 3000)
+    want = query.evaluate_query(par, chain.keys, shape, db, eq)
+    dbh = upload_encoded(ctx, par, plan, db, 3000, 3)
+    a = ([c.data for c in eq.w], [(c.level, c.scale) for c in eq.w], [c.data for c in eq.c],
+         [(c.level, c.scale) for c in eq.c], eq.t.data, (eq.t.level, eq.t.scale), np.array(stages))
+    table = ctx.autotune(dbh, *a, reps=2)
+    assert sorted((b, g) for b, g, _ in table) == [(0, 3), (0, 4), (1, 3), (1, 4)]
+    best = min(table, key=lambda e: e[2])
+    assert (ctx.get_option(T.OPT_BLOCKS_PER_LAUNCH), ctx.get_option(T.OPT_NTT_GROUP)) == best[:2]
+    for grp in (3, 4):
+        ctx.set_option(T.OPT_NTT_GROUP, grp)
+        assert np.array_equal(ctx.evaluate_query(dbh, *a)[0], want.data), grp
+    ctx.set_option(T.OPT_NTT_GROUP, 3)
+    ctx.set_option(T.OPT_BLOCKS_PER_LAUNCH, 0)
+    ctx.free_database(dbh)
+
+
+def test_partition_normalisation_bit_exact(chain):
+    """A partition of a larger database normalised by the total record count
+    (the horizontally partitioned database of Section 4.4)."""
+    par, ctx = chain.par, chain.ctx
+    vals = synth.database(synth.stream(41, "db"), 2048, 4)
+    qv = synth.query_values(synth.stream(41, "qv"), 4, 3)
+    shape = query.QueryShape(2048, 4, 3, [query.F3], norm_records=6144)
+    plan = query.make_plan(par, shape)
+    db = query.encode_database(par, plan, vals)
+    eq = query.encrypt_query(par, chain.s, qv, 41)
+    want = query.evaluate_query(par, chain.keys, shape, db, eq)
+    dbh = upload_encoded(ctx, par, plan, db, 2048, 4)
+    got = ctx.evaluate_query(dbh, *[v for v in (
+        [c.data for c in eq.w], [(c.level, c.scale) for c in eq.w], [c.data for c in eq.c],
+        [(c.level, c.scale) for c in eq.c], eq.t.data, (eq.t.level, eq.t.scale), np.array([query.F3]))],
+        total_records=6144)[0]
+    assert np.array_equal(got, want.data)
+    ctx.free_database(dbh)
+
+
 def test_device_buffers_match_host(chain):
     torch = pytest.importorskip("torch")
     par, ctx = chain.par, chain.ctx
