@@ -296,6 +296,60 @@ def run_c3(args):
     ctx.close()
 
 
+def run_c4(args):
+    """Uneven batch: 64 independent ciphertexts at ring degrees drawn from
+    {2^14, 2^15, 2^16} and levels from [4, 19] (seeded), each through
+    rescale(ct * pt) -> 1..16 rotations -> relinearise(y * y).  Times the
+    fixed per-item schedule against merged launches, and the automatic choice."""
+    import torch
+    import paper_2412_13269_gb300 as T
+    rank, world, local_rank = dist_env()
+    torch.cuda.set_device(local_rank)
+    T.build()
+    q, p = primes()
+    Delta = WL["scale"]
+    seed = 4000 + rank
+    ctxs = {}
+    for log_n in (14, 15, 16):
+        N = 1 << log_n
+        ctx = T.Ctx(log_n, q, p, Delta, device=local_rank)
+        s = synth.ternary_secret(synth.stream(seed, f"secret{log_n}"), N, WL["hw"])
+        dnum = -(-WL["n_q"] // WL["alpha"])
+        d = synth.switch_key_draws(seed, f"relin{log_n}", dnum, q + p, N)
+        ctx.keygen_relin(s, d.a, d.e, WL["alpha"])
+        for g in galois_elements(N):
+            d = synth.switch_key_draws(seed, f"rot{g}.{log_n}", dnum, q + p, N)
+            ctx.keygen_rotation(g, s, d.a, d.e, WL["alpha"])
+        ctxs[log_n] = ctx
+    g = np.random.default_rng(seed)
+    items = []
+    for i in range(64):
+        log_n = int(g.choice([14, 15, 16]))
+        N = 1 << log_n
+        level = int(g.integers(4, WL["n_q"]))
+        rot = int(g.integers(1, 17))
+        ct = np.stack([np.stack([g.integers(0, m, N, dtype=np.uint64) for m in q[: level + 1]]) for _ in range(2)])
+        pt = np.stack([g.integers(0, m, N, dtype=np.uint64) for m in q[: level + 1]])
+        items.append((ctxs[log_n], level, ct, pt, rot))
+    res = {}
+    for name, sched in (("per_item", T.SCHED_PER_ITEM), ("merged", T.SCHED_MERGED)):
+        T.batch_run(items, sched)  # warm-up (module loading, first allocations)
+        times = [T.batch_run(items, sched)[2] for _ in range(max(3, args.steps // 4))]
+        res[name] = statistics.median(times)
+    outs, used, ms_auto = T.batch_run(items, T.SCHED_AUTO)
+    line = {"metric": "uneven batch: device ms per batch of 64 ciphertexts", "workload": "c4", "unit": "ms",
+            "higher_is_better": False, "value": min(res.values()), "fixed_schedule_ms": res["per_item"],
+            "merged_ms": res["merged"], "auto_choice": "merged" if used == T.SCHED_MERGED else "per_item",
+            "auto_ms": ms_auto, "dtype": "u64", "data": "synthetic (seeded uniform residues)",
+            "config": {"workload": "64 ciphertexts, N in {2^14, 2^15, 2^16}, levels 4..19, 1..16 rotations each, "
+                                   "rescale(ct*pt) -> rotations -> relinearise(y*y); 20x50b + 3x60b primes, alpha 3",
+                       "degrees": {str(k): sum(1 for it in items if it[0] is v) for k, v in ctxs.items()},
+                       "rotations_total": sum(it[4] for it in items)}}
+    print(json.dumps(line), flush=True)
+    for c in ctxs.values():
+        c.close()
+
+
 SERVE_DBS = [(1 << 14, 8), (1 << 16, 16), (1 << 18, 24), (1 << 19, 32)]
 SERVE_TYPES = [("linear+threshold", 1), ("degree-15 poly+threshold", 15), ("degree-31 poly+composite sign", 31)]
 
@@ -383,7 +437,7 @@ def main():
     ap.add_argument("--no-plain", action="store_true")
     ap.add_argument("--ncu", action="store_true", help="profile exactly one query between cudaProfilerStart/Stop")
     ap.add_argument("--serve", action="store_true", help="serving workload: Poisson arrivals, mixed queries")
-    ap.add_argument("--workload", default="c2", choices=["c2", "c3"],
+    ap.add_argument("--workload", default="c2", choices=["c2", "c3", "c4"],
                     help="c2: 131072 x 16 (the default line); c3: batching, 524288 x 32 with the autotuner")
     ap.add_argument("--micro-keyswitch", type=int, default=0, metavar="CALLS",
                     help="top-level keyswitch via tetris_op, CALLS times; the last call between cudaProfilerStart/Stop")
@@ -398,6 +452,8 @@ def main():
         return run_micro_keyswitch(args.micro_keyswitch)
     if args.workload == "c3":
         return run_c3(args)
+    if args.workload == "c4":
+        return run_c4(args)
 
     import torch
     rank, world, local_rank = dist_env()

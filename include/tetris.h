@@ -269,6 +269,34 @@ int tetris_op(tetris_ctx *ctx, int opcode, const tetris_ct_in *a, const tetris_c
               int64_t arg, tetris_ct_out *out);
 
 /* ---------------------------------------------------------------------------
+ * Batches of independent ciphertext jobs at uneven ring degrees and levels.
+ * Item i, on its own context (ring degree), computes
+ *     y = rescale(ct * pt)                   (Section 2.5, App. A.1.2 slot product)
+ *     y = Rot(y), rotations times            (Rot by 5^(2^(k mod (log_n - 1))), k = 0, 1, ...)
+ *     out = relinearise(y * y)               (Appendix A.2)
+ * ct: [2][level+1][N] and pt: [level+1][N] host, coefficient domain,
+ * 1 <= level < n_q; out: [2][level][N] host.  Every item's context needs the
+ * relinearisation key and the rotation keys it uses; all contexts must be on
+ * one device.  Schedules give identical results:
+ *   TETRIS_SCHED_PER_ITEM  items one after another, each operation its own launches;
+ *   TETRIS_SCHED_MERGED    the k-th launch of all items of one ring degree that
+ *                          share kernel and mode is one launch (mixing levels);
+ *                          ring degrees run as concurrent programs;
+ *   TETRIS_SCHED_AUTO      times both, keeps the faster (*schedule_used).
+ * *device_ms receives the device time of the run (CUDA events). */
+typedef struct {
+    tetris_ctx *ctx;
+    uint32_t level;
+    const uint64_t *ct;
+    const uint64_t *pt;
+    uint32_t rotations;
+    uint64_t *out;
+} tetris_batch_item;
+enum { TETRIS_SCHED_PER_ITEM = 0, TETRIS_SCHED_MERGED = 1, TETRIS_SCHED_AUTO = 2 };
+int tetris_batch_run(const tetris_batch_item *items, uint32_t n_items, int schedule, int *schedule_used,
+                     double *device_ms);
+
+/* ---------------------------------------------------------------------------
  * Serving.  tetris_serve_start starts a server thread that owns the GPU work
  * of the context until tetris_serve_stop; in between, only tetris_submit,
  * tetris_poll, tetris_serve_stats and tetris_serve_stop may be called on the

@@ -71,6 +71,33 @@ class ServeStats(C.Structure):
                 ("p99_ms", C.c_double), ("device_bytes", C.c_size_t), ("peak_device_bytes", C.c_size_t)]
 
 
+class BatchItem(C.Structure):
+    _fields_ = [("ctx", C.c_void_p), ("level", C.c_uint32), ("ct", C.c_void_p), ("pt", C.c_void_p),
+                ("rotations", C.c_uint32), ("out", C.c_void_p)]
+
+
+SCHED_PER_ITEM, SCHED_MERGED, SCHED_AUTO = 0, 1, 2
+
+
+def batch_run(items, schedule: int = SCHED_AUTO):
+    """items: list of (Ctx, level, ct [2][level+1][N] uint64, pt [level+1][N] uint64, rotations).
+    Returns (outputs, schedule_used, device_ms)."""
+    keep, outs = [], []
+    arr = (BatchItem * len(items))()
+    for i, (ctx, level, ct, pt, rot) in enumerate(items):
+        ct = np.ascontiguousarray(ct, dtype=np.uint64)
+        pt = np.ascontiguousarray(pt, dtype=np.uint64)
+        out = np.empty((2, level, ctx.N), dtype=np.uint64)
+        keep += [ct, pt]
+        outs.append(out)
+        arr[i] = BatchItem(ctx.h.value if isinstance(ctx.h, C.c_void_p) else ctx.h, level, ct.ctypes.data,
+                           pt.ctypes.data, rot, out.ctypes.data)
+    used = C.c_int()
+    ms = C.c_double()
+    check(lib().tetris_batch_run(arr, len(items), schedule, C.byref(used), C.byref(ms)))
+    return outs, used.value, ms.value
+
+
 class TuneEntry(C.Structure):
     _fields_ = [("blocks_per_launch", C.c_int32), ("ntt_group_log2", C.c_int32), ("ms", C.c_double)]
 
@@ -102,6 +129,7 @@ SIGNATURES = {
     "tetris_evaluate_query_device": [_vp, _u32, C.POINTER(Query), C.POINTER(CtOut), _vp],
     "tetris_plan": [_vp, _u32, _u32, _u32, C.POINTER(PlanInfo)],
     "tetris_reduce_sum_device": [_vp, _vp, _u32, _u32, _vp],
+    "tetris_batch_run": [C.POINTER(BatchItem), _u32, C.c_int, C.POINTER(C.c_int), C.POINTER(C.c_double)],
     "tetris_autotune": [_vp, _u32, C.POINTER(Query), _u32, C.POINTER(TuneEntry), _u32, C.POINTER(_u32)],
     "tetris_set_option": [_vp, C.c_int, _i64],
     "tetris_get_option": [_vp, C.c_int, C.POINTER(_i64)],

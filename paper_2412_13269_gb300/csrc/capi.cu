@@ -6,10 +6,6 @@
 
 #include "program.h"
 
-struct tetris_ctx {
-    tetris::Ctx c;
-};
-
 namespace tetris {
 
 static thread_local std::string g_last_error;
@@ -739,6 +735,13 @@ int tetris_get_option(tetris_ctx *ctx, int option, int64_t *value) {
             case TETRIS_OPT_NTT_GROUP: *value = C.nt.loge; break;
             default: throw Error(TETRIS_EINVAL, "unknown option");
         }
+    });
+}
+
+int tetris_batch_run(const tetris_batch_item *items, uint32_t n, int schedule, int *used, double *device_ms) {
+    return guarded([&] {
+        TREQUIRE(schedule >= TETRIS_SCHED_PER_ITEM && schedule <= TETRIS_SCHED_AUTO, TETRIS_EINVAL, "unknown schedule");
+        batch_run(items, n, schedule, used, device_ms);
     });
 }
 

@@ -3,6 +3,7 @@
 // (rescale), Appendix A.2 (relinearisation, automorphism + key switch).
 #include <algorithm>
 #include <cstring>
+#include <type_traits>
 
 #include "program.h"
 
@@ -165,7 +166,7 @@ CtH Rec::new_ct(int B, int comps, int level) {
     c.level = level;
     c.cstride = (size_t)(level + 1) * C.N;
     c.bstride = c.cstride * comps;
-    c.buf = P.pool.alloc(c.bstride * B);
+    c.buf = pool().alloc(c.bstride * B);
     c.base = c.buf->ptr;
     return c;
 }
@@ -221,8 +222,52 @@ const char *ew_name(int op) {
 }
 }  // namespace
 
+template <class J>
+static Deferred make_deferred(int type, const std::vector<J> &jobs, const std::string &kind, double bytes) {
+    Deferred d;
+    d.type = type;
+    d.job_size = sizeof(J);
+    d.jobs.resize(jobs.size() * sizeof(J));
+    std::memcpy(d.jobs.data(), jobs.data(), d.jobs.size());
+    d.kind = kind;
+    d.bytes = bytes;
+    return d;
+}
+
+void Rec::emit(const Deferred &d) {
+    auto *saved = defer;
+    defer = nullptr;
+    const size_t n = d.jobs.size() / d.job_size;
+    auto as = [&](auto *tag) {
+        using J = std::remove_pointer_t<decltype(tag)>;
+        std::vector<J> v(n);
+        std::memcpy(v.data(), d.jobs.data(), d.jobs.size());
+        return v;
+    };
+    const std::string saved_prefix = prefix;
+    prefix.clear();
+    switch (d.type) {
+        case 0: ntt(d.inverse, as((NttJob *)nullptr), d.load_mode, d.store_mode); break;
+        case 1: ew(as((EwJob *)nullptr)); break;
+        case 2: aut(as((AutJob *)nullptr), d.galois); break;
+        case 3: kip(as((KipJob *)nullptr)); break;
+        case 4: lin(as((LinJob *)nullptr)); break;
+        case 5: red(as((RedJob *)nullptr)); break;
+    }
+    prefix = saved_prefix;
+    defer = saved;
+}
+
 void Rec::ntt(bool inverse, const std::vector<NttJob> &jobs, int load_mode, int store_mode) {
     if (jobs.empty()) return;
+    if (defer) {
+        Deferred d = make_deferred(0, jobs, prefix, 0);
+        d.inverse = inverse;
+        d.load_mode = load_mode;
+        d.store_mode = store_mode;
+        defer->push_back(std::move(d));
+        return;
+    }
     size_t off = P.add_jobs(jobs.data(), jobs.size() * sizeof(NttJob));
     int n = (int)jobs.size(), logn = C.log_n;
     NttTables t = C.nt;
@@ -250,6 +295,10 @@ void Rec::ntt(bool inverse, const std::vector<NttJob> &jobs, int load_mode, int 
 
 void Rec::ew(const std::vector<EwJob> &jobs) {
     if (jobs.empty()) return;
+    if (defer) {
+        defer->push_back(make_deferred(1, jobs, prefix + std::to_string(jobs[0].op), 0));
+        return;
+    }
     size_t off = P.add_jobs(jobs.data(), jobs.size() * sizeof(EwJob));
     int n = (int)jobs.size(), logn = C.log_n;
     const ModInfo *m = C.nt.mods;
@@ -270,6 +319,12 @@ void Rec::ew(const std::vector<EwJob> &jobs) {
 
 void Rec::aut(const std::vector<AutJob> &jobs, uint32_t g) {
     if (jobs.empty()) return;
+    if (defer) {
+        Deferred d = make_deferred(2, jobs, prefix, 0);
+        d.galois = g;
+        defer->push_back(std::move(d));
+        return;
+    }
     size_t off = P.add_jobs(jobs.data(), jobs.size() * sizeof(AutJob));
     int n = (int)jobs.size(), logn = C.log_n;
     P.add_launch([=](cudaStream_t s, const uint8_t *a) {
@@ -279,6 +334,10 @@ void Rec::aut(const std::vector<AutJob> &jobs, uint32_t g) {
 
 void Rec::kip(const std::vector<KipJob> &jobs) {
     if (jobs.empty()) return;
+    if (defer) {
+        defer->push_back(make_deferred(3, jobs, prefix, 0));
+        return;
+    }
     size_t off = P.add_jobs(jobs.data(), jobs.size() * sizeof(KipJob));
     int n = (int)jobs.size(), logn = C.log_n;
     const ModInfo *m = C.nt.mods;
@@ -296,6 +355,10 @@ void Rec::kip(const std::vector<KipJob> &jobs) {
 
 void Rec::lin(const std::vector<LinJob> &jobs) {
     if (jobs.empty()) return;
+    if (defer) {
+        defer->push_back(make_deferred(4, jobs, prefix, 0));
+        return;
+    }
     size_t off = P.add_jobs(jobs.data(), jobs.size() * sizeof(LinJob));
     int n = (int)jobs.size(), logn = C.log_n;
     const ModInfo *m = C.nt.mods;
@@ -313,6 +376,10 @@ void Rec::lin(const std::vector<LinJob> &jobs) {
 
 void Rec::red(const std::vector<RedJob> &jobs) {
     if (jobs.empty()) return;
+    if (defer) {
+        defer->push_back(make_deferred(5, jobs, prefix, 0));
+        return;
+    }
     size_t off = P.add_jobs(jobs.data(), jobs.size() * sizeof(RedJob));
     int n = (int)jobs.size(), logn = C.log_n;
     const ModInfo *m = C.nt.mods;
@@ -513,7 +580,7 @@ CtH Rec::keyswitch(int B, int l, const std::function<const u64 *(int, int)> &d, 
     P.ks_bytes += ((double)B * nl + 2.0 * dnum * ntg + 2.0 * B * nl) * N * 8;
     // 1. d -> coefficient domain, each limb already multiplied by its digit's
     //    [(Q_j/q_i)^-1]_{q_i} (folded with N^-1 into the transform's last store)
-    BufPtr dcoef = P.pool.alloc((size_t)B * nl * N);
+    BufPtr dcoef = pool().alloc((size_t)B * nl * N);
     {
         std::vector<NttJob> jobs;
         for (int i = 0; i < nl; i++) {
@@ -537,7 +604,7 @@ CtH Rec::keyswitch(int B, int l, const std::function<const u64 *(int, int)> &d, 
         ntt(true, jobs, LOAD_PLAIN, STORE_SCALED);
     }
     // 2. ModUp: digit j -> every prime outside it, then NTT (conversion fused into the load)
-    BufPtr mu = P.pool.alloc((size_t)B * dnum * ntg * N);
+    BufPtr mu = pool().alloc((size_t)B * dnum * ntg * N);
     auto mul = [&](int b, int j, int t) { return mu->ptr + (((size_t)b * dnum + j) * ntg + t) * N; };
     {
         std::vector<NttJob> jobs;
@@ -557,7 +624,7 @@ CtH Rec::keyswitch(int B, int l, const std::function<const u64 *(int, int)> &d, 
         ntt(false, jobs, LOAD_CONV_PRE, STORE_PLAIN);
     }
     // 3. key inner product over Q_l P
-    BufPtr acc = P.pool.alloc((size_t)B * 2 * ntg * N);
+    BufPtr acc = pool().alloc((size_t)B * 2 * ntg * N);
     auto accl = [&](int b, int c, int t) { return acc->ptr + (((size_t)b * 2 + c) * ntg + t) * N; };
     {
         std::vector<KipJob> jobs;
@@ -583,7 +650,7 @@ CtH Rec::keyswitch(int B, int l, const std::function<const u64 *(int, int)> &d, 
     dcoef.reset();
     // 4. ModDown: special limbs to the coefficient domain, stored as
     //    [(c_k + floor(P/2)) * (P/p_k)^-1]_{p_k} (floor(P/2) = (p_k - 1)/2 mod p_k)
-    BufPtr pc = P.pool.alloc((size_t)B * 2 * K * N);
+    BufPtr pc = pool().alloc((size_t)B * 2 * K * N);
     {
         std::vector<NttJob> jobs;
         for (int k = 0; k < K; k++) {
@@ -658,7 +725,7 @@ CtH Rec::rescale(const CtH &a) {
     const size_t N = C.N;
     const u64 ql = C.q[l], half = (ql - 1) / 2;
     // top limb to the coefficient domain, stored as [a_l + floor(q_l/2)]_{q_l}
-    BufPtr tmp = P.pool.alloc((size_t)a.B * a.comps * N);
+    BufPtr tmp = pool().alloc((size_t)a.B * a.comps * N);
     {
         std::vector<NttJob> jobs;
         for (int b = 0; b < a.B; b++)

@@ -124,12 +124,33 @@ struct Program {
     void add_launch(std::function<void(cudaStream_t, const uint8_t *)> fn, const std::string &kind, double bytes);
 };
 
+// A launch recorded but not yet emitted (batch schedules merge these): the
+// kernel, its parameters and its job table.
+struct Deferred {
+    int type = 0;  // 0 NTT (both passes), 1 elementwise, 2 automorphism, 3 key inner product, 4 lincomb, 5 reduce
+    bool inverse = false;
+    int load_mode = 0, store_mode = 0;
+    uint32_t galois = 0;
+    size_t job_size = 0;
+    std::vector<uint8_t> jobs;
+    std::string kind;
+    double bytes = 0;
+    std::string merge_key() const {
+        return std::to_string(type) + ":" + std::to_string(inverse) + ":" + std::to_string(load_mode) + ":" +
+               std::to_string(store_mode) + ":" + std::to_string(galois) + ":" + kind;
+    }
+};
+
 class Rec {
   public:
     Rec(Ctx &c, Program &p) : C(c), P(p) {}
     Ctx &C;
     Program &P;
-    std::string prefix;  // prepended to the kind of every launch recorded (profiling scopes)
+    std::string prefix;                     // prepended to the kind of every launch recorded (profiling scopes)
+    std::vector<Deferred> *defer = nullptr; // when set, launches are collected here instead of emitted
+    Pool *pool_override = nullptr;          // when set, buffers come from (and return to) this pool
+    Pool &pool() { return pool_override ? *pool_override : P.pool; }
+    void emit(const Deferred &d);           // turn a collected launch into a real one
 
     CtH new_ct(int B, int comps, int level);
     CtH view(const BufPtr &buf, u64 *base, int B, int comps, int level, size_t bstride, size_t cstride, double scale);
@@ -215,8 +236,16 @@ int serve_poll(Ctx &C, uint64_t ticket, tetris_ct_out *out, uint32_t timeout_ms)
 void serve_stats(Ctx &C, tetris_serve_stats *st, bool reset);
 void serve_stop(Ctx &C);
 
+// batch.cu
+void batch_run(const tetris_batch_item *items, uint32_t n, int schedule, int *used, double *device_ms);
+
 // noalloc.cu
 void rescale_ntt_noalloc(Ctx &C, const u64 *in, u64 *out, int level, int ncomp, cudaStream_t s);
 size_t noalloc_scratch_bytes();
 
 }  // namespace tetris
+
+// the opaque handle of the C ABI
+struct tetris_ctx {
+    tetris::Ctx c;
+};
