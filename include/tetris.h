@@ -243,7 +243,14 @@ typedef struct {
     uint32_t launches;
     double total_ms;
     double alg_bytes;
+    double alg_modmuls;   /* modular multiplications: butterflies, conversion and key products */
 } tetris_kernel_stat;
+
+/* Measured throughput of lazy Shoup modular multiplications (the operation
+ * every butterfly, conversion and constant product is built on) on a device:
+ * independent products in registers, no memory traffic, timed with CUDA
+ * events.  The integer-ALU roofline of the transforms is quoted against it. */
+int tetris_modmul_peak(int device, double *gmodmul_per_s);
 int tetris_get_kernel_stats(tetris_ctx *ctx, tetris_kernel_stat *out, uint32_t cap, uint32_t *n_out);
 
 /* ---------------------------------------------------------------------------

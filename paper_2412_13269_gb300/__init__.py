@@ -103,7 +103,8 @@ class TuneEntry(C.Structure):
 
 
 class KernelStat(C.Structure):
-    _fields_ = [("kind", C.c_char * 48), ("launches", C.c_uint32), ("total_ms", C.c_double), ("alg_bytes", C.c_double)]
+    _fields_ = [("kind", C.c_char * 48), ("launches", C.c_uint32), ("total_ms", C.c_double), ("alg_bytes", C.c_double),
+                ("alg_modmuls", C.c_double)]
 
 
 _vp, _u32, _u64, _i64, _sz, _d = C.c_void_p, C.c_uint32, C.c_uint64, C.c_int64, C.c_size_t, C.c_double
@@ -134,6 +135,7 @@ SIGNATURES = {
     "tetris_set_option": [_vp, C.c_int, _i64],
     "tetris_get_option": [_vp, C.c_int, C.POINTER(_i64)],
     "tetris_op": [_vp, C.c_int, C.POINTER(CtIn), C.POINTER(CtIn), _i64, C.POINTER(CtOut)],
+    "tetris_modmul_peak": [C.c_int, C.POINTER(C.c_double)],
     "tetris_get_kernel_stats": [_vp, C.POINTER(KernelStat), _u32, C.POINTER(_u32)],
     "tetris_rescale_ntt_noalloc": [_vp, _vp, _vp, _u32, _u32, _vp],
     "tetris_serve_start": [_vp, _sz, _u32],
@@ -173,6 +175,13 @@ def _ptr(a) -> int:
 
 def _is_device(a) -> bool:
     return not isinstance(a, np.ndarray)
+
+
+def modmul_peak(device: int = 0) -> float:
+    """Measured lazy-Shoup modular multiplications per second (G/s)."""
+    r = C.c_double()
+    check(lib().tetris_modmul_peak(device, C.byref(r)))
+    return r.value
 
 
 def gen_primes(bits: int, count: int, congruence_log2: int = 17, exclude=()) -> list:
@@ -301,7 +310,8 @@ class Ctx:
         buf = (KernelStat * 256)()
         n = C.c_uint32()
         check(lib().tetris_get_kernel_stats(self.h, buf, 256, C.byref(n)))
-        return {buf[i].kind.decode(): (buf[i].launches, buf[i].total_ms, buf[i].alg_bytes) for i in range(n.value)}
+        return {buf[i].kind.decode(): (buf[i].launches, buf[i].total_ms, buf[i].alg_bytes, buf[i].alg_modmuls)
+                for i in range(n.value)}
 
     def rescale_ntt_noalloc(self, src, dst, level: int, ncomp: int, stream: int = 0):
         """Allocation-free rescale of a device-resident NTT-order ciphertext

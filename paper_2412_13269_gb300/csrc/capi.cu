@@ -798,6 +798,14 @@ int tetris_rescale_ntt_noalloc(tetris_ctx *ctx, const uint64_t *in, uint64_t *ou
 
 size_t tetris_noalloc_scratch_bytes(void) { return noalloc_scratch_bytes(); }
 
+int tetris_modmul_peak(int device, double *rate) {
+    return guarded([&] {
+        TREQUIRE(rate, TETRIS_EINVAL, "null pointer");
+        TCHECK_CUDA(cudaSetDevice(device));
+        *rate = modmul_peak_probe();
+    });
+}
+
 int tetris_get_kernel_stats(tetris_ctx *ctx, tetris_kernel_stat *out, uint32_t cap, uint32_t *n_out) {
     return guarded([&] {
         TREQUIRE(ctx && n_out && (out || cap == 0), TETRIS_EINVAL, "null pointer");
@@ -810,6 +818,7 @@ int tetris_get_kernel_stats(tetris_ctx *ctx, tetris_kernel_stat *out, uint32_t c
                 o.launches = kv.second.launches;
                 o.total_ms = kv.second.ms;
                 o.alg_bytes = kv.second.bytes;
+                o.alg_modmuls = kv.second.modmuls;
             }
             n++;
         }

@@ -98,8 +98,9 @@ void Program::finalize() {
     TCHECK_CUDA(cudaMemcpy(arena_dev->ptr, arena.data(), arena.size(), cudaMemcpyHostToDevice));
 }
 
-void Program::add_launch(std::function<void(cudaStream_t, const uint8_t *)> fn, const std::string &kind, double bytes) {
-    launches.push_back({std::move(fn), kind, bytes});
+void Program::add_launch(std::function<void(cudaStream_t, const uint8_t *)> fn, const std::string &kind, double bytes,
+                         double modmuls) {
+    launches.push_back({std::move(fn), kind, bytes, modmuls});
     kernel_launches += 1;
 }
 
@@ -129,6 +130,7 @@ void Program::run_profiled(cudaStream_t s, std::map<std::string, KernelStat> &st
         k.launches += 1;
         k.ms += ms;
         k.bytes += launches[i].bytes;
+        k.modmuls += launches[i].modmuls;
         if (launches[i].kind.compare(0, 3, "ks.") == 0) ks_ms += ms;
     }
     if (ks_count) {
@@ -283,14 +285,22 @@ void Rec::ntt(bool inverse, const std::vector<NttJob> &jobs, int load_mode, int 
     }
     const double limb = (double)N * 8, w = n * limb;
     const std::string dir = inverse ? "ntt_inv" : "ntt_fwd";
+    const int log1 = (logn + 1) / 2, log2 = logn / 2;
+    double conv = 0;
+    if (load_mode == LOAD_CONV || load_mode == LOAD_CONV_PRE)
+        for (auto &j : jobs) conv += j.nsrc;
+    const double first_log = inverse ? log2 : log1, second_log = inverse ? log1 : log2;
+    const double mm1 = (double)n * N * first_log / 2 + conv * N;
+    const double mm2 = (double)n * N * (second_log / 2 + ((store_mode != STORE_PLAIN || inverse) ? 1 : 0));
     P.add_launch([=](cudaStream_t s, const uint8_t *a) {
         launch_ntt(inverse, logn, t, reinterpret_cast<const NttJob *>(a + off), n, load_mode, store_mode, s, 0);
-    }, prefix + dir + "_p1_" + load_name(load_mode), distinct_bytes(srcs, N) + w);
+    }, prefix + dir + "_p1_" + load_name(load_mode), distinct_bytes(srcs, N) + w, mm1);
     double b2 = 2 * w;
     if (store_mode == STORE_COMBINE) b2 += distinct_bytes(bases, N) + distinct_bytes(extras, N);
     P.add_launch([=](cudaStream_t s, const uint8_t *a) {
         launch_ntt(inverse, logn, t, reinterpret_cast<const NttJob *>(a + off), n, load_mode, store_mode, s, 1);
-    }, prefix + dir + "_p2_" + (store_mode == STORE_COMBINE ? "combine" : store_mode == STORE_SCALED ? "scaled" : "plain"), b2);
+    }, prefix + dir + "_p2_" + (store_mode == STORE_COMBINE ? "combine" : store_mode == STORE_SCALED ? "scaled" : "plain"), b2,
+                 mm2);
 }
 
 void Rec::ew(const std::vector<EwJob> &jobs) {
@@ -348,9 +358,11 @@ void Rec::kip(const std::vector<KipJob> &jobs) {
             rd.push_back(j.key0[d]);
             rd.push_back(j.key1[d]);
         }
+    double prods = 0;
+    for (auto &j : jobs) prods += 2.0 * j.ndig;
     P.add_launch([=](cudaStream_t s, const uint8_t *a) {
         launch_keyip(reinterpret_cast<const KipJob *>(a + off), n, logn, m, s);
-    }, prefix + "keyip", distinct_bytes(rd, C.N) + 2.0 * n * C.N * 8);
+    }, prefix + "keyip", distinct_bytes(rd, C.N) + 2.0 * n * C.N * 8, prods * C.N);
 }
 
 void Rec::lin(const std::vector<LinJob> &jobs) {

@@ -195,7 +195,46 @@ __global__ void __launch_bounds__(kEwThreads) reduce_i64_kernel(const RedJob *jo
     }
 }
 
+// Eight independent chains of lazy Shoup products per thread (the operation
+// of a butterfly); the chains never leave registers.
+__global__ void __launch_bounds__(kEwThreads) modmul_probe_kernel(u64 *sink, u64 q, u64 w, u64 wsh, int iters) {
+    u64 x[8];
+#pragma unroll
+    for (int k = 0; k < 8; k++) x[k] = (blockIdx.x * 1315423911ull + threadIdx.x * 2654435761ull + k) % q;
+    for (int it = 0; it < iters; it++) {
+#pragma unroll
+        for (int k = 0; k < 8; k++) x[k] = shoup_lazy(x[k], w, wsh, q);
+    }
+    u64 r = 0;
+#pragma unroll
+    for (int k = 0; k < 8; k++) r ^= x[k];
+    if (r == 0x12345) sink[0] = r;  // keeps the chains live; practically never taken
+}
+
 }  // namespace
+
+double modmul_peak_probe() {
+    const u64 q = 1152921504606584833ull;  // a 60-bit prime = 1 mod 2^17
+    const u64 w = 123456789012345ull % q;
+    const u64 wsh = (u64)(((u128)w << 64) / q);
+    const int sms = sm_count(), blocks = sms * 8, iters = 2048;
+    u64 *sink = nullptr;
+    TCHECK_CUDA(cudaMalloc(&sink, 8));
+    cudaEvent_t a, b;
+    TCHECK_CUDA(cudaEventCreate(&a));
+    TCHECK_CUDA(cudaEventCreate(&b));
+    modmul_probe_kernel<<<blocks, kEwThreads>>>(sink, q, w, wsh, 64);  // warm-up
+    TCHECK_CUDA(cudaEventRecord(a));
+    modmul_probe_kernel<<<blocks, kEwThreads>>>(sink, q, w, wsh, iters);
+    TCHECK_CUDA(cudaEventRecord(b));
+    TCHECK_CUDA(cudaEventSynchronize(b));
+    float ms = 0;
+    TCHECK_CUDA(cudaEventElapsedTime(&ms, a, b));
+    cudaEventDestroy(a);
+    cudaEventDestroy(b);
+    cudaFree(sink);
+    return (double)blocks * kEwThreads * iters * 8 / (ms * 1e-3) / 1e9;
+}
 
 void launch_ew(const EwJob *jobs, int njobs, int log_n, const ModInfo *mods, cudaStream_t s) {
     if (njobs <= 0) return;

@@ -185,6 +185,9 @@ struct RedJob {
 };
 void launch_reduce_i64(const RedJob *jobs_dev, int njobs, int log_n, const ModInfo *mods, cudaStream_t s);
 
+// measured lazy-Shoup modular multiplications per second (G/s) on the current device
+double modmul_peak_probe();
+
 // ---------------------------------------------------------------------------
 // FP64 encoder (encode.cu)
 // ---------------------------------------------------------------------------

@@ -36,7 +36,7 @@ struct Program;
 
 struct KernelStat {
     uint32_t launches = 0;
-    double ms = 0, bytes = 0;
+    double ms = 0, bytes = 0, modmuls = 0;
 };
 
 struct Ctx {
@@ -91,6 +91,7 @@ struct Launch {
     std::function<void(cudaStream_t, const uint8_t *)> fn;
     std::string kind;
     double bytes = 0;
+    double modmuls = 0;  // algorithmic modular multiplications (butterflies, conversion and key products)
 };
 
 struct Program {
@@ -121,7 +122,8 @@ struct Program {
     void run(cudaStream_t s);
     void run_graph(cudaStream_t s);
     void run_profiled(cudaStream_t s, std::map<std::string, KernelStat> &stats);
-    void add_launch(std::function<void(cudaStream_t, const uint8_t *)> fn, const std::string &kind, double bytes);
+    void add_launch(std::function<void(cudaStream_t, const uint8_t *)> fn, const std::string &kind, double bytes,
+                    double modmuls = 0);
 };
 
 // A launch recorded but not yet emitted (batch schedules merge these): the
