@@ -270,7 +270,9 @@ enum {
     TETRIS_OP_MUL_PLAIN = 11,   /* b is a plaintext (ncomp = 1, residues): a * b */
     TETRIS_OP_NTT = 12,         /* a -> internal evaluation order NTT (bit-reversed order) */
     TETRIS_OP_INNERSUM = 13,    /* sum of rotations by 2^k, k < log_n - 1 */
-    TETRIS_OP_DROP = 14         /* keep primes q_0..q_arg */
+    TETRIS_OP_DROP = 14,        /* keep primes q_0..q_arg */
+    TETRIS_OP_RELIN_RESCALE = 15, /* rescale(relin(a)) in one pass over the targets (same result) */
+    TETRIS_OP_RESCALE_MUL_INT = 16 /* rescale(a * arg) with the factor folded into the rescale (same result) */
 };
 int tetris_op(tetris_ctx *ctx, int opcode, const tetris_ct_in *a, const tetris_ct_in *b,
               int64_t arg, tetris_ct_out *out);

@@ -890,6 +890,8 @@ int tetris_op(tetris_ctx *ctx, int op, const tetris_ct_in *a, const tetris_ct_in
                 break;
             }
             case TETRIS_OP_DROP: r = R.drop(x, (int)arg); break;
+            case TETRIS_OP_RELIN_RESCALE: r = R.relin_rescale(x); break;
+            case TETRIS_OP_RESCALE_MUL_INT: r = R.rescale(x, arg); break;
             default: throw Error(TETRIS_EINVAL, "unknown opcode");
         }
         CtH o = R.from_ntt(r);

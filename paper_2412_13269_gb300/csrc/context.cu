@@ -260,8 +260,19 @@ void Rec::emit(const Deferred &d) {
     defer = saved;
 }
 
-void Rec::ntt(bool inverse, const std::vector<NttJob> &jobs, int load_mode, int store_mode) {
+static const char *store_name(int m) {
+    switch (m) {
+        case STORE_COMBINE: return "combine";
+        case STORE_SCALED: return "scaled";
+        case STORE_SCALED_CONV: return "scaledconv";
+    }
+    return "plain";
+}
+
+void Rec::ntt(bool inverse, const std::vector<NttJob> &jobs, int load_mode, int store_mode, int split,
+              int store_mode_b) {
     if (jobs.empty()) return;
+    TREQUIRE(split < 0 || !defer, TETRIS_EINVAL, "split transforms are not deferred");
     if (defer) {
         Deferred d = make_deferred(0, jobs, prefix, 0);
         d.inverse = inverse;
@@ -274,14 +285,12 @@ void Rec::ntt(bool inverse, const std::vector<NttJob> &jobs, int load_mode, int 
     int n = (int)jobs.size(), logn = C.log_n;
     NttTables t = C.nt;
     const size_t N = C.N;
-    std::vector<const void *> srcs, bases, extras;
+    std::vector<const void *> srcs;
     for (auto &j : jobs) {
         if (load_mode == LOAD_CONV || load_mode == LOAD_CONV_PRE)
             for (uint32_t s = 0; s < j.nsrc; s++) srcs.push_back(j.src + s * j.src_stride);
         else
             srcs.push_back(j.src);
-        bases.push_back(j.base);
-        extras.push_back(j.extra);
     }
     const double limb = (double)N * 8, w = n * limb;
     const std::string dir = inverse ? "ntt_inv" : "ntt_fwd";
@@ -291,16 +300,37 @@ void Rec::ntt(bool inverse, const std::vector<NttJob> &jobs, int load_mode, int 
         for (auto &j : jobs) conv += j.nsrc;
     const double first_log = inverse ? log2 : log1, second_log = inverse ? log1 : log2;
     const double mm1 = (double)n * N * first_log / 2 + conv * N;
-    const double mm2 = (double)n * N * (second_log / 2 + ((store_mode != STORE_PLAIN || inverse) ? 1 : 0));
     P.add_launch([=](cudaStream_t s, const uint8_t *a) {
         launch_ntt(inverse, logn, t, reinterpret_cast<const NttJob *>(a + off), n, load_mode, store_mode, s, 0);
     }, prefix + dir + "_p1_" + load_name(load_mode), distinct_bytes(srcs, N) + w, mm1);
-    double b2 = 2 * w;
-    if (store_mode == STORE_COMBINE) b2 += distinct_bytes(bases, N) + distinct_bytes(extras, N);
-    P.add_launch([=](cudaStream_t s, const uint8_t *a) {
-        launch_ntt(inverse, logn, t, reinterpret_cast<const NttJob *>(a + off), n, load_mode, store_mode, s, 1);
-    }, prefix + dir + "_p2_" + (store_mode == STORE_COMBINE ? "combine" : store_mode == STORE_SCALED ? "scaled" : "plain"), b2,
-                 mm2);
+    // second pass: one launch per store segment
+    auto second = [&](int j0, int j1, int mode) {
+        const int m = j1 - j0;
+        if (m <= 0) return;
+        double b2 = 2.0 * m * limb, extra_mm = 0;
+        std::vector<const void *> rd;
+        for (int j = j0; j < j1; j++) {
+            if (mode == STORE_COMBINE) {
+                rd.push_back(jobs[j].base);
+                rd.push_back(jobs[j].extra);
+            } else if (mode == STORE_SCALED_CONV) {
+                for (uint32_t k = 0; k < jobs[j].nsrc; k++) rd.push_back(jobs[j].base + k * jobs[j].src_stride);
+                extra_mm += jobs[j].nsrc;
+            }
+        }
+        b2 += distinct_bytes(rd, N);
+        const double mm2 = (double)m * N * (second_log / 2 + ((mode != STORE_PLAIN || inverse) ? 1 : 0)) + extra_mm * N;
+        const size_t o2 = off + (size_t)j0 * sizeof(NttJob);
+        P.add_launch([=](cudaStream_t s, const uint8_t *a) {
+            launch_ntt(inverse, logn, t, reinterpret_cast<const NttJob *>(a + o2), m, load_mode, mode, s, 1);
+        }, prefix + dir + "_p2_" + store_name(mode), b2, mm2);
+    };
+    if (split < 0 || split >= n) {
+        second(0, n, store_mode);
+    } else {
+        second(0, split, store_mode);
+        second(split, n, store_mode_b);
+    }
 }
 
 void Rec::ew(const std::vector<EwJob> &jobs) {
@@ -352,14 +382,17 @@ void Rec::kip(const std::vector<KipJob> &jobs) {
     int n = (int)jobs.size(), logn = C.log_n;
     const ModInfo *m = C.nt.mods;
     std::vector<const void *> rd;
-    for (auto &j : jobs)
+    double prods = 0;
+    for (auto &j : jobs) {
         for (uint32_t d = 0; d < j.ndig; d++) {
             rd.push_back(j.src[d]);
             rd.push_back(j.key0[d]);
             rd.push_back(j.key1[d]);
         }
-    double prods = 0;
-    for (auto &j : jobs) prods += 2.0 * j.ndig;
+        rd.push_back(j.ex0);
+        rd.push_back(j.ex1);
+        prods += 2.0 * j.ndig + (j.ex0 ? 1 : 0) + (j.ex1 ? 1 : 0);
+    }
     P.add_launch([=](cudaStream_t s, const uint8_t *a) {
         launch_keyip(reinterpret_cast<const KipJob *>(a + off), n, logn, m, s);
     }, prefix + "keyip", distinct_bytes(rd, C.N) + 2.0 * n * C.N * 8, prods * C.N);
@@ -577,9 +610,21 @@ NttJob Rec::conv_job(uint32_t dst_prime, const u64 *src, uint32_t first, int nsr
 // Hybrid SwitchKey (Section 2.4.1) on B polynomials d(b, i), i <= l, NTT domain:
 // ModUp each CRT digit to Q_l P, inner product with the key, ModDown by P.
 // extra(b, c, i) (may return null) is added to component c of the result.
+//
+// rescale_after (l >= 1, K < 4): the result is rescaled by q_l as well, with
+// the same arithmetic as rescale(keyswitch(...)) but one forward transform per
+// remaining target instead of two.  By linearity of the NTT modulo q_i, for
+// i < l
+//   out_i = ((acc_i + P e_i) - NTT(P u_i)) (P q_l)^-1,
+//   u_i   = sum_k y_k [p_k^-1]_{q_i} + [a_l]_{q_i} - [floor(P/2) P^-1 + floor(q_l/2)]_{q_i},
+// where y_k are the scaled special limbs (step 4), e the extra term and a_l the
+// coefficient-domain top limb of the unrescaled result plus floor(q_l/2), which
+// the inverse transform of acc_l + P e_l yields with the conversion to q_l
+// subtracted in its store.  P e is folded into the key inner product.
 CtH Rec::keyswitch(int B, int l, const std::function<const u64 *(int, int)> &d, const Key &key,
-                   const std::function<const u64 *(int, int, int)> &extra) {
+                   const std::function<const u64 *(int, int, int)> &extra, bool rescale_after) {
     const int nl = l + 1, K = C.K(), ntg = nl + K, alpha = C.alpha;
+    const bool fused = rescale_after && l >= 1 && K + 1 <= kMaxConvSrc;
     const int dnum = (nl + alpha - 1) / alpha;
     const size_t N = C.N;
     TREQUIRE(K >= 1 && K <= kMaxConvSrc && alpha <= kMaxConvSrc, TETRIS_EINVAL, "keyswitch: K or alpha too large");
@@ -635,6 +680,17 @@ CtH Rec::keyswitch(int B, int l, const std::function<const u64 *(int, int)> &d, 
         }
         ntt(false, jobs, LOAD_CONV_PRE, STORE_PLAIN);
     }
+    // P mod q_i, floor(P/2) mod q_i
+    auto pmod = [&](int i) {
+        const u64 qi = C.q[i];
+        u64 pm = 1 % qi;
+        for (int k = 0; k < K; k++) pm = h_mulmod(pm, C.p[k] % qi, qi);
+        return pm;
+    };
+    auto halfp = [&](int i) {
+        const u64 qi = C.q[i];
+        return h_mulmod((pmod(i) + qi - 1) % qi, h_invmod(2, qi), qi);
+    };
     // 3. key inner product over Q_l P
     BufPtr acc = pool().alloc((size_t)B * 2 * ntg * N);
     auto accl = [&](int b, int c, int t) { return acc->ptr + (((size_t)b * 2 + c) * ntg + t) * N; };
@@ -654,12 +710,99 @@ CtH Rec::keyswitch(int B, int l, const std::function<const u64 *(int, int)> &d, 
                 k.acc1 = accl(b, 1, t);
                 k.prime = gp;
                 k.ndig = dnum;
+                if (fused && t < nl && extra) {
+                    k.ex0 = extra(b, 0, t);
+                    k.ex1 = extra(b, 1, t);
+                    k.pm = pmod(t);
+                }
                 jobs.push_back(k);
             }
         kip(jobs);
     }
     mu.reset();
     dcoef.reset();
+    if (fused) {
+        // 4'. the special limbs as in step 4 into slots 0..K-1 of each (b, c), and
+        //     acc_l + P e_l into slot K as a_l = [x N^-1 P^-1 - sum_k y_k p_k^-1
+        //     + floor(P/2) P^-1 + floor(q_l/2)]_{q_l} (its store reads slots 0..K-1)
+        const int K1 = K + 1;
+        BufPtr pc = pool().alloc((size_t)B * 2 * K1 * N);
+        auto slot = [&](int b, int c, int k) { return pc->ptr + (((size_t)b * 2 + c) * K1 + k) * N; };
+        std::vector<NttJob> jobs;
+        for (int k = 0; k < K; k++) {
+            const uint32_t gp = C.L() + 1 + k;
+            const u64 pk = C.p[k];
+            u64 hat = 1 % pk;
+            for (int r = 0; r < K; r++)
+                if (r != k) hat = h_mulmod(hat, C.p[r] % pk, pk);
+            const u64 c1 = h_invmod(hat, pk);
+            NttJob proto{};
+            proto.prime = gp;
+            proto.mul = h_mulmod(C.mods_host[gp].ninv, c1, pk);
+            proto.mul_sh = h_shoup(proto.mul, pk);
+            proto.conv_sub = h_mulmod((pk - 1) / 2, c1, pk);
+            for (int b = 0; b < B; b++)
+                for (int c = 0; c < 2; c++) {
+                    NttJob j = proto;
+                    j.src = accl(b, c, nl + k);
+                    j.dst = slot(b, c, k);
+                    jobs.push_back(j);
+                }
+        }
+        const int split = (int)jobs.size();
+        {
+            const u64 ql = C.q[l];
+            const u64 pinv = h_invmod(pmod(l), ql);
+            NttJob proto{};
+            proto.prime = l;
+            proto.mul = h_mulmod(C.mods_host[l].ninv, pinv, ql);
+            proto.mul_sh = h_shoup(proto.mul, ql);
+            proto.conv_sub = (h_mulmod(halfp(l), pinv, ql) + (ql - 1) / 2) % ql;
+            proto.nsrc = K;
+            proto.src_stride = N;
+            for (int k = 0; k < K; k++) {
+                proto.c2[k] = h_invmod(C.p[k] % ql, ql);
+                proto.c2_sh[k] = h_shoup(proto.c2[k], ql);
+            }
+            for (int b = 0; b < B; b++)
+                for (int c = 0; c < 2; c++) {
+                    NttJob j = proto;
+                    j.src = accl(b, c, l);
+                    j.dst = slot(b, c, K);
+                    j.base = slot(b, c, 0);
+                    jobs.push_back(j);
+                }
+        }
+        ntt(true, jobs, LOAD_PLAIN, STORE_SCALED, split, STORE_SCALED_CONV);
+        // 5'. targets i < l: load P u_i (K + 1 sources), out_i = (acc_i - x) (P q_l)^-1
+        CtH out = new_ct(B, 2, l - 1);
+        jobs.clear();
+        const u64 ql = C.q[l];
+        for (int i = 0; i < l; i++) {
+            const u64 qi = C.q[i];
+            const u64 pm = pmod(i);
+            NttJob proto = conv_job(i, nullptr, C.L() + 1, K, nullptr);
+            proto.nsrc = K1;
+            proto.src_prime[K] = l;
+            proto.c2[K] = pm;
+            proto.c2_sh[K] = h_shoup(pm, qi);
+            proto.conv_sub = (halfp(i) + h_mulmod(pm, ((ql - 1) / 2) % qi, qi)) % qi;
+            proto.mul = h_invmod(h_mulmod(pm, ql % qi, qi), qi);
+            proto.mul_sh = h_shoup(proto.mul, qi);
+            for (int b = 0; b < B; b++)
+                for (int c = 0; c < 2; c++) {
+                    NttJob jb = proto;
+                    jb.src = slot(b, c, 0);
+                    jb.base = accl(b, c, i);
+                    jb.dst = out.limb(b, c, i);
+                    jobs.push_back(jb);
+                }
+        }
+        ntt(false, jobs, LOAD_CONV_PRE, STORE_COMBINE);
+        P.rescales++;
+        prefix = saved_prefix;
+        return out;
+    }
     // 4. ModDown: special limbs to the coefficient domain, stored as
     //    [(c_k + floor(P/2)) * (P/p_k)^-1]_{p_k} (floor(P/2) = (p_k - 1)/2 mod p_k)
     BufPtr pc = pool().alloc((size_t)B * 2 * K * N);
@@ -728,12 +871,33 @@ CtH Rec::relin(const CtH &t) {
     return o;
 }
 
+CtH Rec::relin_rescale(const CtH &t) {
+    TREQUIRE(t.comps == 3, TETRIS_EINVAL, "relin: needs a degree-2 ciphertext");
+    TREQUIRE(t.level >= 1, TETRIS_ELEVEL, "rescale at level 0");
+    if (defer || C.K() + 1 > kMaxConvSrc) return rescale(relin(t));
+    const Key &k = find_key(C, 0);
+    CtH o = keyswitch(t.B, t.level, [&](int b, int i) { return (const u64 *)t.limb(b, 2, i); }, k,
+                      [&](int b, int c, int i) { return (const u64 *)t.limb(b, c, i); }, true);
+    o.scale = t.scale / (double)C.q[t.level];
+    P.relins++;
+    return o;
+}
+
 // Rescale (Section 2.5), per coefficient:
 //   out_i = (a_i + [floor(q_l/2)]_{q_i} - [[a_l + floor(q_l/2)]_{q_l}]_{q_i}) * q_l^-1;
 // the two constants are folded into the converted top limb before its NTT.
-CtH Rec::rescale(const CtH &a) {
+// With an integer factor f the input is f*a (rescale(mul_int(a, f))): f goes
+// into the top limb's inverse-transform store, and for i < l
+//   out_i = (a_i - NTT(f^-1 ([t]_{q_i} - [floor(q_l/2)]_{q_i}))) * f q_l^-1,
+// t the converted top limb, which needs f invertible modulo every q_i.
+CtH Rec::rescale(const CtH &a, int64_t factor) {
     const int l = a.level;
     TREQUIRE(l >= 1, TETRIS_ELEVEL, "rescale at level 0");
+    if (factor != 1) {
+        bool invertible = true;
+        for (int i = 0; i <= l; i++) invertible = invertible && signed_mod(factor, C.q[i]) != 0;
+        if (!invertible) return rescale(mul_int(a, factor));
+    }
     const size_t N = C.N;
     const u64 ql = C.q[l], half = (ql - 1) / 2;
     // top limb to the coefficient domain, stored as [a_l + floor(q_l/2)]_{q_l}
@@ -746,8 +910,8 @@ CtH Rec::rescale(const CtH &a) {
                 j.src = a.limb(b, c, l);
                 j.dst = tmp->ptr + ((size_t)b * a.comps + c) * N;
                 j.prime = l;
-                j.mul = C.mods_host[l].ninv;
-                j.mul_sh = C.mods_host[l].ninv_sh;
+                j.mul = h_mulmod(C.mods_host[l].ninv, signed_mod(factor, ql), ql);
+                j.mul_sh = h_shoup(j.mul, ql);
                 j.conv_sub = half;
                 jobs.push_back(j);
             }
@@ -762,6 +926,13 @@ CtH Rec::rescale(const CtH &a) {
         proto.prime = i;
         proto.conv_sub = half % qi;
         proto.mul = h_invmod(ql % qi, qi);
+        if (factor != 1) {
+            const u64 f = signed_mod(factor, qi), finv = h_invmod(f, qi);
+            proto.c2[0] = finv;
+            proto.c2_sh[0] = h_shoup(finv, qi);
+            proto.conv_sub = h_mulmod(proto.conv_sub, finv, qi);
+            proto.mul = h_mulmod(proto.mul, f, qi);
+        }
         proto.mul_sh = h_shoup(proto.mul, qi);
         for (int b = 0; b < a.B; b++)
             for (int c = 0; c < a.comps; c++) {
@@ -844,14 +1015,14 @@ CtH Rec::adjust(const CtH &a, int lt, double factor) {
     TREQUIRE(a.level > lt, TETRIS_ELEVEL, "input ciphertext level too low");
     CtH v = drop(a, lt + 1);
     const int64_t cst = round_half_up(((factor * C.S[lt]) * (double)C.q[lt + 1]) / a.scale);
-    CtH o = rescale(mul_int(v, cst));
+    CtH o = rescale(v, cst);
     o.scale = C.S[lt];
     return o;
 }
 
 CtH Rec::mul(const CtH &a, const CtH &b) {
     TREQUIRE(a.level == b.level, TETRIS_EINVAL, "mul: levels differ");
-    CtH o = rescale(relin(tensor(a, b)));
+    CtH o = relin_rescale(tensor(a, b));
     o.scale = C.S[a.level - 1];
     return o;
 }

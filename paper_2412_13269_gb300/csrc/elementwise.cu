@@ -155,6 +155,8 @@ __global__ void __launch_bounds__(kEwThreads) keyip_kernel(const KipJob *jobs, i
             acc_mad(a0, x, __ldg(J.key0[d] + p));
             acc_mad(a1, x, __ldg(J.key1[d] + p));
         }
+        if (J.ex0) acc_mad(a0, J.ex0[p], J.pm);
+        if (J.ex1) acc_mad(a1, J.ex1[p], J.pm);
         J.acc0[p] = reduce128(a0.hi, a0.lo, m);
         J.acc1[p] = reduce128(a1.hi, a1.lo, m);
     }

@@ -78,11 +78,14 @@ class Pool {
 // LOAD_CONV:     sum_s [(src_s + add_s) * c1_s]_{q_s} * c2_s - conv_sub
 // LOAD_CONV_PRE: sum_s src_s * c2_s - conv_sub (sources already scaled by c1_s, see STORE_SCALED;
 //                each product a lazy Shoup product, so nsrc * 2q < 2^64)
-// LOAD_REDUCE:   [src]_{q_dst} - conv_sub (a single source of another prime)
+// LOAD_REDUCE:   [src * c]_{q_dst} - conv_sub (a single source of another prime;
+//                c = c2[0] when nonzero, else 1)
 enum LoadMode { LOAD_PLAIN = 0, LOAD_CONV = 1, LOAD_INT64 = 2, LOAD_CONV_PRE = 3, LOAD_REDUCE = 4 };
 // STORE_SCALED (inverse transforms only): x * mul + conv_sub, where mul already
 // carries N^-1; it precomputes the per-source factor of a following conversion.
-enum StoreMode { STORE_PLAIN = 0, STORE_COMBINE = 1, STORE_SCALED = 2 };
+// STORE_SCALED_CONV (inverse only): x * mul + conv_sub - sum_s base_s * c2_s, the
+// nsrc sources base + s*src_stride in the coefficient domain.
+enum StoreMode { STORE_PLAIN = 0, STORE_COMBINE = 1, STORE_SCALED = 2, STORE_SCALED_CONV = 3 };
 
 // One limb transform.  LOAD_CONV computes, per coefficient,
 //   sum_s [ (src_s + add_s) * c1_s ]_{q_s} * c2_s - conv_sub  mod q_dst
@@ -160,6 +163,8 @@ struct KipJob {
     const u64 *key0[32];  // per digit key limb for component 0
     const u64 *key1[32];
     u64 *acc0, *acc1;
+    const u64 *ex0, *ex1;  // optional: acc_c += pm * ex_c (ModDown's P * d folded into the sum)
+    u64 pm;
     uint32_t prime;
     uint32_t ndig;
 };

@@ -78,9 +78,11 @@ struct Group {
 // MODE: 0/1/2 = first pass loading plain / int64 / base conversion;
 //       3/4 = second pass storing plain / combined.
 //       5/6 = first pass loading pre-scaled conversion sources / a reduction;
-//       7 = second pass of an inverse transform storing x * mul + add.
-enum { M_PLAIN = 0, M_INT64 = 1, M_CONV = 2, M_STORE = 3, M_COMBINE = 4, M_CONVPRE = 5, M_REDUCE = 6, M_SCALED = 7 };
-constexpr bool is_second(int m) { return m == M_STORE || m == M_COMBINE || m == M_SCALED; }
+//       7 = second pass of an inverse transform storing x * mul + add;
+//       8 = as 7, less a base conversion of coefficient-domain sources.
+enum { M_PLAIN = 0, M_INT64 = 1, M_CONV = 2, M_STORE = 3, M_COMBINE = 4, M_CONVPRE = 5, M_REDUCE = 6, M_SCALED = 7,
+       M_SCALED_CONV = 8 };
+constexpr bool is_second(int m) { return m == M_STORE || m == M_COMBINE || m == M_SCALED || m == M_SCALED_CONV; }
 
 template <int LOGM, bool INV, bool COL, int MODE, int LOGEV>
 __global__ void __launch_bounds__(kThreads, MODE == M_CONV ? 2 : (LOGEV >= 4 ? 3 : 4)) ntt_pass_kernel(PassParams P) {
@@ -137,10 +139,10 @@ __global__ void __launch_bounds__(kThreads, MODE == M_CONV ? 2 : (LOGEV >= 4 ? 3
     } else if (MODE == M_REDUCE) {
         const u64 *src = J.src;
         const u64 sub = J.conv_sub;
+        const u64 c = J.c2[0] ? J.c2[0] : 1, csh = J.c2[0] ? J.c2_sh[0] : mi.one_sh;
 #pragma unroll
         for (int k = 0; k < E; k++) {
-            u64 v = src[gidx(lrow(k))];
-            v = v - __umul64hi(v, mi.one_sh) * q;  // Shoup product with w = 1: [0, 2q)
+            u64 v = shoup_lazy(src[gidx(lrow(k))], c, csh, q);  // [0, 2q) for any 64-bit source
             v = v >= q ? v - q : v;
             x[k] = sub_mod(v, sub, q);
         }
@@ -276,7 +278,7 @@ __global__ void __launch_bounds__(kThreads, MODE == M_CONV ? 2 : (LOGEV >= 4 ? 3
         for (int k = 0; k < E; k++) {
             const size_t gi = gidx(srow(k));
             u64 v = x[k];
-            if (MODE == M_SCALED) v = add_mod(shoup(v, mul, mulsh, q), addk, q);
+            if (MODE == M_SCALED || MODE == M_SCALED_CONV) v = add_mod(shoup(v, mul, mulsh, q), addk, q);
             else if (INV) v = shoup(v, mi.ninv, mi.ninv_sh, q);
             else {
                 v = v >= q2 ? v - q2 : v;
@@ -285,6 +287,17 @@ __global__ void __launch_bounds__(kThreads, MODE == M_CONV ? 2 : (LOGEV >= 4 ? 3
             if (MODE == M_COMBINE) {
                 v = shoup(sub_mod(base[gi], v, q), mul, mulsh, q);
                 if (extra) v = add_mod(v, extra[gi], q);
+            }
+            if (MODE == M_SCALED_CONV) {
+                // sum_s base_s * c2_s as lazy Shoup products (< 8q), reduced, subtracted
+                u64 c = 0;
+#pragma unroll
+                for (int sidx = 0; sidx < kMaxConvSrc; sidx++)
+                    if (sidx < (int)J.nsrc) c += shoup_lazy(base[sidx * J.src_stride + gi], J.c2[sidx], J.c2_sh[sidx], q);
+                c = c >= 4 * q ? c - 4 * q : c;
+                c = c >= q2 ? c - q2 : c;
+                c = c >= q ? c - q : c;
+                v = sub_mod(v, c, q);
             }
             dst[gi] = v;
         }
@@ -345,6 +358,10 @@ void second_pass(int store_mode, int logm, const PassParams &P, int njobs, cudaS
     if constexpr (INV) {
         if (store_mode == STORE_SCALED) {
             by_size<INV, INV, M_SCALED>(logm, P, njobs, st);
+            return;
+        }
+        if (store_mode == STORE_SCALED_CONV) {
+            by_size<INV, INV, M_SCALED_CONV>(logm, P, njobs, st);
             return;
         }
     }

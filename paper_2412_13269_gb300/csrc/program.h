@@ -157,7 +157,10 @@ class Rec {
     CtH new_ct(int B, int comps, int level);
     CtH view(const BufPtr &buf, u64 *base, int B, int comps, int level, size_t bstride, size_t cstride, double scale);
 
-    void ntt(bool inverse, const std::vector<NttJob> &jobs, int load_mode, int store_mode);
+    // split >= 0: the second pass stores jobs[0, split) with store_mode, then
+    // jobs[split, n) with store_mode_b (a later launch, so it may read the former)
+    void ntt(bool inverse, const std::vector<NttJob> &jobs, int load_mode, int store_mode, int split = -1,
+             int store_mode_b = STORE_PLAIN);
     void ew(const std::vector<EwJob> &jobs);
     void aut(const std::vector<AutJob> &jobs, uint32_t g);
     void kip(const std::vector<KipJob> &jobs);
@@ -173,10 +176,13 @@ class Rec {
     CtH add_int(const CtH &a, int64_t c);
     CtH mul_plain(const CtH &a, const u64 *pt_limb0, size_t pt_bstride);
     CtH tensor(const CtH &a, const CtH &b);
+    // rescale_after: return the result rescaled by q_l (relin_rescale), exactly
+    // as rescale(keyswitch(...)) computes it
     CtH keyswitch(int B, int l, const std::function<const u64 *(int, int)> &d, const Key &key,
-                  const std::function<const u64 *(int, int, int)> &extra);
+                  const std::function<const u64 *(int, int, int)> &extra, bool rescale_after = false);
     CtH relin(const CtH &t3);
-    CtH rescale(const CtH &a);
+    CtH relin_rescale(const CtH &t3);    // rescale(relin(t3)) in one pass over the targets
+    CtH rescale(const CtH &a, int64_t factor = 1);  // rescale(mul_int(a, factor))
     CtH drop(const CtH &a, int level);
     CtH automorphism(const CtH &a, uint32_t g);
     CtH rotate(const CtH &a, uint32_t g);

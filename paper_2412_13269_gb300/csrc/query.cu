@@ -133,7 +133,7 @@ static CtH eval_blocks(Rec &R, const Database &db, const QPlan &pl, int b0, int 
     }
     Pw.clear();
     cache.clear();
-    CtH y = R.rescale(R.relin(T));
+    CtH y = R.relin_rescale(T);
     T = CtH();
     y.scale = C.S[pl.l_y];
     y = R.add(y, ck[0]);

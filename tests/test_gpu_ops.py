@@ -113,6 +113,26 @@ def test_keyswitch_relin_rotate(fx, request):
         assert np.array_equal(got, ckks.rotate(par, ckks.Ct(a, l, 1.0), g, keys.rot[g], S.alpha).data), l
 
 
+@pytest.mark.parametrize("fx", ["small", "wide"])
+def test_fused_relin_rescale_and_factor_rescale(fx, request):
+    """The fused forms equal the oracle's compositions: rescale(relinearize(t))
+    and rescale(mul_int(a, f)), including factors that are not invertible
+    modulo a prime of the chain (the unfused fallback)."""
+    S = request.getfixturevalue(fx)
+    par, ctx, keys = S.par, S.ctx, S.keys
+    for l in range(1, par.L + 1):
+        t3 = rand_ct(par, 3, l, 80 + l)
+        got, lev, _ = ctx.op(T.OP_RELIN_RESCALE, t3, l, out_comps=2)
+        want = ckks.rescale(par, ckks.relinearize(par, ckks.Ct(t3, l, 1.0), keys.rlk, S.alpha))
+        assert lev == l - 1 and np.array_equal(got, want.data), l
+    l = par.L
+    a = rand_ct(par, 2, l, 90)
+    for f in (1, 3, -7, (1 << 45) + 12345, -(1 << 50) - 3, par.q[0], -par.q[l], 2 * par.q[1]):
+        got, lev, _ = ctx.op(T.OP_RESCALE_MUL_INT, a, l, arg=f)
+        want = ckks.rescale(par, ckks.mul_int(par, ckks.Ct(a, l, 1.0), f))
+        assert lev == l - 1 and np.array_equal(got, want.data), f
+
+
 def test_innersum(small):
     par, ctx = small.par, small.ctx
     a = rand_ct(par, 2, 1, 60)
@@ -188,6 +208,9 @@ def test_full_size_primitives():
     assert np.array_equal(got, ckks.relinearize(par, ckks.Ct(a, l, 1.0), rlk, alpha).data)
     got, lev, _ = ctx.op(T.OP_RESCALE, a, l)
     assert np.array_equal(got, ckks.rescale(par, ckks.Ct(a, l, 1.0)).data)
+    got, lev, _ = ctx.op(T.OP_RELIN_RESCALE, a, l, out_comps=2)
+    want = ckks.rescale(par, ckks.relinearize(par, ckks.Ct(a, l, 1.0), rlk, alpha))
+    assert lev == l - 1 and np.array_equal(got, want.data)
     ctx.close()
 
 
