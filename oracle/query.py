@@ -92,11 +92,43 @@ def ceil_log2(k: int) -> int:
     return (k - 1).bit_length()
 
 
+def poly_schedule(degree: int):
+    """Baby-step giant-step form of y = sum_k c_k x^k with encrypted c_k (a
+    reading: the paper does not say how the private polynomial is evaluated).
+
+    With g = 2^b baby steps and m = ceil((d+1)/g) giant steps,
+      y = s_0 + sum_{i>=1} s_i * x^{g i},  s_i = sum_{j<g} c_{g i + j} x^j,
+    every s_i (i >= 1) relinearised once and the degree-2 products of the last
+    sum sharing one relinearisation.  Relinearisations: (g - 2) baby powers,
+    (m - 1) giant powers, one per s_i with a j >= 1 term, one final.  Depths
+    (rescales after x): baby power x^j ceil_log2(j), giant x^{g i}
+    b + ceil_log2(i), s_i ceil_log2(g-1) + 1, the final products at
+    D_f = max(ceil_log2(g-1) + 1, b + ceil_log2(m-1)).  A schedule is taken
+    only if D_f <= ceil_log2(d) (y lands no lower than with plain powers) and it
+    needs strictly fewer relinearisations than the d of plain powers; among
+    those the fewest relinearisations, then the smallest g.
+    Returns None (plain powers) or (g, m, bb, D_f) with bb = ceil_log2(g-1)."""
+    best = None
+    for b in range(1, ceil_log2(degree + 1) + 1):
+        g = 1 << b
+        m = -(-(degree + 1) // g)
+        if m < 2:
+            break
+        bb = ceil_log2(g - 1)
+        df = max(bb + 1, b + ceil_log2(m - 1))
+        if df > ceil_log2(degree):
+            continue
+        relins = (g - 2) + (m - 1) + sum(1 for i in range(1, m) if g * i + 1 <= degree) + 1
+        if relins < degree and (best is None or relins < best[0]):
+            best = (relins, g, m, bb, df)
+    return None if best is None else best[1:]
+
+
 @dataclass
 class Plan:
     S: list
     l_lin: int          # level of the linear combination x
-    l_d: int            # level at which the c_k x^k products are formed
+    l_d: int            # level at which the c_k x^k products are formed (plain powers)
     l_y: int            # level of y = f(x) and z = y - t
     l_u: int            # level after the sign stages and step affine
     l_out: int          # level of the returned ciphertext
@@ -105,6 +137,24 @@ class Plan:
     ragged: bool
     stage_coeffs: list = field(default_factory=list)   # folded coefficients per stage
     step_const: float = 0.0
+    bsgs: tuple | None = None   # poly_schedule(degree): (g, m, bb, D_f) or None
+    degree: int = 0
+
+    def coef_level(self, k: int) -> int:
+        """Level at which the encrypted coefficient c_k is used."""
+        if k == 0:
+            return self.l_y
+        if self.bsgs is None:
+            return self.l_d
+        g, m, bb, df = self.bsgs
+        i, j = divmod(k, g)
+        if i == 0:
+            return self.l_lin - df            # s_0 terms, formed with the final products
+        if j >= 1:
+            return self.l_lin - bb            # tensors of s_i
+        if k + 1 <= self.degree:
+            return self.l_lin - bb - 1        # added to s_i after its relinearisation
+        return self.l_lin - df                # s_i = c_k alone (k = d)
 
 
 def make_plan(par: Params, shape: QueryShape) -> Plan:
@@ -135,7 +185,8 @@ def make_plan(par: Params, shape: QueryShape) -> Plan:
     return Plan(S=S, l_lin=l_lin, l_d=l_d, l_y=l_y, l_u=l_u, l_out=l_out,
                 pt_scale=(S[L - 1] * float(par.q[L])) / S[L],
                 mask_scale=((S[l_u - 1] * float(par.q[l_u])) / S[l_u]) if ragged else 0.0,
-                ragged=ragged, stage_coeffs=stages, step_const=1.0 / (2.0 * R))
+                ragged=ragged, stage_coeffs=stages, step_const=1.0 / (2.0 * R),
+                bsgs=poly_schedule(shape.degree), degree=shape.degree)
 
 
 def adjust_const(plan: Plan, par: Params, lt: int, a: float, scale: float) -> int:
@@ -258,18 +309,29 @@ class Evaluator:
     def add(self, a: Ct, b: Ct) -> Ct:
         return ckks.add(self.par, a, b)
 
+    def relin_rescale(self, t: Ct, level_out: int) -> Ct:
+        par = self.par
+        out = ckks.rescale(par, ckks.relinearize(par, t, self.keys.rlk, self.keys.alpha))
+        out.scale = self.plan.S[level_out]
+        return out
+
     def sign_stage(self, u: Ct, co) -> Ct:
+        """p(u) = a0 u + a1 u^3 + a2 u^5 + a3 u^7 in depth 3 with four
+        relinearisations: a0 u + [(a1 u) u^2 + ((a3 u) u^2 + a2 u) u^4], the two
+        degree-2 products in brackets formed at level l-2 and relinearised once."""
+        par = self.par
         l = u.level
         u2 = self.mul(u, u)
         u4 = self.mul(u2, u2)
-        b1 = self.adjust(u, l - 1, co[1])
         b3 = self.adjust(u, l - 1, co[3])
-        t3 = self.mul(b1, u2)
         t7 = self.mul(b3, u2)
         inner = self.add(t7, self.adjust(u, l - 2, co[2]))
-        t57 = self.mul(inner, u4)
+        b1 = self.adjust(u, l - 2, co[1])
+        u2d = self.adjust(u2, l - 2)
+        T = ckks.add(par, ckks.tensor(par, b1, u2d), ckks.tensor(par, inner, u4))
+        t = self.relin_rescale(T, l - 3)
         t1 = self.adjust(u, l - 3, co[0])
-        return self.add(self.add(t1, self.adjust(t3, l - 3)), t57)
+        return self.add(t1, t)
 
     def per_query(self, q: EncQuery, degree: int):
         """Bring the encrypted coefficients and threshold to their levels (once per query)."""
@@ -277,7 +339,7 @@ class Evaluator:
         for w in q.w:
             if w.level != self.par.L or w.scale != p.S[self.par.L]:
                 raise ValueError("linear-combination coefficients must be fresh top-level ciphertexts")
-        ck = [self.adjust(q.c[0], p.l_y)] + [self.adjust(q.c[k], p.l_d) for k in range(1, degree + 1)]
+        ck = [self.adjust(q.c[k], p.coef_level(k)) for k in range(degree + 1)]
         return ck, self.adjust(q.t, p.l_y)
 
     def block(self, pts: list, q: EncQuery, ck: list, tadj: Ct, degree: int) -> Ct:
@@ -301,20 +363,59 @@ class Evaluator:
                 cache[(k, lt)] = self.adjust(P[k], lt)
             return cache[(k, lt)]
 
-        for k in range(2, degree + 1):
+        def power_rule(Q, k, at):
+            # x^k = x^a x^(k-a), a the largest power of two <= k (depth ceil_log2(k))
             a = 1 << (k.bit_length() - 1)
             if a == k:
-                P[k] = self.mul(P[k // 2], P[k // 2])
-            else:
-                A = P[a]
-                P[k] = self.mul(A, lvl(k - a, A.level))
-        # y = sum_k c_k x^k: degree-2 products summed, one relinearisation
-        T = None
-        for k in range(1, degree + 1):
-            tk = ckks.tensor(par, ck[k], lvl(k, p.l_d))
-            T = tk if T is None else ckks.add(par, T, tk)
-        y = ckks.rescale(par, ckks.relinearize(par, T, self.keys.rlk, self.keys.alpha))
-        y.scale = p.S[p.l_y]
+                return self.mul(Q[k // 2], Q[k // 2])
+            return self.mul(Q[a], at(k - a, Q[a].level))
+
+        if p.bsgs is None:
+            for k in range(2, degree + 1):
+                P[k] = power_rule(P, k, lvl)
+            # y = sum_k c_k x^k: degree-2 products summed, one relinearisation
+            T = None
+            for k in range(1, degree + 1):
+                tk = ckks.tensor(par, ck[k], lvl(k, p.l_d))
+                T = tk if T is None else ckks.add(par, T, tk)
+            y = self.relin_rescale(T, p.l_y)
+        else:
+            g, m, bb, df = p.bsgs
+            l_b, l_f = p.l_lin - bb, p.l_lin - df
+            for k in range(2, g):
+                P[k] = power_rule(P, k, lvl)
+            G = {1: self.mul(P[g // 2], P[g // 2])}     # giant powers x^(g i)
+            gcache = {}
+
+            def glvl(i: int, lt: int) -> Ct:
+                if G[i].level == lt:
+                    return G[i]
+                if (i, lt) not in gcache:
+                    gcache[(i, lt)] = self.adjust(G[i], lt)
+                return gcache[(i, lt)]
+
+            for i in range(2, m):
+                G[i] = power_rule(G, i, glvl)
+            # s_i, i >= 1: sum_{j>=1} c_{gi+j} x^j at l_b, relinearised, plus c_{gi}
+            T = None
+            for j in range(1, g):          # s_0's terms at l_f
+                tk = ckks.tensor(par, ck[j], lvl(j, l_f))
+                T = tk if T is None else ckks.add(par, T, tk)
+            for i in range(1, m):
+                Ti = None
+                for j in range(1, g):
+                    if g * i + j > degree:
+                        break
+                    tk = ckks.tensor(par, ck[g * i + j], lvl(j, l_b))
+                    Ti = tk if Ti is None else ckks.add(par, Ti, tk)
+                if Ti is None:
+                    si = ck[g * i]
+                else:
+                    si = ckks.add(par, self.relin_rescale(Ti, l_b - 1), ck[g * i])
+                    si = self.adjust(si, l_f)
+                T = ckks.add(par, T, ckks.tensor(par, si, glvl(i, l_f)))
+            y = self.relin_rescale(T, l_f - 1)
+            y = self.adjust(y, p.l_y)
         y = ckks.add(par, y, ck[0])
         # z = y - t (the 1/2 is folded into the first sign stage)
         u = ckks.sub(par, y, tadj)

@@ -26,12 +26,52 @@ struct QPlan {
     double mask_scale;
     std::vector<std::array<double, 4>> co;
     double step_const;
+    int degree = 0;
+    int g = 0, m = 0, bb = 0, df = 0;  // baby-step giant-step schedule (g = 0: plain powers)
+    int coef_level(int k) const;
 };
 
 static int ceil_log2(int k) {
     int r = 0;
     while ((1 << r) < k) r++;
     return r;
+}
+
+// Baby-step giant-step form of y = sum_k c_k x^k with encrypted c_k:
+//   y = s_0 + sum_{i>=1} s_i x^{g i},  s_i = sum_{j<g} c_{g i + j} x^j,
+// g = 2^b, m = ceil((d+1)/g); every s_i (i >= 1) with a j >= 1 term is
+// relinearised once, the degree-2 products of the last sum share one.
+// Relinearisations: (g-2) + (m-1) + #{i >= 1 : g i + 1 <= d} + 1; the final
+// products sit at depth D_f = max(ceil_log2(g-1) + 1, b + ceil_log2(m-1)).
+// Taken when D_f <= ceil_log2(d) and it needs fewer than the d of plain
+// powers (fewest relinearisations, then smallest g).
+static void poly_schedule(QPlan &p, int d) {
+    int best = -1;
+    p.g = 0;
+    for (int b = 1; b <= ceil_log2(d + 1); b++) {
+        const int g = 1 << b, m = (d + 1 + g - 1) / g;
+        if (m < 2) break;
+        const int bb = ceil_log2(g - 1);
+        const int df = std::max(bb + 1, b + ceil_log2(m - 1));
+        if (df > ceil_log2(d)) continue;
+        int relins = (g - 2) + (m - 1) + 1;
+        for (int i = 1; i < m; i++) relins += (g * i + 1 <= d) ? 1 : 0;
+        if (relins < d && (best < 0 || relins < best)) {
+            best = relins;
+            p.g = g; p.m = m; p.bb = bb; p.df = df;
+        }
+    }
+}
+
+// level at which the encrypted coefficient c_k is used
+int QPlan::coef_level(int k) const {
+    if (k == 0) return l_y;
+    if (g == 0) return l_d;
+    const int i = k / g, j = k % g;
+    if (i == 0) return l_lin - df;          // s_0 terms, formed with the final products
+    if (j >= 1) return l_lin - bb;          // tensors of s_i
+    if (k + 1 <= degree) return l_lin - bb - 1;  // added to s_i after its relinearisation
+    return l_lin - df;                      // s_i = c_k alone (k = d)
 }
 
 QPlan make_plan(const Ctx &C, uint64_t records, int degree, const std::vector<std::array<double, 4>> &stages,
@@ -59,23 +99,33 @@ QPlan make_plan(const Ctx &C, uint64_t records, int degree, const std::vector<st
     }
     p.step_const = 1.0 / (2.0 * R);
     p.mask_scale = p.ragged ? (C.S[p.l_u - 1] * (double)C.q[p.l_u]) / C.S[p.l_u] : 0.0;
+    p.degree = degree;
+    poly_schedule(p, degree);
     return p;
 }
 
-// p(u) = a0 u + a1 u^3 + a2 u^5 + a3 u^7 in depth 3:
-//   a0 u + (a1 u) u^2 + ((a3 u) u^2 + a2 u) u^4
+static CtH relin_rescale_to(Rec &R, const CtH &t, int level_out) {
+    CtH o = R.relin_rescale(t);
+    o.scale = R.C.S[level_out];
+    return o;
+}
+
+// p(u) = a0 u + a1 u^3 + a2 u^5 + a3 u^7 in depth 3 with four relinearisations:
+//   a0 u + [(a1 u) u^2 + ((a3 u) u^2 + a2 u) u^4],
+// the two degree-2 products in brackets formed at level l-2 and relinearised once.
 static CtH sign_stage(Rec &R, const CtH &u, const std::array<double, 4> &co) {
     const int l = u.level;
     CtH u2 = R.mul(u, u);
     CtH u4 = R.mul(u2, u2);
-    CtH b1 = R.adjust(u, l - 1, co[1]);
     CtH b3 = R.adjust(u, l - 1, co[3]);
-    CtH t3 = R.mul(b1, u2);
     CtH t7 = R.mul(b3, u2);
     CtH inner = R.add(t7, R.adjust(u, l - 2, co[2]));
-    CtH t57 = R.mul(inner, u4);
+    CtH b1 = R.adjust(u, l - 2, co[1]);
+    CtH u2d = R.adjust(u2, l - 2, 1.0);
+    CtH T = R.add(R.tensor(b1, u2d), R.tensor(inner, u4));
+    CtH t = relin_rescale_to(R, T, l - 3);
     CtH t1 = R.adjust(u, l - 3, co[0]);
-    return R.add(R.add(t1, R.adjust(t3, l - 3, 1.0)), t57);
+    return R.add(t1, t);
 }
 
 static CtH eval_blocks(Rec &R, const Database &db, const QPlan &pl, int b0, int nb, const u64 *wbase,
@@ -119,23 +169,62 @@ static CtH eval_blocks(Rec &R, const Database &db, const QPlan &pl, int b0, int 
         cache[key] = a;
         return a;
     };
-    for (int k = 2; k <= degree; k++) {
+    // x^k = x^a x^(k-a), a the largest power of two <= k (depth ceil_log2(k))
+    auto power_rule = [&](std::map<int, CtH> &Q, int k, const std::function<CtH(int, int)> &at) {
         int a = 1;
         while (a * 2 <= k) a *= 2;
-        if (a == k) Pw[k] = R.mul(Pw[k / 2], Pw[k / 2]);
-        else Pw[k] = R.mul(Pw[a], lvl(k - a, Pw[a].level));
-    }
-    // y = sum_k c_k x^k with one relinearisation
-    CtH T;
-    for (int k = 1; k <= degree; k++) {
-        CtH tk = R.tensor(ck[k], lvl(k, pl.l_d));
-        T = (k == 1) ? tk : R.add(T, tk);
+        if (a == k) return R.mul(Q[k / 2], Q[k / 2]);
+        return R.mul(Q[a], at(k - a, Q[a].level));
+    };
+    CtH y;
+    if (pl.g == 0) {
+        for (int k = 2; k <= degree; k++) Pw[k] = power_rule(Pw, k, lvl);
+        // y = sum_k c_k x^k with one relinearisation
+        CtH T;
+        for (int k = 1; k <= degree; k++) {
+            CtH tk = R.tensor(ck[k], lvl(k, pl.l_d));
+            T = (k == 1) ? tk : R.add(T, tk);
+        }
+        y = relin_rescale_to(R, T, pl.l_y);
+    } else {
+        const int g = pl.g, m = pl.m, l_b = pl.l_lin - pl.bb, l_f = pl.l_lin - pl.df;
+        for (int k = 2; k < g; k++) Pw[k] = power_rule(Pw, k, lvl);
+        std::map<int, CtH> G;  // giant powers x^(g i)
+        std::map<std::pair<int, int>, CtH> gcache;
+        G[1] = R.mul(Pw[g / 2], Pw[g / 2]);
+        auto glvl = [&](int i, int lt) -> CtH {
+            if (G[i].level == lt) return G[i];
+            auto key = std::make_pair(i, lt);
+            auto it = gcache.find(key);
+            if (it != gcache.end()) return it->second;
+            CtH a = R.adjust(G[i], lt, 1.0);
+            gcache[key] = a;
+            return a;
+        };
+        for (int i = 2; i < m; i++) G[i] = power_rule(G, i, glvl);
+        CtH T;
+        for (int j = 1; j < g; j++) {  // s_0's terms at l_f
+            CtH tk = R.tensor(ck[j], lvl(j, l_f));
+            T = (j == 1) ? tk : R.add(T, tk);
+        }
+        for (int i = 1; i < m; i++) {
+            CtH Ti;
+            bool any = false;
+            for (int j = 1; j < g && g * i + j <= degree; j++) {
+                CtH tk = R.tensor(ck[g * i + j], lvl(j, l_b));
+                Ti = any ? R.add(Ti, tk) : tk;
+                any = true;
+            }
+            CtH si = ck[g * i];
+            if (any) si = R.adjust(R.add(relin_rescale_to(R, Ti, l_b - 1), ck[g * i]), l_f, 1.0);
+            T = R.add(T, R.tensor(si, glvl(i, l_f)));
+        }
+        G.clear();
+        gcache.clear();
+        y = R.adjust(relin_rescale_to(R, T, l_f - 1), pl.l_y, 1.0);
     }
     Pw.clear();
     cache.clear();
-    CtH y = R.relin_rescale(T);
-    T = CtH();
-    y.scale = C.S[pl.l_y];
     y = R.add(y, ck[0]);
     CtH u = R.sub(y, tadj);
     for (auto &co : pl.co) u = sign_stage(R, u, co);
@@ -184,8 +273,7 @@ std::unique_ptr<Program> record_query(Ctx &C, const Database &db, const QuerySpe
     }
     // per-query: coefficients and threshold moved to their levels
     std::vector<CtH> ck;
-    ck.push_back(R.adjust(cin[0], pl.l_y, 1.0));
-    for (int k = 1; k <= q.degree; k++) ck.push_back(R.adjust(cin[k], pl.l_d, 1.0));
+    for (int k = 0; k <= q.degree; k++) ck.push_back(R.adjust(cin[k], pl.coef_level(k), 1.0));
     CtH tadj = R.adjust(tin, pl.l_y, 1.0);
     // block groups
     const int B = db.blocks;

@@ -66,7 +66,8 @@ def gpu_query(ctx, dbh, eq, stages):
                               eq.t.data, (eq.t.level, eq.t.scale), np.array(stages))
 
 
-@pytest.mark.parametrize("records,attrs,degree,nst", [(2048, 8, 7, 1), (1500, 4, 3, 1), (3000, 3, 2, 1)])
+@pytest.mark.parametrize("records,attrs,degree,nst", [(2048, 8, 7, 1), (1500, 4, 3, 1), (3000, 3, 2, 1),
+                                                     (2048, 4, 12, 1), (2048, 4, 15, 1)])
 def test_query_bit_exact(chain, records, attrs, degree, nst):
     par, ctx = chain.par, chain.ctx
     vals, qv, stages, shape, plan, db, eq = make_case(par, chain.s, records, attrs, degree, nst, records)

@@ -90,3 +90,37 @@ def test_exact_count_outside_margin():
     got, _ = run(par, vals, qv, stages)
     R = vals.shape[0]
     assert int(np.rint(got[0] * R)) == ref.exact == int((side > 0).sum())
+
+
+def test_poly_schedule():
+    """Baby-step giant-step choice: fewest relinearisations with y no deeper than plain powers."""
+    assert all(query.poly_schedule(d) is None for d in (1, 2, 3))
+    assert query.poly_schedule(7) == (4, 2, 2, 3)
+    assert query.poly_schedule(8) == (4, 3, 2, 3)
+    assert query.poly_schedule(12) == (4, 4, 2, 4)
+    assert query.poly_schedule(15) == (4, 4, 2, 4)
+    assert query.poly_schedule(31) == (8, 4, 3, 5)
+    for d in range(1, 64):
+        s = query.poly_schedule(d)
+        if s is not None:
+            g, m, bb, df = s
+            assert g * (m - 1) <= d < g * m and df <= query.ceil_log2(d)
+
+
+@pytest.mark.parametrize("degree,relins", [(12, 8 + 4), (15, 9 + 4), (8, 6 + 4), (3, 3 + 4)])
+def test_bsgs_polynomial_matches_fp64(monkeypatch, degree, relins):
+    """The polynomial (baby-step giant-step above degree 3, including a last
+    block holding one coefficient) and one sign stage: the decrypted count
+    matches the FP64 pipeline, and the relinearisations are the schedule's plus
+    the stage's four."""
+    calls = []
+    real = ckks.relinearize
+    monkeypatch.setattr(ckks, "relinearize", lambda *a, **k: calls.append(1) or real(*a, **k))
+    par = chain_params(12)
+    vals = synth.database(synth.stream(degree, "db"), 2048, 4)
+    qv = synth.query_values(synth.stream(degree, "qv"), 4, degree)
+    got, plan = run(par, vals, qv, [query.F3])
+    ref = query.fp64_pipeline(vals, qv, [query.F3])
+    assert len(calls) == relins
+    assert np.ptp(got) < 1e-6
+    assert abs(got[0] * 2048 - ref.count) < 0.05
