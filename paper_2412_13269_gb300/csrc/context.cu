@@ -199,7 +199,6 @@ double distinct_bytes(const std::vector<const void *> &ptrs, size_t N) {
 }
 const char *load_name(int m) {
     switch (m) {
-        case LOAD_CONV: return "conv";
         case LOAD_CONV_PRE: return "convpre";
         case LOAD_REDUCE: return "reduce";
         case LOAD_INT64: return "int64";
@@ -287,7 +286,7 @@ void Rec::ntt(bool inverse, const std::vector<NttJob> &jobs, int load_mode, int 
     const size_t N = C.N;
     std::vector<const void *> srcs;
     for (auto &j : jobs) {
-        if (load_mode == LOAD_CONV || load_mode == LOAD_CONV_PRE)
+        if (load_mode == LOAD_CONV_PRE)
             for (uint32_t s = 0; s < j.nsrc; s++) srcs.push_back(j.src + s * j.src_stride);
         else
             srcs.push_back(j.src);
@@ -296,7 +295,7 @@ void Rec::ntt(bool inverse, const std::vector<NttJob> &jobs, int load_mode, int 
     const std::string dir = inverse ? "ntt_inv" : "ntt_fwd";
     const int log1 = (logn + 1) / 2, log2 = logn / 2;
     double conv = 0;
-    if (load_mode == LOAD_CONV || load_mode == LOAD_CONV_PRE)
+    if (load_mode == LOAD_CONV_PRE)
         for (auto &j : jobs) conv += j.nsrc;
     const double first_log = inverse ? log2 : log1, second_log = inverse ? log1 : log2;
     const double mm1 = (double)n * N * first_log / 2 + conv * N;
@@ -578,11 +577,11 @@ CtH Rec::tensor(const CtH &a, const CtH &b) {
 }
 
 // Fast base conversion from the consecutive primes first..first+nsrc-1 to
-// dst_prime: x -> sum_s [(x_s + add_s) * (Qs/q_s)^-1]_{q_s} * (Qs/q_s mod q_dst).
+// dst_prime: x -> sum_s [x_s * (Qs/q_s)^-1]_{q_s} * (Qs/q_s mod q_dst).
 // The recorded transforms fold the first factor into the inverse NTT that
 // produces the sources (STORE_SCALED) and load with LOAD_CONV_PRE, which only
 // uses c2 = Qs/q_s mod q_dst.
-NttJob Rec::conv_job(uint32_t dst_prime, const u64 *src, uint32_t first, int nsrc, const u64 *adds) {
+NttJob Rec::conv_job(uint32_t dst_prime, const u64 *src, uint32_t first, int nsrc) {
     NttJob j{};
     j.src = src;
     j.src_stride = C.N;
@@ -590,17 +589,9 @@ NttJob Rec::conv_job(uint32_t dst_prime, const u64 *src, uint32_t first, int nsr
     j.prime = dst_prime;
     const u64 qd = C.all[dst_prime];
     for (int s = 0; s < nsrc; s++) {
-        const u64 qs = C.all[first + s];
-        u64 hat_s = 1 % qs, hat_d = 1 % qd;
+        u64 hat_d = 1 % qd;
         for (int r = 0; r < nsrc; r++)
-            if (r != s) {
-                hat_s = h_mulmod(hat_s, C.all[first + r] % qs, qs);
-                hat_d = h_mulmod(hat_d, C.all[first + r] % qd, qd);
-            }
-        j.src_prime[s] = first + s;
-        j.add_s[s] = adds ? adds[s] : 0;
-        j.c1[s] = h_invmod(hat_s, qs);
-        j.c1_sh[s] = h_shoup(j.c1[s], qs);
+            if (r != s) hat_d = h_mulmod(hat_d, C.all[first + r] % qd, qd);
         j.c2[s] = hat_d;
         j.c2_sh[s] = h_shoup(hat_d, qd);
     }
@@ -669,7 +660,7 @@ CtH Rec::keyswitch(int B, int l, const std::function<const u64 *(int, int)> &d, 
             const int lo = j * alpha, hi = std::min(nl, (j + 1) * alpha);
             for (int t = 0; t < ntg; t++) {
                 if (t >= lo && t < hi) continue;
-                NttJob proto = conv_job(C.qp_prime(l, t), nullptr, lo, hi - lo, nullptr);
+                NttJob proto = conv_job(C.qp_prime(l, t), nullptr, lo, hi - lo);
                 for (int b = 0; b < B; b++) {
                     NttJob jb = proto;
                     jb.src = dcoef->ptr + ((size_t)b * nl + lo) * N;
@@ -695,9 +686,11 @@ CtH Rec::keyswitch(int B, int l, const std::function<const u64 *(int, int)> &d, 
     BufPtr acc = pool().alloc((size_t)B * 2 * ntg * N);
     auto accl = [&](int b, int c, int t) { return acc->ptr + (((size_t)b * 2 + c) * ntg + t) * N; };
     {
+        // blocks innermost: the B jobs of one target read the same key limbs
+        // back to back, so the key comes from DRAM once per launch
         std::vector<KipJob> jobs;
-        for (int b = 0; b < B; b++)
-            for (int t = 0; t < ntg; t++) {
+        for (int t = 0; t < ntg; t++)
+            for (int b = 0; b < B; b++) {
                 KipJob k{};
                 const uint32_t gp = C.qp_prime(l, t);
                 for (int j = 0; j < dnum; j++) {
@@ -781,9 +774,8 @@ CtH Rec::keyswitch(int B, int l, const std::function<const u64 *(int, int)> &d, 
         for (int i = 0; i < l; i++) {
             const u64 qi = C.q[i];
             const u64 pm = pmod(i);
-            NttJob proto = conv_job(i, nullptr, C.L() + 1, K, nullptr);
+            NttJob proto = conv_job(i, nullptr, C.L() + 1, K);
             proto.nsrc = K1;
-            proto.src_prime[K] = l;
             proto.c2[K] = pm;
             proto.c2_sh[K] = h_shoup(pm, qi);
             proto.conv_sub = (halfp(i) + h_mulmod(pm, ((ql - 1) / 2) % qi, qi)) % qi;
@@ -841,7 +833,7 @@ CtH Rec::keyswitch(int B, int l, const std::function<const u64 *(int, int)> &d, 
             for (int k = 0; k < K; k++) pm = h_mulmod(pm, C.p[k] % qi, qi);
             const u64 half = h_mulmod((pm + qi - 1) % qi, h_invmod(2, qi), qi);
             const u64 pinv = h_invmod(pm, qi);
-            NttJob proto = conv_job(i, nullptr, C.L() + 1, K, nullptr);
+            NttJob proto = conv_job(i, nullptr, C.L() + 1, K);
             proto.conv_sub = half;
             proto.mul = pinv;
             proto.mul_sh = h_shoup(pinv, qi);

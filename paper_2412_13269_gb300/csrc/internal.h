@@ -75,22 +75,22 @@ class Pool {
 // ---------------------------------------------------------------------------
 // Kernel job descriptors
 // ---------------------------------------------------------------------------
-// LOAD_CONV:     sum_s [(src_s + add_s) * c1_s]_{q_s} * c2_s - conv_sub
-// LOAD_CONV_PRE: sum_s src_s * c2_s - conv_sub (sources already scaled by c1_s, see STORE_SCALED;
-//                each product a lazy Shoup product, so nsrc * 2q < 2^64)
+// LOAD_CONV_PRE: sum_s src_s * c2_s - conv_sub (sources already scaled by their
+//                factor [(Q/q_s)^-1]_{q_s}, see STORE_SCALED; each product a lazy
+//                Shoup product, so nsrc * 2q < 2^64)
 // LOAD_REDUCE:   [src * c]_{q_dst} - conv_sub (a single source of another prime;
 //                c = c2[0] when nonzero, else 1)
-enum LoadMode { LOAD_PLAIN = 0, LOAD_CONV = 1, LOAD_INT64 = 2, LOAD_CONV_PRE = 3, LOAD_REDUCE = 4 };
-// STORE_SCALED (inverse transforms only): x * mul + conv_sub, where mul already
-// carries N^-1; it precomputes the per-source factor of a following conversion.
+// LOAD_INT64:    signed 64-bit integers reduced modulo q_dst
+// Forward transforms take every load mode; inverse transforms load plain limbs.
+enum LoadMode { LOAD_PLAIN = 0, LOAD_INT64 = 2, LOAD_CONV_PRE = 3, LOAD_REDUCE = 4 };
+// STORE_COMBINE (forward only): (extra ? extra : 0) + (base - x) * mul.
+// STORE_SCALED (inverse only): x * mul + conv_sub, where mul already carries
+// N^-1; it precomputes the per-source factor of a following conversion.
 // STORE_SCALED_CONV (inverse only): x * mul + conv_sub - sum_s base_s * c2_s, the
 // nsrc sources base + s*src_stride in the coefficient domain.
 enum StoreMode { STORE_PLAIN = 0, STORE_COMBINE = 1, STORE_SCALED = 2, STORE_SCALED_CONV = 3 };
 
-// One limb transform.  LOAD_CONV computes, per coefficient,
-//   sum_s [ (src_s + add_s) * c1_s ]_{q_s} * c2_s - conv_sub  mod q_dst
-// from nsrc source limbs src + s*src_stride (coefficient domain).
-// STORE_COMBINE writes (extra ? extra : 0) + (base - x) * mul mod q_dst.
+// One limb transform: src -> dst (in place when equal), prime index `prime`.
 struct NttJob {
     const u64 *src;
     u64 *dst;
@@ -99,9 +99,6 @@ struct NttJob {
     uint32_t prime;
     uint32_t nsrc;
     uint64_t src_stride;
-    uint32_t src_prime[kMaxConvSrc];
-    u64 add_s[kMaxConvSrc];
-    u64 c1[kMaxConvSrc], c1_sh[kMaxConvSrc];
     u64 c2[kMaxConvSrc], c2_sh[kMaxConvSrc];  // c2_sh: Shoup companions of c2 modulo q_dst
     u64 conv_sub, mul, mul_sh;
 };

@@ -22,9 +22,11 @@
 // Load modes fuse the producer: plain, int64 -> residue, or a fast base
 // conversion from up to four source limbs (ModUp / ModDown / rescale), less a
 // per-coefficient constant.  The combine store fuses the consumer:
-// (extra) + (base - x) * mul.  Butterflies are lazy (Harvey): values stay in
-// [0, 4q) (forward) or [0, 2q) (inverse) between stages and between the two
-// passes, and are reduced once when the second pass stores them.
+// (extra) + (base - x) * mul; the inverse stores can scale, add a constant and
+// subtract a base conversion.  Butterflies are lazy: forward transforms modulo
+// primes below 2^58 run with no correction at all (values grow by at most 2q
+// per stage and stay below 41q), the others as Harvey's, in [0, 4q) (forward)
+// or [0, 2q) (inverse) between stages and passes; the second pass reduces.
 #include "internal.h"
 
 namespace tetris {
@@ -52,6 +54,14 @@ __device__ __forceinline__ void ct_bfly(u64 &x, u64 &y, u64 w, u64 wsh, u64 q, u
     x = X + T;
     y = X - T + q2;
 }
+// Forward butterfly without correction: the Shoup product is < 2q for any
+// 64-bit y, so each stage adds at most 2q to the bound of its inputs.
+__device__ __forceinline__ void ct_bfly_open(u64 &x, u64 &y, u64 w, u64 wsh, u64 q, u64 q2) {
+    u64 T = shoup_lazy(y, w, wsh, q);
+    u64 X = x;
+    x = X + T;
+    y = X - T + q2;
+}
 __device__ __forceinline__ void gs_bfly(u64 &x, u64 &y, u64 w, u64 wsh, u64 q, u64 q2) {
     u64 S = x + y;
     S = S >= q2 ? S - q2 : S;
@@ -59,6 +69,13 @@ __device__ __forceinline__ void gs_bfly(u64 &x, u64 &y, u64 w, u64 wsh, u64 q, u
     x = S;
     y = shoup_lazy(D, w, wsh, q);
 }
+
+// Forward transforms modulo q < 2^58 run "open" (no correction inside the two
+// passes): loads give values below (2 nsrc + 1) q <= 9q, sixteen stages add at
+// most 32q, so every intermediate stays below 41q < 2^64; the second pass's
+// store reduces once.  Larger primes (the 60-bit special primes) take
+// Harvey's corrected butterflies.
+constexpr u64 kOpenBound = 1ull << 58;
 
 // Register window of butterfly group g: the thread holds the E elements whose
 // row index differs only in bits [lo, lo + LOGE); stages run on bits [blo, bhi].
@@ -75,38 +92,27 @@ struct Group {
     }
 };
 
-// MODE: 0/1/2 = first pass loading plain / int64 / base conversion;
-//       3/4 = second pass storing plain / combined.
-//       5/6 = first pass loading pre-scaled conversion sources / a reduction;
-//       7 = second pass of an inverse transform storing x * mul + add;
-//       8 = as 7, less a base conversion of coefficient-domain sources.
-enum { M_PLAIN = 0, M_INT64 = 1, M_CONV = 2, M_STORE = 3, M_COMBINE = 4, M_CONVPRE = 5, M_REDUCE = 6, M_SCALED = 7,
+// MODE: first pass (forward) loading plain / int64 / pre-scaled conversion
+//       sources / a reduction; second pass storing plain / combined;
+//       inverse: first pass plain, second pass storing plain / x * mul + add /
+//       as the latter less a base conversion of coefficient-domain sources.
+enum { M_PLAIN = 0, M_INT64 = 1, M_STORE = 3, M_COMBINE = 4, M_CONVPRE = 5, M_REDUCE = 6, M_SCALED = 7,
        M_SCALED_CONV = 8 };
 constexpr bool is_second(int m) { return m == M_STORE || m == M_COMBINE || m == M_SCALED || m == M_SCALED_CONV; }
 
-template <int LOGM, bool INV, bool COL, int MODE, int LOGEV>
-__global__ void __launch_bounds__(kThreads, MODE == M_CONV ? 2 : (LOGEV >= 4 ? 3 : 4)) ntt_pass_kernel(PassParams P) {
+template <int LOGM, bool INV, bool COL, int MODE, int LOGEV, bool OPEN>
+__device__ __forceinline__ void pass_body(const PassParams &P, const NttJob &J, u64 *sm, const ModInfo &mi) {
     constexpr int M = 1 << LOGM;
     constexpr int LOGE = LOGM >= LOGEV ? LOGEV : LOGM;
     constexpr int E = 1 << LOGE;
     constexpr int T = M / E;
     constexpr int NG = (LOGM + LOGE - 1) / LOGE;
     using G = Group<LOGM, LOGE, INV>;
-    extern __shared__ u64 sm[];
-    __shared__ NttJob J;
-
-    {   // the job descriptor, once per CTA
-        const u64 *gj = reinterpret_cast<const u64 *>(P.jobs + blockIdx.y);
-        u64 *dj = reinterpret_cast<u64 *>(&J);
-        for (int i = threadIdx.x; i < (int)(sizeof(NttJob) / 8); i += blockDim.x) dj[i] = gj[i];
-    }
-    __syncthreads();
     const int N1 = 1 << P.log1, N2 = 1 << P.log2;
     const int nsub = COL ? N2 : N1;
     const int sub_cta = min(kThreads / T, nsub);
     const int sub0 = blockIdx.x * sub_cta;
     const int tid = threadIdx.x;
-    const ModInfo mi = P.t.mods[J.prime];
     const u64 q = mi.q, q2 = 2 * q;
     const size_t N = (size_t)N1 * N2;
     const u64 *tw = (INV ? P.t.itw : P.t.tw) + (size_t)J.prime * N;
@@ -122,6 +128,13 @@ __global__ void __launch_bounds__(kThreads, MODE == M_CONV ? 2 : (LOGEV >= 4 ? 3
     auto row = [&](int g, int k) -> int {
         const int l = G::lo(g);
         return (t & ((1 << l) - 1)) | (k << l) | ((t >> l) << (l + LOGE));
+    };
+    // A row-pass sub-problem lives in one warp (T <= 32 consecutive threads),
+    // so its exchanges only synchronise the warp; column sub-problems span warps.
+    static_assert(COL || T <= 32, "row sub-problem wider than a warp");
+    auto sync = [&]() {
+        if (COL) __syncthreads();
+        else __syncwarp();
     };
     // In the row pass a group whose register window is the low bits holds
     // contiguous words per thread; those ends go through shared memory so the
@@ -143,8 +156,12 @@ __global__ void __launch_bounds__(kThreads, MODE == M_CONV ? 2 : (LOGEV >= 4 ? 3
 #pragma unroll
         for (int k = 0; k < E; k++) {
             u64 v = shoup_lazy(src[gidx(lrow(k))], c, csh, q);  // [0, 2q) for any 64-bit source
-            v = v >= q ? v - q : v;
-            x[k] = sub_mod(v, sub, q);
+            if (OPEN) {
+                x[k] = v + (q - sub);  // < 3q
+            } else {
+                v = v >= q ? v - q : v;
+                x[k] = sub_mod(v, sub, q);
+            }
         }
     } else if (MODE == M_CONVPRE) {
         // sum_s y_s * c2_s with lazy Shoup products: each term < 2q, the sum < 8q
@@ -153,7 +170,7 @@ __global__ void __launch_bounds__(kThreads, MODE == M_CONV ? 2 : (LOGEV >= 4 ? 3
         const int ns = (int)J.nsrc;
         const u64 sub = J.conv_sub, q4 = 4 * q;
 #pragma unroll
-        for (int k = 0; k < E; k++) x[k] = 0;
+        for (int k = 0; k < E; k++) x[k] = OPEN ? q - sub : 0;
 #pragma unroll
         for (int sidx = 0; sidx < kMaxConvSrc; sidx++) {
             if (sidx < ns) {
@@ -163,58 +180,33 @@ __global__ void __launch_bounds__(kThreads, MODE == M_CONV ? 2 : (LOGEV >= 4 ? 3
                 for (int k = 0; k < E; k++) x[k] += shoup_lazy(sp[gidx(lrow(k))], c2, c2sh, q);
             }
         }
+        if (!OPEN) {
 #pragma unroll
-        for (int k = 0; k < E; k++) {
-            u64 v = x[k];
-            v = v >= q4 ? v - q4 : v;
-            v = v >= q2 ? v - q2 : v;
-            v = v >= q ? v - q : v;
-            x[k] = sub_mod(v, sub, q);
+            for (int k = 0; k < E; k++) {
+                u64 v = x[k];
+                v = v >= q4 ? v - q4 : v;
+                v = v >= q2 ? v - q2 : v;
+                v = v >= q ? v - q : v;
+                x[k] = sub_mod(v, sub, q);
+            }
         }
     } else if (MODE == M_PLAIN) {
         const u64 *src = J.src;
 #pragma unroll
         for (int k = 0; k < E; k++) x[k] = src[gidx(lrow(k))];
-    } else if (MODE == M_INT64) {
+    } else {  // M_INT64
         const int64_t *src = reinterpret_cast<const int64_t *>(J.src);
 #pragma unroll
         for (int k = 0; k < E; k++) {
             const int64_t v = src[gidx(lrow(k))];
             x[k] = v >= 0 ? (u64)v % q : q - 1 - ((u64)(-(v + 1)) % q);
         }
-    } else {  // LOAD_CONV: sum_s [(src_s + add_s) c1_s]_{q_s} c2_s - conv_sub, four elements at a time
-        const u64 *src = J.src;
-        const u64 stride = J.src_stride;
-        const int ns = (int)J.nsrc;
-        const u64 sub = J.conv_sub;
-        constexpr int C4 = E < 4 ? E : 4;
-#pragma unroll
-        for (int k0 = 0; k0 < E; k0 += C4) {
-            Acc128 acc[C4];
-#pragma unroll
-            for (int k = 0; k < C4; k++) acc[k] = {0, 0};
-#pragma unroll
-            for (int sidx = 0; sidx < kMaxConvSrc; sidx++) {
-                if (sidx < ns) {
-                    const u64 qs = P.t.mods[J.src_prime[sidx]].q;
-                    const u64 add = J.add_s[sidx], c1 = J.c1[sidx], c1sh = J.c1_sh[sidx], c2 = J.c2[sidx];
-                    const u64 *sp = src + sidx * stride;
-                    u64 v[C4];
-#pragma unroll
-                    for (int k = 0; k < C4; k++) v[k] = sp[gidx(lrow(k0 + k))];
-#pragma unroll
-                    for (int k = 0; k < C4; k++) acc_mad(acc[k], shoup(add_mod(v[k], add, qs), c1, c1sh, qs), c2);
-                }
-            }
-#pragma unroll
-            for (int k = 0; k < C4; k++) x[k0 + k] = sub_mod(reduce128(acc[k].hi, acc[k].lo, mi), sub, q);
-        }
     }
 
     if (IN_STAGE) {
 #pragma unroll
         for (int k = 0; k < E; k++) sm[smidx(lrow(k))] = x[k];
-        __syncthreads();
+        sync();
 #pragma unroll
         for (int k = 0; k < E; k++) x[k] = sm[smidx(row(0, k))];
     }
@@ -223,10 +215,10 @@ __global__ void __launch_bounds__(kThreads, MODE == M_CONV ? 2 : (LOGEV >= 4 ? 3
 #pragma unroll
     for (int g = 0; g < NG; g++) {
         if (g > 0) {
-            __syncthreads();  // (g > 1) every thread has read the previous exchange
+            sync();  // (g > 1) every thread has read the previous exchange
 #pragma unroll
             for (int k = 0; k < E; k++) sm[smidx(row(g - 1, k))] = x[k];
-            __syncthreads();
+            sync();
 #pragma unroll
             for (int k = 0; k < E; k++) x[k] = sm[smidx(row(g, k))];
         }
@@ -249,8 +241,9 @@ __global__ void __launch_bounds__(kThreads, MODE == M_CONV ? 2 : (LOGEV >= 4 ? 3
 #pragma unroll
                     for (int j = 0; j < E; j++) {
                         if (j >= (1 << bb)) continue;
-                        if (!INV) ct_bfly(x[k + j], x[k + j + (1 << bb)], w, wsh, q, q2);
-                        else gs_bfly(x[k + j], x[k + j + (1 << bb)], w, wsh, q, q2);
+                        if (INV) gs_bfly(x[k + j], x[k + j + (1 << bb)], w, wsh, q, q2);
+                        else if (OPEN) ct_bfly_open(x[k + j], x[k + j + (1 << bb)], w, wsh, q, q2);
+                        else ct_bfly(x[k + j], x[k + j + (1 << bb)], w, wsh, q, q2);
                     }
                 }
             }
@@ -261,10 +254,10 @@ __global__ void __launch_bounds__(kThreads, MODE == M_CONV ? 2 : (LOGEV >= 4 ? 3
     //    lazy values, the second reduces them and fuses the consumer
     u64 *dst = J.dst;
     if (OUT_STAGE) {
-        __syncthreads();
+        sync();
 #pragma unroll
         for (int k = 0; k < E; k++) sm[smidx(row(NG - 1, k))] = x[k];
-        __syncthreads();
+        sync();
 #pragma unroll
         for (int k = 0; k < E; k++) x[k] = sm[smidx(srow(k))];
     }
@@ -280,7 +273,10 @@ __global__ void __launch_bounds__(kThreads, MODE == M_CONV ? 2 : (LOGEV >= 4 ? 3
             u64 v = x[k];
             if (MODE == M_SCALED || MODE == M_SCALED_CONV) v = add_mod(shoup(v, mul, mulsh, q), addk, q);
             else if (INV) v = shoup(v, mi.ninv, mi.ninv_sh, q);
-            else {
+            else if (OPEN) {
+                v = v - __umul64hi(v, mi.one_sh) * q;  // Shoup product with w = 1: [0, 2q)
+                v = v >= q ? v - q : v;
+            } else {
                 v = v >= q2 ? v - q2 : v;
                 v = v >= q ? v - q : v;
             }
@@ -301,6 +297,25 @@ __global__ void __launch_bounds__(kThreads, MODE == M_CONV ? 2 : (LOGEV >= 4 ? 3
             }
             dst[gi] = v;
         }
+    }
+}
+
+template <int LOGM, bool INV, bool COL, int MODE, int LOGEV>
+__global__ void __launch_bounds__(kThreads, LOGEV >= 4 ? 3 : 4) ntt_pass_kernel(PassParams P) {
+    extern __shared__ u64 sm[];
+    __shared__ NttJob J;
+    {   // the job descriptor, once per CTA
+        const u64 *gj = reinterpret_cast<const u64 *>(P.jobs + blockIdx.y);
+        u64 *dj = reinterpret_cast<u64 *>(&J);
+        for (int i = threadIdx.x; i < (int)(sizeof(NttJob) / 8); i += blockDim.x) dj[i] = gj[i];
+    }
+    __syncthreads();
+    const ModInfo mi = P.t.mods[J.prime];
+    if constexpr (!INV) {
+        if (mi.q < kOpenBound) pass_body<LOGM, INV, COL, MODE, LOGEV, true>(P, J, sm, mi);
+        else pass_body<LOGM, INV, COL, MODE, LOGEV, false>(P, J, sm, mi);
+    } else {
+        pass_body<LOGM, INV, COL, MODE, LOGEV, false>(P, J, sm, mi);
     }
 }
 
@@ -339,33 +354,33 @@ void by_size(int logm, const PassParams &P, int njobs, cudaStream_t st) {
     else by_size_v<INV, COL, MODE, 3>(logm, P, njobs, st);
 }
 
-// first pass: forward = column pass, inverse = row pass
+// first pass: forward = column pass, inverse = row pass (inverse loads are plain)
 template <bool INV>
 void first_pass(int load_mode, int logm, const PassParams &P, int njobs, cudaStream_t st) {
-    if (load_mode == LOAD_CONV) by_size<INV, !INV, M_CONV>(logm, P, njobs, st);
-    else if (load_mode == LOAD_CONV_PRE) by_size<INV, !INV, M_CONVPRE>(logm, P, njobs, st);
-    else if (load_mode == LOAD_REDUCE) by_size<INV, !INV, M_REDUCE>(logm, P, njobs, st);
-    else if (load_mode == LOAD_INT64) by_size<INV, !INV, M_INT64>(logm, P, njobs, st);
-    else by_size<INV, !INV, M_PLAIN>(logm, P, njobs, st);
+    if constexpr (INV) {
+        if (load_mode != LOAD_PLAIN) throw Error(-1, "inverse transforms load plain limbs");
+        by_size<INV, !INV, M_PLAIN>(logm, P, njobs, st);
+    } else {
+        if (load_mode == LOAD_CONV_PRE) by_size<INV, !INV, M_CONVPRE>(logm, P, njobs, st);
+        else if (load_mode == LOAD_REDUCE) by_size<INV, !INV, M_REDUCE>(logm, P, njobs, st);
+        else if (load_mode == LOAD_INT64) by_size<INV, !INV, M_INT64>(logm, P, njobs, st);
+        else if (load_mode == LOAD_PLAIN) by_size<INV, !INV, M_PLAIN>(logm, P, njobs, st);
+        else throw Error(-1, "unsupported load mode");
+    }
 }
 
 template <bool INV>
 void second_pass(int store_mode, int logm, const PassParams &P, int njobs, cudaStream_t st) {
-    if (store_mode == STORE_COMBINE) {
-        by_size<INV, INV, M_COMBINE>(logm, P, njobs, st);
-        return;
-    }
     if constexpr (INV) {
-        if (store_mode == STORE_SCALED) {
-            by_size<INV, INV, M_SCALED>(logm, P, njobs, st);
-            return;
-        }
-        if (store_mode == STORE_SCALED_CONV) {
-            by_size<INV, INV, M_SCALED_CONV>(logm, P, njobs, st);
-            return;
-        }
+        if (store_mode == STORE_SCALED) by_size<INV, INV, M_SCALED>(logm, P, njobs, st);
+        else if (store_mode == STORE_SCALED_CONV) by_size<INV, INV, M_SCALED_CONV>(logm, P, njobs, st);
+        else if (store_mode == STORE_PLAIN) by_size<INV, INV, M_STORE>(logm, P, njobs, st);
+        else throw Error(-1, "unsupported inverse store mode");
+    } else {
+        if (store_mode == STORE_COMBINE) by_size<INV, INV, M_COMBINE>(logm, P, njobs, st);
+        else if (store_mode == STORE_PLAIN) by_size<INV, INV, M_STORE>(logm, P, njobs, st);
+        else throw Error(-1, "unsupported forward store mode");
     }
-    by_size<INV, INV, M_STORE>(logm, P, njobs, st);
 }
 
 }  // namespace

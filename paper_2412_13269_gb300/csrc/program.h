@@ -191,7 +191,7 @@ class Rec {
     CtH mul(const CtH &a, const CtH &b);
 
   private:
-    NttJob conv_job(uint32_t dst_prime, const u64 *src, uint32_t first_src_prime, int nsrc, const u64 *adds);
+    NttJob conv_job(uint32_t dst_prime, const u64 *src, uint32_t first_src_prime, int nsrc);
 };
 
 int64_t round_half_up(double x);
