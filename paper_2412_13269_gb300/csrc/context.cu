@@ -216,6 +216,7 @@ const char *ew_name(int op) {
         case EW_COPY: return "copy";
         case EW_FMA: return "fma";
         case EW_TENSOR: return "tensor";
+        case EW_TENSOR_ACC: return "tensor_acc";
         case EW_ADD_MUL_CONST: return "addmulc";
         case EW_REDUCE: return "reduce";
     }
@@ -349,7 +350,9 @@ void Rec::ew(const std::vector<EwJob> &jobs) {
         rd.push_back(j.c);
         rd.push_back(j.a1);
         rd.push_back(j.b1);
-        writes += j.op == EW_TENSOR ? 3 : 1;
+        rd.push_back(j.c1);
+        rd.push_back(j.c2);
+        writes += (j.op == EW_TENSOR || j.op == EW_TENSOR_ACC) ? 3 : 1;
     }
     P.add_launch([=](cudaStream_t s, const uint8_t *a) {
         launch_ew(reinterpret_cast<const EwJob *>(a + off), n, logn, m, s);
@@ -556,20 +559,34 @@ CtH Rec::mul_plain(const CtH &a, const u64 *pt, size_t pt_bstride) {
     return o;
 }
 
-CtH Rec::tensor(const CtH &a, const CtH &b) {
+CtH Rec::tensor(const CtH &a, const CtH &b) { return tensor_add(CtH(), a, b); }
+
+// acc + a (x) b in one pass (acc empty: the tensor alone)
+CtH Rec::tensor_add(const CtH &acc, const CtH &a, const CtH &b) {
     TREQUIRE(a.level == b.level && a.comps == 2 && b.comps == 2, TETRIS_EINVAL, "tensor: operands differ");
     TREQUIRE(a.B == b.B || a.B == 1 || b.B == 1, TETRIS_EINVAL, "tensor: batch sizes differ");
     int B = std::max(a.B, b.B);
+    const bool add = acc.buf != nullptr;
+    if (add) {
+        TREQUIRE(acc.comps == 3 && acc.level == a.level && (acc.B == B || acc.B == 1), TETRIS_EINVAL,
+                 "tensor_add: accumulator differs");
+        B = std::max(B, acc.B);
+    }
     CtH o = new_ct(B, 3, a.level);
     o.scale = a.scale * b.scale;
     std::vector<EwJob> jobs;
     for (int k = 0; k < B; k++)
         for (int i = 0; i <= a.level; i++) {
-            EwJob j = ewj(EW_TENSOR, i, o.limb(k, 0, i), a.limb(k, 0, i), b.limb(k, 0, i));
+            EwJob j = ewj(add ? EW_TENSOR_ACC : EW_TENSOR, i, o.limb(k, 0, i), a.limb(k, 0, i), b.limb(k, 0, i));
             j.a1 = a.limb(k, 1, i);
             j.b1 = b.limb(k, 1, i);
             j.d1 = o.limb(k, 1, i);
             j.d2 = o.limb(k, 2, i);
+            if (add) {
+                j.c = acc.limb(k, 0, i);
+                j.c1 = acc.limb(k, 1, i);
+                j.c2 = acc.limb(k, 2, i);
+            }
             jobs.push_back(j);
         }
     ew(jobs);
@@ -882,62 +899,83 @@ CtH Rec::relin_rescale(const CtH &t) {
 // into the top limb's inverse-transform store, and for i < l
 //   out_i = (a_i - NTT(f^-1 ([t]_{q_i} - [floor(q_l/2)]_{q_i}))) * f q_l^-1,
 // t the converted top limb, which needs f invertible modulo every q_i.
-CtH Rec::rescale(const CtH &a, int64_t factor) {
-    const int l = a.level;
-    TREQUIRE(l >= 1, TETRIS_ELEVEL, "rescale at level 0");
-    if (factor != 1) {
-        bool invertible = true;
-        for (int i = 0; i <= l; i++) invertible = invertible && signed_mod(factor, C.q[i]) != 0;
-        if (!invertible) return rescale(mul_int(a, factor));
-    }
+CtH Rec::rescale(const CtH &a, int64_t factor) { return rescale_many({{a, factor}})[0]; }
+
+// Independent rescales, each at its own level and factor, in one inverse and
+// one forward transform (every job carries its own prime).
+std::vector<CtH> Rec::rescale_many(const std::vector<std::pair<CtH, int64_t>> &items) {
+    std::vector<CtH> outs(items.size());
     const size_t N = C.N;
-    const u64 ql = C.q[l], half = (ql - 1) / 2;
-    // top limb to the coefficient domain, stored as [a_l + floor(q_l/2)]_{q_l}
-    BufPtr tmp = pool().alloc((size_t)a.B * a.comps * N);
-    {
-        std::vector<NttJob> jobs;
+    std::vector<size_t> idx;
+    size_t words = 0;
+    for (size_t n = 0; n < items.size(); n++) {
+        const CtH &a = items[n].first;
+        const int64_t factor = items[n].second;
+        TREQUIRE(a.level >= 1, TETRIS_ELEVEL, "rescale at level 0");
+        bool invertible = true;
+        if (factor != 1)
+            for (int i = 0; i <= a.level; i++) invertible = invertible && signed_mod(factor, C.q[i]) != 0;
+        if (!invertible) {
+            outs[n] = rescale(mul_int(a, factor));
+            continue;
+        }
+        idx.push_back(n);
+        words += (size_t)a.B * a.comps * N;
+    }
+    if (idx.empty()) return outs;
+    // top limbs to the coefficient domain, stored as [f a_l + floor(q_l/2)]_{q_l}
+    BufPtr tmp = pool().alloc(words);
+    std::vector<NttJob> ji, jf;
+    size_t off = 0;
+    for (size_t n : idx) {
+        const CtH &a = items[n].first;
+        const int64_t factor = items[n].second;
+        const int l = a.level;
+        const u64 ql = C.q[l], half = (ql - 1) / 2;
+        u64 *top = tmp->ptr + off;
+        off += (size_t)a.B * a.comps * N;
         for (int b = 0; b < a.B; b++)
             for (int c = 0; c < a.comps; c++) {
                 NttJob j{};
                 j.src = a.limb(b, c, l);
-                j.dst = tmp->ptr + ((size_t)b * a.comps + c) * N;
+                j.dst = top + ((size_t)b * a.comps + c) * N;
                 j.prime = l;
                 j.mul = h_mulmod(C.mods_host[l].ninv, signed_mod(factor, ql), ql);
                 j.mul_sh = h_shoup(j.mul, ql);
                 j.conv_sub = half;
-                jobs.push_back(j);
+                ji.push_back(j);
             }
-        ntt(true, jobs, LOAD_PLAIN, STORE_SCALED);
-    }
-    CtH o = new_ct(a.B, a.comps, l - 1);
-    o.scale = a.scale / (double)C.q[l];
-    std::vector<NttJob> jobs;
-    for (int i = 0; i < l; i++) {
-        const u64 qi = C.q[i];
-        NttJob proto{};
-        proto.prime = i;
-        proto.conv_sub = half % qi;
-        proto.mul = h_invmod(ql % qi, qi);
-        if (factor != 1) {
-            const u64 f = signed_mod(factor, qi), finv = h_invmod(f, qi);
-            proto.c2[0] = finv;
-            proto.c2_sh[0] = h_shoup(finv, qi);
-            proto.conv_sub = h_mulmod(proto.conv_sub, finv, qi);
-            proto.mul = h_mulmod(proto.mul, f, qi);
+        CtH o = new_ct(a.B, a.comps, l - 1);
+        o.scale = a.scale / (double)C.q[l];
+        for (int i = 0; i < l; i++) {
+            const u64 qi = C.q[i];
+            NttJob proto{};
+            proto.prime = i;
+            proto.conv_sub = half % qi;
+            proto.mul = h_invmod(ql % qi, qi);
+            if (factor != 1) {
+                const u64 f = signed_mod(factor, qi), finv = h_invmod(f, qi);
+                proto.c2[0] = finv;
+                proto.c2_sh[0] = h_shoup(finv, qi);
+                proto.conv_sub = h_mulmod(proto.conv_sub, finv, qi);
+                proto.mul = h_mulmod(proto.mul, f, qi);
+            }
+            proto.mul_sh = h_shoup(proto.mul, qi);
+            for (int b = 0; b < a.B; b++)
+                for (int c = 0; c < a.comps; c++) {
+                    NttJob jb = proto;
+                    jb.src = top + ((size_t)b * a.comps + c) * N;
+                    jb.base = a.limb(b, c, i);
+                    jb.dst = o.limb(b, c, i);
+                    jf.push_back(jb);
+                }
         }
-        proto.mul_sh = h_shoup(proto.mul, qi);
-        for (int b = 0; b < a.B; b++)
-            for (int c = 0; c < a.comps; c++) {
-                NttJob jb = proto;
-                jb.src = tmp->ptr + ((size_t)b * a.comps + c) * N;
-                jb.base = a.limb(b, c, i);
-                jb.dst = o.limb(b, c, i);
-                jobs.push_back(jb);
-            }
+        outs[n] = o;
+        P.rescales++;
     }
-    ntt(false, jobs, LOAD_REDUCE, STORE_COMBINE);
-    P.rescales++;
-    return o;
+    ntt(true, ji, LOAD_PLAIN, STORE_SCALED);
+    ntt(false, jf, LOAD_REDUCE, STORE_COMBINE);
+    return outs;
 }
 
 CtH Rec::drop(const CtH &a, int level) {
@@ -999,17 +1037,33 @@ CtH Rec::sum_batch(const CtH &a) {
 
 // Move to level lt with the standard scale S[lt], applying a public factor:
 // keep q_0..q_{lt+1}, multiply by floor(factor * S[lt] * q_{lt+1} / scale + 1/2), rescale.
-CtH Rec::adjust(const CtH &a, int lt, double factor) {
-    if (a.level == lt) {
-        TREQUIRE(factor == 1.0 && a.scale == C.S[lt], TETRIS_EINVAL, "adjust at the same level");
-        return a;
+CtH Rec::adjust(const CtH &a, int lt, double factor) { return adjust_many({{a, lt, factor}})[0]; }
+
+// Independent adjusts recorded as one rescale_many.
+std::vector<CtH> Rec::adjust_many(const std::vector<AdjustItem> &items) {
+    std::vector<CtH> outs(items.size());
+    std::vector<std::pair<CtH, int64_t>> rs;
+    std::vector<size_t> where;
+    for (size_t n = 0; n < items.size(); n++) {
+        const CtH &a = items[n].ct;
+        const int lt = items[n].level;
+        const double factor = items[n].factor;
+        if (a.level == lt) {
+            TREQUIRE(factor == 1.0 && a.scale == C.S[lt], TETRIS_EINVAL, "adjust at the same level");
+            outs[n] = a;
+            continue;
+        }
+        TREQUIRE(a.level > lt, TETRIS_ELEVEL, "input ciphertext level too low");
+        const int64_t cst = round_half_up(((factor * C.S[lt]) * (double)C.q[lt + 1]) / a.scale);
+        rs.push_back({drop(a, lt + 1), cst});
+        where.push_back(n);
     }
-    TREQUIRE(a.level > lt, TETRIS_ELEVEL, "input ciphertext level too low");
-    CtH v = drop(a, lt + 1);
-    const int64_t cst = round_half_up(((factor * C.S[lt]) * (double)C.q[lt + 1]) / a.scale);
-    CtH o = rescale(v, cst);
-    o.scale = C.S[lt];
-    return o;
+    std::vector<CtH> r = rescale_many(rs);
+    for (size_t k = 0; k < where.size(); k++) {
+        outs[where[k]] = r[k];
+        outs[where[k]].scale = C.S[items[where[k]].level];
+    }
+    return outs;
 }
 
 CtH Rec::mul(const CtH &a, const CtH &b) {

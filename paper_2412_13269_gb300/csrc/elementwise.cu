@@ -98,7 +98,8 @@ __global__ void __launch_bounds__(kEwThreads) ew_kernel(const EwJob *jobs, int n
                 r[1] = y >= q ? y - q : y;
                 break;
             }
-            case EW_TENSOR: {
+            case EW_TENSOR:
+            case EW_TENSOR_ACC: {
                 ulonglong2 a0 = *reinterpret_cast<const ulonglong2 *>(J.a + p);
                 ulonglong2 a1 = *reinterpret_cast<const ulonglong2 *>(J.a1 + p);
                 ulonglong2 b0 = *reinterpret_cast<const ulonglong2 *>(J.b + p);
@@ -113,6 +114,14 @@ __global__ void __launch_bounds__(kEwThreads) ew_kernel(const EwJob *jobs, int n
                     Acc128 e = {0, 0};
                     acc_mad(e, a0.y, b1.y); acc_mad(e, a1.y, b0.y);
                     d1.y = reduce128(e.hi, e.lo, m);
+                }
+                if (J.op == EW_TENSOR_ACC) {
+                    const ulonglong2 c0 = *reinterpret_cast<const ulonglong2 *>(J.c + p);
+                    const ulonglong2 c1 = *reinterpret_cast<const ulonglong2 *>(J.c1 + p);
+                    const ulonglong2 c2 = *reinterpret_cast<const ulonglong2 *>(J.c2 + p);
+                    d0.x = add_mod(d0.x, c0.x, q); d0.y = add_mod(d0.y, c0.y, q);
+                    d1.x = add_mod(d1.x, c1.x, q); d1.y = add_mod(d1.y, c1.y, q);
+                    d2.x = add_mod(d2.x, c2.x, q); d2.y = add_mod(d2.y, c2.y, q);
                 }
                 *reinterpret_cast<ulonglong2 *>(J.dst + p) = d0;
                 *reinterpret_cast<ulonglong2 *>(J.d1 + p) = d1;
@@ -183,23 +192,33 @@ __global__ void __launch_bounds__(kEwThreads) keyip_kernel(const KipJob *jobs, i
         make_ulonglong2(reduce128(a1x.hi, a1x.lo, m), reduce128(a1y.hi, a1y.lo, m));
 }
 
-__global__ void __launch_bounds__(kEwThreads) lincomb_kernel(const LinJob *jobs, int njobs, int log_n, const ModInfo *mods) {
-    const size_t n = (size_t)1 << log_n;
-    const size_t total = n * njobs;
-    for (size_t it = blockIdx.x * (size_t)blockDim.x + threadIdx.x; it < total; it += (size_t)gridDim.x * blockDim.x) {
-        const int j = (int)(it >> log_n);
-        const size_t p = it & (n - 1);
-        const LinJob &J = jobs[j];
-        const ModInfo m = mods[J.prime];
-        Acc128 a0 = {0, 0}, a1 = {0, 0};
-        for (uint32_t a = 0; a < J.nattr; a++) {
-            const u64 pt = J.pt[a * J.pt_stride + p];
-            acc_mad(a0, pt, J.w0[a * J.w_stride + p]);
-            acc_mad(a1, pt, J.w1[a * J.w_stride + p]);
-        }
-        J.d0[p] = reduce128(a0.hi, a0.lo, m);
-        J.d1[p] = reduce128(a1.hi, a1.lo, m);
+// One CTA per (job, chunk of 2 * kEwThreads positions), like the key inner
+// product: 16-byte pairs, attribute loop unrolled for loads in flight.
+__global__ void __launch_bounds__(kEwThreads) lincomb_kernel(const LinJob *jobs, int log_n, const ModInfo *mods) {
+    __shared__ LinJob J;
+    {
+        const u64 *gj = reinterpret_cast<const u64 *>(jobs + blockIdx.y);
+        u64 *dj = reinterpret_cast<u64 *>(&J);
+        for (int i = threadIdx.x; i < (int)(sizeof(LinJob) / 8); i += blockDim.x) dj[i] = gj[i];
     }
+    __syncthreads();
+    const size_t p = ((size_t)blockIdx.x * kEwThreads + threadIdx.x) * 2;
+    if (p >= ((size_t)1 << log_n)) return;
+    const ModInfo m = mods[J.prime];
+    Acc128 a0x = {0, 0}, a0y = {0, 0}, a1x = {0, 0}, a1y = {0, 0};
+    const int na = (int)J.nattr;
+#pragma unroll 4
+    for (int a = 0; a < na; a++) {
+        const ulonglong2 pt = __ldg(reinterpret_cast<const ulonglong2 *>(J.pt + a * J.pt_stride + p));
+        const ulonglong2 w0 = *reinterpret_cast<const ulonglong2 *>(J.w0 + a * J.w_stride + p);
+        const ulonglong2 w1 = *reinterpret_cast<const ulonglong2 *>(J.w1 + a * J.w_stride + p);
+        acc_mad(a0x, pt.x, w0.x);
+        acc_mad(a0y, pt.y, w0.y);
+        acc_mad(a1x, pt.x, w1.x);
+        acc_mad(a1y, pt.y, w1.y);
+    }
+    *reinterpret_cast<ulonglong2 *>(J.d0 + p) = make_ulonglong2(reduce128(a0x.hi, a0x.lo, m), reduce128(a0y.hi, a0y.lo, m));
+    *reinterpret_cast<ulonglong2 *>(J.d1 + p) = make_ulonglong2(reduce128(a1x.hi, a1x.lo, m), reduce128(a1y.hi, a1y.lo, m));
 }
 
 __global__ void __launch_bounds__(kEwThreads) reduce_i64_kernel(const RedJob *jobs, int njobs, int log_n, const ModInfo *mods) {
@@ -278,7 +297,12 @@ void launch_keyip(const KipJob *jobs, int njobs, int log_n, const ModInfo *mods,
 }
 void launch_lincomb(const LinJob *jobs, int njobs, int log_n, const ModInfo *mods, cudaStream_t s) {
     if (njobs <= 0) return;
-    lincomb_kernel<<<grid_for((size_t)njobs << log_n), kEwThreads, 0, s>>>(jobs, njobs, log_n, mods);
+    const size_t per_cta = 2 * (size_t)kEwThreads;
+    const unsigned chunks = (unsigned)((((size_t)1 << log_n) + per_cta - 1) / per_cta);
+    for (int j0 = 0; j0 < njobs; j0 += 65535) {
+        dim3 grid(chunks, (unsigned)std::min(65535, njobs - j0));
+        lincomb_kernel<<<grid, kEwThreads, 0, s>>>(jobs + j0, log_n, mods);
+    }
 }
 void launch_reduce_i64(const RedJob *jobs, int njobs, int log_n, const ModInfo *mods, cudaStream_t s) {
     if (njobs <= 0) return;

@@ -132,7 +132,8 @@ enum EwOp {
     EW_FMA = 7,       // dst = a * b + c
     EW_TENSOR = 8,    // a0,a1,b0,b1 -> d0,d1,d2 (pointers a,b,c,d with strides)
     EW_ADD_MUL_CONST = 9, // dst = b + k * a  (used by key generation)
-    EW_REDUCE = 10        // dst = a mod q for any 64-bit a
+    EW_REDUCE = 10,       // dst = a mod q for any 64-bit a
+    EW_TENSOR_ACC = 11    // tensor of (a, a1) and (b, b1) plus the degree-2 ciphertext (c, c1, c2)
 };
 struct EwJob {
     const u64 *a, *b, *c;
@@ -143,6 +144,8 @@ struct EwJob {
     // tensor: second components
     const u64 *a1, *b1;
     u64 *d1, *d2;
+    // tensor with accumulation: components 1 and 2 of the added ciphertext (c is component 0)
+    const u64 *c1, *c2;
 };
 void launch_ew(const EwJob *jobs_dev, int njobs, int log_n, const ModInfo *mods, cudaStream_t s);
 

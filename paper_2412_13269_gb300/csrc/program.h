@@ -176,6 +176,7 @@ class Rec {
     CtH add_int(const CtH &a, int64_t c);
     CtH mul_plain(const CtH &a, const u64 *pt_limb0, size_t pt_bstride);
     CtH tensor(const CtH &a, const CtH &b);
+    CtH tensor_add(const CtH &acc, const CtH &a, const CtH &b);  // acc + a (x) b
     // rescale_after: return the result rescaled by q_l (relin_rescale), exactly
     // as rescale(keyswitch(...)) computes it
     CtH keyswitch(int B, int l, const std::function<const u64 *(int, int)> &d, const Key &key,
@@ -183,11 +184,18 @@ class Rec {
     CtH relin(const CtH &t3);
     CtH relin_rescale(const CtH &t3);    // rescale(relin(t3)) in one pass over the targets
     CtH rescale(const CtH &a, int64_t factor = 1);  // rescale(mul_int(a, factor))
+    std::vector<CtH> rescale_many(const std::vector<std::pair<CtH, int64_t>> &items);
     CtH drop(const CtH &a, int level);
     CtH automorphism(const CtH &a, uint32_t g);
     CtH rotate(const CtH &a, uint32_t g);
     CtH sum_batch(const CtH &a);
     CtH adjust(const CtH &a, int lt, double factor);
+    struct AdjustItem {
+        CtH ct;
+        int level;
+        double factor;
+    };
+    std::vector<CtH> adjust_many(const std::vector<AdjustItem> &items);
     CtH mul(const CtH &a, const CtH &b);
 
   private:

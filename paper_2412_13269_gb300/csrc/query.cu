@@ -115,16 +115,16 @@ static CtH relin_rescale_to(Rec &R, const CtH &t, int level_out) {
 // the two degree-2 products in brackets formed at level l-2 and relinearised once.
 static CtH sign_stage(Rec &R, const CtH &u, const std::array<double, 4> &co) {
     const int l = u.level;
+    // the four adjusts of u are independent: one pair of transforms
+    std::vector<CtH> a = R.adjust_many({{u, l - 1, co[3]}, {u, l - 2, co[2]}, {u, l - 2, co[1]}, {u, l - 3, co[0]}});
+    const CtH &b3 = a[0], &a2u = a[1], &b1 = a[2], &t1 = a[3];
     CtH u2 = R.mul(u, u);
     CtH u4 = R.mul(u2, u2);
-    CtH b3 = R.adjust(u, l - 1, co[3]);
     CtH t7 = R.mul(b3, u2);
-    CtH inner = R.add(t7, R.adjust(u, l - 2, co[2]));
-    CtH b1 = R.adjust(u, l - 2, co[1]);
+    CtH inner = R.add(t7, a2u);
     CtH u2d = R.adjust(u2, l - 2, 1.0);
-    CtH T = R.add(R.tensor(b1, u2d), R.tensor(inner, u4));
+    CtH T = R.tensor_add(R.tensor(b1, u2d), inner, u4);
     CtH t = relin_rescale_to(R, T, l - 3);
-    CtH t1 = R.adjust(u, l - 3, co[0]);
     return R.add(t1, t);
 }
 
@@ -136,9 +136,10 @@ static CtH eval_blocks(Rec &R, const Database &db, const QPlan &pl, int b0, int 
     // x = sum_j pt_j * Enc(w_j), then rescale
     CtH x0 = R.new_ct(nb, 2, L);
     {
+        // blocks innermost: the B jobs of one prime read the same w_j limbs back to back
         std::vector<LinJob> jobs;
-        for (int b = 0; b < nb; b++)
-            for (int i = 0; i <= L; i++) {
+        for (int i = 0; i <= L; i++)
+            for (int b = 0; b < nb; b++) {
                 LinJob j{};
                 j.pt = db.pts->ptr + (((size_t)(b0 + b) * db.attrs) * nq + i) * N;
                 j.pt_stride = nq * N;
@@ -181,10 +182,7 @@ static CtH eval_blocks(Rec &R, const Database &db, const QPlan &pl, int b0, int 
         for (int k = 2; k <= degree; k++) Pw[k] = power_rule(Pw, k, lvl);
         // y = sum_k c_k x^k with one relinearisation
         CtH T;
-        for (int k = 1; k <= degree; k++) {
-            CtH tk = R.tensor(ck[k], lvl(k, pl.l_d));
-            T = (k == 1) ? tk : R.add(T, tk);
-        }
+        for (int k = 1; k <= degree; k++) T = R.tensor_add(T, ck[k], lvl(k, pl.l_d));
         y = relin_rescale_to(R, T, pl.l_y);
     } else {
         const int g = pl.g, m = pl.m, l_b = pl.l_lin - pl.bb, l_f = pl.l_lin - pl.df;
@@ -203,21 +201,13 @@ static CtH eval_blocks(Rec &R, const Database &db, const QPlan &pl, int b0, int 
         };
         for (int i = 2; i < m; i++) G[i] = power_rule(G, i, glvl);
         CtH T;
-        for (int j = 1; j < g; j++) {  // s_0's terms at l_f
-            CtH tk = R.tensor(ck[j], lvl(j, l_f));
-            T = (j == 1) ? tk : R.add(T, tk);
-        }
+        for (int j = 1; j < g; j++) T = R.tensor_add(T, ck[j], lvl(j, l_f));  // s_0's terms at l_f
         for (int i = 1; i < m; i++) {
             CtH Ti;
-            bool any = false;
-            for (int j = 1; j < g && g * i + j <= degree; j++) {
-                CtH tk = R.tensor(ck[g * i + j], lvl(j, l_b));
-                Ti = any ? R.add(Ti, tk) : tk;
-                any = true;
-            }
+            for (int j = 1; j < g && g * i + j <= degree; j++) Ti = R.tensor_add(Ti, ck[g * i + j], lvl(j, l_b));
             CtH si = ck[g * i];
-            if (any) si = R.adjust(R.add(relin_rescale_to(R, Ti, l_b - 1), ck[g * i]), l_f, 1.0);
-            T = R.add(T, R.tensor(si, glvl(i, l_f)));
+            if (Ti.buf) si = R.adjust(R.add(relin_rescale_to(R, Ti, l_b - 1), ck[g * i]), l_f, 1.0);
+            T = R.tensor_add(T, si, glvl(i, l_f));
         }
         G.clear();
         gcache.clear();
@@ -272,9 +262,13 @@ std::unique_ptr<Program> record_query(Ctx &C, const Database &db, const QuerySpe
         R.ntt(false, jobs, LOAD_PLAIN, STORE_PLAIN);
     }
     // per-query: coefficients and threshold moved to their levels
-    std::vector<CtH> ck;
-    for (int k = 0; k <= q.degree; k++) ck.push_back(R.adjust(cin[k], pl.coef_level(k), 1.0));
-    CtH tadj = R.adjust(tin, pl.l_y, 1.0);
+    // one pair of transforms for all of them
+    std::vector<Rec::AdjustItem> items;
+    for (int k = 0; k <= q.degree; k++) items.push_back({cin[k], pl.coef_level(k), 1.0});
+    items.push_back({tin, pl.l_y, 1.0});
+    std::vector<CtH> ck = R.adjust_many(items);
+    CtH tadj = ck.back();
+    ck.pop_back();
     // block groups
     const int B = db.blocks;
     const int bpl = q.bpl <= 0 ? B : std::min(q.bpl, B);
