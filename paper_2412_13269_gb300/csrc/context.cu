@@ -249,10 +249,10 @@ void Rec::emit(const Deferred &d) {
     const std::string saved_prefix = prefix;
     prefix.clear();
     switch (d.type) {
-        case 0: ntt(d.inverse, as((NttJob *)nullptr), d.load_mode, d.store_mode); break;
+        case 0: ntt(d.inverse, as((NttJob *)nullptr), d.load_mode, d.store_mode, -1, STORE_PLAIN, d.passes); break;
         case 1: ew(as((EwJob *)nullptr)); break;
         case 2: aut(as((AutJob *)nullptr), d.galois); break;
-        case 3: kip(as((KipJob *)nullptr)); break;
+        case 3: ksup(as((KsJob *)nullptr)); break;
         case 4: lin(as((LinJob *)nullptr)); break;
         case 5: red(as((RedJob *)nullptr)); break;
     }
@@ -270,14 +270,16 @@ static const char *store_name(int m) {
 }
 
 void Rec::ntt(bool inverse, const std::vector<NttJob> &jobs, int load_mode, int store_mode, int split,
-              int store_mode_b) {
+              int store_mode_b, int passes) {
     if (jobs.empty()) return;
     TREQUIRE(split < 0 || !defer, TETRIS_EINVAL, "split transforms are not deferred");
+    TREQUIRE(passes >= 1 && passes <= 3, TETRIS_EINVAL, "no transform pass selected");
     if (defer) {
         Deferred d = make_deferred(0, jobs, prefix, 0);
         d.inverse = inverse;
         d.load_mode = load_mode;
         d.store_mode = store_mode;
+        d.passes = passes;
         defer->push_back(std::move(d));
         return;
     }
@@ -300,9 +302,11 @@ void Rec::ntt(bool inverse, const std::vector<NttJob> &jobs, int load_mode, int 
         for (auto &j : jobs) conv += j.nsrc;
     const double first_log = inverse ? log2 : log1, second_log = inverse ? log1 : log2;
     const double mm1 = (double)n * N * first_log / 2 + conv * N;
-    P.add_launch([=](cudaStream_t s, const uint8_t *a) {
-        launch_ntt(inverse, logn, t, reinterpret_cast<const NttJob *>(a + off), n, load_mode, store_mode, s, 0);
-    }, prefix + dir + "_p1_" + load_name(load_mode), distinct_bytes(srcs, N) + w, mm1);
+    if (passes & 1)
+        P.add_launch([=](cudaStream_t s, const uint8_t *a) {
+            launch_ntt(inverse, logn, t, reinterpret_cast<const NttJob *>(a + off), n, load_mode, store_mode, s, 0);
+        }, prefix + dir + "_p1_" + load_name(load_mode), distinct_bytes(srcs, N) + w, mm1);
+    if (!(passes & 2)) return;
     // second pass: one launch per store segment
     auto second = [&](int j0, int j1, int mode) {
         const int m = j1 - j0;
@@ -374,30 +378,33 @@ void Rec::aut(const std::vector<AutJob> &jobs, uint32_t g) {
     }, prefix + "automorphism", 2.0 * n * C.N * 8);
 }
 
-void Rec::kip(const std::vector<KipJob> &jobs) {
+void Rec::ksup(const std::vector<KsJob> &jobs) {
     if (jobs.empty()) return;
     if (defer) {
         defer->push_back(make_deferred(3, jobs, prefix, 0));
         return;
     }
-    size_t off = P.add_jobs(jobs.data(), jobs.size() * sizeof(KipJob));
+    size_t off = P.add_jobs(jobs.data(), jobs.size() * sizeof(KsJob));
     int n = (int)jobs.size(), logn = C.log_n;
-    const ModInfo *m = C.nt.mods;
+    NttTables t = C.nt;
     std::vector<const void *> rd;
-    double prods = 0;
+    double prods = 0, transforms = 0;
     for (auto &j : jobs) {
         for (uint32_t d = 0; d < j.ndig; d++) {
             rd.push_back(j.src[d]);
             rd.push_back(j.key0[d]);
             rd.push_back(j.key1[d]);
+            if ((int)d != j.own) transforms += 1;
         }
         rd.push_back(j.ex0);
         rd.push_back(j.ex1);
-        prods += 2.0 * j.ndig + (j.ex0 ? 1 : 0) + (j.ex1 ? 1 : 0);
+        prods += 2.0 * j.ndig + (j.own >= 0 ? 1 : 0) + (j.ex0 ? 1 : 0) + (j.ex1 ? 1 : 0);
     }
+    // the row pass of each transformed digit (log2(N2)/2 butterfly products per word) and the products above
+    const double mm = (transforms * (logn / 2) / 2.0 + prods) * C.N;
     P.add_launch([=](cudaStream_t s, const uint8_t *a) {
-        launch_keyip(reinterpret_cast<const KipJob *>(a + off), n, logn, m, s);
-    }, prefix + "keyip", distinct_bytes(rd, C.N) + 2.0 * n * C.N * 8, prods * C.N);
+        launch_keyswitch_up(logn, t, reinterpret_cast<const KsJob *>(a + off), n, s);
+    }, prefix + "modup_keyip", distinct_bytes(rd, C.N) + 2.0 * n * C.N * 8, mm);
 }
 
 void Rec::lin(const std::vector<LinJob> &jobs) {
@@ -668,7 +675,9 @@ CtH Rec::keyswitch(int B, int l, const std::function<const u64 *(int, int)> &d, 
         }
         ntt(true, jobs, LOAD_PLAIN, STORE_SCALED);
     }
-    // 2. ModUp: digit j -> every prime outside it, then NTT (conversion fused into the load)
+    // 2. ModUp, first (column) pass: digit j -> every prime outside it, the
+    //    conversion fused into the load; its constants carry R = 2^64 mod q_t
+    //    for the Montgomery products of step 3
     BufPtr mu = pool().alloc((size_t)B * dnum * ntg * N);
     auto mul = [&](int b, int j, int t) { return mu->ptr + (((size_t)b * dnum + j) * ntg + t) * N; };
     {
@@ -677,7 +686,13 @@ CtH Rec::keyswitch(int B, int l, const std::function<const u64 *(int, int)> &d, 
             const int lo = j * alpha, hi = std::min(nl, (j + 1) * alpha);
             for (int t = 0; t < ntg; t++) {
                 if (t >= lo && t < hi) continue;
-                NttJob proto = conv_job(C.qp_prime(l, t), nullptr, lo, hi - lo);
+                const uint32_t gp = C.qp_prime(l, t);
+                const u64 qt = C.all[gp];
+                NttJob proto = conv_job(gp, nullptr, lo, hi - lo);
+                for (int s2 = 0; s2 < hi - lo; s2++) {
+                    proto.c2[s2] = h_mulmod(proto.c2[s2], C.mods_host[gp].r64, qt);
+                    proto.c2_sh[s2] = h_shoup(proto.c2[s2], qt);
+                }
                 for (int b = 0; b < B; b++) {
                     NttJob jb = proto;
                     jb.src = dcoef->ptr + ((size_t)b * nl + lo) * N;
@@ -686,7 +701,7 @@ CtH Rec::keyswitch(int B, int l, const std::function<const u64 *(int, int)> &d, 
                 }
             }
         }
-        ntt(false, jobs, LOAD_CONV_PRE, STORE_PLAIN);
+        ntt(false, jobs, LOAD_CONV_PRE, STORE_PLAIN, -1, STORE_PLAIN, 1);
     }
     // P mod q_i, floor(P/2) mod q_i
     auto pmod = [&](int i) {
@@ -699,20 +714,24 @@ CtH Rec::keyswitch(int B, int l, const std::function<const u64 *(int, int)> &d, 
         const u64 qi = C.q[i];
         return h_mulmod((pmod(i) + qi - 1) % qi, h_invmod(2, qi), qi);
     };
-    // 3. key inner product over Q_l P
+    // 3. ModUp second (row) pass of every digit fused with the key inner
+    //    product over Q_l P; blocks innermost, so the B jobs of one target read
+    //    the same key limbs back to back and the key comes from DRAM once
     BufPtr acc = pool().alloc((size_t)B * 2 * ntg * N);
     auto accl = [&](int b, int c, int t) { return acc->ptr + (((size_t)b * 2 + c) * ntg + t) * N; };
     {
-        // blocks innermost: the B jobs of one target read the same key limbs
-        // back to back, so the key comes from DRAM once per launch
-        std::vector<KipJob> jobs;
+        std::vector<KsJob> jobs;
         for (int t = 0; t < ntg; t++)
             for (int b = 0; b < B; b++) {
-                KipJob k{};
+                KsJob k{};
                 const uint32_t gp = C.qp_prime(l, t);
+                const u64 qt = C.all[gp];
+                k.own = -1;
                 for (int j = 0; j < dnum; j++) {
                     const int lo = j * alpha, hi = std::min(nl, (j + 1) * alpha);
-                    k.src[j] = (t >= lo && t < hi) ? d(b, t) : mul(b, j, t);
+                    const bool own = t >= lo && t < hi;
+                    if (own) k.own = j;
+                    k.src[j] = own ? d(b, t) : mul(b, j, t);
                     k.key0[j] = key.buf->ptr + (((size_t)j * 2 + 0) * nQP + gp) * N;
                     k.key1[j] = key.buf->ptr + (((size_t)j * 2 + 1) * nQP + gp) * N;
                 }
@@ -720,14 +739,16 @@ CtH Rec::keyswitch(int B, int l, const std::function<const u64 *(int, int)> &d, 
                 k.acc1 = accl(b, 1, t);
                 k.prime = gp;
                 k.ndig = dnum;
+                k.qinv = h_inv64(qt);
                 if (fused && t < nl && extra) {
                     k.ex0 = extra(b, 0, t);
                     k.ex1 = extra(b, 1, t);
                     k.pm = pmod(t);
+                    k.pm_sh = h_shoup(k.pm, qt);
                 }
                 jobs.push_back(k);
             }
-        kip(jobs);
+        ksup(jobs);
     }
     mu.reset();
     dcoef.reset();

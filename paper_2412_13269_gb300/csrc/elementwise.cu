@@ -150,50 +150,8 @@ __global__ void __launch_bounds__(kEwThreads) aut_kernel(const AutJob *jobs, int
     }
 }
 
-// One CTA per (job, chunk of 2 * kEwThreads positions): the descriptor is
-// staged in shared memory once, each thread takes a 16-byte pair of positions,
-// and the digit loop is unrolled so several loads per thread are in flight.
-__global__ void __launch_bounds__(kEwThreads) keyip_kernel(const KipJob *jobs, int log_n, const ModInfo *mods) {
-    __shared__ KipJob J;
-    {
-        const u64 *gj = reinterpret_cast<const u64 *>(jobs + blockIdx.y);
-        u64 *dj = reinterpret_cast<u64 *>(&J);
-        for (int i = threadIdx.x; i < (int)(sizeof(KipJob) / 8); i += blockDim.x) dj[i] = gj[i];
-    }
-    __syncthreads();
-    const size_t p = ((size_t)blockIdx.x * kEwThreads + threadIdx.x) * 2;
-    if (p >= ((size_t)1 << log_n)) return;
-    const ModInfo m = mods[J.prime];
-    Acc128 a0x = {0, 0}, a0y = {0, 0}, a1x = {0, 0}, a1y = {0, 0};
-    const int nd = (int)J.ndig;
-#pragma unroll 4
-    for (int d = 0; d < nd; d++) {
-        const ulonglong2 x = *reinterpret_cast<const ulonglong2 *>(J.src[d] + p);
-        const ulonglong2 k0 = __ldg(reinterpret_cast<const ulonglong2 *>(J.key0[d] + p));
-        const ulonglong2 k1 = __ldg(reinterpret_cast<const ulonglong2 *>(J.key1[d] + p));
-        acc_mad(a0x, x.x, k0.x);
-        acc_mad(a0y, x.y, k0.y);
-        acc_mad(a1x, x.x, k1.x);
-        acc_mad(a1y, x.y, k1.y);
-    }
-    if (J.ex0) {
-        const ulonglong2 e = *reinterpret_cast<const ulonglong2 *>(J.ex0 + p);
-        acc_mad(a0x, e.x, J.pm);
-        acc_mad(a0y, e.y, J.pm);
-    }
-    if (J.ex1) {
-        const ulonglong2 e = *reinterpret_cast<const ulonglong2 *>(J.ex1 + p);
-        acc_mad(a1x, e.x, J.pm);
-        acc_mad(a1y, e.y, J.pm);
-    }
-    *reinterpret_cast<ulonglong2 *>(J.acc0 + p) =
-        make_ulonglong2(reduce128(a0x.hi, a0x.lo, m), reduce128(a0y.hi, a0y.lo, m));
-    *reinterpret_cast<ulonglong2 *>(J.acc1 + p) =
-        make_ulonglong2(reduce128(a1x.hi, a1x.lo, m), reduce128(a1y.hi, a1y.lo, m));
-}
-
-// One CTA per (job, chunk of 2 * kEwThreads positions), like the key inner
-// product: 16-byte pairs, attribute loop unrolled for loads in flight.
+// One CTA per (job, chunk of 2 * kEwThreads positions): the descriptor staged
+// in shared memory once, 16-byte pairs, attribute loop unrolled for loads in flight.
 __global__ void __launch_bounds__(kEwThreads) lincomb_kernel(const LinJob *jobs, int log_n, const ModInfo *mods) {
     __shared__ LinJob J;
     {
@@ -285,15 +243,6 @@ void launch_ew(const EwJob *jobs, int njobs, int log_n, const ModInfo *mods, cud
 void launch_automorphism(const AutJob *jobs, int njobs, int log_n, uint32_t galois, cudaStream_t s) {
     if (njobs <= 0) return;
     aut_kernel<<<grid_for((size_t)njobs << log_n), kEwThreads, 0, s>>>(jobs, njobs, log_n, galois);
-}
-void launch_keyip(const KipJob *jobs, int njobs, int log_n, const ModInfo *mods, cudaStream_t s) {
-    if (njobs <= 0) return;
-    const size_t per_cta = 2 * (size_t)kEwThreads;
-    const unsigned chunks = (unsigned)((((size_t)1 << log_n) + per_cta - 1) / per_cta);
-    for (int j0 = 0; j0 < njobs; j0 += 65535) {
-        dim3 grid(chunks, (unsigned)std::min(65535, njobs - j0));
-        keyip_kernel<<<grid, kEwThreads, 0, s>>>(jobs + j0, log_n, mods);
-    }
 }
 void launch_lincomb(const LinJob *jobs, int njobs, int log_n, const ModInfo *mods, cudaStream_t s) {
     if (njobs <= 0) return;

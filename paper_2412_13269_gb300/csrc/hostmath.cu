@@ -22,6 +22,13 @@ u64 h_powmod(u64 a, u64 e, u64 q) {
 u64 h_invmod(u64 a, u64 q) { return h_powmod(a, q - 2, q); }  // q prime
 
 u64 h_shoup(u64 w, u64 q) { return (u64)(((u128)w << 64) / q); }
+// Newton's iteration x <- x (2 - q x) doubles the correct low bits; x = q is
+// right to 3 bits for odd q (q^2 = 1 mod 8), five steps reach 96 > 64.
+u64 h_inv64(u64 q) {
+    u64 x = q;
+    for (int i = 0; i < 5; i++) x *= 2 - q * x;
+    return x;
+}
 
 // Deterministic Miller-Rabin for 64-bit n (first twelve prime bases).
 bool h_is_prime(u64 n) {

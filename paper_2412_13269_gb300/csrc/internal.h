@@ -43,6 +43,7 @@ u64 h_mulmod(u64 a, u64 b, u64 q);
 u64 h_powmod(u64 a, u64 e, u64 q);
 u64 h_invmod(u64 a, u64 q);
 u64 h_shoup(u64 w, u64 q);  // floor(w * 2^64 / q)
+u64 h_inv64(u64 q);          // q^-1 mod 2^64 (q odd)
 bool h_is_prime(u64 n);
 u64 h_primitive_2n_root(u64 q, u64 n);
 std::vector<u64> h_gen_primes(int bits, int count, int cong_log2, const std::vector<u64> &exclude);
@@ -156,19 +157,24 @@ struct AutJob {
 };
 void launch_automorphism(const AutJob *jobs_dev, int njobs, int log_n, uint32_t galois, cudaStream_t s);
 
-// key inner product: for each (batch, target limb t):
-//   acc_c[t] = sum_j src_j[t] * key_j[c][t]  (c = 0, 1)
-struct KipJob {
-    const u64 *src[32];   // per digit source limb (NTT domain)
-    const u64 *key0[32];  // per digit key limb for component 0
+// ModUp second pass fused with the key inner product (ntt.cu), one job per
+// (target limb t, block): for every digit j, x_j is the row pass of src[j] (the
+// ModUp column-pass output, whose conversion constants carry R = 2^64 mod q_t)
+// or, for the digit own that holds t, R * src[own] (the input limb, NTT domain);
+// then acc_c[t] = sum_j x_j key_j[c][t] R^-1 (Montgomery products) + pm ex_c[t].
+struct KsJob {
+    const u64 *src[32];
+    const u64 *key0[32];
     const u64 *key1[32];
     u64 *acc0, *acc1;
-    const u64 *ex0, *ex1;  // optional: acc_c += pm * ex_c (ModDown's P * d folded into the sum)
-    u64 pm;
-    uint32_t prime;
-    uint32_t ndig;
+    const u64 *ex0, *ex1;  // optional: P e folded in (pm = [P]_{q_t}, Shoup companion pm_sh)
+    u64 pm, pm_sh;
+    u64 qinv;              // q_t^-1 mod 2^64
+    uint32_t prime, ndig;
+    int32_t own;           // digit whose source is the NTT-domain input, -1 if none
+    uint32_t pad;
 };
-void launch_keyip(const KipJob *jobs_dev, int njobs, int log_n, const ModInfo *mods, cudaStream_t s);
+void launch_keyswitch_up(int log_n, const NttTables &t, const KsJob *jobs_dev, int njobs, cudaStream_t s);
 
 // linear combination: dst_c[limb] = sum_j pt_j[limb] * w_j[c][limb], c = 0,1
 struct LinJob {

@@ -100,62 +100,139 @@ enum { M_PLAIN = 0, M_INT64 = 1, M_STORE = 3, M_COMBINE = 4, M_CONVPRE = 5, M_RE
        M_SCALED_CONV = 8 };
 constexpr bool is_second(int m) { return m == M_STORE || m == M_COMBINE || m == M_SCALED || m == M_SCALED_CONV; }
 
-template <int LOGM, bool INV, bool COL, int MODE, int LOGEV, bool OPEN>
-__device__ __forceinline__ void pass_body(const PassParams &P, const NttJob &J, u64 *sm, const ModInfo &mi) {
-    constexpr int M = 1 << LOGM;
-    constexpr int LOGE = LOGM >= LOGEV ? LOGEV : LOGM;
-    constexpr int E = 1 << LOGE;
-    constexpr int T = M / E;
-    constexpr int NG = (LOGM + LOGE - 1) / LOGE;
+// Geometry of one pass: which sub-problem s and lane t a thread takes, where
+// its elements sit in global and shared memory, and the register windows.
+template <int LOGM, bool INV, bool COL, int LOGEV>
+struct Geo {
+    static constexpr int M = 1 << LOGM;
+    static constexpr int LOGE = LOGM >= LOGEV ? LOGEV : LOGM;
+    static constexpr int E = 1 << LOGE;
+    static constexpr int T = M / E;
+    static constexpr int NG = (LOGM + LOGE - 1) / LOGE;
     using G = Group<LOGM, LOGE, INV>;
-    const int N1 = 1 << P.log1, N2 = 1 << P.log2;
-    const int nsub = COL ? N2 : N1;
-    const int sub_cta = min(kThreads / T, nsub);
-    const int sub0 = blockIdx.x * sub_cta;
-    const int tid = threadIdx.x;
-    const u64 q = mi.q, q2 = 2 * q;
-    const size_t N = (size_t)N1 * N2;
-    const u64 *tw = (INV ? P.t.itw : P.t.tw) + (size_t)J.prime * N;
-    const u64 *twsh = (INV ? P.t.itw_sh : P.t.tw_sh) + (size_t)J.prime * N;
-
-    // thread -> (sub-problem s, lane t): consecutive threads take consecutive
-    // columns in the column pass and consecutive lanes of a row in the row pass
-    const int s = COL ? tid % sub_cta : tid / T;
-    const int t = COL ? tid / sub_cta : tid % T;
-    const u64 o = COL ? 1 : (u64)(N1 + sub0 + s);
-    auto smidx = [&](int r) -> int { return COL ? r * sub_cta + s : s * (M + M / 16) + r + (r >> 4); };
-    auto gidx = [&](int r) -> size_t { return COL ? (size_t)r * N2 + sub0 + s : (size_t)(sub0 + s) * N2 + r; };
-    auto row = [&](int g, int k) -> int {
-        const int l = G::lo(g);
-        return (t & ((1 << l) - 1)) | (k << l) | ((t >> l) << (l + LOGE));
-    };
-    // A row-pass sub-problem lives in one warp (T <= 32 consecutive threads),
-    // so its exchanges only synchronise the warp; column sub-problems span warps.
-    static_assert(COL || T <= 32, "row sub-problem wider than a warp");
-    auto sync = [&]() {
-        if (COL) __syncthreads();
-        else __syncwarp();
-    };
     // In the row pass a group whose register window is the low bits holds
     // contiguous words per thread; those ends go through shared memory so the
     // global accesses stay coalesced (lane t takes words t, t + T, t + 2T, ...).
-    constexpr bool IN_STAGE = !COL && G::lo(0) != LOGM - LOGE;
-    constexpr bool OUT_STAGE = !COL && G::lo(NG - 1) != LOGM - LOGE;
-    auto lrow = [&](int k) -> int { return IN_STAGE ? t + T * k : row(0, k); };
-    auto srow = [&](int k) -> int { return OUT_STAGE ? t + T * k : row(NG - 1, k); };
+    static constexpr bool IN_STAGE = !COL && G::lo(0) != LOGM - LOGE;
+    static constexpr bool OUT_STAGE = !COL && G::lo(NG - 1) != LOGM - LOGE;
+    // A row-pass sub-problem lives in one warp (T <= 32 consecutive threads),
+    // so its exchanges only synchronise the warp; column sub-problems span warps.
+    static_assert(COL || T <= 32, "row sub-problem wider than a warp");
+
+    int N1, N2, sub_cta, sub0, s, t;
+    u64 o;
+    __device__ Geo(const PassParams &P) {
+        N1 = 1 << P.log1;
+        N2 = 1 << P.log2;
+        const int nsub = COL ? N2 : N1;
+        sub_cta = min(kThreads / T, nsub);
+        sub0 = blockIdx.x * sub_cta;
+        // consecutive threads take consecutive columns in the column pass and
+        // consecutive lanes of a row in the row pass
+        s = COL ? (int)threadIdx.x % sub_cta : (int)threadIdx.x / T;
+        t = COL ? (int)threadIdx.x / sub_cta : (int)threadIdx.x % T;
+        o = COL ? 1 : (u64)(N1 + sub0 + s);
+    }
+    __device__ int smidx(int r) const { return COL ? r * sub_cta + s : s * (M + M / 16) + r + (r >> 4); }
+    __device__ size_t gidx(int r) const { return COL ? (size_t)r * N2 + sub0 + s : (size_t)(sub0 + s) * N2 + r; }
+    __device__ int row(int g, int k) const {
+        const int l = G::lo(g);
+        return (t & ((1 << l) - 1)) | (k << l) | ((t >> l) << (l + LOGE));
+    }
+    __device__ int lrow(int k) const { return IN_STAGE ? t + T * k : row(0, k); }
+    __device__ int srow(int k) const { return OUT_STAGE ? t + T * k : row(NG - 1, k); }
+    __device__ void sync() const {
+        if (COL) __syncthreads();
+        else __syncwarp();
+    }
+};
+
+// The butterfly stages of one pass on the thread's registers x (loaded at
+// lrow), leaving them at srow: shared-memory exchanges between groups and the
+// staging of non-coalesced ends.
+template <int LOGM, bool INV, bool COL, int LOGEV, bool OPEN>
+__device__ __forceinline__ void run_stages(const Geo<LOGM, INV, COL, LOGEV> &g, u64 (&x)[Geo<LOGM, INV, COL, LOGEV>::E],
+                                           u64 *sm, const u64 *tw, const u64 *twsh, u64 q) {
+    using GG = Geo<LOGM, INV, COL, LOGEV>;
+    using G = typename GG::G;
+    constexpr int M = GG::M, E = GG::E, LOGE = GG::LOGE, NG = GG::NG;
+    const u64 q2 = 2 * q;
+    if (GG::IN_STAGE) {
+#pragma unroll
+        for (int k = 0; k < E; k++) sm[g.smidx(g.lrow(k))] = x[k];
+        g.sync();
+#pragma unroll
+        for (int k = 0; k < E; k++) x[k] = sm[g.smidx(g.row(0, k))];
+    }
+#pragma unroll
+    for (int gi = 0; gi < NG; gi++) {
+        if (gi > 0) {
+            g.sync();  // (gi > 1) every thread has read the previous exchange
+#pragma unroll
+            for (int k = 0; k < E; k++) sm[g.smidx(g.row(gi - 1, k))] = x[k];
+            g.sync();
+#pragma unroll
+            for (int k = 0; k < E; k++) x[k] = sm[g.smidx(g.row(gi, k))];
+        }
+        const int blo = G::blo(gi), bhi = G::bhi(gi), lo = G::lo(gi);
+        const int tlow = g.t & ((1 << lo) - 1);
+        const int thigh = (g.t >> lo) << (lo + LOGE);
+#pragma unroll
+        for (int st = 0; st < LOGE; st++) {
+            const int b = INV ? blo + st : bhi - st;
+            if (b >= blo && b <= bhi) {
+                const int bb = b - lo;
+#pragma unroll
+                for (int k = 0; k < E; k++) {
+                    if (k & (1 << bb)) continue;
+                    // pairs that agree above bit bb share a twiddle; load it once
+                    if (k & ((1 << bb) - 1)) continue;
+                    const int r0 = tlow | (k << lo) | thigh;
+                    const u64 widx = (u64)(M >> (b + 1)) * g.o + (u64)(r0 >> (b + 1));
+                    const u64 w = __ldg(tw + widx), wsh = __ldg(twsh + widx);
+#pragma unroll
+                    for (int j = 0; j < E; j++) {
+                        if (j >= (1 << bb)) continue;
+                        if (INV) gs_bfly(x[k + j], x[k + j + (1 << bb)], w, wsh, q, q2);
+                        else if (OPEN) ct_bfly_open(x[k + j], x[k + j + (1 << bb)], w, wsh, q, q2);
+                        else ct_bfly(x[k + j], x[k + j + (1 << bb)], w, wsh, q, q2);
+                    }
+                }
+            }
+        }
+    }
+    if (GG::OUT_STAGE) {
+        g.sync();
+#pragma unroll
+        for (int k = 0; k < E; k++) sm[g.smidx(g.row(NG - 1, k))] = x[k];
+        g.sync();
+#pragma unroll
+        for (int k = 0; k < E; k++) x[k] = sm[g.smidx(g.srow(k))];
+    }
+}
+
+template <int LOGM, bool INV, bool COL, int MODE, int LOGEV, bool OPEN>
+__device__ __forceinline__ void pass_body(const PassParams &P, const NttJob &J, u64 *sm, const ModInfo &mi) {
+    using GG = Geo<LOGM, INV, COL, LOGEV>;
+    constexpr int E = GG::E;
+    const GG g(P);
+    const u64 q = mi.q, q2 = 2 * q;
+    const size_t N = (size_t)g.N1 * g.N2;
+    const u64 *tw = (INV ? P.t.itw : P.t.tw) + (size_t)J.prime * N;
+    const u64 *twsh = (INV ? P.t.itw_sh : P.t.tw_sh) + (size_t)J.prime * N;
 
     u64 x[E];
     // 1. load straight into the first group's registers, through the producer's load mode
     if (is_second(MODE)) {
 #pragma unroll
-        for (int k = 0; k < E; k++) x[k] = J.dst[gidx(lrow(k))];
+        for (int k = 0; k < E; k++) x[k] = J.dst[g.gidx(g.lrow(k))];
     } else if (MODE == M_REDUCE) {
         const u64 *src = J.src;
         const u64 sub = J.conv_sub;
         const u64 c = J.c2[0] ? J.c2[0] : 1, csh = J.c2[0] ? J.c2_sh[0] : mi.one_sh;
 #pragma unroll
         for (int k = 0; k < E; k++) {
-            u64 v = shoup_lazy(src[gidx(lrow(k))], c, csh, q);  // [0, 2q) for any 64-bit source
+            u64 v = shoup_lazy(src[g.gidx(g.lrow(k))], c, csh, q);  // [0, 2q) for any 64-bit source
             if (OPEN) {
                 x[k] = v + (q - sub);  // < 3q
             } else {
@@ -177,7 +254,7 @@ __device__ __forceinline__ void pass_body(const PassParams &P, const NttJob &J, 
                 const u64 c2 = J.c2[sidx], c2sh = J.c2_sh[sidx];
                 const u64 *sp = src + sidx * stride;
 #pragma unroll
-                for (int k = 0; k < E; k++) x[k] += shoup_lazy(sp[gidx(lrow(k))], c2, c2sh, q);
+                for (int k = 0; k < E; k++) x[k] += shoup_lazy(sp[g.gidx(g.lrow(k))], c2, c2sh, q);
             }
         }
         if (!OPEN) {
@@ -193,83 +270,31 @@ __device__ __forceinline__ void pass_body(const PassParams &P, const NttJob &J, 
     } else if (MODE == M_PLAIN) {
         const u64 *src = J.src;
 #pragma unroll
-        for (int k = 0; k < E; k++) x[k] = src[gidx(lrow(k))];
+        for (int k = 0; k < E; k++) x[k] = src[g.gidx(g.lrow(k))];
     } else {  // M_INT64
         const int64_t *src = reinterpret_cast<const int64_t *>(J.src);
 #pragma unroll
         for (int k = 0; k < E; k++) {
-            const int64_t v = src[gidx(lrow(k))];
+            const int64_t v = src[g.gidx(g.lrow(k))];
             x[k] = v >= 0 ? (u64)v % q : q - 1 - ((u64)(-(v + 1)) % q);
         }
     }
 
-    if (IN_STAGE) {
-#pragma unroll
-        for (int k = 0; k < E; k++) sm[smidx(lrow(k))] = x[k];
-        sync();
-#pragma unroll
-        for (int k = 0; k < E; k++) x[k] = sm[smidx(row(0, k))];
-    }
-
-    // 2. butterfly groups; one shared-memory exchange between consecutive groups
-#pragma unroll
-    for (int g = 0; g < NG; g++) {
-        if (g > 0) {
-            sync();  // (g > 1) every thread has read the previous exchange
-#pragma unroll
-            for (int k = 0; k < E; k++) sm[smidx(row(g - 1, k))] = x[k];
-            sync();
-#pragma unroll
-            for (int k = 0; k < E; k++) x[k] = sm[smidx(row(g, k))];
-        }
-        const int blo = G::blo(g), bhi = G::bhi(g), lo = G::lo(g);
-        const int tlow = t & ((1 << lo) - 1);
-        const int thigh = (t >> lo) << (lo + LOGE);
-#pragma unroll
-        for (int st = 0; st < LOGE; st++) {
-            const int b = INV ? blo + st : bhi - st;
-            if (b >= blo && b <= bhi) {
-                const int bb = b - lo;
-#pragma unroll
-                for (int k = 0; k < E; k++) {
-                    if (k & (1 << bb)) continue;
-                    // pairs that agree above bit bb share a twiddle; load it once
-                    if (k & ((1 << bb) - 1)) continue;
-                    const int r0 = tlow | (k << lo) | thigh;
-                    const u64 widx = (u64)(M >> (b + 1)) * o + (u64)(r0 >> (b + 1));
-                    const u64 w = __ldg(tw + widx), wsh = __ldg(twsh + widx);
-#pragma unroll
-                    for (int j = 0; j < E; j++) {
-                        if (j >= (1 << bb)) continue;
-                        if (INV) gs_bfly(x[k + j], x[k + j + (1 << bb)], w, wsh, q, q2);
-                        else if (OPEN) ct_bfly_open(x[k + j], x[k + j + (1 << bb)], w, wsh, q, q2);
-                        else ct_bfly(x[k + j], x[k + j + (1 << bb)], w, wsh, q, q2);
-                    }
-                }
-            }
-        }
-    }
+    // 2. butterfly groups
+    run_stages<LOGM, INV, COL, LOGEV, OPEN>(g, x, sm, tw, twsh, q);
 
     // 3. store straight from the last group's registers; the first pass keeps
     //    lazy values, the second reduces them and fuses the consumer
     u64 *dst = J.dst;
-    if (OUT_STAGE) {
-        sync();
-#pragma unroll
-        for (int k = 0; k < E; k++) sm[smidx(row(NG - 1, k))] = x[k];
-        sync();
-#pragma unroll
-        for (int k = 0; k < E; k++) x[k] = sm[smidx(srow(k))];
-    }
     if (!is_second(MODE)) {
 #pragma unroll
-        for (int k = 0; k < E; k++) dst[gidx(srow(k))] = x[k];
+        for (int k = 0; k < E; k++) dst[g.gidx(g.srow(k))] = x[k];
     } else {
         const u64 *base = J.base, *extra = J.extra;
         const u64 mul = J.mul, mulsh = J.mul_sh, addk = J.conv_sub;
 #pragma unroll
         for (int k = 0; k < E; k++) {
-            const size_t gi = gidx(srow(k));
+            const size_t gi = g.gidx(g.srow(k));
             u64 v = x[k];
             if (MODE == M_SCALED || MODE == M_SCALED_CONV) v = add_mod(shoup(v, mul, mulsh, q), addk, q);
             else if (INV) v = shoup(v, mi.ninv, mi.ninv_sh, q);
@@ -383,7 +408,139 @@ void second_pass(int store_mode, int logm, const PassParams &P, int njobs, cudaS
     }
 }
 
+// x * k * 2^-64 mod q in (0, 2q) for any 64-bit x and k < q (Montgomery
+// reduction with R = 2^64: m = (x k mod R) q^-1 mod R cancels the low word,
+// (x k - m q) / R = hi(x k) - hi(m q) lies in (-q, q)).
+__device__ __forceinline__ u64 mont_lazy(u64 x, u64 k, u64 q, u64 qinv) {
+    const u64 lo = x * k, hi = __umul64hi(x, k);
+    const u64 m = lo * qinv;
+    return (hi + q) - __umul64hi(m, q);
+}
+
+// Shared memory of the fused kernel: the row-pass exchange buffer, then the
+// two accumulators of every thread's E elements, thread-private slots laid out
+// [component][element][thread] (consecutive threads, consecutive words).
+template <int LOGM, int LOGEV>
+struct KsSmem {
+    using GG = Geo<LOGM, false, false, LOGEV>;
+    __host__ __device__ static size_t exch_words(int sub_cta) { return (size_t)sub_cta * (GG::M + GG::M / 16); }
+    __host__ __device__ static size_t bytes(int sub_cta) { return (exch_words(sub_cta) + 2 * (size_t)GG::E * kThreads) * 8; }
+};
+
+template <int LOGM, int LOGEV, bool OPEN>
+__device__ __forceinline__ void keyswitch_up_body(const PassParams &P, const KsJob &J, u64 *sm, const ModInfo &mi) {
+    using GG = Geo<LOGM, false, false, LOGEV>;
+    constexpr int E = GG::E;
+    const GG g(P);
+    const u64 q = mi.q, q2 = 2 * q;
+    const size_t N = (size_t)g.N1 * g.N2;
+    const u64 *tw = P.t.tw + (size_t)J.prime * N;
+    const u64 *twsh = P.t.tw_sh + (size_t)J.prime * N;
+    const int nthr = blockDim.x, tid = threadIdx.x;
+    u64 *acc = sm + KsSmem<LOGM, LOGEV>::exch_words(g.sub_cta);
+    auto slot = [&](int c, int k) -> u64 & { return acc[(c * E + k) * nthr + tid]; };
+    const int nd = (int)J.ndig;
+    for (int d = 0; d < nd; d++) {
+        u64 x[E];
+        const u64 *src = J.src[d];
+        if (d == J.own) {
+#pragma unroll
+            for (int k = 0; k < E; k++) x[k] = shoup_lazy(src[g.gidx(g.srow(k))], mi.r64, mi.r64_sh, q);
+        } else {
+#pragma unroll
+            for (int k = 0; k < E; k++) x[k] = src[g.gidx(g.lrow(k))];
+            run_stages<LOGM, false, false, LOGEV, OPEN>(g, x, sm, tw, twsh, q);
+        }
+        const u64 *k0 = J.key0[d], *k1 = J.key1[d];
+#pragma unroll
+        for (int k = 0; k < E; k++) {
+            const size_t gi = g.gidx(g.srow(k));
+            u64 v0 = mont_lazy(x[k], __ldg(k0 + gi), q, J.qinv);
+            u64 v1 = mont_lazy(x[k], __ldg(k1 + gi), q, J.qinv);
+            if (d > 0) {
+                v0 += slot(0, k);
+                v1 += slot(1, k);
+                v0 = v0 >= q2 ? v0 - q2 : v0;
+                v1 = v1 >= q2 ? v1 - q2 : v1;
+            }
+            slot(0, k) = v0;
+            slot(1, k) = v1;
+        }
+    }
+#pragma unroll
+    for (int k = 0; k < E; k++) {
+        const size_t gi = g.gidx(g.srow(k));
+        u64 v0 = slot(0, k), v1 = slot(1, k);
+        if (J.ex0) {
+            v0 += shoup_lazy(J.ex0[gi], J.pm, J.pm_sh, q);
+            v0 = v0 >= q2 ? v0 - q2 : v0;
+        }
+        if (J.ex1) {
+            v1 += shoup_lazy(J.ex1[gi], J.pm, J.pm_sh, q);
+            v1 = v1 >= q2 ? v1 - q2 : v1;
+        }
+        J.acc0[gi] = v0 >= q ? v0 - q : v0;
+        J.acc1[gi] = v1 >= q ? v1 - q : v1;
+    }
+}
+
+template <int LOGM, int LOGEV>
+__global__ void __launch_bounds__(kThreads, LOGEV >= 4 ? 2 : 4) keyswitch_up_kernel(PassParams P, const KsJob *jobs) {
+    extern __shared__ u64 sm[];
+    __shared__ KsJob J;
+    {
+        const u64 *gj = reinterpret_cast<const u64 *>(jobs + blockIdx.y);
+        u64 *dj = reinterpret_cast<u64 *>(&J);
+        for (int i = threadIdx.x; i < (int)(sizeof(KsJob) / 8); i += blockDim.x) dj[i] = gj[i];
+    }
+    __syncthreads();
+    const ModInfo mi = P.t.mods[J.prime];
+    if (mi.q < kOpenBound) keyswitch_up_body<LOGM, LOGEV, true>(P, J, sm, mi);
+    else keyswitch_up_body<LOGM, LOGEV, false>(P, J, sm, mi);
+}
+
+template <int LOGM, int LOGEV>
+void run_keyswitch_up(const PassParams &P, const KsJob *jobs, int njobs, cudaStream_t st) {
+    using GG = Geo<LOGM, false, false, LOGEV>;
+    const int nsub = 1 << P.log1;
+    const int sub_cta = std::min(kThreads / GG::T, nsub);
+    TREQUIRE(sub_cta * GG::T == kThreads, -1, "fused ModUp pass needs full CTAs");
+    const size_t smem = KsSmem<LOGM, LOGEV>::bytes(sub_cta);
+    static bool opted = false;  // dynamic shared memory above 48 KB needs an opt-in per kernel
+    if (!opted) {
+        TCHECK_CUDA(cudaFuncSetAttribute(keyswitch_up_kernel<LOGM, LOGEV>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)KsSmem<LOGM, LOGEV>::bytes(kThreads / GG::T)));
+        opted = true;
+    }
+    for (int j0 = 0; j0 < njobs; j0 += 65535) {
+        dim3 grid(nsub / sub_cta, std::min(65535, njobs - j0));
+        keyswitch_up_kernel<LOGM, LOGEV><<<grid, sub_cta * GG::T, smem, st>>>(P, jobs + j0);
+    }
+}
+
+template <int LOGEV>
+void keyswitch_up_by_size(int logm, const PassParams &P, const KsJob *jobs, int njobs, cudaStream_t st) {
+    switch (logm) {
+        case 5: run_keyswitch_up<5, LOGEV>(P, jobs, njobs, st); break;
+        case 6: run_keyswitch_up<6, LOGEV>(P, jobs, njobs, st); break;
+        case 7: run_keyswitch_up<7, LOGEV>(P, jobs, njobs, st); break;
+        case 8: run_keyswitch_up<8, LOGEV>(P, jobs, njobs, st); break;
+        default: throw Error(-1, "unsupported NTT pass size");
+    }
+}
+
 }  // namespace
+
+void launch_keyswitch_up(int log_n, const NttTables &t, const KsJob *jobs_dev, int njobs, cudaStream_t s) {
+    if (njobs <= 0) return;
+    PassParams P{};
+    P.t = t;
+    P.log1 = (log_n + 1) / 2;
+    P.log2 = log_n / 2;
+    // the row pass of a forward transform: sub-problems of N2 points, N1 of them
+    if (t.loge == 4) keyswitch_up_by_size<4>(P.log2, P, jobs_dev, njobs, s);
+    else keyswitch_up_by_size<3>(P.log2, P, jobs_dev, njobs, s);
+}
 
 void launch_ntt(bool inverse, int log_n, const NttTables &t, const NttJob *jobs_dev, int njobs, int load_mode,
                 int store_mode, cudaStream_t s, int pass) {

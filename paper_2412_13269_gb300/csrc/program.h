@@ -129,9 +129,9 @@ struct Program {
 // A launch recorded but not yet emitted (batch schedules merge these): the
 // kernel, its parameters and its job table.
 struct Deferred {
-    int type = 0;  // 0 NTT (both passes), 1 elementwise, 2 automorphism, 3 key inner product, 4 lincomb, 5 reduce
+    int type = 0;  // 0 NTT, 1 elementwise, 2 automorphism, 3 ModUp row pass + key inner product, 4 lincomb, 5 reduce
     bool inverse = false;
-    int load_mode = 0, store_mode = 0;
+    int load_mode = 0, store_mode = 0, passes = 3;
     uint32_t galois = 0;
     size_t job_size = 0;
     std::vector<uint8_t> jobs;
@@ -139,7 +139,7 @@ struct Deferred {
     double bytes = 0;
     std::string merge_key() const {
         return std::to_string(type) + ":" + std::to_string(inverse) + ":" + std::to_string(load_mode) + ":" +
-               std::to_string(store_mode) + ":" + std::to_string(galois) + ":" + kind;
+               std::to_string(store_mode) + ":" + std::to_string(passes) + ":" + std::to_string(galois) + ":" + kind;
     }
 };
 
@@ -159,11 +159,12 @@ class Rec {
 
     // split >= 0: the second pass stores jobs[0, split) with store_mode, then
     // jobs[split, n) with store_mode_b (a later launch, so it may read the former)
+    // passes: 1 = first pass only, 2 = second only, 3 = both
     void ntt(bool inverse, const std::vector<NttJob> &jobs, int load_mode, int store_mode, int split = -1,
-             int store_mode_b = STORE_PLAIN);
+             int store_mode_b = STORE_PLAIN, int passes = 3);
     void ew(const std::vector<EwJob> &jobs);
     void aut(const std::vector<AutJob> &jobs, uint32_t g);
-    void kip(const std::vector<KipJob> &jobs);
+    void ksup(const std::vector<KsJob> &jobs);
     void lin(const std::vector<LinJob> &jobs);
     void red(const std::vector<RedJob> &jobs);
 
