@@ -217,6 +217,7 @@ const char *ew_name(int op) {
         case EW_FMA: return "fma";
         case EW_TENSOR: return "tensor";
         case EW_TENSOR_ACC: return "tensor_acc";
+        case EW_RESCALE_COEF: return "rescale_coef";
         case EW_ADD_MUL_CONST: return "addmulc";
         case EW_REDUCE: return "reduce";
     }
@@ -1059,6 +1060,57 @@ CtH Rec::sum_batch(const CtH &a) {
 // Move to level lt with the standard scale S[lt], applying a public factor:
 // keep q_0..q_{lt+1}, multiply by floor(factor * S[lt] * q_{lt+1} / scale + 1/2), rescale.
 CtH Rec::adjust(const CtH &a, int lt, double factor) { return adjust_many({{a, lt, factor}})[0]; }
+
+// adjust_many on coefficient-domain ciphertexts, where the rescale is a per
+// coefficient operation (the formula of rescale() with no transform); results
+// stay in the coefficient domain.  Items already at their level are returned as they are.
+std::vector<CtH> Rec::adjust_many_coef(const std::vector<AdjustItem> &items) {
+    std::vector<CtH> outs(items.size());
+    std::vector<EwJob> jobs;
+    for (size_t n = 0; n < items.size(); n++) {
+        const CtH &a = items[n].ct;
+        const int lt = items[n].level;
+        const double factor = items[n].factor;
+        if (a.level == lt) {
+            TREQUIRE(factor == 1.0 && a.scale == C.S[lt], TETRIS_EINVAL, "adjust at the same level");
+            outs[n] = a;
+            continue;
+        }
+        TREQUIRE(a.level > lt, TETRIS_ELEVEL, "input ciphertext level too low");
+        const int64_t f = round_half_up(((factor * C.S[lt]) * (double)C.q[lt + 1]) / a.scale);
+        const int l = lt + 1;
+        const u64 ql = C.q[l], half = (ql - 1) / 2;
+        CtH o = new_ct(a.B, a.comps, lt);
+        o.scale = C.S[lt];
+        for (int i = 0; i < l; i++) {
+            const u64 qi = C.q[i];
+            EwJob proto{};
+            proto.op = EW_RESCALE_COEF;
+            proto.prime = i;
+            proto.prime2 = l;
+            proto.k = signed_mod(f, qi);
+            proto.k_sh = h_shoup(proto.k, qi);
+            proto.k2 = signed_mod(f, ql);
+            proto.k2_sh = h_shoup(proto.k2, ql);
+            proto.k3 = h_invmod(ql % qi, qi);
+            proto.k3_sh = h_shoup(proto.k3, qi);
+            proto.k4 = half;
+            proto.k5 = half % qi;
+            for (int b = 0; b < a.B; b++)
+                for (int c = 0; c < a.comps; c++) {
+                    EwJob j = proto;
+                    j.a = a.limb(b, c, i);
+                    j.b = a.limb(b, c, l);
+                    j.dst = o.limb(b, c, i);
+                    jobs.push_back(j);
+                }
+        }
+        outs[n] = o;
+        P.rescales++;
+    }
+    ew(jobs);
+    return outs;
+}
 
 // Independent adjusts recorded as one rescale_many.
 std::vector<CtH> Rec::adjust_many(const std::vector<AdjustItem> &items) {

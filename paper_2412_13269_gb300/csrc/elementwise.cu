@@ -128,6 +128,21 @@ __global__ void __launch_bounds__(kEwThreads) ew_kernel(const EwJob *jobs, int n
                 *reinterpret_cast<ulonglong2 *>(J.d2 + p) = d2;
                 continue;
             }
+            case EW_RESCALE_COEF: {
+                // t = [k2 b + k4]_{q2} (b < q2), then (k a - [t]_q + k5) * k3 modulo q
+                const ModInfo m2 = mods[J.prime2];
+                ulonglong2 a = *reinterpret_cast<const ulonglong2 *>(J.a + p);
+                ulonglong2 b = *reinterpret_cast<const ulonglong2 *>(J.b + p);
+                u64 t0 = add_mod(shoup(b.x, J.k2, J.k2_sh, m2.q), J.k4, m2.q);
+                u64 t1 = add_mod(shoup(b.y, J.k2, J.k2_sh, m2.q), J.k4, m2.q);
+                t0 = t0 - __umul64hi(t0, m.one_sh) * q;
+                t1 = t1 - __umul64hi(t1, m.one_sh) * q;
+                t0 = t0 >= q ? t0 - q : t0;
+                t1 = t1 >= q ? t1 - q : t1;
+                r[0] = shoup(add_mod(sub_mod(shoup(a.x, J.k, J.k_sh, q), t0, q), J.k5, q), J.k3, J.k3_sh, q);
+                r[1] = shoup(add_mod(sub_mod(shoup(a.y, J.k, J.k_sh, q), t1, q), J.k5, q), J.k3, J.k3_sh, q);
+                break;
+            }
             default:
                 r[0] = r[1] = 0;
         }

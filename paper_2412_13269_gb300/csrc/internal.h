@@ -134,7 +134,9 @@ enum EwOp {
     EW_TENSOR = 8,    // a0,a1,b0,b1 -> d0,d1,d2 (pointers a,b,c,d with strides)
     EW_ADD_MUL_CONST = 9, // dst = b + k * a  (used by key generation)
     EW_REDUCE = 10,       // dst = a mod q for any 64-bit a
-    EW_TENSOR_ACC = 11    // tensor of (a, a1) and (b, b1) plus the degree-2 ciphertext (c, c1, c2)
+    EW_TENSOR_ACC = 11,   // tensor of (a, a1) and (b, b1) plus the degree-2 ciphertext (c, c1, c2)
+    EW_RESCALE_COEF = 12  // coefficient domain: dst = (k a - [[k2 b + k4]_{q2}]_q + k5) * k3, b the top
+                          // limb modulo q2 = prime2 (rescale of k * ciphertext by q2)
 };
 struct EwJob {
     const u64 *a, *b, *c;
@@ -147,6 +149,9 @@ struct EwJob {
     u64 *d1, *d2;
     // tensor with accumulation: components 1 and 2 of the added ciphertext (c is component 0)
     const u64 *c1, *c2;
+    // coefficient-domain rescale: second prime and constants
+    u64 k2, k2_sh, k3, k3_sh, k4, k5;
+    uint32_t prime2, pad2;
 };
 void launch_ew(const EwJob *jobs_dev, int njobs, int log_n, const ModInfo *mods, cudaStream_t s);
 

@@ -197,6 +197,7 @@ class Rec {
         double factor;
     };
     std::vector<CtH> adjust_many(const std::vector<AdjustItem> &items);
+    std::vector<CtH> adjust_many_coef(const std::vector<AdjustItem> &items);  // coefficient domain in and out
     CtH mul(const CtH &a, const CtH &b);
 
   private:

@@ -245,30 +245,32 @@ std::unique_ptr<Program> record_query(Ctx &C, const Database &db, const QuerySpe
     tin.scale = q.t_scale;
     P->hold.push_back(tin.buf);
     P->in_slots.push_back({tin.base, tin.bstride});
-    {
-        std::vector<NttJob> jobs;
-        auto add_limbs = [&](u64 *base, int level) {
-            for (int c = 0; c < 2; c++)
-                for (int i = 0; i <= level; i++) {
-                    NttJob j{};
-                    j.src = j.dst = base + ((size_t)c * (level + 1) + i) * N;
-                    j.prime = i;
-                    jobs.push_back(j);
-                }
-        };
-        for (int j = 0; j < q.attrs; j++) add_limbs(wbuf->ptr + j * wwords, L);
-        for (auto &c : cin) add_limbs(c.base, c.level);
-        add_limbs(tin.base, tin.level);
-        R.ntt(false, jobs, LOAD_PLAIN, STORE_PLAIN);
-    }
-    // per-query: coefficients and threshold moved to their levels
-    // one pair of transforms for all of them
+    // per-query: the coefficients and the threshold move to their levels while
+    // still in the coefficient domain (a rescale is per coefficient there), so
+    // only their remaining limbs are transformed, together with the w_j
     std::vector<Rec::AdjustItem> items;
     for (int k = 0; k <= q.degree; k++) items.push_back({cin[k], pl.coef_level(k), 1.0});
     items.push_back({tin, pl.l_y, 1.0});
-    std::vector<CtH> ck = R.adjust_many(items);
+    std::vector<CtH> ck = R.adjust_many_coef(items);
     CtH tadj = ck.back();
     ck.pop_back();
+    {
+        std::vector<NttJob> jobs;
+        auto add_limbs = [&](const CtH &c) {
+            for (int b = 0; b < c.B; b++)
+                for (int k = 0; k < c.comps; k++)
+                    for (int i = 0; i <= c.level; i++) {
+                        NttJob j{};
+                        j.src = j.dst = c.limb(b, k, i);
+                        j.prime = i;
+                        jobs.push_back(j);
+                    }
+        };
+        for (int j = 0; j < q.attrs; j++) add_limbs(R.view(wbuf, wbuf->ptr + j * wwords, 1, 2, L, wwords, (L + 1) * N, 0));
+        for (auto &c : ck) add_limbs(c);
+        add_limbs(tadj);
+        R.ntt(false, jobs, LOAD_PLAIN, STORE_PLAIN);
+    }
     // block groups
     const int B = db.blocks;
     const int bpl = q.bpl <= 0 ? B : std::min(q.bpl, B);
