@@ -27,14 +27,19 @@ int grid_for(size_t work_items) {
     return (int)std::max<size_t>(1, std::min(want, cap));
 }
 
-// one thread handles two consecutive positions (a 16-byte pair)
-__global__ void __launch_bounds__(kEwThreads) ew_kernel(const EwJob *jobs, int njobs, int log_n, const ModInfo *mods) {
-    const size_t half = (size_t)1 << (log_n - 1);
-    const size_t total = half * njobs;
-    for (size_t it = blockIdx.x * (size_t)blockDim.x + threadIdx.x; it < total; it += (size_t)gridDim.x * blockDim.x) {
-        const int j = (int)(it >> (log_n - 1));
-        const size_t p = (it & (half - 1)) * 2;
-        const EwJob &J = jobs[j];
+// One CTA per (job, chunk of 2 * kEwThreads positions): the descriptor is
+// staged in shared memory once and each thread handles one 16-byte pair.
+__global__ void __launch_bounds__(kEwThreads) ew_kernel(const EwJob *jobs, int log_n, const ModInfo *mods) {
+    __shared__ EwJob J;
+    {
+        const u64 *gj = reinterpret_cast<const u64 *>(jobs + blockIdx.y);
+        u64 *dj = reinterpret_cast<u64 *>(&J);
+        for (int i = threadIdx.x; i < (int)(sizeof(EwJob) / 8); i += blockDim.x) dj[i] = gj[i];
+    }
+    __syncthreads();
+    const size_t p = ((size_t)blockIdx.x * kEwThreads + threadIdx.x) * 2;
+    if (p >= ((size_t)1 << log_n)) return;
+    {
         const ModInfo m = mods[J.prime];
         const u64 q = m.q;
         u64 r[2];
@@ -126,7 +131,7 @@ __global__ void __launch_bounds__(kEwThreads) ew_kernel(const EwJob *jobs, int n
                 *reinterpret_cast<ulonglong2 *>(J.dst + p) = d0;
                 *reinterpret_cast<ulonglong2 *>(J.d1 + p) = d1;
                 *reinterpret_cast<ulonglong2 *>(J.d2 + p) = d2;
-                continue;
+                return;
             }
             case EW_RESCALE_COEF: {
                 // t = [k2 b + k4]_{q2} (b < q2), then (k a - [t]_q + k5) * k3 modulo q
@@ -253,7 +258,12 @@ double modmul_peak_probe() {
 
 void launch_ew(const EwJob *jobs, int njobs, int log_n, const ModInfo *mods, cudaStream_t s) {
     if (njobs <= 0) return;
-    ew_kernel<<<grid_for(((size_t)njobs << log_n) / 2), kEwThreads, 0, s>>>(jobs, njobs, log_n, mods);
+    const size_t per_cta = 2 * (size_t)kEwThreads;
+    const unsigned chunks = (unsigned)((((size_t)1 << log_n) + per_cta - 1) / per_cta);
+    for (int j0 = 0; j0 < njobs; j0 += 65535) {
+        dim3 grid(chunks, (unsigned)std::min(65535, njobs - j0));
+        ew_kernel<<<grid, kEwThreads, 0, s>>>(jobs + j0, log_n, mods);
+    }
 }
 void launch_automorphism(const AutJob *jobs, int njobs, int log_n, uint32_t galois, cudaStream_t s) {
     if (njobs <= 0) return;
