@@ -192,7 +192,7 @@ def oracle_sample(rank: int, nblocks_full: int, seed_offset: int = 0):
     t1 = time.perf_counter()
     u = ev.block(db.pts[0], eq, ck, tadj, WL["degree"])
     t2 = time.perf_counter()
-    ev.innersum(u)
+    ev.innersum(ckks.drop_to(u, plan.l_ret))
     t3 = time.perf_counter()
     total = (t1 - t0) + nblocks_full * (t2 - t1) + (t3 - t2)
     threads = int(rns.lib().or_num_threads())
@@ -633,7 +633,7 @@ def main():
         "cpu_baseline": cpu, "clocks": clk,
         "gpu_launches": info.kernel_launches * args.steps,
         "plan": {"relins": info.relins, "rescales": info.rescales, "rotations": info.rotations,
-                 "launches_per_query": info.kernel_launches, "l_out": info.l_out},
+                 "launches_per_query": info.kernel_launches, "l_out": info.l_out, "l_ret": info.l_ret},
     }
     if rank == 0:
         print(json.dumps(line), flush=True)

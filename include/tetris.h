@@ -197,10 +197,12 @@ int tetris_evaluate_query_device(tetris_ctx *ctx, uint32_t db, const tetris_quer
 int tetris_reduce_sum_device(tetris_ctx *ctx, uint64_t *data, uint32_t level, uint32_t ncomp, void *stream);
 
 typedef struct {
-    int32_t l_lin, l_d, l_y, l_u, l_out;
+    int32_t l_lin, l_d, l_y, l_u, l_out; /* l_out: level of the summed step values (scale S[l_out]) */
     uint32_t ragged;
     uint32_t relins, rescales, rotations, kernel_launches;
     double pt_scale, mask_scale;
+    int32_t l_ret; /* level of the returned ciphertext: InnerSum runs after dropping to it */
+    uint32_t pad;
 } tetris_plan_info;
 /* Levels and operation counts of the plan for a query shape on a database. */
 int tetris_plan(tetris_ctx *ctx, uint32_t db, uint32_t f_degree, uint32_t sign_stages,

@@ -131,7 +131,7 @@ class Plan:
     l_d: int            # level at which the c_k x^k products are formed (plain powers)
     l_y: int            # level of y = f(x) and z = y - t
     l_u: int            # level after the sign stages and step affine
-    l_out: int          # level of the returned ciphertext
+    l_out: int          # level of the summed step values (scale S[l_out])
     pt_scale: float     # scale of the database plaintexts
     mask_scale: float   # scale of the ragged-block mask plaintext (0 if none)
     ragged: bool
@@ -139,6 +139,11 @@ class Plan:
     step_const: float = 0.0
     bsgs: tuple | None = None   # poly_schedule(degree): (g, m, bb, D_f) or None
     degree: int = 0
+    # level of the returned ciphertext: the sum is dropped to it before InnerSum
+    # (a reading: the paper does not fix where the rotations run; at level 1
+    # their key switches cover two primes, and |value| <= S[l_out] stays far
+    # inside q_0 q_1)
+    l_ret: int = 1
 
     def coef_level(self, k: int) -> int:
         """Level at which the encrypted coefficient c_k is used."""
@@ -450,6 +455,8 @@ def evaluate_query(par: Params, keys: Keys, shape: QueryShape, db: EncodedDB, q:
         acc = m if full is None else ckks.add(par, ev.adjust(full, plan.l_out), m)
     else:
         acc = full
+    if acc.level > plan.l_ret:
+        acc = ckks.drop_to(acc, plan.l_ret)
     return ev.innersum(acc)
 
 

@@ -64,7 +64,7 @@ class PlanInfo(C.Structure):
     _fields_ = [("l_lin", C.c_int32), ("l_d", C.c_int32), ("l_y", C.c_int32), ("l_u", C.c_int32),
                 ("l_out", C.c_int32), ("ragged", C.c_uint32), ("relins", C.c_uint32), ("rescales", C.c_uint32),
                 ("rotations", C.c_uint32), ("kernel_launches", C.c_uint32), ("pt_scale", C.c_double),
-                ("mask_scale", C.c_double)]
+                ("mask_scale", C.c_double), ("l_ret", C.c_int32), ("pad", C.c_uint32)]
 
 
 class ServeStats(C.Structure):

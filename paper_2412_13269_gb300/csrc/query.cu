@@ -22,6 +22,7 @@ namespace tetris {
 
 struct QPlan {
     int l_lin, l_d, l_y, l_u, l_out;
+    int l_ret = 1;  // the InnerSum and the returned ciphertext: drop to level 1 first
     bool ragged;
     double mask_scale;
     std::vector<std::array<double, 4>> co;
@@ -315,7 +316,11 @@ std::unique_ptr<Program> record_query(Ctx &C, const Database &db, const QuerySpe
     } else {
         acc = full;
     }
-    // InnerSum: acc += Rot_{2^k}(acc)
+    // InnerSum: acc += Rot_{2^k}(acc), after dropping to level l_ret (the
+    // rotations' key switches then work on two primes; the value, below
+    // S[l_out] in magnitude, is far inside q_0 q_1)
+    const double acc_scale = acc.scale;
+    acc = R.drop(acc, std::min(acc.level, pl.l_ret));
     for (int k = 0; k + 1 < C.log_n; k++) {
         const uint32_t g = (uint32_t)h_powmod(5, 1ull << k, 2 * C.N);
         acc = R.add(acc, R.rotate(acc, g));
@@ -326,7 +331,7 @@ std::unique_ptr<Program> record_query(Ctx &C, const Database &db, const QuerySpe
     P->out_words = o.bstride;
     P->out_level = acc.level;
     P->out_comps = 2;
-    P->out_scale = C.S[acc.level];
+    P->out_scale = acc_scale;
     P->finalize();
     return P;
 }
@@ -511,6 +516,7 @@ void plan_info(Ctx &C, uint32_t dbh, uint32_t degree, uint32_t stages, tetris_pl
     out->l_y = pl.l_y;
     out->l_u = pl.l_u;
     out->l_out = pl.l_out;
+    out->l_ret = pl.l_ret;
     out->ragged = pl.ragged;
     out->relins = P.relins;
     out->rescales = P.rescales;

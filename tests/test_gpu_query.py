@@ -77,7 +77,7 @@ def test_query_bit_exact(chain, records, attrs, degree, nst):
         ctx.set_option(T.OPT_BLOCKS_PER_LAUNCH, bpl)
         ctx.set_option(T.OPT_USE_GRAPH, graph)
         got, lev, sc = gpu_query(ctx, dbh, eq, stages)
-        assert lev == want.level == plan.l_out
+        assert lev == want.level == plan.l_ret
         assert np.array_equal(got, want.data), (bpl, graph)
         assert sc == plan.S[plan.l_out]
     ctx.set_option(T.OPT_BLOCKS_PER_LAUNCH, 0)
@@ -166,6 +166,7 @@ def test_plan_counts(chain):
     info = ctx.plan(dbh, 7, 1)
     p = query.make_plan(par, query.QueryShape(2048, 8, 7, [query.F3]))
     assert (info.l_lin, info.l_d, info.l_y, info.l_u, info.l_out) == (p.l_lin, p.l_d, p.l_y, p.l_u, p.l_out)
+    assert info.l_ret == p.l_ret == 1
     assert info.rotations == par.log_n - 1 and info.relins > 0 and info.kernel_launches > 0
     assert info.pt_scale == p.pt_scale
     ctx.free_database(dbh)

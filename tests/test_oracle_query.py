@@ -24,7 +24,7 @@ def run(par, vals, qv, stages, seed=1, alpha=1):
     db = query.encode_database(par, plan, vals)
     eq = query.encrypt_query(par, s, qv, seed)
     out = query.evaluate_query(par, keys, shape, db, eq)
-    assert out.level == plan.l_out
+    assert out.level == plan.l_ret == 1
     return ckks.decrypt_slots(par, out, s).real, plan
 
 
