@@ -164,7 +164,8 @@ int tetris_encode_real(tetris_ctx *ctx, const double *slots, uint32_t n_values, 
  * one, each at any level at or above where it is used (the library moves it
  * down).  Keys needed: relinearisation and rotations by 5^(2^k) mod 2N,
  * k < log_n - 1.  The result, at the level reported in out, decrypts to
- * count / records in every slot.
+ * count / records in every slot (or, with a global threshold, to the bit
+ * [count >= t1]).
  * ------------------------------------------------------------------------- */
 typedef struct {
     uint32_t n_attrs;
@@ -180,6 +181,16 @@ typedef struct {
                                  when a database is split across GPUs or owners (the
                                  horizontally partitioned database of Section 4.4): the
                                  partitions' results then add up residue-wise */
+    /* Optional global threshold (Algorithm 2, last line), NULL for none: the
+     * result becomes step((count - t1 + 1/2) / records) in every slot, i.e. 1 iff
+     * at least t1 records pass (the 1/2 is Section 4.3.2's epsilon/2 shift for
+     * integer counts).  global_threshold encrypts t1 as a count (not normalised),
+     * at a level above the step values'; global_stages odd degree-7 stages,
+     * global_coeffs their coefficients of x, x^3, x^5, x^7.  Needs
+     * 3 global_stages levels below the step values' level. */
+    const tetris_ct_in *global_threshold;
+    uint32_t global_stages;
+    const double *global_coeffs;
 } tetris_query;
 
 /* Host buffers in and out; blocks until the result is in out. */

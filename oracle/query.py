@@ -75,6 +75,7 @@ class QueryShape:
     sign_stages: list            # list of (a0, a1, a2, a3) for x, x^3, x^5, x^7
     norm_records: int = 0        # records the count is normalised by (0: this database's own);
                                  # the total over partitions for a horizontally split database (Section 4.4)
+    global_stages: list = field(default_factory=list)   # stages of the global threshold (empty: none)
 
     def blocks(self, n_slots: int) -> int:
         return -(-self.records // n_slots)
@@ -144,6 +145,12 @@ class Plan:
     # their key switches cover two primes, and |value| <= S[l_out] stays far
     # inside q_0 q_1)
     l_ret: int = 1
+    # global threshold (Algorithm 2, last line): step((count - t1 + 1/2) / R) on
+    # the InnerSum result at l_out; the 1/2 is the epsilon/2 shift of Section
+    # 4.3.2 for integer counts (so the bit is count >= t1); the last stage's
+    # coefficients carry the 1/2 of step = (p + 1)/2
+    global_coeffs: list = field(default_factory=list)
+    records_norm: float = 0.0
 
     def coef_level(self, k: int) -> int:
         """Level at which the encrypted coefficient c_k is used."""
@@ -187,7 +194,19 @@ def make_plan(par: Params, shape: QueryShape) -> Plan:
         if s == ns - 1:   # step = (p + 1) / 2, normalised by 1/records
             co = [c / (2.0 * R) for c in co]
         stages.append(co)
-    return Plan(S=S, l_lin=l_lin, l_d=l_d, l_y=l_y, l_u=l_u, l_out=l_out,
+    gco = []
+    for s, co in enumerate(shape.global_stages):
+        co = [float(c) for c in co]
+        if len(co) != 4:
+            raise ValueError("sign stages are odd degree-7 polynomials")
+        if s == len(shape.global_stages) - 1:
+            co = [c / 2.0 for c in co]
+        gco.append(co)
+    l_ret = l_out - 3 * len(gco) if gco else 1
+    if l_ret < 1:
+        raise ValueError(f"global threshold needs more levels: ends at level {l_ret}")
+    return Plan(S=S, l_lin=l_lin, l_d=l_d, l_y=l_y, l_u=l_u, l_out=l_out, l_ret=l_ret, global_coeffs=gco,
+                records_norm=R,
                 pt_scale=(S[L - 1] * float(par.q[L])) / S[L],
                 mask_scale=((S[l_u - 1] * float(par.q[l_u])) / S[l_u]) if ragged else 0.0,
                 ragged=ragged, stage_coeffs=stages, step_const=1.0 / (2.0 * R),
@@ -276,12 +295,14 @@ class EncQuery:
     w: list
     c: list
     t: Ct
+    t1: Ct | None = None
 
 
 def encrypt_query(par: Params, s: np.ndarray, qv: synth.QueryValues, seed: int) -> EncQuery:
     return EncQuery(w=[encrypt_value(par, s, float(v), seed, f"w{j}") for j, v in enumerate(qv.w)],
                     c=[encrypt_value(par, s, float(v), seed, f"c{k}") for k, v in enumerate(qv.c)],
-                    t=encrypt_value(par, s, float(qv.t), seed, "t"))
+                    t=encrypt_value(par, s, float(qv.t), seed, "t"),
+                    t1=None if qv.t1 is None else encrypt_value(par, s, float(qv.t1), seed, "t1"))
 
 
 # ---------------------------------------------------------------------------
@@ -428,6 +449,17 @@ class Evaluator:
             u = self.sign_stage(u, co)
         return ckks.add_int_const(par, u, round_half_up(p.step_const * p.S[u.level]))
 
+    def global_threshold(self, v: Ct, t1: Ct) -> Ct:
+        """step((count - t1 + 1/2) / R) from v = count / R (Algorithm 2, last line)."""
+        par, p = self.par, self.plan
+        if t1 is None:
+            raise ValueError("the global threshold needs an encrypted t1")
+        z = ckks.sub(par, v, self.adjust(t1, v.level, 1.0 / p.records_norm))
+        z = ckks.add_int_const(par, z, round_half_up(p.S[z.level] / (2.0 * p.records_norm)))
+        for co in p.global_coeffs:
+            z = self.sign_stage(z, co)
+        return ckks.add_int_const(par, z, round_half_up(0.5 * p.S[z.level]))
+
     def innersum(self, acc: Ct) -> Ct:
         for g in innersum_galois(self.par):
             acc = ckks.add(self.par, acc, ckks.rotate(self.par, acc, g, self.keys.rot[g], self.keys.alpha))
@@ -455,6 +487,8 @@ def evaluate_query(par: Params, keys: Keys, shape: QueryShape, db: EncodedDB, q:
         acc = m if full is None else ckks.add(par, ev.adjust(full, plan.l_out), m)
     else:
         acc = full
+    if plan.global_coeffs:
+        return ev.global_threshold(ev.innersum(acc), q.t1)
     if acc.level > plan.l_ret:
         acc = ckks.drop_to(acc, plan.l_ret)
     return ev.innersum(acc)
@@ -471,12 +505,21 @@ class Fp64Result:
     u: np.ndarray        # per-record step approximation
     count: float         # sum of u
     exact: int           # number of records with z > 0
+    z2: float = 0.0      # global threshold input (count - t1 + 1/2) / R
+    bit: float = 0.0     # its step approximation
+    exact_bit: int = 0   # 1 iff exact >= t1
 
 
-def fp64_pipeline(vals_u8: np.ndarray, qv: synth.QueryValues, stages) -> Fp64Result:
+def fp64_pipeline(vals_u8: np.ndarray, qv: synth.QueryValues, stages, global_stages=(), records=0) -> Fp64Result:
     h = vals_u8.shape[1]
     x = (normalise(vals_u8) / h) @ np.asarray(qv.w, dtype=np.float64)
     y = sum(c * x ** k for k, c in enumerate(qv.c))
     z = (y - qv.t) / 2.0
     u = (composite_sign(stages, z) + 1.0) / 2.0
-    return Fp64Result(x=x, y=y, z=z, u=u, count=float(u.sum()), exact=int((z > 0).sum()))
+    r = Fp64Result(x=x, y=y, z=z, u=u, count=float(u.sum()), exact=int((z > 0).sum()))
+    if global_stages:
+        R = float(records or vals_u8.shape[0])
+        r.z2 = (r.count - qv.t1 + 0.5) / R
+        r.bit = float((composite_sign(global_stages, np.array([r.z2]))[0] + 1.0) / 2.0)
+        r.exact_bit = int(r.exact >= qv.t1)
+    return r

@@ -52,7 +52,9 @@ class CtOut(C.Structure):
 class Query(C.Structure):
     _fields_ = [("n_attrs", C.c_uint32), ("w", C.POINTER(CtIn)), ("f_degree", C.c_uint32),
                 ("f_coeffs", C.POINTER(CtIn)), ("threshold", C.POINTER(CtIn)), ("sign_stages", C.c_uint32),
-                ("sign_degree", C.c_uint32), ("sign_coeffs", C.POINTER(C.c_double)), ("total_records", C.c_uint64)]
+                ("sign_degree", C.c_uint32), ("sign_coeffs", C.POINTER(C.c_double)), ("total_records", C.c_uint64),
+                ("global_threshold", C.POINTER(CtIn)), ("global_stages", C.c_uint32),
+                ("global_coeffs", C.POINTER(C.c_double))]
 
 
 class CtxInfo(C.Structure):
@@ -338,19 +340,31 @@ class Ctx:
         return p
 
     # query
-    def _query_struct(self, w, w_meta, c, c_meta, t, t_meta, sign_coeffs, total_records=0):
+    def _query_struct(self, w, w_meta, c, c_meta, t, t_meta, sign_coeffs, total_records=0, glob=None):
+        """glob: optional global threshold (t1 ciphertext, (level, scale), stage coefficients)."""
         W = (CtIn * len(w))(*[CtIn(lv, 2, sc, _ptr(x)) for x, (lv, sc) in zip(w, w_meta)])
         Cc = (CtIn * len(c))(*[CtIn(lv, 2, sc, _ptr(x)) for x, (lv, sc) in zip(c, c_meta)])
         T = CtIn(t_meta[0], 2, t_meta[1], _ptr(t))
         sc = np.ascontiguousarray(np.asarray(sign_coeffs, dtype=np.float64).reshape(-1))
         q = Query(len(w), W, len(c) - 1, Cc, C.pointer(T), sc.size // 4, 7,
                   sc.ctypes.data_as(C.POINTER(C.c_double)), int(total_records))
-        return q, (W, Cc, T, sc)
+        keep = [W, Cc, T, sc]
+        if glob is not None:
+            t1, (lv, scl), gco = glob
+            T1 = CtIn(lv, 2, scl, _ptr(t1))
+            g = np.ascontiguousarray(np.asarray(gco, dtype=np.float64).reshape(-1))
+            q.global_threshold = C.pointer(T1)
+            q.global_stages = g.size // 4
+            q.global_coeffs = g.ctypes.data_as(C.POINTER(C.c_double))
+            keep += [T1, g]
+        return q, keep
 
-    def evaluate_query(self, db: int, w, w_meta, c, c_meta, t, t_meta, sign_coeffs, out=None, total_records=0):
-        """Host arrays: w/c/t are [2][level+1][N] uint64; metas are (level, scale).
-        Returns (out array, level, scale)."""
-        q, keep = self._query_struct(w, w_meta, c, c_meta, t, t_meta, sign_coeffs, total_records)
+    def evaluate_query(self, db: int, w, w_meta, c, c_meta, t, t_meta, sign_coeffs, out=None, total_records=0,
+                       glob=None):
+        """Host arrays: w/c/t are [2][level+1][N] uint64; metas are (level, scale);
+        glob = (t1, (level, scale), global stage coefficients) adds the global
+        threshold.  Returns (out array, level, scale)."""
+        q, keep = self._query_struct(w, w_meta, c, c_meta, t, t_meta, sign_coeffs, total_records, glob)
         if out is None:
             out = np.empty(2 * (self.L + 1) * self.N, dtype=np.uint64)
         o = CtOut(0, 0, 0.0, _ptr(out), out.size if isinstance(out, np.ndarray) else out.numel())
@@ -359,9 +373,9 @@ class Ctx:
         return out[:n].reshape(2, o.level + 1, self.N), o.level, o.scale
 
     def evaluate_query_device(self, db: int, w, w_meta, c, c_meta, t, t_meta, sign_coeffs, out, stream: int,
-                              total_records=0):
+                              total_records=0, glob=None):
         """torch CUDA tensors in and out; enqueued on ``stream`` (a cudaStream_t as int)."""
-        q, keep = self._query_struct(w, w_meta, c, c_meta, t, t_meta, sign_coeffs, total_records)
+        q, keep = self._query_struct(w, w_meta, c, c_meta, t, t_meta, sign_coeffs, total_records, glob)
         o = CtOut(0, 0, 0.0, _ptr(out), out.numel())
         check(lib().tetris_evaluate_query_device(self.h, db, C.byref(q), C.byref(o), stream))
         return o.level, o.scale
@@ -370,8 +384,8 @@ class Ctx:
     def serve_start(self, budget_bytes: int, max_inflight: int):
         check(lib().tetris_serve_start(self.h, budget_bytes, max_inflight))
 
-    def submit(self, db: int, w, w_meta, c, c_meta, t, t_meta, sign_coeffs) -> int:
-        q, keep = self._query_struct(w, w_meta, c, c_meta, t, t_meta, sign_coeffs)
+    def submit(self, db: int, w, w_meta, c, c_meta, t, t_meta, sign_coeffs, glob=None) -> int:
+        q, keep = self._query_struct(w, w_meta, c, c_meta, t, t_meta, sign_coeffs, 0, glob)
         tk = C.c_uint64()
         check(lib().tetris_submit(self.h, db, C.byref(q), C.byref(tk)))
         return tk.value

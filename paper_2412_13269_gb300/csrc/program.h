@@ -218,6 +218,10 @@ struct QuerySpec {
     int bpl = 0;
     int loge = 3;                // NTT register-group width (log2 elements per thread)
     uint64_t total_records = 0;  // 0: the database's own record count
+    // global threshold (none when gstages is empty): t1's level and scale
+    int g_level = 0;
+    double g_scale = 0;
+    std::vector<std::array<double, 4>> gstages;
     std::string key(uint32_t db) const {
         std::ostringstream o;
         o << "q" << db << ":" << attrs << ":" << degree << ":" << bpl << ":" << loge << ":" << t_level << ":"
@@ -234,6 +238,12 @@ struct QuerySpec {
         }
         for (auto &s : stages)
             for (double v : s) bits(v);
+        if (!gstages.empty()) {
+            o << "g" << g_level << ":";
+            bits(g_scale);
+            for (auto &s : gstages)
+                for (double v : s) bits(v);
+        }
         return o.str();
     }
 };
@@ -241,6 +251,7 @@ struct QuerySpec {
 // query.cu
 std::unique_ptr<Program> record_query(Ctx &C, const Database &db, const QuerySpec &q);
 QuerySpec spec_of(const Ctx &C, const Database &db, const tetris_query *q);
+std::vector<const tetris_ct_in *> query_inputs(const tetris_query *q);  // in input-slot order
 void evaluate_query(Ctx &C, uint32_t db, const tetris_query *q, tetris_ct_out *out, cudaStream_t s, bool device);
 void plan_info(Ctx &C, uint32_t db, uint32_t degree, uint32_t stages, tetris_plan_info *out);
 void drop_programs_of_db(Ctx &C, uint32_t db);

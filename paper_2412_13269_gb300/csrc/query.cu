@@ -29,6 +29,9 @@ struct QPlan {
     double step_const;
     int degree = 0;
     int g = 0, m = 0, bb = 0, df = 0;  // baby-step giant-step schedule (g = 0: plain powers)
+    // global threshold: folded stage coefficients (empty: none) and the record count R
+    std::vector<std::array<double, 4>> gco;
+    double records_norm = 0;
     int coef_level(int k) const;
 };
 
@@ -76,7 +79,7 @@ int QPlan::coef_level(int k) const {
 }
 
 QPlan make_plan(const Ctx &C, uint64_t records, int degree, const std::vector<std::array<double, 4>> &stages,
-                uint64_t norm_records = 0) {
+                uint64_t norm_records = 0, const std::vector<std::array<double, 4>> &gstages = {}) {
     TREQUIRE(degree >= 1 && !stages.empty() && records >= 1, TETRIS_EINVAL, "empty query");
     QPlan p;
     const int L = C.L();
@@ -102,6 +105,19 @@ QPlan make_plan(const Ctx &C, uint64_t records, int degree, const std::vector<st
     p.mask_scale = p.ragged ? (C.S[p.l_u - 1] * (double)C.q[p.l_u]) / C.S[p.l_u] : 0.0;
     p.degree = degree;
     poly_schedule(p, degree);
+    // global threshold: step = (p + 1)/2 folded into the last stage
+    p.records_norm = R;
+    for (size_t s = 0; s < gstages.size(); s++) {
+        std::array<double, 4> c = gstages[s];
+        if (s + 1 == gstages.size())
+            for (int k = 0; k < 4; k++) c[k] = c[k] / 2.0;
+        p.gco.push_back(c);
+    }
+    if (!p.gco.empty()) {
+        p.l_ret = p.l_out - 3 * (int)p.gco.size();
+        TREQUIRE(p.l_ret >= 1, TETRIS_ELEVEL,
+                 "global threshold needs more levels: it would end at level " + std::to_string(p.l_ret));
+    }
     return p;
 }
 
@@ -226,7 +242,7 @@ std::unique_ptr<Program> record_query(Ctx &C, const Database &db, const QuerySpe
     auto P = std::make_unique<Program>();
     P->ctx = &C;
     Rec R(C, *P);
-    const QPlan pl = make_plan(C, db.records, q.degree, q.stages, q.total_records);
+    const QPlan pl = make_plan(C, db.records, q.degree, q.stages, q.total_records, q.gstages);
     const int L = C.L();
     const size_t N = C.N;
     // staging buffers for the inputs (coefficient domain on arrival, NTT in place)
@@ -246,6 +262,13 @@ std::unique_ptr<Program> record_query(Ctx &C, const Database &db, const QuerySpe
     tin.scale = q.t_scale;
     P->hold.push_back(tin.buf);
     P->in_slots.push_back({tin.base, tin.bstride});
+    CtH t1in;
+    if (!q.gstages.empty()) {
+        t1in = R.new_ct(1, 2, q.g_level);
+        t1in.scale = q.g_scale;
+        P->hold.push_back(t1in.buf);
+        P->in_slots.push_back({t1in.base, t1in.bstride});
+    }
     // per-query: the coefficients and the threshold move to their levels while
     // still in the coefficient domain (a rescale is per coefficient there), so
     // only their remaining limbs are transformed, together with the w_j
@@ -318,12 +341,34 @@ std::unique_ptr<Program> record_query(Ctx &C, const Database &db, const QuerySpe
     }
     // InnerSum: acc += Rot_{2^k}(acc), after dropping to level l_ret (the
     // rotations' key switches then work on two primes; the value, below
-    // S[l_out] in magnitude, is far inside q_0 q_1)
-    const double acc_scale = acc.scale;
-    acc = R.drop(acc, std::min(acc.level, pl.l_ret));
+    // S[l_out] in magnitude, is far inside q_0 q_1) -- unless a global
+    // threshold follows, which needs the levels
+    double acc_scale = acc.scale;
+    if (pl.gco.empty()) acc = R.drop(acc, std::min(acc.level, pl.l_ret));
     for (int k = 0; k + 1 < C.log_n; k++) {
         const uint32_t g = (uint32_t)h_powmod(5, 1ull << k, 2 * C.N);
         acc = R.add(acc, R.rotate(acc, g));
+    }
+    if (!pl.gco.empty()) {
+        // global threshold (Algorithm 2, last line): step((count - t1 + 1/2) / R)
+        // from acc = count / R; t1 enters as a count scaled by 1/R in its adjust
+        const double R0 = pl.records_norm;
+        CtH t1 = R.adjust_many_coef({{t1in, acc.level, 1.0 / R0}})[0];
+        {
+            std::vector<NttJob> jobs;
+            for (int c = 0; c < 2; c++)
+                for (int i = 0; i <= t1.level; i++) {
+                    NttJob j{};
+                    j.src = j.dst = t1.limb(0, c, i);
+                    j.prime = i;
+                    jobs.push_back(j);
+                }
+            R.ntt(false, jobs, LOAD_PLAIN, STORE_PLAIN);
+        }
+        CtH z = R.add_int(R.sub(acc, t1), round_half_up(C.S[acc.level] / (2.0 * R0)));
+        for (auto &co : pl.gco) z = sign_stage(R, z, co);
+        acc = R.add_int(z, round_half_up(0.5 * C.S[z.level]));
+        acc_scale = C.S[acc.level];
     }
     CtH o = R.from_ntt(acc);
     P->out_buf = o.buf;
@@ -369,7 +414,29 @@ QuerySpec spec_of(const Ctx &C, const Database &db, const tetris_query *q) {
     TREQUIRE(q->total_records == 0 || q->total_records >= db.records, TETRIS_EINVAL,
              "query: total_records is smaller than the database");
     s.total_records = q->total_records;
+    if (q->global_threshold) {
+        const tetris_ct_in &g = *q->global_threshold;
+        TREQUIRE(q->global_stages >= 1 && q->global_coeffs, TETRIS_EINVAL, "query: global threshold without stages");
+        TREQUIRE(g.ncomp == 2 && (int)g.level <= L && g.data && g.scale > 0, TETRIS_EINVAL,
+                 "query: bad global threshold ciphertext");
+        s.g_level = g.level;
+        s.g_scale = g.scale;
+        for (uint32_t st = 0; st < q->global_stages; st++) {
+            std::array<double, 4> a;
+            for (int k = 0; k < 4; k++) a[k] = q->global_coeffs[st * 4 + k];
+            s.gstages.push_back(a);
+        }
+    }
     return s;
+}
+
+std::vector<const tetris_ct_in *> query_inputs(const tetris_query *q) {
+    std::vector<const tetris_ct_in *> ins;
+    for (uint32_t j = 0; j < q->n_attrs; j++) ins.push_back(&q->w[j]);
+    for (uint32_t k = 0; k <= q->f_degree; k++) ins.push_back(&q->f_coeffs[k]);
+    ins.push_back(q->threshold);
+    if (q->global_threshold) ins.push_back(q->global_threshold);
+    return ins;
 }
 
 static Program &get_program(Ctx &C, uint32_t dbh, const QuerySpec &s) {
@@ -400,14 +467,10 @@ void evaluate_query(Ctx &C, uint32_t dbh, const tetris_query *q, tetris_ct_out *
     Program &P = get_program(C, dbh, spec);
     TREQUIRE(out->cap_words >= P.out_words, TETRIS_EINVAL, "query: output buffer too small");
     const cudaMemcpyKind in_kind = device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
-    size_t slot = 0;
-    auto put = [&](const tetris_ct_in &c) {
-        TCHECK_CUDA(cudaMemcpyAsync(P.in_slots[slot].first, c.data, P.in_slots[slot].second * 8, in_kind, s));
-        slot++;
-    };
-    for (uint32_t j = 0; j < q->n_attrs; j++) put(q->w[j]);
-    for (uint32_t k = 0; k <= q->f_degree; k++) put(q->f_coeffs[k]);
-    put(*q->threshold);
+    const auto ins = query_inputs(q);
+    TREQUIRE(ins.size() == P.in_slots.size(), TETRIS_EINVAL, "query: inputs do not match the program");
+    for (size_t slot = 0; slot < ins.size(); slot++)
+        TCHECK_CUDA(cudaMemcpyAsync(P.in_slots[slot].first, ins[slot]->data, P.in_slots[slot].second * 8, in_kind, s));
     if (C.profile) P.run_profiled(s, C.stats);
     else if (C.use_graph) P.run_graph(s);
     else P.run(s);
@@ -461,15 +524,10 @@ void autotune(Ctx &C, uint32_t dbh, const tetris_query *q, int reps, std::vector
             QuerySpec spec = spec_of(C, it->second, q);
             const std::string key = spec.key(dbh);
             Program &P = get_program(C, dbh, spec);
-            size_t slot = 0;
-            auto put = [&](const tetris_ct_in &c) {
-                TCHECK_CUDA(cudaMemcpyAsync(P.in_slots[slot].first, c.data, P.in_slots[slot].second * 8,
+            const auto ins = query_inputs(q);
+            for (size_t slot = 0; slot < ins.size(); slot++)
+                TCHECK_CUDA(cudaMemcpyAsync(P.in_slots[slot].first, ins[slot]->data, P.in_slots[slot].second * 8,
                                             cudaMemcpyHostToDevice, C.stream));
-                slot++;
-            };
-            for (uint32_t j = 0; j < q->n_attrs; j++) put(q->w[j]);
-            for (uint32_t k = 0; k <= q->f_degree; k++) put(q->f_coeffs[k]);
-            put(*q->threshold);
             P.run_graph(C.stream);
             TCHECK_CUDA(cudaEventRecord(e0, C.stream));
             for (int r = 0; r < reps; r++) P.run_graph(C.stream);

@@ -306,10 +306,7 @@ uint64_t serve_submit(Ctx &C, uint32_t db, const tetris_query *q) {
     req->key = req->spec.key(db);
     const size_t N = C.N;
     auto words = [&](const tetris_ct_in &c) { return (size_t)2 * (c.level + 1) * N; };
-    std::vector<const tetris_ct_in *> ins;
-    for (uint32_t j = 0; j < q->n_attrs; j++) ins.push_back(&q->w[j]);
-    for (uint32_t k = 0; k <= q->f_degree; k++) ins.push_back(&q->f_coeffs[k]);
-    ins.push_back(q->threshold);
+    const std::vector<const tetris_ct_in *> ins = query_inputs(q);
     for (auto c : ins) {
         req->in_words.push_back(words(*c));
         req->total_in += words(*c);

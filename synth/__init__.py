@@ -80,6 +80,7 @@ class QueryValues:
     w: np.ndarray        # float64[attrs], linear-combination coefficients in [-1, 1]
     c: np.ndarray        # float64[degree+1], coefficients of f
     t: float             # threshold in [-0.5, 0.5]
+    t1: float | None = None  # global threshold, a record count (None: no global threshold)
 
 
 def query_values(g: np.random.Generator, attrs: int, degree: int) -> QueryValues:

@@ -219,3 +219,39 @@ def test_full_size_benchmark_workload_decrypts(full):
     assert np.ptp(z) < 1e-6
     assert abs(z[0] * 131072 - ref.count) < 0.5
     ctx.free_database(dbh)
+
+
+@pytest.fixture(scope="module")
+def deep():
+    """Test-only chain with 18 primes of 40 bits after q_0: room for 3 local and 2 global sign stages."""
+    return Chain(n40=18, seed=9)
+
+
+@pytest.mark.parametrize("p_pos,t1_frac", [(0.9, 0.2), (0.1, 0.8)])
+def test_global_threshold_bit_exact(deep, p_pos, t1_frac):
+    """Algorithm 2's last line (step((count - t1 + 1/2) / R)) after InnerSum:
+    residues equal the oracle's; the decrypted bit is exact."""
+    from test_oracle_query import skewed_margin_dataset
+    par, ctx = deep.par, deep.ctx
+    stages, gstages = [query.F3] * 3, [query.F3] * 2
+    R = 2048
+    vals, w, side = skewed_margin_dataset(R, 8, 23, p_pos)
+    qv = synth.QueryValues(w=w, c=np.array([0.0, 1.0]), t=0.0, t1=float(int(t1_frac * R)))
+    shape = query.QueryShape(R, 8, 1, stages, global_stages=gstages)
+    plan = query.make_plan(par, shape)
+    db = query.encode_database(par, plan, vals)
+    eq = query.encrypt_query(par, deep.s, qv, 23)
+    want = query.evaluate_query(par, deep.keys, shape, db, eq)
+    dbh = upload_encoded(ctx, par, plan, db, R, 8)
+    for bpl in (0, 1):
+        ctx.set_option(T.OPT_BLOCKS_PER_LAUNCH, bpl)
+        got, lev, sc = ctx.evaluate_query(dbh, [c.data for c in eq.w], [(c.level, c.scale) for c in eq.w],
+                                          [c.data for c in eq.c], [(c.level, c.scale) for c in eq.c], eq.t.data,
+                                          (eq.t.level, eq.t.scale), np.array(stages),
+                                          glob=(eq.t1.data, (eq.t1.level, eq.t1.scale), np.array(gstages)))
+        assert lev == want.level == plan.l_ret and sc == plan.S[plan.l_ret]
+        assert np.array_equal(got, want.data), bpl
+    ctx.set_option(T.OPT_BLOCKS_PER_LAUNCH, 0)
+    bit = ckks.decrypt_slots(par, ckks.Ct(got.copy(), lev, sc), deep.s).real
+    assert np.max(np.abs(bit - (1 if p_pos > 0.5 else 0))) < 2.0 ** -12
+    ctx.free_database(dbh)

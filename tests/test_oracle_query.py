@@ -124,3 +124,45 @@ def test_bsgs_polynomial_matches_fp64(monkeypatch, degree, relins):
     assert len(calls) == relins
     assert np.ptp(got) < 1e-6
     assert abs(got[0] * 2048 - ref.count) < 0.05
+
+
+def skewed_margin_dataset(records, attrs, seed, p_pos):
+    """As margin_dataset, with a fraction p_pos of the records on the positive side."""
+    g = np.random.default_rng(seed)
+    w = g.choice([-1.0, 1.0], size=attrs)
+    side = np.where(g.uniform(size=records) < p_pos, 1.0, -1.0)
+    mag = g.uniform(0.75, 1.0, size=(records, attrs))
+    xh = side[:, None] * w[None, :] * mag
+    vals = np.clip(np.rint(xh * 127.5 + 127.5), 0, 255).astype(np.uint8)
+    return vals, w, side
+
+
+@pytest.mark.parametrize("p_pos,t1_frac", [(0.9, 0.2), (0.1, 0.8)])
+def test_global_threshold_bit(p_pos, t1_frac):
+    """Algorithm 2's last line on the count: with every record outside the
+    local sign margin (exact count) and (count - t1 + 1/2)/R outside the
+    global margin of two f3 stages at tolerance 2^-12, the decrypted output is
+    the exact bit [count >= t1] within 2^-12 in every slot, and matches the FP64
+    pipeline's value of the same polynomials."""
+    stages, gstages = [query.F3] * 3, [query.F3] * 2
+    R = 2048
+    vals, w, side = skewed_margin_dataset(R, 8, 17, p_pos)
+    t1 = float(int(t1_frac * R))
+    qv = synth.QueryValues(w=w, c=np.array([0.0, 1.0]), t=0.0, t1=t1)
+    par = chain_params(18)
+    shape = query.QueryShape(R, 8, 1, stages, global_stages=gstages)
+    plan = query.make_plan(par, shape)
+    assert plan.l_ret == plan.l_out - 6 >= 1
+    s = query.secret(par, 3, 2 * par.N // 3)
+    keys = query.make_keys(par, s, 3, 1, query.innersum_galois(par))
+    db = query.encode_database(par, plan, vals)
+    eq = query.encrypt_query(par, s, qv, 3)
+    out = query.evaluate_query(par, keys, shape, db, eq)
+    assert out.level == plan.l_ret
+    got = ckks.decrypt_slots(par, out, s).real
+    ref = query.fp64_pipeline(vals, qv, stages, gstages)
+    assert ref.exact == int((side > 0).sum())
+    assert abs(ref.z2) > query.sign_margin(gstages, 2.0 ** -12)
+    assert ref.exact_bit == int(ref.exact >= t1) == (1 if p_pos > 0.5 else 0)
+    assert np.max(np.abs(got - ref.exact_bit)) < 2.0 ** -12
+    assert np.max(np.abs(got - ref.bit)) < 1e-6
