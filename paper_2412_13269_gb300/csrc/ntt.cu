@@ -427,6 +427,13 @@ struct KsSmem {
     __host__ __device__ static size_t bytes(int sub_cta) { return (exch_words(sub_cta) + 2 * (size_t)GG::E * kThreads) * 8; }
 };
 
+// Bulk-copy (TMA) prefetch of a contiguous range into L2: no shared memory, no
+// completion to wait for.  The address must be 16-byte aligned and the size a
+// multiple of 16 bytes.
+__device__ __forceinline__ void prefetch_l2_bulk(const void *p, uint32_t bytes) {
+    asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(p), "r"(bytes) : "memory");
+}
+
 template <int LOGM, int LOGEV, bool OPEN>
 __device__ __forceinline__ void keyswitch_up_body(const PassParams &P, const KsJob &J, u64 *sm, const ModInfo &mi) {
     using GG = Geo<LOGM, false, false, LOGEV>;
@@ -440,7 +447,21 @@ __device__ __forceinline__ void keyswitch_up_body(const PassParams &P, const KsJ
     u64 *acc = sm + KsSmem<LOGM, LOGEV>::exch_words(g.sub_cta);
     auto slot = [&](int c, int k) -> u64 & { return acc[(c * E + k) * nthr + tid]; };
     const int nd = (int)J.ndig;
+    // the CTA's rows are one contiguous tile of every limb it reads: while digit
+    // d is transformed, the tiles of digit d + 1 (two key limbs and its source)
+    // are prefetched into L2 by the bulk-copy engine
+    const uint32_t tile_off = (uint32_t)g.sub0 * (uint32_t)g.N2;
+    const uint32_t tile_bytes = (uint32_t)g.sub_cta * (uint32_t)g.N2 * 8;
+    auto prefetch_digit = [&](int d) {
+        if (tid == 0 && d < nd && tile_bytes % 16 == 0) {
+            prefetch_l2_bulk(J.key0[d] + tile_off, tile_bytes);
+            prefetch_l2_bulk(J.key1[d] + tile_off, tile_bytes);
+            prefetch_l2_bulk(J.src[d] + tile_off, tile_bytes);
+        }
+    };
+    prefetch_digit(0);
     for (int d = 0; d < nd; d++) {
+        prefetch_digit(d + 1);
         u64 x[E];
         const u64 *src = J.src[d];
         if (d == J.own) {
