@@ -365,6 +365,78 @@ def run_c4(args):
         c.close()
 
 
+def run_pfe(args):
+    """PFE scoring step (Section 4.1.1) at the paper's Set I shape: N = 2^12,
+    one 55-bit modulus, m = 16 encrypted scoring functions, 131072 records
+    whose attribute values (the paper's feature distribution for half the
+    columns, uniform u8 for the rest) are placed in the exponent as
+    round(N g(x)).  Each step computes every record's ct_i = sum_j U_j X^{e_ij}
+    (output 8 GiB, larger than L2); device-resident inputs, CUDA events."""
+    import torch
+    import paper_2412_13269_gb300 as T
+    rank, world, local_rank = dist_env()
+    torch.cuda.set_device(local_rank)
+    T.build()
+    log_n, m, records = 12, 16, args.pfe_records
+    n = 1 << log_n
+    q = T.gen_primes(55, 1)
+    ctx = T.Ctx(log_n, q, T.gen_primes(54, 1, exclude=q), 2.0 ** 40, device=local_rank)
+    seed = 5000 + rank
+    g = np.random.default_rng(seed)
+    u = g.integers(0, q[0], (m, 2, n), dtype=np.uint64)          # the encrypted function polynomials
+    vals = synth.database(synth.stream(seed, "db"), records, m, "mixed")
+    exps = np.minimum(np.floor(n * (vals.astype(np.float64) / 255.0) + 0.5), n - 1).astype(np.int32)
+    du = torch.from_numpy(u.view(np.int64)).cuda()
+    de = torch.from_numpy(exps).cuda()
+    out = torch.empty((records, 2, n), dtype=torch.int64, device="cuda")
+    stream = torch.cuda.Stream()
+    step = lambda: ctx.pfe_scores_device(du, de, out, m, records, stream.cuda_stream)
+    for _ in range(args.warmup):
+        step()
+    stream.synchronize()
+    clocks = Clocks(local_rank)
+    clocks.start()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        step()
+    e1.record(stream)
+    e1.synchronize()
+    clk = clocks.stop()
+    ms = e0.elapsed_time(e1) / args.steps
+    # DRAM: every output word written once, the exponents and the m inputs read once.  The
+    # bound is shared memory: every term X^k U_j[t] is one 8-byte shared-memory read
+    # (records * 2 * N * m of them); peak = 152 SMs x 128 B/clk x the SM clock seen
+    alg = records * 2 * n * 8 + exps.nbytes + u.nbytes
+    peaks, peak_kind = measured_peaks()
+    hbm = float(peaks.get("hbm_gbs", 6800.0))
+    gbs = alg / (ms * 1e-3) / 1e9
+    sm_bytes = records * 2 * n * m * 8
+    sm_gbs = sm_bytes / (ms * 1e-3) / 1e9
+    mhz = (clk or {}).get("sm_mhz") or 2070.0
+    sm_peak = 152 * 128 * mhz * 1e6 / 1e9
+    # CPU oracle on a bounded sample of the same records
+    from oracle import pfe as opfe
+    sample = 64
+    t0 = time.perf_counter()
+    opfe.scores(u, exps[:sample], q[0])
+    cpu_s = time.perf_counter() - t0
+    line = {"metric": "PFE scoring: us/record (m = 16 encrypted functions, N = 2^12)", "workload": "pfe",
+            "value": ms * 1e3 / records, "unit": "us/record", "ms_per_step": ms, "steps": args.steps,
+            "warmup": args.warmup, "higher_is_better": False, "dtype": "u64", "data": "synthetic (seeded)",
+            "roofline": {"kernel": "pfe_staged_kernel", "bound": "smem", "achieved": sm_gbs, "peak": sm_peak,
+                         "unit": "GB/s", "frac": sm_gbs / sm_peak, "traffic": None,
+                         "peak_source": "derived: 152 SMs x 128 B/clk shared-memory bandwidth x median SM clock",
+                         "hbm": {"achieved": gbs, "peak": hbm, "frac": gbs / hbm, "peak_source": f"{peak_kind} hbm_gbs"}},
+            "cpu_baseline": {"value": cpu_s * 1e6 / sample, "unit": "us/record", "cores": 1, "kind": "oracle",
+                             "sample": f"oracle pfe.scores on {sample} of {records} records (numpy, one thread)"},
+            "clocks": clk, "gpu_launches": args.steps,
+            "config": {"workload": f"PFE scores: N=2^12, one 55-bit modulus, {m} functions, {records} records; "
+                                   f"output {records * 2 * n * 8 / 2**30:.2f} GiB"}}
+    print(json.dumps(line), flush=True)
+    ctx.close()
+
+
 SERVE_DBS = [(1 << 14, 8), (1 << 16, 16), (1 << 18, 24), (1 << 19, 32)]
 SERVE_TYPES = [("linear+threshold", 1), ("degree-15 poly+threshold", 15), ("degree-31 poly+composite sign", 31)]
 
@@ -452,8 +524,9 @@ def main():
     ap.add_argument("--no-plain", action="store_true")
     ap.add_argument("--ncu", action="store_true", help="profile exactly one query between cudaProfilerStart/Stop")
     ap.add_argument("--serve", action="store_true", help="serving workload: Poisson arrivals, mixed queries")
-    ap.add_argument("--workload", default="c2", choices=["c2", "c3", "c4"],
+    ap.add_argument("--workload", default="c2", choices=["c2", "c3", "c4", "pfe"],
                     help="c2: 131072 x 16 (the default line); c3: batching, 524288 x 32 with the autotuner")
+    ap.add_argument("--pfe-records", type=int, default=1 << 17, help="records of the pfe workload")
     ap.add_argument("--micro-keyswitch", type=int, default=0, metavar="CALLS",
                     help="top-level keyswitch via tetris_op, CALLS times; the last call between cudaProfilerStart/Stop")
     ap.add_argument("--rates", default="5,10,20,40", help="arrival rates (queries/s) for --serve")
@@ -469,6 +542,8 @@ def main():
         return run_c3(args)
     if args.workload == "c4":
         return run_c4(args)
+    if args.workload == "pfe":
+        return run_pfe(args)
 
     import torch
     rank, world, local_rank = dist_env()

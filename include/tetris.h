@@ -378,6 +378,28 @@ int tetris_rescale_ntt_noalloc(tetris_ctx *ctx, const uint64_t *in, uint64_t *ou
                                uint32_t ncomp, void *stream);
 size_t tetris_noalloc_scratch_bytes(void);
 
+/* ---------------------------------------------------------------------------
+ * PFE scoring step (Section 4.1.1; Algorithm 2, the loop building ct_i): for
+ * every record i,
+ *   out[i] = sum_{j<m} X^{exps[i*m + j]} u[j]   in (Z_{q_0}[X] / (X^N + 1))^2,
+ * where u[j] encrypts the scientist's scoring polynomial u_{f_j} (its value
+ * table placed so that X^k u_{f_j} has f_j at point k in coefficient 0) and
+ * exps holds the records' attribute values in the exponent (taken mod 2N).
+ * Uses the context's N and first prime q_0 (the paper's Set I: N = 2^12, one
+ * 55-bit modulus).
+ * u:    [m][2][N] uint64 residues mod q_0, coefficient domain;
+ * exps: [p][m] uint32; out: [p][2][N] uint64.
+ * _device: all three are device pointers (caller-owned), enqueued on stream
+ * (cudaStream_t, NULL = legacy default), nothing allocated.  Without the
+ * suffix: host pointers; the call copies in, runs and copies out (blocking).
+ * Errors: TETRIS_EINVAL for null buffers, m outside [1, 4096] or p outside
+ * [1, 2^30 - 1].
+ * ------------------------------------------------------------------------- */
+int tetris_pfe_scores(tetris_ctx *ctx, const uint64_t *u, uint32_t m, const uint32_t *exps, uint64_t p,
+                      uint64_t *out);
+int tetris_pfe_scores_device(tetris_ctx *ctx, const uint64_t *u, uint32_t m, const uint32_t *exps, uint64_t p,
+                             uint64_t *out, void *stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -147,6 +147,8 @@ SIGNATURES = {
     "tetris_serve_stats_get": [_vp, C.POINTER(ServeStats), C.c_int],
     "tetris_serve_stop": [_vp],
     "tetris_noalloc_scratch_bytes": [],
+    "tetris_pfe_scores": [_vp, _vp, _u32, _vp, _u64, _vp],
+    "tetris_pfe_scores_device": [_vp, _vp, _u32, _vp, _u64, _vp, _vp],
 }
 
 
@@ -315,6 +317,19 @@ class Ctx:
         check(lib().tetris_get_kernel_stats(self.h, buf, 256, C.byref(n)))
         return {buf[i].kind.decode(): (buf[i].launches, buf[i].total_ms, buf[i].alg_bytes, buf[i].alg_modmuls)
                 for i in range(n.value)}
+
+    def pfe_scores(self, u: np.ndarray, exps: np.ndarray) -> np.ndarray:
+        """PFE scoring step, host arrays: u uint64 [m][2][N], exps [p][m] -> uint64 [p][2][N]."""
+        u = np.ascontiguousarray(u, dtype=np.uint64)
+        e = np.ascontiguousarray(exps, dtype=np.uint32)
+        m, p = u.shape[0], e.shape[0]
+        out = np.empty((p, 2, self.N), dtype=np.uint64)
+        check(lib().tetris_pfe_scores(self.h, u.ctypes.data, m, e.ctypes.data, p, out.ctypes.data))
+        return out
+
+    def pfe_scores_device(self, u, exps, out, m: int, p: int, stream: int = 0):
+        """PFE scoring step on torch CUDA tensors (u int64 [m][2][N], exps int32 [p][m], out int64 [p][2][N])."""
+        check(lib().tetris_pfe_scores_device(self.h, _ptr(u), m, _ptr(exps), p, _ptr(out), stream))
 
     def rescale_ntt_noalloc(self, src, dst, level: int, ncomp: int, stream: int = 0):
         """Allocation-free rescale of a device-resident NTT-order ciphertext

@@ -798,6 +798,48 @@ int tetris_rescale_ntt_noalloc(tetris_ctx *ctx, const uint64_t *in, uint64_t *ou
 
 size_t tetris_noalloc_scratch_bytes(void) { return noalloc_scratch_bytes(); }
 
+int tetris_pfe_scores_device(tetris_ctx *ctx, const uint64_t *u, uint32_t m, const uint32_t *exps, uint64_t p,
+                             uint64_t *out, void *stream) {
+    return guarded([&] {
+        TREQUIRE(ctx, TETRIS_EINVAL, "null context");
+        cudaSetDevice(ctx->c.device);
+        pfe_scores(ctx->c, u, m, exps, p, out, reinterpret_cast<cudaStream_t>(stream));
+    });
+}
+
+int tetris_pfe_scores(tetris_ctx *ctx, const uint64_t *u, uint32_t m, const uint32_t *exps, uint64_t p,
+                      uint64_t *out) {
+    return guarded([&] {
+        TREQUIRE(ctx && u && exps && out, TETRIS_EINVAL, "pfe: null pointer");
+        TREQUIRE(m >= 1 && m <= 4096 && p >= 1 && p < (1ull << 30), TETRIS_EINVAL, "pfe: bad sizes");
+        Ctx &C = ctx->c;
+        cudaSetDevice(C.device);
+        const size_t uw = (size_t)m * 2 * C.N, ow = (size_t)p * 2 * C.N, ew = (size_t)p * m;
+        u64 *du = nullptr, *dout = nullptr;
+        uint32_t *de = nullptr;
+        auto release = [&] {
+            cudaFree(du);
+            cudaFree(dout);
+            cudaFree(de);
+        };
+        try {
+            TCHECK_CUDA(cudaMalloc(&du, uw * 8));
+            TCHECK_CUDA(cudaMalloc(&dout, ow * 8));
+            TCHECK_CUDA(cudaMalloc(&de, ew * 4));
+            TCHECK_CUDA(cudaMemcpyAsync(du, u, uw * 8, cudaMemcpyHostToDevice, C.stream));
+            TCHECK_CUDA(cudaMemcpyAsync(de, exps, ew * 4, cudaMemcpyHostToDevice, C.stream));
+            pfe_scores(C, du, m, de, p, dout, C.stream);
+            TCHECK_CUDA(cudaMemcpyAsync(out, dout, ow * 8, cudaMemcpyDeviceToHost, C.stream));
+            TCHECK_CUDA(cudaStreamSynchronize(C.stream));
+        } catch (...) {
+            cudaStreamSynchronize(C.stream);
+            release();
+            throw;
+        }
+        release();
+    });
+}
+
 int tetris_modmul_peak(int device, double *rate) {
     return guarded([&] {
         TREQUIRE(rate, TETRIS_EINVAL, "null pointer");

@@ -272,6 +272,9 @@ void batch_run(const tetris_batch_item *items, uint32_t n, int schedule, int *us
 void rescale_ntt_noalloc(Ctx &C, const u64 *in, u64 *out, int level, int ncomp, cudaStream_t s);
 size_t noalloc_scratch_bytes();
 
+// pfe.cu
+void pfe_scores(Ctx &C, const u64 *u, uint32_t m, const uint32_t *exps, uint64_t p, u64 *out, cudaStream_t s);
+
 }  // namespace tetris
 
 // the opaque handle of the C ABI
