@@ -67,3 +67,47 @@ def exponent(x, a: float, b: float, n: int) -> np.ndarray:
     kept below N (g(b) = 1 would wrap to X^N = -1)."""
     g = 0.5 * ((2.0 * np.asarray(x, dtype=np.float64) - b - a) / (b - a) + 1.0)
     return np.minimum(np.floor(n * g + 0.5).astype(np.int64), n - 1)
+
+
+# ---------------------------------------------------------------------------
+# Ring repacking (Algorithm 1, after Chen-Dai-Kim-Song): n <= N ciphertexts
+# whose messages carry x_i in their constant coefficient become one ciphertext
+# of sum_i x_i X^i.  All inputs are first multiplied by N^-1 mod Q (the log N
+# rounds double the coefficients they keep).  Round r (r = 0 .. log N - 1)
+# pairs c_j with c_{j+t}, t = N / 2^(r+1), and replaces c_j by
+#     (c_j + X^t c_{j+t}) + phi_g(c_j - X^t c_{j+t}),
+# phi_g the automorphism X -> X^g followed by its key switch, g = 2N - 1 in the
+# first round and 5^(2^(r-1)) mod 2N after it.  Missing inputs are zero.
+# ---------------------------------------------------------------------------
+def repack_galois(n: int) -> list:
+    """The Galois elements the rounds use, in round order."""
+    logn = n.bit_length() - 1
+    return [2 * n - 1] + [pow(5, 1 << (r - 1), 2 * n) for r in range(1, logn)]
+
+
+def ct_monomial_mul(ct, t: int, moduli):
+    """X^t times every component, limb by limb (a negacyclic rotation)."""
+    from .ckks import Ct
+    data = np.stack([np.stack([monomial_mul(ct.data[c, i], t, int(moduli[i])) for i in range(ct.level + 1)])
+                     for c in range(ct.comps)])
+    return Ct(data, ct.level, ct.scale)
+
+
+def repack(par, cts: list, rot_keys: dict, alpha: int):
+    """Algorithm 1 on ciphertexts at one level (coefficient domain)."""
+    from . import ckks
+    n = par.N
+    if not 1 <= len(cts) <= n:
+        raise ValueError("repack takes 1 to N ciphertexts")
+    level = cts[0].level
+    mods = par.q[: level + 1]
+    ninv = pow(n, -1, int(np.prod([int(m) for m in mods], dtype=object)))
+    zero = ckks.Ct(np.zeros_like(cts[0].data), level, cts[0].scale)
+    c = [ckks.mul_int(par, x, ninv) for x in cts] + [zero] * (n - len(cts))
+    for r, g in enumerate(repack_galois(n)):
+        t = n >> (r + 1)
+        for j in range(t):
+            s = ct_monomial_mul(c[j + t], t, mods)
+            c[j] = ckks.add(par, ckks.add(par, c[j], s),
+                            ckks.rotate(par, ckks.sub(par, c[j], s), g, rot_keys[g], alpha))
+    return c[0]

@@ -90,3 +90,53 @@ def test_decrypted_scores_are_function_sums():
         c0 = ckks.decrypt_int(par, ckks.Ct(out[i][:, None, :], 0, par.scale), s)[0]
         want = sum(tables[j][exps[i, j]] for j in range(m))
         assert abs(c0 / par.scale - want) < 1e-5, i
+
+
+def repack_params(log_n=6):
+    q = rns.gen_primes(50, 1) + rns.gen_primes(40, 1)
+    return ckks.Params(log_n, q, rns.gen_primes(60, 1), 2.0 ** 30)
+
+
+def test_repack_galois_elements():
+    assert pfe.repack_galois(16) == [31, 5, 25, 17]
+    assert pfe.repack_galois(4096)[0] == 8191 and len(pfe.repack_galois(4096)) == 12
+
+
+@pytest.mark.parametrize("count", [64, 37, 1])
+def test_repack_trivial_ciphertexts_exact(count):
+    """With c1 = 0 every key switch sees a zero polynomial and returns zero,
+    so Algorithm 1 acts on the plaintexts alone: the result is exactly
+    sum_i m_i[0] X^i (mod Q) -- the N^-1 premultiplication cancels the log N
+    doublings and every other coefficient cancels (Lemma 1)."""
+    par = repack_params()
+    s = query.secret(par, 2, 2 * par.N // 3)
+    keys = query.make_keys(par, s, 2, 1, pfe.repack_galois(par.N))
+    g = np.random.default_rng(count)
+    mods = par.q[: par.L + 1]
+    msgs = [g.integers(-(1 << 20), 1 << 20, par.N) for _ in range(count)]
+    cts = [ckks.Ct(np.stack([rns.to_rns(m, mods), np.zeros((par.L + 1, par.N), dtype=np.uint64)]), par.L, 1.0)
+           for m in msgs]
+    out = pfe.repack(par, cts, keys.rot, 1)
+    want = np.zeros(par.N, dtype=np.int64)
+    want[:count] = [int(m[0]) for m in msgs]
+    assert np.array_equal(out.data[0], rns.to_rns(want, mods))
+    assert not out.data[1].any()
+
+
+def test_repack_decrypts_to_constant_coefficients():
+    """Real encryptions: the repacked ciphertext decrypts to sum_i m_i[0] X^i up
+    to the key-switching noise (N e_ks after log N rounds, far below Delta)."""
+    par = repack_params()
+    s = query.secret(par, 3, 2 * par.N // 3)
+    keys = query.make_keys(par, s, 3, 1, pfe.repack_galois(par.N))
+    g = np.random.default_rng(9)
+    vals = g.uniform(-1, 1, par.N)
+    cts = []
+    for i in range(par.N):
+        m = np.round(g.uniform(-1, 1, par.N) * par.scale).astype(np.int64)
+        m[0] = int(round(vals[i] * par.scale))
+        d = synth.encryption_draws(3, f"r{i}", par.q, par.N)
+        cts.append(ckks.encrypt(par, m, s, d.a, d.e, par.L, par.scale))
+    out = pfe.repack(par, cts, keys.rot, 1)
+    dec = np.array(ckks.decrypt_int(par, out, s), dtype=np.float64) / par.scale
+    assert np.max(np.abs(dec - vals)) < 2.0 ** -12
