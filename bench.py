@@ -437,6 +437,85 @@ def run_pfe(args):
     ctx.close()
 
 
+def run_repack(args):
+    """Ring repacking (Algorithm 1) at the Set I shape: N = 2^12, one 55-bit
+    ciphertext prime, one 54-bit special prime (one-prime digits; the paper's
+    extra base-2^30 decomposition is not built), 4096 input ciphertexts ->
+    12 rounds, 4095 automorphisms with key switches, each round one batch.
+    Device-resident inputs, CUDA events, CUDA-graph replay."""
+    import torch
+    import paper_2412_13269_gb300 as T
+    rank, world, local_rank = dist_env()
+    torch.cuda.set_device(local_rank)
+    T.build()
+    log_n = 12
+    n = 1 << log_n
+    q = T.gen_primes(55, 1)
+    p = T.gen_primes(54, 1, exclude=q)
+    scale = 2.0 ** 40
+    ctx = T.Ctx(log_n, q, p, scale, device=local_rank)
+    seed = 6000 + rank
+    s = synth.ternary_secret(synth.stream(seed, "secret"), n, 2 * n // 3)
+    gal = [2 * n - 1] + [pow(5, 1 << (r - 1), 2 * n) for r in range(1, log_n)]
+    for g in gal:
+        d = synth.switch_key_draws(seed, f"rot{g}", 1, q + p, n)
+        ctx.keygen_rotation(g, s, d.a, d.e, 1)
+    g = np.random.default_rng(seed)
+    data = g.integers(0, q[0], (n, 2, 1, n), dtype=np.uint64)     # n ciphertexts at level 0
+    dc = torch.from_numpy(data.view(np.int64)).cuda()
+    out = torch.empty((2, 1, n), dtype=torch.int64, device="cuda")
+    stream = torch.cuda.Stream()
+    step = lambda: ctx.repack_device(dc, n, 0, scale, out, stream.cuda_stream)
+    for _ in range(args.warmup):
+        step()
+    stream.synchronize()
+    clocks = Clocks(local_rank)
+    clocks.start()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        step()
+    e1.record(stream)
+    e1.synchronize()
+    clk = clocks.stop()
+    ms = e0.elapsed_time(e1) / args.steps
+    # per-kernel profile of one repack
+    ctx.set_option(T.OPT_PROFILE, 1)
+    step()
+    stream.synchronize()
+    ctx.set_option(T.OPT_PROFILE, 0)
+    kern = {k: v for k, v in ctx.kernel_stats().items() if k != "keyswitch(total)"}
+    tot = sum(v[1] for v in kern.values())
+    dom = max(kern, key=lambda k: kern[k][1])
+    nl, dms, db, dmm = kern[dom]
+    mm_peak = T.modmul_peak(local_rank)
+    achieved = dmm / (dms * 1e-3) / 1e9
+    # CPU oracle: a bounded sample of the rotations (each costs the same), scaled to all n - 1
+    from oracle import ckks as ock, query as oq
+    par = ock.Params(log_n, q, p, scale)
+    keys = oq.make_keys(par, np.asarray(s), seed, 1, gal[:1])
+    sample = 64
+    ct = ock.Ct(data[0], 0, scale)
+    t0 = time.perf_counter()
+    for _ in range(sample):
+        ock.rotate(par, ct, gal[0], keys.rot[gal[0]], 1)
+    cpu_ms = (time.perf_counter() - t0) / sample * (n - 1) * 1e3
+    line = {"metric": "ring repacking: ms per repack of 4096 ciphertexts (N = 2^12)", "workload": "repack",
+            "value": ms, "unit": "ms", "us_per_input": ms * 1e3 / n, "steps": args.steps, "warmup": args.warmup,
+            "higher_is_better": False, "dtype": "u64", "data": "synthetic (seeded uniform residues)",
+            "roofline": {"kernel": dom, "bound": "alu", "achieved": achieved, "peak": mm_peak, "unit": "Gmodmul/s",
+                         "frac": achieved / mm_peak, "share": dms / tot, "traffic": None,
+                         "peak_source": "measured: lazy Shoup modular products in registers (tetris_modmul_peak)"},
+            "kernels": [{"kind": k, "launches": v[0], "ms": round(v[1], 4)} for k, v in
+                        sorted(kern.items(), key=lambda kv: -kv[1][1])[:6]],
+            "cpu_baseline": {"value": cpu_ms, "unit": "ms", "cores": 1, "kind": "oracle",
+                             "sample": f"oracle: {sample} of the {n - 1} automorphism + key switches timed, scaled"},
+            "clocks": clk, "key_switches": n - 1, "rounds": log_n,
+            "config": {"workload": "repack 4096 ciphertexts, N=2^12, q 55-bit, p 54-bit, one-prime digits"}}
+    print(json.dumps(line), flush=True)
+    ctx.close()
+
+
 SERVE_DBS = [(1 << 14, 8), (1 << 16, 16), (1 << 18, 24), (1 << 19, 32)]
 SERVE_TYPES = [("linear+threshold", 1), ("degree-15 poly+threshold", 15), ("degree-31 poly+composite sign", 31)]
 
@@ -524,7 +603,7 @@ def main():
     ap.add_argument("--no-plain", action="store_true")
     ap.add_argument("--ncu", action="store_true", help="profile exactly one query between cudaProfilerStart/Stop")
     ap.add_argument("--serve", action="store_true", help="serving workload: Poisson arrivals, mixed queries")
-    ap.add_argument("--workload", default="c2", choices=["c2", "c3", "c4", "pfe"],
+    ap.add_argument("--workload", default="c2", choices=["c2", "c3", "c4", "pfe", "repack"],
                     help="c2: 131072 x 16 (the default line); c3: batching, 524288 x 32 with the autotuner")
     ap.add_argument("--pfe-records", type=int, default=1 << 17, help="records of the pfe workload")
     ap.add_argument("--micro-keyswitch", type=int, default=0, metavar="CALLS",
@@ -544,6 +623,8 @@ def main():
         return run_c4(args)
     if args.workload == "pfe":
         return run_pfe(args)
+    if args.workload == "repack":
+        return run_repack(args)
 
     import torch
     rank, world, local_rank = dist_env()

@@ -400,6 +400,24 @@ int tetris_pfe_scores(tetris_ctx *ctx, const uint64_t *u, uint32_t m, const uint
 int tetris_pfe_scores_device(tetris_ctx *ctx, const uint64_t *u, uint32_t m, const uint32_t *exps, uint64_t p,
                              uint64_t *out, void *stream);
 
+/* ---------------------------------------------------------------------------
+ * Ring repacking (Algorithm 1): n <= N ciphertexts whose messages carry x_i in
+ * their constant coefficient become one ciphertext of sum_i x_i X^i (every
+ * input premultiplied by N^-1 mod Q, then log N rounds of
+ * c_j <- (c_j + X^t c_{j+t}) + phi_g(c_j - X^t c_{j+t}), g = 2N - 1 first,
+ * then 5^(2^(r-1)) mod 2N).  Needs rotation keys for those Galois elements.
+ * cts: [n][2][level+1][N] uint64, coefficient domain, all at `level` with the
+ * same scale; out->data: [2][level+1][N] (cap_words >= 2 (level+1) N).
+ * _device: device pointers, enqueued on stream; otherwise host pointers,
+ * blocking.  The recorded program is kept per (n, level, scale).
+ * Errors: TETRIS_EINVAL (n outside [1, N], null buffers, small output),
+ * TETRIS_ELEVEL (level), TETRIS_ENOTFOUND (a rotation key missing).
+ * ------------------------------------------------------------------------- */
+int tetris_repack(tetris_ctx *ctx, const uint64_t *cts, uint32_t n, uint32_t level, double scale,
+                  tetris_ct_out *out);
+int tetris_repack_device(tetris_ctx *ctx, const uint64_t *cts, uint32_t n, uint32_t level, double scale,
+                         tetris_ct_out *out, void *stream);
+
 #ifdef __cplusplus
 }
 #endif

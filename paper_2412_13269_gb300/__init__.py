@@ -147,6 +147,8 @@ SIGNATURES = {
     "tetris_serve_stats_get": [_vp, C.POINTER(ServeStats), C.c_int],
     "tetris_serve_stop": [_vp],
     "tetris_noalloc_scratch_bytes": [],
+    "tetris_repack": [_vp, _vp, _u32, _u32, _d, C.POINTER(CtOut)],
+    "tetris_repack_device": [_vp, _vp, _u32, _u32, _d, C.POINTER(CtOut), _vp],
     "tetris_pfe_scores": [_vp, _vp, _u32, _vp, _u64, _vp],
     "tetris_pfe_scores_device": [_vp, _vp, _u32, _vp, _u64, _vp, _vp],
 }
@@ -317,6 +319,21 @@ class Ctx:
         check(lib().tetris_get_kernel_stats(self.h, buf, 256, C.byref(n)))
         return {buf[i].kind.decode(): (buf[i].launches, buf[i].total_ms, buf[i].alg_bytes, buf[i].alg_modmuls)
                 for i in range(n.value)}
+
+    def repack(self, cts: np.ndarray, level: int, scale: float):
+        """Ring repacking (Algorithm 1), host arrays: cts uint64 [n][2][level+1][N] ->
+        (out [2][level+1][N], level, scale)."""
+        cts = np.ascontiguousarray(cts, dtype=np.uint64)
+        out = np.empty((2, level + 1, self.N), dtype=np.uint64)
+        o = CtOut(0, 0, 0.0, out.ctypes.data, out.size)
+        check(lib().tetris_repack(self.h, cts.ctypes.data, cts.shape[0], level, scale, C.byref(o)))
+        return out, o.level, o.scale
+
+    def repack_device(self, cts, n: int, level: int, scale: float, out, stream: int = 0):
+        """Ring repacking on torch CUDA tensors (cts int64 [n][2][level+1][N], out int64 [2][level+1][N])."""
+        o = CtOut(0, 0, 0.0, _ptr(out), out.numel())
+        check(lib().tetris_repack_device(self.h, _ptr(cts), n, level, scale, C.byref(o), stream))
+        return o.level, o.scale
 
     def pfe_scores(self, u: np.ndarray, exps: np.ndarray) -> np.ndarray:
         """PFE scoring step, host arrays: u uint64 [m][2][N], exps [p][m] -> uint64 [p][2][N]."""

@@ -12,7 +12,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 SRC = os.path.join(HERE, "csrc")
 OUT = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT, "libtetris.so")
-SOURCES = ["hostmath.cu", "ntt.cu", "elementwise.cu", "encode.cu", "context.cu", "query.cu", "serve.cu", "batch.cu", "noalloc.cu", "pfe.cu", "capi.cu"]
+SOURCES = ["hostmath.cu", "ntt.cu", "elementwise.cu", "encode.cu", "context.cu", "query.cu", "serve.cu", "batch.cu", "noalloc.cu", "pfe.cu", "repack.cu", "capi.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-ffp-contract=off",
          "--expt-relaxed-constexpr", "-Xptxas", "-warn-spills"]

@@ -798,6 +798,32 @@ int tetris_rescale_ntt_noalloc(tetris_ctx *ctx, const uint64_t *in, uint64_t *ou
 
 size_t tetris_noalloc_scratch_bytes(void) { return noalloc_scratch_bytes(); }
 
+static int repack_call(tetris_ctx *ctx, const uint64_t *cts, uint32_t n, uint32_t level, double scale,
+                       tetris_ct_out *out, void *stream, bool device) {
+    return guarded([&] {
+        TREQUIRE(ctx && out && out->data, TETRIS_EINVAL, "repack: null pointer");
+        Ctx &C = ctx->c;
+        cudaSetDevice(C.device);
+        TREQUIRE((int)level <= C.L(), TETRIS_ELEVEL, "repack: bad level");
+        TREQUIRE(out->cap_words >= (size_t)2 * (level + 1) * C.N, TETRIS_EINVAL, "repack: output buffer too small");
+        cudaStream_t s = device ? reinterpret_cast<cudaStream_t>(stream) : C.stream;
+        repack(C, cts, n, (int)level, scale, out->data, s, device);
+        out->level = level;
+        out->ncomp = 2;
+        out->scale = scale;
+    });
+}
+
+int tetris_repack(tetris_ctx *ctx, const uint64_t *cts, uint32_t n, uint32_t level, double scale,
+                  tetris_ct_out *out) {
+    return repack_call(ctx, cts, n, level, scale, out, nullptr, false);
+}
+
+int tetris_repack_device(tetris_ctx *ctx, const uint64_t *cts, uint32_t n, uint32_t level, double scale,
+                         tetris_ct_out *out, void *stream) {
+    return repack_call(ctx, cts, n, level, scale, out, stream, true);
+}
+
 int tetris_pfe_scores_device(tetris_ctx *ctx, const uint64_t *u, uint32_t m, const uint32_t *exps, uint64_t p,
                              uint64_t *out, void *stream) {
     return guarded([&] {

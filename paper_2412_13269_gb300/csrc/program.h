@@ -272,6 +272,9 @@ void batch_run(const tetris_batch_item *items, uint32_t n, int schedule, int *us
 void rescale_ntt_noalloc(Ctx &C, const u64 *in, u64 *out, int level, int ncomp, cudaStream_t s);
 size_t noalloc_scratch_bytes();
 
+// repack.cu
+void repack(Ctx &C, const u64 *cts, uint32_t count, int level, double scale, u64 *out, cudaStream_t s, bool device);
+
 // pfe.cu
 void pfe_scores(Ctx &C, const u64 *u, uint32_t m, const uint32_t *exps, uint64_t p, u64 *out, cudaStream_t s);
 

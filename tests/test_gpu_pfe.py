@@ -56,3 +56,51 @@ def test_pfe_rejects_bad_sizes(set1):
     u = np.zeros((0, 2, ctx.N), dtype=np.uint64)
     with pytest.raises(T.TetrisError):
         ctx.pfe_scores(u, np.zeros((3, 0), dtype=np.uint32))
+
+
+@pytest.fixture(scope="module")
+def repack_setup():
+    """N = 2^12, a 50-bit and a 40-bit prime and one 60-bit special prime,
+    one-prime digits; rotation keys for Algorithm 1's Galois elements."""
+    from oracle import ckks, query
+    T.build()
+    q, p = rns.gen_primes(50, 1) + rns.gen_primes(40, 1), rns.gen_primes(60, 1)
+    par = ckks.Params(12, q, p, 2.0 ** 30)
+    ctx = T.Ctx(12, q, p, 2.0 ** 30)
+    s = query.secret(par, 6, 2 * par.N // 3)
+    keys = query.make_keys(par, s, 6, 1, pfe.repack_galois(par.N))
+    for g, k in keys.rot.items():
+        ctx.load_rotation_key(g, k, 1)
+    return par, ctx, s, keys
+
+
+@pytest.mark.parametrize("count", [4096, 1000])
+def test_repack_bit_exact(repack_setup, count):
+    """Algorithm 1 on the GPU (each round one batch of t ciphertexts) equals the oracle."""
+    from oracle import ckks
+    par, ctx, s, keys = repack_setup
+    g = np.random.default_rng(count)
+    level = par.L
+    data = np.stack([np.stack([np.stack([g.integers(0, q, par.N, dtype=np.uint64) for q in par.q])
+                               for _ in range(2)]) for _ in range(count)])
+    want = pfe.repack(par, [ckks.Ct(d, level, par.scale) for d in data], keys.rot, 1)
+    got, lev, sc = ctx.repack(data, level, par.scale)
+    assert lev == level and sc == par.scale
+    assert np.array_equal(got, want.data)
+    if count == 1000:
+        torch = pytest.importorskip("torch")
+        dc = torch.from_numpy(data.view(np.int64)).cuda()
+        out = torch.empty((2, level + 1, par.N), dtype=torch.int64, device="cuda")
+        stream = torch.cuda.current_stream()
+        ctx.repack_device(dc, count, level, par.scale, out, stream.cuda_stream)
+        stream.synchronize()
+        assert np.array_equal(out.cpu().numpy().view(np.uint64), want.data)
+
+
+def test_repack_needs_its_keys():
+    T.build()
+    q, p = rns.gen_primes(50, 1) + rns.gen_primes(40, 1), rns.gen_primes(60, 1)
+    ctx = T.Ctx(12, q, p, 2.0 ** 30)
+    with pytest.raises(T.TetrisError):
+        ctx.repack(np.zeros((4, 2, 2, ctx.N), dtype=np.uint64), 1, 2.0 ** 30)
+    ctx.close()
