@@ -158,8 +158,9 @@ int tetris_encode_real(tetris_ctx *ctx, const double *slots, uint32_t n_values, 
  *   z = (y - Enc(t)) / 2                       (private threshold, Sec. 4.3.2)
  *   u = (p_S(...p_1(z)) + 1) / (2 * records)   (composite sign -> step)
  *   out = InnerSum(sum over blocks of u)       (Algorithm 2, InnerSum)
- * Each p_s is odd of degree sign_degree (7): sign_coeffs holds, per stage,
- * the coefficients of x, x^3, x^5, x^7.  w: n_attrs fresh ciphertexts at the
+ * Each p_s is odd of degree sign_degree, 7 or 15: sign_coeffs holds, per
+ * stage, the (sign_degree + 1)/2 coefficients of x, x^3, ...; a degree-7 stage
+ * takes 3 levels, a degree-15 stage 4 (Table 2's [15, 15, 15] composites).  w: n_attrs fresh ciphertexts at the
  * top level with scale Delta; f_coeffs: f_degree+1 ciphertexts, threshold:
  * one, each at any level at or above where it is used (the library moves it
  * down).  Keys needed: relinearisation and rotations by 5^(2^k) mod 2N,
@@ -185,9 +186,9 @@ typedef struct {
      * result becomes step((count - t1 + 1/2) / records) in every slot, i.e. 1 iff
      * at least t1 records pass (the 1/2 is Section 4.3.2's epsilon/2 shift for
      * integer counts).  global_threshold encrypts t1 as a count (not normalised),
-     * at a level above the step values'; global_stages odd degree-7 stages,
-     * global_coeffs their coefficients of x, x^3, x^5, x^7.  Needs
-     * 3 global_stages levels below the step values' level. */
+     * at a level above the step values'; global_stages odd stages of degree
+     * sign_degree, global_coeffs their coefficients (laid out as sign_coeffs).
+     * Needs 3 (4) levels per degree-7 (15) stage below the step values' level. */
     const tetris_ct_in *global_threshold;
     uint32_t global_stages;
     const double *global_coeffs;

@@ -169,6 +169,13 @@ class Plan:
         return self.l_lin - df                # s_i = c_k alone (k = d)
 
 
+def stage_depth(co) -> int:
+    """Levels a sign stage consumes: odd degree 7 (4 coefficients) in 3, degree 15 (8) in 4."""
+    if len(co) not in (4, 8):
+        raise ValueError("sign stages are odd polynomials of degree 7 or 15")
+    return 3 if len(co) == 4 else 4
+
+
 def make_plan(par: Params, shape: QueryShape) -> Plan:
     if shape.degree < 1 or shape.attrs < 1 or shape.records < 1 or not shape.sign_stages:
         raise ValueError("empty query")
@@ -176,7 +183,7 @@ def make_plan(par: Params, shape: QueryShape) -> Plan:
     l_lin = L - 1
     l_d = l_lin - ceil_log2(shape.degree)
     l_y = l_d - 1
-    l_u = l_y - 3 * len(shape.sign_stages)
+    l_u = l_y - sum(stage_depth(co) for co in shape.sign_stages)
     n = par.n_slots
     ragged = shape.records % n != 0
     l_out = l_u - 1 if ragged else l_u
@@ -187,8 +194,7 @@ def make_plan(par: Params, shape: QueryShape) -> Plan:
     ns = len(shape.sign_stages)
     for s, co in enumerate(shape.sign_stages):
         co = [float(c) for c in co]
-        if len(co) != 4:
-            raise ValueError("sign stages are odd degree-7 polynomials")
+        stage_depth(co)
         if s == 0:   # z = (y - t)/2 folded in: a_k -> a_k * 2^-(2k+1)
             co = [c * (0.5 ** (2 * k + 1)) for k, c in enumerate(co)]
         if s == ns - 1:   # step = (p + 1) / 2, normalised by 1/records
@@ -197,12 +203,11 @@ def make_plan(par: Params, shape: QueryShape) -> Plan:
     gco = []
     for s, co in enumerate(shape.global_stages):
         co = [float(c) for c in co]
-        if len(co) != 4:
-            raise ValueError("sign stages are odd degree-7 polynomials")
+        stage_depth(co)
         if s == len(shape.global_stages) - 1:
             co = [c / 2.0 for c in co]
         gco.append(co)
-    l_ret = l_out - 3 * len(gco) if gco else 1
+    l_ret = l_out - sum(stage_depth(co) for co in gco) if gco else 1
     if l_ret < 1:
         raise ValueError(f"global threshold needs more levels: ends at level {l_ret}")
     return Plan(S=S, l_lin=l_lin, l_d=l_d, l_y=l_y, l_u=l_u, l_out=l_out, l_ret=l_ret, global_coeffs=gco,
@@ -341,23 +346,37 @@ class Evaluator:
         out.scale = self.plan.S[level_out]
         return out
 
-    def sign_stage(self, u: Ct, co) -> Ct:
-        """p(u) = a0 u + a1 u^3 + a2 u^5 + a3 u^7 in depth 3 with four
-        relinearisations: a0 u + [(a1 u) u^2 + ((a3 u) u^2 + a2 u) u^4], the two
-        degree-2 products in brackets formed at level l-2 and relinearised once."""
+    def odd7(self, a, u2: Ct, u2d: Ct, u4: Ct, l: int) -> Ct:
+        """a0 u + [(a1 u) u^2 + ((a3 u) u^2 + a2 u) u^4] from the adjusts
+        a = (a3 u at l-1, a2 u at l-2, a1 u at l-2, a0 u at l-3): the two
+        degree-2 products in brackets formed at level l-2 and relinearised
+        once; ends at level l-3."""
         par = self.par
+        t7 = self.mul(a[0], u2)
+        inner = self.add(t7, a[1])
+        T = ckks.add(par, ckks.tensor(par, a[2], u2d), ckks.tensor(par, inner, u4))
+        return self.add(a[3], self.relin_rescale(T, l - 3))
+
+    def sign_stage(self, u: Ct, co) -> Ct:
+        """p(u) = sum_k a_k u^(2k+1).  Degree 7 (4 coefficients): depth 3,
+        four relinearisations.  Degree 15 (8): depth 4 as A(u) + u^8 B(u),
+        A and B the degree-7 parts of the low and high coefficients (u^2, u^4
+        shared), eight relinearisations."""
         l = u.level
+        lv = [l - 1, l - 2, l - 2, l - 3]
+        a = [self.adjust(u, lv[i], co[3 - i]) for i in range(4)]
+        if len(co) == 8:
+            a += [self.adjust(u, lv[i], co[7 - i]) for i in range(4)]
         u2 = self.mul(u, u)
         u4 = self.mul(u2, u2)
-        b3 = self.adjust(u, l - 1, co[3])
-        t7 = self.mul(b3, u2)
-        inner = self.add(t7, self.adjust(u, l - 2, co[2]))
-        b1 = self.adjust(u, l - 2, co[1])
         u2d = self.adjust(u2, l - 2)
-        T = ckks.add(par, ckks.tensor(par, b1, u2d), ckks.tensor(par, inner, u4))
-        t = self.relin_rescale(T, l - 3)
-        t1 = self.adjust(u, l - 3, co[0])
-        return self.add(t1, t)
+        A = self.odd7(a[:4], u2, u2d, u4, l)
+        if len(co) == 4:
+            return A
+        u8 = self.mul(u4, u4)
+        B = self.odd7(a[4:], u2, u2d, u4, l)
+        P = self.relin_rescale(ckks.tensor(self.par, u8, B), l - 4)
+        return self.add(self.adjust(A, l - 4), P)
 
     def per_query(self, q: EncQuery, degree: int):
         """Bring the encrypted coefficients and threshold to their levels (once per query)."""

@@ -377,8 +377,10 @@ class Ctx:
         W = (CtIn * len(w))(*[CtIn(lv, 2, sc, _ptr(x)) for x, (lv, sc) in zip(w, w_meta)])
         Cc = (CtIn * len(c))(*[CtIn(lv, 2, sc, _ptr(x)) for x, (lv, sc) in zip(c, c_meta)])
         T = CtIn(t_meta[0], 2, t_meta[1], _ptr(t))
-        sc = np.ascontiguousarray(np.asarray(sign_coeffs, dtype=np.float64).reshape(-1))
-        q = Query(len(w), W, len(c) - 1, Cc, C.pointer(T), sc.size // 4, 7,
+        sc2 = np.asarray(sign_coeffs, dtype=np.float64)
+        ncoef = sc2.shape[-1] if sc2.ndim == 2 else 4      # per stage: 4 (degree 7) or 8 (degree 15)
+        sc = np.ascontiguousarray(sc2.reshape(-1))
+        q = Query(len(w), W, len(c) - 1, Cc, C.pointer(T), sc.size // ncoef, 2 * ncoef - 1,
                   sc.ctypes.data_as(C.POINTER(C.c_double)), int(total_records))
         keep = [W, Cc, T, sc]
         if glob is not None:
@@ -386,7 +388,7 @@ class Ctx:
             T1 = CtIn(lv, 2, scl, _ptr(t1))
             g = np.ascontiguousarray(np.asarray(gco, dtype=np.float64).reshape(-1))
             q.global_threshold = C.pointer(T1)
-            q.global_stages = g.size // 4
+            q.global_stages = g.size // ncoef
             q.global_coeffs = g.ctypes.data_as(C.POINTER(C.c_double))
             keep += [T1, g]
         return q, keep

@@ -214,14 +214,14 @@ struct QuerySpec {
     std::vector<double> c_scale;
     int t_level = 0;
     double t_scale = 0;
-    std::vector<std::array<double, 4>> stages;
+    std::vector<std::vector<double>> stages;   // per stage: coefficients of x, x^3, ... (4 or 8)
     int bpl = 0;
     int loge = 3;                // NTT register-group width (log2 elements per thread)
     uint64_t total_records = 0;  // 0: the database's own record count
     // global threshold (none when gstages is empty): t1's level and scale
     int g_level = 0;
     double g_scale = 0;
-    std::vector<std::array<double, 4>> gstages;
+    std::vector<std::vector<double>> gstages;
     std::string key(uint32_t db) const {
         std::ostringstream o;
         o << "q" << db << ":" << attrs << ":" << degree << ":" << bpl << ":" << loge << ":" << t_level << ":"

@@ -25,12 +25,12 @@ struct QPlan {
     int l_ret = 1;  // the InnerSum and the returned ciphertext: drop to level 1 first
     bool ragged;
     double mask_scale;
-    std::vector<std::array<double, 4>> co;
+    std::vector<std::vector<double>> co;
     double step_const;
     int degree = 0;
     int g = 0, m = 0, bb = 0, df = 0;  // baby-step giant-step schedule (g = 0: plain powers)
     // global threshold: folded stage coefficients (empty: none) and the record count R
-    std::vector<std::array<double, 4>> gco;
+    std::vector<std::vector<double>> gco;
     double records_norm = 0;
     int coef_level(int k) const;
 };
@@ -78,15 +78,22 @@ int QPlan::coef_level(int k) const {
     return l_lin - df;                      // s_i = c_k alone (k = d)
 }
 
-QPlan make_plan(const Ctx &C, uint64_t records, int degree, const std::vector<std::array<double, 4>> &stages,
-                uint64_t norm_records = 0, const std::vector<std::array<double, 4>> &gstages = {}) {
+// levels a sign stage consumes: 3 for degree 7, 4 for degree 15
+static int stage_depth(const std::vector<double> &co) {
+    TREQUIRE(co.size() == 4 || co.size() == 8, TETRIS_EINVAL, "sign stages are odd polynomials of degree 7 or 15");
+    return co.size() == 4 ? 3 : 4;
+}
+
+QPlan make_plan(const Ctx &C, uint64_t records, int degree, const std::vector<std::vector<double>> &stages,
+                uint64_t norm_records = 0, const std::vector<std::vector<double>> &gstages = {}) {
     TREQUIRE(degree >= 1 && !stages.empty() && records >= 1, TETRIS_EINVAL, "empty query");
     QPlan p;
     const int L = C.L();
     p.l_lin = L - 1;
     p.l_d = p.l_lin - ceil_log2(degree);
     p.l_y = p.l_d - 1;
-    p.l_u = p.l_y - 3 * (int)stages.size();
+    p.l_u = p.l_y;
+    for (auto &co : stages) p.l_u -= stage_depth(co);
     const uint64_t n = C.N / 2;
     p.ragged = records % n != 0;
     p.l_out = p.ragged ? p.l_u - 1 : p.l_u;
@@ -94,11 +101,11 @@ QPlan make_plan(const Ctx &C, uint64_t records, int degree, const std::vector<st
     const double R = (double)(norm_records ? norm_records : records);
     const size_t ns = stages.size();
     for (size_t s = 0; s < ns; s++) {
-        std::array<double, 4> c = stages[s];
+        std::vector<double> c = stages[s];
         if (s == 0)  // z = (y - t)/2 folded into the first stage
-            for (int k = 0; k < 4; k++) c[k] = c[k] * std::ldexp(1.0, -(2 * k + 1));
+            for (size_t k = 0; k < c.size(); k++) c[k] = c[k] * std::ldexp(1.0, -(2 * (int)k + 1));
         if (s == ns - 1)  // step = (p + 1)/2, normalised by 1/records
-            for (int k = 0; k < 4; k++) c[k] = c[k] / (2.0 * R);
+            for (size_t k = 0; k < c.size(); k++) c[k] = c[k] / (2.0 * R);
         p.co.push_back(c);
     }
     p.step_const = 1.0 / (2.0 * R);
@@ -108,13 +115,14 @@ QPlan make_plan(const Ctx &C, uint64_t records, int degree, const std::vector<st
     // global threshold: step = (p + 1)/2 folded into the last stage
     p.records_norm = R;
     for (size_t s = 0; s < gstages.size(); s++) {
-        std::array<double, 4> c = gstages[s];
+        std::vector<double> c = gstages[s];
         if (s + 1 == gstages.size())
-            for (int k = 0; k < 4; k++) c[k] = c[k] / 2.0;
+            for (size_t k = 0; k < c.size(); k++) c[k] = c[k] / 2.0;
         p.gco.push_back(c);
     }
     if (!p.gco.empty()) {
-        p.l_ret = p.l_out - 3 * (int)p.gco.size();
+        p.l_ret = p.l_out;
+        for (auto &co : p.gco) p.l_ret -= stage_depth(co);
         TREQUIRE(p.l_ret >= 1, TETRIS_ELEVEL,
                  "global threshold needs more levels: it would end at level " + std::to_string(p.l_ret));
     }
@@ -127,22 +135,37 @@ static CtH relin_rescale_to(Rec &R, const CtH &t, int level_out) {
     return o;
 }
 
-// p(u) = a0 u + a1 u^3 + a2 u^5 + a3 u^7 in depth 3 with four relinearisations:
-//   a0 u + [(a1 u) u^2 + ((a3 u) u^2 + a2 u) u^4],
-// the two degree-2 products in brackets formed at level l-2 and relinearised once.
-static CtH sign_stage(Rec &R, const CtH &u, const std::array<double, 4> &co) {
+// The odd degree-7 part a0 u + [(a1 u) u^2 + ((a3 u) u^2 + a2 u) u^4] of a stage
+// at level l, from the adjusts a = (a3 u at l-1, a2 u at l-2, a1 u at l-2,
+// a0 u at l-3), u2 (l-1), u2d = u2 at l-2 and u4 (l-2): the two degree-2
+// products in brackets formed at level l-2 and relinearised once; ends at l-3.
+static CtH odd7(Rec &R, const CtH *a, const CtH &u2, const CtH &u2d, const CtH &u4, int l) {
+    CtH t7 = R.mul(a[0], u2);
+    CtH inner = R.add(t7, a[1]);
+    CtH T = R.tensor_add(R.tensor(a[2], u2d), inner, u4);
+    CtH t = relin_rescale_to(R, T, l - 3);
+    return R.add(a[3], t);
+}
+
+// One sign stage p(u) = sum_k a_k u^(2k+1): degree 7 in depth 3 with four
+// relinearisations; degree 15 in depth 4 as A(u) + u^8 B(u), A and B the
+// degree-7 parts of the low and high coefficients (u^2, u^4 shared), eight
+// relinearisations.  The adjusts of u are independent: one pair of transforms.
+static CtH sign_stage(Rec &R, const CtH &u, const std::vector<double> &co) {
     const int l = u.level;
-    // the four adjusts of u are independent: one pair of transforms
-    std::vector<CtH> a = R.adjust_many({{u, l - 1, co[3]}, {u, l - 2, co[2]}, {u, l - 2, co[1]}, {u, l - 3, co[0]}});
-    const CtH &b3 = a[0], &a2u = a[1], &b1 = a[2], &t1 = a[3];
+    std::vector<Rec::AdjustItem> items = {{u, l - 1, co[3]}, {u, l - 2, co[2]}, {u, l - 2, co[1]}, {u, l - 3, co[0]}};
+    if (co.size() == 8)
+        for (int h = 7; h >= 4; h--) items.push_back({u, h == 7 ? l - 1 : (h == 4 ? l - 3 : l - 2), co[h]});
+    std::vector<CtH> a = R.adjust_many(items);
     CtH u2 = R.mul(u, u);
     CtH u4 = R.mul(u2, u2);
-    CtH t7 = R.mul(b3, u2);
-    CtH inner = R.add(t7, a2u);
     CtH u2d = R.adjust(u2, l - 2, 1.0);
-    CtH T = R.tensor_add(R.tensor(b1, u2d), inner, u4);
-    CtH t = relin_rescale_to(R, T, l - 3);
-    return R.add(t1, t);
+    CtH A = odd7(R, a.data(), u2, u2d, u4, l);
+    if (co.size() == 4) return A;
+    CtH u8 = R.mul(u4, u4);
+    CtH B = odd7(R, a.data() + 4, u2, u2d, u4, l);
+    CtH P = relin_rescale_to(R, R.tensor(u8, B), l - 4);
+    return R.add(R.adjust(A, l - 4, 1.0), P);
 }
 
 static CtH eval_blocks(Rec &R, const Database &db, const QPlan &pl, int b0, int nb, const u64 *wbase,
@@ -384,7 +407,9 @@ std::unique_ptr<Program> record_query(Ctx &C, const Database &db, const QuerySpe
 QuerySpec spec_of(const Ctx &C, const Database &db, const tetris_query *q) {
     TREQUIRE(q && q->w && q->f_coeffs && q->threshold && q->sign_coeffs, TETRIS_EINVAL, "query: null pointer");
     TREQUIRE((int)q->n_attrs == db.attrs, TETRIS_EINVAL, "query: attribute count differs from the database");
-    TREQUIRE(q->sign_degree == 7, TETRIS_EINVAL, "query: sign stages must be odd degree-7 polynomials");
+    TREQUIRE(q->sign_degree == 7 || q->sign_degree == 15, TETRIS_EINVAL,
+             "query: sign stages must be odd polynomials of degree 7 or 15");
+    const uint32_t nco = (q->sign_degree + 1) / 2;
     TREQUIRE(q->sign_stages >= 1 && q->f_degree >= 1, TETRIS_EINVAL, "query: empty polynomial");
     QuerySpec s;
     s.attrs = q->n_attrs;
@@ -404,11 +429,8 @@ QuerySpec spec_of(const Ctx &C, const Database &db, const tetris_query *q) {
              TETRIS_EINVAL, "query: bad threshold ciphertext");
     s.t_level = q->threshold->level;
     s.t_scale = q->threshold->scale;
-    for (uint32_t st = 0; st < q->sign_stages; st++) {
-        std::array<double, 4> a;
-        for (int k = 0; k < 4; k++) a[k] = q->sign_coeffs[st * 4 + k];
-        s.stages.push_back(a);
-    }
+    for (uint32_t st = 0; st < q->sign_stages; st++)
+        s.stages.push_back(std::vector<double>(q->sign_coeffs + st * nco, q->sign_coeffs + (st + 1) * nco));
     s.bpl = C.blocks_per_launch;
     s.loge = C.nt.loge;
     TREQUIRE(q->total_records == 0 || q->total_records >= db.records, TETRIS_EINVAL,
@@ -421,11 +443,8 @@ QuerySpec spec_of(const Ctx &C, const Database &db, const tetris_query *q) {
                  "query: bad global threshold ciphertext");
         s.g_level = g.level;
         s.g_scale = g.scale;
-        for (uint32_t st = 0; st < q->global_stages; st++) {
-            std::array<double, 4> a;
-            for (int k = 0; k < 4; k++) a[k] = q->global_coeffs[st * 4 + k];
-            s.gstages.push_back(a);
-        }
+        for (uint32_t st = 0; st < q->global_stages; st++)
+            s.gstages.push_back(std::vector<double>(q->global_coeffs + st * nco, q->global_coeffs + (st + 1) * nco));
     }
     return s;
 }
@@ -564,7 +583,7 @@ void plan_info(Ctx &C, uint32_t dbh, uint32_t degree, uint32_t stages, tetris_pl
     }
     s.t_level = C.L();
     s.t_scale = C.scale;
-    for (uint32_t i = 0; i < stages; i++) s.stages.push_back({35.0 / 16, -35.0 / 16, 21.0 / 16, -5.0 / 16});
+    for (uint32_t i = 0; i < stages; i++) s.stages.push_back({35.0 / 16, -35.0 / 16, 21.0 / 16, -5.0 / 16});  // f3
     s.bpl = C.blocks_per_launch;
     s.loge = C.nt.loge;
     QPlan pl = make_plan(C, it->second.records, degree, s.stages);

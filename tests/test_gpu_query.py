@@ -255,3 +255,35 @@ def test_global_threshold_bit_exact(deep, p_pos, t1_frac):
     bit = ckks.decrypt_slots(par, ckks.Ct(got.copy(), lev, sc), deep.s).real
     assert np.max(np.abs(bit - (1 if p_pos > 0.5 else 0))) < 2.0 ** -12
     ctx.free_database(dbh)
+
+
+@pytest.fixture(scope="module")
+def chain15():
+    """Test-only chain with 15 primes of 40 bits after q_0: three degree-15 stages."""
+    return Chain(n40=15, seed=12)
+
+
+def test_degree15_minimax_stages_bit_exact(chain15):
+    """Three degree-15 minimax stages (alpha = 8, the stored Remez coefficients):
+    residues equal the oracle's; the count is exact for records within 2^-7.4 of
+    the threshold."""
+    import json
+    import os
+    with open(os.path.join(os.path.dirname(__file__), "golden", "minimax_sign.json")) as f:
+        stages = np.array(json.load(f)["alpha8_15x3"]["stages"])
+    par, ctx = chain15.par, chain15.ctx
+    R = 2048
+    v = np.random.default_rng(22).integers(0, 254, R)
+    vals = np.where(v >= 127, v + 2, v).astype(np.uint8)[:, None]
+    qv = synth.QueryValues(w=np.array([1.0]), c=np.array([0.0, 1.0]), t=0.0)
+    shape = query.QueryShape(R, 1, 1, [list(s) for s in stages])
+    plan = query.make_plan(par, shape)
+    db = query.encode_database(par, plan, vals)
+    eq = query.encrypt_query(par, chain15.s, qv, 22)
+    want = query.evaluate_query(par, chain15.keys, shape, db, eq)
+    dbh = upload_encoded(ctx, par, plan, db, R, 1)
+    got, lev, sc = gpu_query(ctx, dbh, eq, stages)
+    assert lev == want.level and np.array_equal(got, want.data)
+    z = ckks.decrypt_slots(par, ckks.Ct(got.copy(), lev, sc), chain15.s).real
+    assert int(np.rint(z[0] * R)) == int((vals[:, 0] > 128).sum())
+    ctx.free_database(dbh)

@@ -67,3 +67,41 @@ def test_golden_file_matches_oracle():
     stages, err = sign.composite_minimax(g["alpha"], g["degrees"])
     assert np.allclose(np.array(stages), np.array(g["stages"]), rtol=1e-12, atol=0)
     assert abs(err - g["error"]) <= 1e-12 * err
+
+
+def load_stages(name):
+    with open(GOLDEN) as f:
+        return json.load(f)[name]
+
+
+def test_degree15_stages_exact_count_near_threshold():
+    """The query with the alpha = 8 composite (three degree-15 stages, depth 4
+    each): one attribute, f(x) = x, t = 0, values avoiding 127-128 so every
+    |z| >= 2^-7.4 > 2^-8.  The decrypted count is the exact count -- which
+    three f3 stages (margin 2^-1.84 at tolerance 2^-12) cannot give here."""
+    import synth
+    from oracle import ckks, rns
+    g = load_stages("alpha8_15x3")
+    stages = g["stages"]
+    q = rns.gen_primes(50, 1) + rns.gen_primes(40, 15)
+    par = ckks.Params(12, q, rns.gen_primes(60, 1), 2.0 ** 40)
+    R = 2048
+    rng = np.random.default_rng(21)
+    v = rng.integers(0, 254, R)
+    vals = np.where(v >= 127, v + 2, v).astype(np.uint8)[:, None]
+    qv = synth.QueryValues(w=np.array([1.0]), c=np.array([0.0, 1.0]), t=0.0)
+    shape = query.QueryShape(R, 1, 1, stages)
+    plan = query.make_plan(par, shape)
+    assert plan.l_u == plan.l_y - 12
+    s = query.secret(par, 4, 2 * par.N // 3)
+    keys = query.make_keys(par, s, 4, 1, query.innersum_galois(par))
+    db = query.encode_database(par, plan, vals)
+    eq = query.encrypt_query(par, s, qv, 4)
+    out = query.evaluate_query(par, keys, shape, db, eq)
+    got = ckks.decrypt_slots(par, out, s).real
+    ref = query.fp64_pipeline(vals, qv, stages)
+    assert np.min(np.abs(ref.z)) > 2.0 ** -8
+    assert int(np.rint(got[0] * R)) == ref.exact == int((vals[:, 0] > 128).sum())
+    assert abs(got[0] * R - ref.count) < 0.05
+    f3 = query.fp64_pipeline(vals, qv, [query.F3] * 3)
+    assert abs(f3.count - f3.exact) > 1.0    # f3 stages miss records this close to the threshold
