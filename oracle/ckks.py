@@ -357,3 +357,66 @@ def rotate(par, ct: Ct, g: int, rotk: np.ndarray, alpha: int) -> Ct:
     ks = keyswitch(par, t.data[1], ct.level, rotk, alpha)
     mods = par.q[: ct.level + 1]
     return Ct(np.stack([rns_add(t.data[0], ks[0], mods), ks[1]]), ct.level, ct.scale)
+
+
+# ---------------------------------------------------------------------------
+# Base-2^w decomposition inside the key switch (Table 1, `base2`: needed when P
+# cannot grow without lowering security).  One-prime digits: the gadget digit
+# (i, b) is q_i's CRT unit times 2^(w b), b < B = ceil(max prime bits / w); the
+# polynomial d splits as d_i = sum_b d_(i,b) 2^(w b) with 0 <= d_(i,b) < 2^w, so
+# the key inner product multiplies the small pieces (noise ~ 2^w instead of q_i)
+# and the pieces need no base conversion (they are the same integers modulo
+# every prime).
+# ---------------------------------------------------------------------------
+def base2_pieces(par: Params, w: int) -> int:
+    return max(-(-int(q).bit_length() // w) for q in par.q)
+
+
+def switch_key_base2(par: Params, s_to: np.ndarray, s_from_rns: np.ndarray, a: np.ndarray, e: np.ndarray,
+                     w: int) -> np.ndarray:
+    """a: uint64[(L+1) B][L+1+K][N], e: int64[(L+1) B][N] -> uint64[(L+1) B][2][L+1+K][N];
+    digit i B + b holds (-a s + e + P 2^(w b) s_from [limb i only], a)."""
+    mods = par.moduli
+    nqp = len(mods)
+    B = base2_pieces(par, w)
+    nd = (par.L + 1) * B
+    assert a.shape == (nd, nqp, par.N) and e.shape == (nd, par.N)
+    s_rns = rns.to_rns(s_to, mods)
+    out = np.empty((nd, 2, nqp, par.N), dtype=np.uint64)
+    for i in range(par.L + 1):
+        qi = int(mods[i])
+        for b in range(B):
+            j = i * B + b
+            as_ = rns_mul(a[j], s_rns, mods, par.psi)
+            bj = rns_sub(rns.to_rns(e[j], mods), as_, mods)
+            term = rns_mul_int(s_from_rns[i:i + 1], (par.P << (w * b)) % qi, [qi])
+            bj[i:i + 1] = rns_add(bj[i:i + 1], term, [qi])
+            out[j, 0] = bj
+            out[j, 1] = a[j]
+    return out
+
+
+def keyswitch_base2(par: Params, d: np.ndarray, level: int, evk: np.ndarray, w: int) -> np.ndarray:
+    """SwitchKey(d, swk) with the base-2^w gadget at the given level: sum over the
+    pieces of d_(i,b) * swk_(i,b) over Q_level P, then ModDown by P."""
+    nl, K, N = level + 1, par.K, par.N
+    B = evk.shape[0] // (par.L + 1)
+    tidx = list(range(nl)) + [par.L + 1 + k for k in range(K)]
+    tmods = [par.moduli[t] for t in tidx]
+    tpsi = [par.psi[t] for t in tidx]
+    acc = np.zeros((2, nl + K, N), dtype=np.uint64)
+    mask = np.uint64((1 << w) - 1)
+    for i in range(nl):
+        di = np.asarray(d[i], dtype=np.uint64)
+        for b in range(B):
+            piece = ((di >> np.uint64(w * b)) & mask).astype(np.int64)
+            pr = rns.to_rns(piece, tmods)
+            key = evk[i * B + b][:, tidx]
+            for c in range(2):
+                acc[c] = rns_add(acc[c], rns_mul(pr, np.ascontiguousarray(key[c]), tmods, tpsi), tmods)
+    out = np.empty((2, nl, N), dtype=np.uint64)
+    for c in range(2):
+        o = np.empty((nl, N), dtype=np.uint64)
+        lib().or_moddown(ptr(np.ascontiguousarray(acc[c])), nl, K, ptr(u64arr(tmods)), N, ptr(o))
+        out[c] = o
+    return out
