@@ -243,7 +243,12 @@ enum {
     TETRIS_OPT_KS_ALPHA = 3,           /* read-only: alpha of the loaded keys */
     TETRIS_OPT_PROFILE = 4,            /* 1: run queries eagerly with a CUDA event pair around
                                           every launch, accumulating per-kernel statistics */
-    TETRIS_OPT_NTT_GROUP = 5           /* log2 of the NTT elements a thread holds: 3 or 4 */
+    TETRIS_OPT_NTT_GROUP = 5,          /* log2 of the NTT elements a thread holds: 3 or 4 */
+    TETRIS_OPT_KS_BASE2 = 6            /* w of the base-2^w decomposition of key-switch digits
+                                          (Table 1's base2), 0 for none, else 8..62; needs
+                                          alpha 1; keys then carry (L+1) ceil(bits/w) digits,
+                                          digit i B + b with P 2^(w b) on limb i.  Set before
+                                          loading or generating keys: changing it drops them */
 };
 int tetris_set_option(tetris_ctx *ctx, int option, int64_t value);
 int tetris_get_option(tetris_ctx *ctx, int option, int64_t *value);

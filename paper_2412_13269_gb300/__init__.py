@@ -26,7 +26,7 @@ ERRORS = {-1: "EINVAL", -2: "ENOMEM", -3: "ECUDA", -4: "ELEVEL", -5: "ENOTFOUND"
 OP_ADD, OP_SUB, OP_TENSOR, OP_RELIN, OP_RESCALE, OP_MUL_INT, OP_ADD_INT = 1, 2, 3, 4, 5, 6, 7
 OP_AUTOMORPHISM, OP_ROTATE, OP_KEYSWITCH, OP_MUL_PLAIN, OP_NTT, OP_INNERSUM, OP_DROP = 8, 9, 10, 11, 12, 13, 14
 OP_RELIN_RESCALE, OP_RESCALE_MUL_INT = 15, 16
-OPT_BLOCKS_PER_LAUNCH, OPT_USE_GRAPH, OPT_KS_ALPHA, OPT_PROFILE, OPT_NTT_GROUP = 1, 2, 3, 4, 5
+OPT_BLOCKS_PER_LAUNCH, OPT_USE_GRAPH, OPT_KS_ALPHA, OPT_PROFILE, OPT_NTT_GROUP, OPT_KS_BASE2 = 1, 2, 3, 4, 5, 6
 
 
 def build(force: bool = False) -> str:

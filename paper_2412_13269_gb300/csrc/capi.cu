@@ -109,26 +109,38 @@ static void build_tables(Ctx &C) {
 // ---------------------------------------------------------------------------
 // Keys
 // ---------------------------------------------------------------------------
+// base-2^w pieces of a one-prime digit (1 without the decomposition)
+static int key_pieces(const Ctx &C) {
+    if (C.base2 == 0) return 1;
+    int bits = 0;
+    for (u64 q : C.q) bits = std::max(bits, 64 - __builtin_clzll(q));
+    return (bits + C.base2 - 1) / C.base2;
+}
+
+static void drop_keys(Ctx &C) {
+    cudaStreamSynchronize(C.stream);
+    C.programs.clear();
+    C.relin = Key();
+    C.rot.clear();
+}
+
 static void set_alpha(Ctx &C, uint32_t alpha) {
     TREQUIRE(alpha >= 1 && (int)alpha <= kMaxConvSrc, TETRIS_EINVAL, "alpha must be in [1, 4]");
-    const int dnum = (C.L() + 1 + alpha - 1) / alpha;
-    TREQUIRE(dnum <= 32, TETRIS_EINVAL, "too many key digits (at most 32)");
-    if (C.alpha != 0 && C.alpha != (int)alpha) {  // a new digit size: the old keys are unusable with it
-        cudaStreamSynchronize(C.stream);
-        C.programs.clear();
-        C.relin = Key();
-        C.rot.clear();
-    }
+    TREQUIRE(C.base2 == 0 || alpha == 1, TETRIS_EINVAL, "the base-2^w decomposition takes one-prime digits (alpha 1)");
+    const int dnum = (C.L() + 1 + alpha - 1) / alpha * key_pieces(C);
+    TREQUIRE(dnum <= kMaxKeyDigits, TETRIS_EINVAL, "too many key digits (at most 64)");
+    if (C.alpha != 0 && C.alpha != (int)alpha) drop_keys(C);  // a new digit size: the old keys are unusable with it
     C.alpha = alpha;
 }
 
 static Key load_key(Ctx &C, const uint64_t *evk, size_t n_words, uint32_t alpha) {
     set_alpha(C, alpha);
-    const int dnum = (C.L() + 1 + alpha - 1) / alpha, nqp = C.nqp();
+    const int dnum = (C.L() + 1 + alpha - 1) / alpha * key_pieces(C), nqp = C.nqp();
     const size_t N = C.N;
     TREQUIRE(evk && n_words == (size_t)dnum * 2 * nqp * N, TETRIS_EINVAL, "key: wrong size");
     Key k;
     k.dnum = dnum;
+    k.pieces = key_pieces(C);
     k.buf = upload(C.pool, evk, n_words * 8, C.stream);
     Program P;
     Rec R(C, P);
@@ -163,10 +175,13 @@ static BufPtr secret_ntt(Ctx &C, Program &P, Rec &R, const int64_t *s, int nlimb
     return out;
 }
 
-// swk_j = (-a_j s + e_j + w_j P s_from, a_j) over Q P, NTT domain (Section 2.4.1)
+// swk_j = (-a_j s + e_j + w_j P s_from, a_j) over Q P, NTT domain (Section 2.4.1);
+// with the base-2^w decomposition (Table 1 base2) digit j = i B + b carries
+// P 2^(w b) s_from on limb i.
 static Key gen_key(Ctx &C, const int64_t *s, const uint64_t *a, const int64_t *e, uint32_t alpha, uint32_t galois) {
     set_alpha(C, alpha);
-    const int dnum = (C.L() + 1 + alpha - 1) / alpha, nqp = C.nqp();
+    const int B = key_pieces(C);
+    const int dnum = (C.L() + 1 + alpha - 1) / alpha * B, nqp = C.nqp();
     const size_t N = C.N;
     TREQUIRE(s && a && e, TETRIS_EINVAL, "keygen: null input");
     Program P;
@@ -191,6 +206,7 @@ static Key gen_key(Ctx &C, const int64_t *s, const uint64_t *a, const int64_t *e
     }
     Key k;
     k.dnum = dnum;
+    k.pieces = B;
     k.buf = C.pool.alloc((size_t)dnum * 2 * nqp * N);
     BufPtr ad = upload(P.pool, a, (size_t)dnum * nqp * N * 8, C.stream);
     BufPtr ed = upload(P.pool, e, (size_t)dnum * N * 8, C.stream);
@@ -231,11 +247,13 @@ static Key gen_key(Ctx &C, const int64_t *s, const uint64_t *a, const int64_t *e
             y.b = x.dst;
             y.dst = kl(j, 0, t);
             m2.push_back(y);
-            const int lo = j * (int)alpha, hi = std::min(C.L() + 1, (j + 1) * (int)alpha);
+            const int jd = j / B, piece = j % B;  // CRT digit and base-2^w piece
+            const int lo = jd * (int)alpha, hi = std::min(C.L() + 1, (jd + 1) * (int)alpha);
             if (t >= lo && t < hi) {
                 const u64 qt = C.all[t];
                 u64 pm = 1 % qt;
                 for (u64 pk : C.p) pm = h_mulmod(pm, pk % qt, qt);
+                for (int r = 0; r < piece * C.base2; r++) pm = h_mulmod(pm, 2, qt);
                 EwJob z{};
                 z.op = EW_ADD_MUL_CONST;
                 z.prime = t;
@@ -717,6 +735,14 @@ int tetris_set_option(tetris_ctx *ctx, int option, int64_t value) {
                 TREQUIRE(value == 3 || value == 4, TETRIS_EINVAL, "NTT group must be 3 or 4");
                 C.nt.loge = (int)value;
                 break;
+            case TETRIS_OPT_KS_BASE2:
+                TREQUIRE(value == 0 || (value >= 8 && value <= 62), TETRIS_EINVAL, "base2 bits must be 0 or 8..62");
+                if (C.base2 != (int)value) {
+                    drop_keys(C);
+                    C.base2 = (int)value;
+                    C.alpha = 0;
+                }
+                break;
             default:
                 throw Error(TETRIS_EINVAL, "unknown or read-only option");
         }
@@ -731,6 +757,7 @@ int tetris_get_option(tetris_ctx *ctx, int option, int64_t *value) {
             case TETRIS_OPT_BLOCKS_PER_LAUNCH: *value = C.blocks_per_launch; break;
             case TETRIS_OPT_USE_GRAPH: *value = C.use_graph; break;
             case TETRIS_OPT_KS_ALPHA: *value = C.alpha; break;
+            case TETRIS_OPT_KS_BASE2: *value = C.base2; break;
             case TETRIS_OPT_PROFILE: *value = C.profile; break;
             case TETRIS_OPT_NTT_GROUP: *value = C.nt.loge; break;
             default: throw Error(TETRIS_EINVAL, "unknown option");

@@ -202,6 +202,7 @@ const char *load_name(int m) {
         case LOAD_CONV_PRE: return "convpre";
         case LOAD_REDUCE: return "reduce";
         case LOAD_INT64: return "int64";
+        case LOAD_PIECE: return "piece";
     }
     return "plain";
 }
@@ -301,6 +302,7 @@ void Rec::ntt(bool inverse, const std::vector<NttJob> &jobs, int load_mode, int 
     double conv = 0;
     if (load_mode == LOAD_CONV_PRE)
         for (auto &j : jobs) conv += j.nsrc;
+    if (load_mode == LOAD_PIECE) conv = n;  // one Shoup product per element
     const double first_log = inverse ? log2 : log1, second_log = inverse ? log1 : log2;
     const double mm1 = (double)n * N * first_log / 2 + conv * N;
     if (passes & 1)
@@ -644,13 +646,16 @@ CtH Rec::keyswitch(int B, int l, const std::function<const u64 *(int, int)> &d, 
     const int dnum = (nl + alpha - 1) / alpha;
     const size_t N = C.N;
     TREQUIRE(K >= 1 && K <= kMaxConvSrc && alpha <= kMaxConvSrc, TETRIS_EINVAL, "keyswitch: K or alpha too large");
-    TREQUIRE(dnum <= key.dnum && dnum <= 32, TETRIS_EINVAL, "keyswitch: key has too few digits");
+    const int pieces = key.pieces;  // base-2^w pieces per one-prime digit (1: plain hybrid)
+    TREQUIRE(pieces == 1 || alpha == 1, TETRIS_EINVAL, "keyswitch: base-2^w pieces need one-prime digits");
+    const int nd = pieces == 1 ? dnum : nl * pieces;  // key digits this level uses
+    TREQUIRE(nd <= key.dnum && nd <= kMaxKeyDigits, TETRIS_EINVAL, "keyswitch: key has too few digits");
     const int nQP = C.nqp();
     const std::string saved_prefix = prefix;
     prefix = "ks." + prefix;
     P.ks_count += 1;
     // algorithmic bytes of one batched keyswitch: B inputs, the key limbs it uses once, 2B outputs
-    P.ks_bytes += ((double)B * nl + 2.0 * dnum * ntg + 2.0 * B * nl) * N * 8;
+    P.ks_bytes += ((double)B * nl + 2.0 * nd * ntg + 2.0 * B * nl) * N * 8;
     // 1. d -> coefficient domain, each limb already multiplied by its digit's
     //    [(Q_j/q_i)^-1]_{q_i} (folded with N^-1 into the transform's last store)
     BufPtr dcoef = pool().alloc((size_t)B * nl * N);
@@ -678,10 +683,33 @@ CtH Rec::keyswitch(int B, int l, const std::function<const u64 *(int, int)> &d, 
     }
     // 2. ModUp, first (column) pass: digit j -> every prime outside it, the
     //    conversion fused into the load; its constants carry R = 2^64 mod q_t
-    //    for the Montgomery products of step 3
-    BufPtr mu = pool().alloc((size_t)B * dnum * ntg * N);
-    auto mul = [&](int b, int j, int t) { return mu->ptr + (((size_t)b * dnum + j) * ntg + t) * N; };
-    {
+    //    for the Montgomery products of step 3.  With base-2^w pieces: piece
+    //    (i, b) = (d_i >> w b) mod 2^w is the same small integer modulo every
+    //    prime, so every target is its R-scaled transform (no conversion).
+    BufPtr mu = pool().alloc((size_t)B * nd * ntg * N);
+    auto mul = [&](int b, int j, int t) { return mu->ptr + (((size_t)b * nd + j) * ntg + t) * N; };
+    if (pieces > 1) {
+        std::vector<NttJob> jobs;
+        for (int j = 0; j < nd; j++) {
+            const int i = j / pieces, pc = j % pieces;
+            for (int t = 0; t < ntg; t++) {
+                const uint32_t gp = C.qp_prime(l, t);
+                NttJob proto{};
+                proto.prime = gp;
+                proto.c2[0] = C.mods_host[gp].r64;
+                proto.c2_sh[0] = C.mods_host[gp].r64_sh;
+                proto.piece_shift = (uint32_t)(C.base2 * pc);
+                proto.piece_mask = (C.base2 >= 64) ? ~0ull : ((1ull << C.base2) - 1);
+                for (int b = 0; b < B; b++) {
+                    NttJob jb = proto;
+                    jb.src = dcoef->ptr + ((size_t)b * nl + i) * N;
+                    jb.dst = mul(b, j, t);
+                    jobs.push_back(jb);
+                }
+            }
+        }
+        ntt(false, jobs, LOAD_PIECE, STORE_PLAIN, -1, STORE_PLAIN, 1);
+    } else {
         std::vector<NttJob> jobs;
         for (int j = 0; j < dnum; j++) {
             const int lo = j * alpha, hi = std::min(nl, (j + 1) * alpha);
@@ -728,9 +756,9 @@ CtH Rec::keyswitch(int B, int l, const std::function<const u64 *(int, int)> &d, 
                 const uint32_t gp = C.qp_prime(l, t);
                 const u64 qt = C.all[gp];
                 k.own = -1;
-                for (int j = 0; j < dnum; j++) {
+                for (int j = 0; j < nd; j++) {
                     const int lo = j * alpha, hi = std::min(nl, (j + 1) * alpha);
-                    const bool own = t >= lo && t < hi;
+                    const bool own = pieces == 1 && t >= lo && t < hi;
                     if (own) k.own = j;
                     k.src[j] = own ? d(b, t) : mul(b, j, t);
                     k.key0[j] = key.buf->ptr + (((size_t)j * 2 + 0) * nQP + gp) * N;
@@ -739,7 +767,7 @@ CtH Rec::keyswitch(int B, int l, const std::function<const u64 *(int, int)> &d, 
                 k.acc0 = accl(b, 0, t);
                 k.acc1 = accl(b, 1, t);
                 k.prime = gp;
-                k.ndig = dnum;
+                k.ndig = nd;
                 k.qinv = h_inv64(qt);
                 if (fused && t < nl && extra) {
                     k.ex0 = extra(b, 0, t);

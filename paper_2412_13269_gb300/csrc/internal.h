@@ -82,8 +82,10 @@ class Pool {
 // LOAD_REDUCE:   [src * c]_{q_dst} - conv_sub (a single source of another prime;
 //                c = c2[0] when nonzero, else 1)
 // LOAD_INT64:    signed 64-bit integers reduced modulo q_dst
+// LOAD_PIECE:    ((src >> shift) & mask) * c2[0] mod q_dst (a base-2^w piece of a
+//                coefficient-domain residue, times the constant c2[0])
 // Forward transforms take every load mode; inverse transforms load plain limbs.
-enum LoadMode { LOAD_PLAIN = 0, LOAD_INT64 = 2, LOAD_CONV_PRE = 3, LOAD_REDUCE = 4 };
+enum LoadMode { LOAD_PLAIN = 0, LOAD_INT64 = 2, LOAD_CONV_PRE = 3, LOAD_REDUCE = 4, LOAD_PIECE = 5 };
 // STORE_COMBINE (forward only): (extra ? extra : 0) + (base - x) * mul.
 // STORE_SCALED (inverse only): x * mul + conv_sub, where mul already carries
 // N^-1; it precomputes the per-source factor of a following conversion.
@@ -102,6 +104,8 @@ struct NttJob {
     uint64_t src_stride;
     u64 c2[kMaxConvSrc], c2_sh[kMaxConvSrc];  // c2_sh: Shoup companions of c2 modulo q_dst
     u64 conv_sub, mul, mul_sh;
+    u64 piece_mask;                           // LOAD_PIECE
+    uint32_t piece_shift, pad;
 };
 
 struct NttTables {
@@ -167,10 +171,11 @@ void launch_automorphism(const AutJob *jobs_dev, int njobs, int log_n, uint32_t 
 // ModUp column-pass output, whose conversion constants carry R = 2^64 mod q_t)
 // or, for the digit own that holds t, R * src[own] (the input limb, NTT domain);
 // then acc_c[t] = sum_j x_j key_j[c][t] R^-1 (Montgomery products) + pm ex_c[t].
+constexpr int kMaxKeyDigits = 64;
 struct KsJob {
-    const u64 *src[32];
-    const u64 *key0[32];
-    const u64 *key1[32];
+    const u64 *src[kMaxKeyDigits];
+    const u64 *key0[kMaxKeyDigits];
+    const u64 *key1[kMaxKeyDigits];
     u64 *acc0, *acc1;
     const u64 *ex0, *ex1;  // optional: P e folded in (pm = [P]_{q_t}, Shoup companion pm_sh)
     u64 pm, pm_sh;

@@ -97,7 +97,7 @@ struct Group {
 //       inverse: first pass plain, second pass storing plain / x * mul + add /
 //       as the latter less a base conversion of coefficient-domain sources.
 enum { M_PLAIN = 0, M_INT64 = 1, M_STORE = 3, M_COMBINE = 4, M_CONVPRE = 5, M_REDUCE = 6, M_SCALED = 7,
-       M_SCALED_CONV = 8 };
+       M_SCALED_CONV = 8, M_PIECE = 9 };
 constexpr bool is_second(int m) { return m == M_STORE || m == M_COMBINE || m == M_SCALED || m == M_SCALED_CONV; }
 
 // Geometry of one pass: which sub-problem s and lane t a thread takes, where
@@ -271,6 +271,13 @@ __device__ __forceinline__ void pass_body(const PassParams &P, const NttJob &J, 
         const u64 *src = J.src;
 #pragma unroll
         for (int k = 0; k < E; k++) x[k] = src[g.gidx(g.lrow(k))];
+    } else if (MODE == M_PIECE) {
+        // a base-2^w piece (< 2^w) of the source residue times c2[0]: a lazy Shoup product, [0, 2q)
+        const u64 *src = J.src;
+        const uint32_t sh = J.piece_shift;
+        const u64 mk = J.piece_mask, c = J.c2[0], csh = J.c2_sh[0];
+#pragma unroll
+        for (int k = 0; k < E; k++) x[k] = shoup_lazy((src[g.gidx(g.lrow(k))] >> sh) & mk, c, csh, q);
     } else {  // M_INT64
         const int64_t *src = reinterpret_cast<const int64_t *>(J.src);
 #pragma unroll
@@ -389,6 +396,7 @@ void first_pass(int load_mode, int logm, const PassParams &P, int njobs, cudaStr
         if (load_mode == LOAD_CONV_PRE) by_size<INV, !INV, M_CONVPRE>(logm, P, njobs, st);
         else if (load_mode == LOAD_REDUCE) by_size<INV, !INV, M_REDUCE>(logm, P, njobs, st);
         else if (load_mode == LOAD_INT64) by_size<INV, !INV, M_INT64>(logm, P, njobs, st);
+        else if (load_mode == LOAD_PIECE) by_size<INV, !INV, M_PIECE>(logm, P, njobs, st);
         else if (load_mode == LOAD_PLAIN) by_size<INV, !INV, M_PLAIN>(logm, P, njobs, st);
         else throw Error(-1, "unsupported load mode");
     }

@@ -20,8 +20,9 @@
 namespace tetris {
 
 struct Key {
-    BufPtr buf;  // NTT domain [dnum][2][nQP][N]
-    int dnum = 0;
+    BufPtr buf;      // NTT domain [dnum][2][nQP][N]
+    int dnum = 0;    // key digits: CRT digits times base-2^w pieces
+    int pieces = 1;  // base-2^w pieces per one-prime digit (1: no decomposition)
 };
 
 struct Database {
@@ -53,6 +54,7 @@ struct Ctx {
     const double *enc_tw = nullptr;
     Pool pool;
     int alpha = 0;
+    int base2 = 0;  // bits w of the base-2^w decomposition of one-prime key-switch digits (0: none)
     Key relin;
     std::map<uint32_t, Key> rot;
     std::map<uint32_t, Database> dbs;
