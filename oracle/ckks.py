@@ -322,10 +322,12 @@ def keyswitch(par: Params, d: np.ndarray, level: int, evk: np.ndarray, alpha: in
     return out
 
 
-def relinearize(par, ct: Ct, rlk: np.ndarray, alpha: int) -> Ct:
-    """SwitchKey(ct[2], swk_{s^2 -> s}) + ct[0:1] (Appendix A.2)."""
+def relinearize(par, ct: Ct, rlk: np.ndarray, alpha: int, base2: int = 0) -> Ct:
+    """SwitchKey(ct[2], swk_{s^2 -> s}) + ct[0:1] (Appendix A.2); base2 = w > 0
+    switches with the base-2^w gadget of Table 1 (keys from switch_key_base2)."""
     assert ct.comps == 3
-    ks = keyswitch(par, ct.data[2], ct.level, rlk, alpha)
+    ks = (keyswitch_base2(par, ct.data[2], ct.level, rlk, base2) if base2
+          else keyswitch(par, ct.data[2], ct.level, rlk, alpha))
     mods = par.q[: ct.level + 1]
     return Ct(np.stack([rns_add(ct.data[0], ks[0], mods), rns_add(ct.data[1], ks[1], mods)]), ct.level, ct.scale)
 
@@ -351,10 +353,12 @@ def automorphism(par, ct: Ct, g: int) -> Ct:
     return Ct(np.stack([automorphism_poly(ct.data[c], g, mods) for c in range(ct.comps)]), ct.level, ct.scale)
 
 
-def rotate(par, ct: Ct, g: int, rotk: np.ndarray, alpha: int) -> Ct:
-    """SwitchKey(phi(c1), swk_{phi(s) -> s}) + (phi(c0), 0) (Appendix A.2)."""
+def rotate(par, ct: Ct, g: int, rotk: np.ndarray, alpha: int, base2: int = 0) -> Ct:
+    """SwitchKey(phi(c1), swk_{phi(s) -> s}) + (phi(c0), 0) (Appendix A.2);
+    base2 as in relinearize."""
     t = automorphism(par, ct, g)
-    ks = keyswitch(par, t.data[1], ct.level, rotk, alpha)
+    ks = (keyswitch_base2(par, t.data[1], ct.level, rotk, base2) if base2
+          else keyswitch(par, t.data[1], ct.level, rotk, alpha))
     mods = par.q[: ct.level + 1]
     return Ct(np.stack([rns_add(t.data[0], ks[0], mods), ks[1]]), ct.level, ct.scale)
 

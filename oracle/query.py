@@ -269,13 +269,30 @@ class Keys:
     alpha: int
     rlk: np.ndarray
     rot: dict           # galois element -> key
+    base2: int = 0      # w of the base-2^w gadget (Table 1), 0 for the plain hybrid switch
 
 
 def secret(par: Params, seed: int, h: int) -> np.ndarray:
     return synth.ternary_secret(synth.stream(seed, "secret"), par.N, h)
 
 
-def make_keys(par: Params, s: np.ndarray, seed: int, alpha: int, galois=()) -> Keys:
+def make_keys(par: Params, s: np.ndarray, seed: int, alpha: int, galois=(), base2: int = 0) -> Keys:
+    """Relinearisation and rotation keys; base2 = w > 0 makes base-2^w keys
+    (one-prime digits, (L+1) B of them, Table 1's base2)."""
+    if base2:
+        if alpha != 1:
+            raise ValueError("the base-2^w gadget takes one-prime digits")
+        dnum = (par.L + 1) * ckks.base2_pieces(par, base2)
+        mods = par.moduli
+        s_rns = rns.to_rns(s, mods)
+        gen = lambda s_from, d: ckks.switch_key_base2(par, s, s_from, d.a, d.e, base2)
+        d = synth.switch_key_draws(seed, "relin", dnum, mods, par.N)
+        rlk = gen(ckks.rns_mul(s_rns, s_rns, mods, par.psi), d)
+        rot = {}
+        for g in galois:
+            d = synth.switch_key_draws(seed, f"rot{g}", dnum, mods, par.N)
+            rot[g] = gen(ckks.automorphism_poly(s_rns, g, mods), d)
+        return Keys(alpha=1, rlk=rlk, rot=rot, base2=base2)
     dnum = ckks.dnum_for(par.L, alpha)
     d = synth.switch_key_draws(seed, "relin", dnum, par.moduli, par.N)
     rlk = ckks.relin_key(par, s, d.a, d.e, alpha)
@@ -333,7 +350,7 @@ class Evaluator:
     def mul(self, a: Ct, b: Ct) -> Ct:
         assert a.level == b.level
         par = self.par
-        out = ckks.rescale(par, ckks.relinearize(par, ckks.tensor(par, a, b), self.keys.rlk, self.keys.alpha))
+        out = ckks.rescale(par, ckks.relinearize(par, ckks.tensor(par, a, b), self.keys.rlk, self.keys.alpha, self.keys.base2))
         out.scale = self.plan.S[a.level - 1]
         return out
 
@@ -342,7 +359,7 @@ class Evaluator:
 
     def relin_rescale(self, t: Ct, level_out: int) -> Ct:
         par = self.par
-        out = ckks.rescale(par, ckks.relinearize(par, t, self.keys.rlk, self.keys.alpha))
+        out = ckks.rescale(par, ckks.relinearize(par, t, self.keys.rlk, self.keys.alpha, self.keys.base2))
         out.scale = self.plan.S[level_out]
         return out
 
@@ -481,7 +498,7 @@ class Evaluator:
 
     def innersum(self, acc: Ct) -> Ct:
         for g in innersum_galois(self.par):
-            acc = ckks.add(self.par, acc, ckks.rotate(self.par, acc, g, self.keys.rot[g], self.keys.alpha))
+            acc = ckks.add(self.par, acc, ckks.rotate(self.par, acc, g, self.keys.rot[g], self.keys.alpha, self.keys.base2))
         return acc
 
 

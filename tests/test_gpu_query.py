@@ -18,15 +18,16 @@ class Chain:
     """Test-only chain at N = 2^12: a 50-bit q_0, n40 primes of 40 bits, one
     60-bit special prime, Delta = 2^40, one-prime digits."""
 
-    def __init__(self, n40=11, seed=5):
+    def __init__(self, n40=11, seed=5, base2=0):
         T.build()
         q = rns.gen_primes(50, 1) + rns.gen_primes(40, n40)
         p = rns.gen_primes(60, 1)
         self.par = ckks.Params(12, q, p, 2.0 ** 40)
         self.ctx = T.Ctx(12, q, p, 2.0 ** 40)
+        self.ctx.set_option(T.OPT_KS_BASE2, base2)
         self.alpha = 1
         self.s = query.secret(self.par, seed, 2 * self.par.N // 3)
-        self.keys = query.make_keys(self.par, self.s, seed, 1, query.innersum_galois(self.par))
+        self.keys = query.make_keys(self.par, self.s, seed, 1, query.innersum_galois(self.par), base2)
         self.ctx.load_relin_key(self.keys.rlk, 1)
         for g, k in self.keys.rot.items():
             self.ctx.load_rotation_key(g, k, 1)
@@ -87,6 +88,22 @@ def test_query_bit_exact(chain, records, attrs, degree, nst):
     ref = query.fp64_pipeline(vals, qv, stages)
     assert np.ptp(z) < 1e-6 and abs(z[0] * records - ref.count) < 0.05
     ctx.free_database(dbh)
+
+
+def test_query_base2_bit_exact():
+    """The whole query with the base-2^w key switch (w = 30, Table 1's Set I)."""
+    ch = Chain(n40=9, seed=6, base2=30)
+    par, ctx = ch.par, ch.ctx
+    vals, qv, stages, shape, plan, db, eq = make_case(par, ch.s, 2048, 4, 7, 1, 77)
+    want = query.evaluate_query(par, ch.keys, shape, db, eq)
+    dbh = upload_encoded(ctx, par, plan, db, 2048, 4)
+    got, lev, sc = gpu_query(ctx, dbh, eq, stages)
+    assert lev == want.level and np.array_equal(got, want.data)
+    z = ckks.decrypt_slots(par, ckks.Ct(got.copy(), lev, sc), ch.s).real
+    ref = query.fp64_pipeline(vals, qv, stages)
+    assert abs(z[0] * 2048 - ref.count) < 0.05
+    ctx.free_database(dbh)
+    ctx.close()
 
 
 def test_autotune_keeps_results(chain):

@@ -16,11 +16,11 @@ def chain_params(n_q40: int, log_n: int = 12):
     return ckks.Params(log_n, q, rns.gen_primes(60, 1), 2.0 ** 40)
 
 
-def run(par, vals, qv, stages, seed=1, alpha=1):
+def run(par, vals, qv, stages, seed=1, alpha=1, base2=0):
     shape = query.QueryShape(vals.shape[0], vals.shape[1], len(qv.c) - 1, stages)
     plan = query.make_plan(par, shape)
     s = query.secret(par, seed, 2 * par.N // 3)
-    keys = query.make_keys(par, s, seed, alpha, query.innersum_galois(par))
+    keys = query.make_keys(par, s, seed, alpha, query.innersum_galois(par), base2)
     db = query.encode_database(par, plan, vals)
     eq = query.encrypt_query(par, s, qv, seed)
     out = query.evaluate_query(par, keys, shape, db, eq)
@@ -55,6 +55,18 @@ def test_query_matches_fp64_pipeline():
     # InnerSum puts the normalised count in every slot
     assert np.ptp(got) < 1e-6
     assert abs(got[0] * R - ref.count) < 0.05
+
+
+def test_query_base2_matches_fp64_pipeline():
+    """With the base-2^w key switch of Table 1's Set I (w = 30, one special
+    prime) the whole circuit still decrypts to the FP64 pipeline's count."""
+    par = chain_params(9)
+    vals = synth.database(synth.stream(12, "db"), 2048, 4)
+    qv = synth.query_values(synth.stream(12, "qv"), 4, 3)
+    got, plan = run(par, vals, qv, [query.F3], seed=2, base2=30)
+    ref = query.fp64_pipeline(vals, qv, [query.F3])
+    assert np.ptp(got) < 1e-6
+    assert abs(got[0] * vals.shape[0] - ref.count) < 0.05
 
 
 def test_query_ragged_mask():
