@@ -151,6 +151,13 @@ class Plan:
     # coefficients carry the 1/2 of step = (p + 1)/2
     global_coeffs: list = field(default_factory=list)
     records_norm: float = 0.0
+    # the circuit starts as low as its depth allows (a reading: Section 2.5
+    # only says each rescale consumes a level, not where a circuit starts):
+    # the w_j are first adjusted from the top level L to l_lin + 1, carrying the
+    # factor w_factor that makes the rescaled product with the database
+    # plaintexts (scale pt_scale, encoded once for any query) land on S[l_lin]
+    # and the circuit end at level 1; w_factor = 0 when l_lin = L - 1
+    w_factor: float = 0.0
 
     def coef_level(self, k: int) -> int:
         """Level at which the encrypted coefficient c_k is used."""
@@ -180,12 +187,16 @@ def make_plan(par: Params, shape: QueryShape) -> Plan:
     if shape.degree < 1 or shape.attrs < 1 or shape.records < 1 or not shape.sign_stages:
         raise ValueError("empty query")
     L, S = par.L, standard_scales(par)
-    l_lin = L - 1
+    n = par.n_slots
+    ragged = shape.records % n != 0
+    # levels consumed below l_lin: the polynomial, the sign stages, the ragged
+    # block's mask, the global threshold
+    used = (ceil_log2(shape.degree) + 1 + sum(stage_depth(co) for co in shape.sign_stages) + (1 if ragged else 0)
+            + sum(stage_depth(co) for co in shape.global_stages))
+    l_lin = min(L - 1, 1 + used)
     l_d = l_lin - ceil_log2(shape.degree)
     l_y = l_d - 1
     l_u = l_y - sum(stage_depth(co) for co in shape.sign_stages)
-    n = par.n_slots
-    ragged = shape.records % n != 0
     l_out = l_u - 1 if ragged else l_u
     if l_out < 1:
         raise ValueError(f"circuit needs more levels: ends at level {l_out}")
@@ -210,9 +221,11 @@ def make_plan(par: Params, shape: QueryShape) -> Plan:
     l_ret = l_out - sum(stage_depth(co) for co in gco) if gco else 1
     if l_ret < 1:
         raise ValueError(f"global threshold needs more levels: ends at level {l_ret}")
+    pt_scale = (S[L - 1] * float(par.q[L])) / S[L]
+    w_factor = (S[l_lin] * float(par.q[l_lin + 1])) / (S[l_lin + 1] * pt_scale) if l_lin < L - 1 else 0.0
     return Plan(S=S, l_lin=l_lin, l_d=l_d, l_y=l_y, l_u=l_u, l_out=l_out, l_ret=l_ret, global_coeffs=gco,
-                records_norm=R,
-                pt_scale=(S[L - 1] * float(par.q[L])) / S[L],
+                records_norm=R, w_factor=w_factor,
+                pt_scale=pt_scale,
                 mask_scale=((S[l_u - 1] * float(par.q[l_u])) / S[l_u]) if ragged else 0.0,
                 ragged=ragged, stage_coeffs=stages, step_const=1.0 / (2.0 * R),
                 bsgs=poly_schedule(shape.degree), degree=shape.degree)
@@ -401,19 +414,21 @@ class Evaluator:
         for w in q.w:
             if w.level != self.par.L or w.scale != p.S[self.par.L]:
                 raise ValueError("linear-combination coefficients must be fresh top-level ciphertexts")
+        # the w_j at level l_lin + 1, where the linear combination is formed
+        self.w_in = [self.adjust(w, p.l_lin + 1, p.w_factor) if p.w_factor else w for w in q.w]
         ck = [self.adjust(q.c[k], p.coef_level(k)) for k in range(degree + 1)]
         return ck, self.adjust(q.t, p.l_y)
 
     def block(self, pts: list, q: EncQuery, ck: list, tadj: Ct, degree: int) -> Ct:
         par, p = self.par, self.plan
         L = par.L
-        # linear combination: sum_j pt_j * Enc(w_j), rescale
+        # linear combination: sum_j pt_j * Enc(w_j) at level l_lin + 1, rescale
         acc = None
-        for pt, w in zip(pts, q.w):
-            prod = ckks.mul_plain(par, w, rns.to_rns(pt, par.q), p.pt_scale)
+        for pt, w in zip(pts, self.w_in):
+            prod = ckks.mul_plain(par, w, rns.to_rns(pt, par.q[: p.l_lin + 2]), p.pt_scale)
             acc = prod if acc is None else ckks.add(par, acc, prod)
         x = ckks.rescale(par, acc)
-        x.scale = p.S[L - 1]
+        x.scale = p.S[p.l_lin]
         # powers x^k, k <= degree
         P = {1: x}
         cache = {}

@@ -32,6 +32,10 @@ struct QPlan {
     // global threshold: folded stage coefficients (empty: none) and the record count R
     std::vector<std::vector<double>> gco;
     double records_norm = 0;
+    // the circuit starts as low as its depth allows and ends at level 1: the
+    // w_j are adjusted from the top level to l_lin + 1 first, times w_factor
+    // (the rescaled linear combination then lands on S[l_lin]); 0: no adjust
+    double w_factor = 0;
     int coef_level(int k) const;
 };
 
@@ -89,13 +93,17 @@ QPlan make_plan(const Ctx &C, uint64_t records, int degree, const std::vector<st
     TREQUIRE(degree >= 1 && !stages.empty() && records >= 1, TETRIS_EINVAL, "empty query");
     QPlan p;
     const int L = C.L();
-    p.l_lin = L - 1;
+    const uint64_t n = C.N / 2;
+    p.ragged = records % n != 0;
+    // levels used below l_lin: polynomial, sign stages, ragged mask, global threshold
+    int used = ceil_log2(degree) + 1 + (p.ragged ? 1 : 0);
+    for (auto &co : stages) used += stage_depth(co);
+    for (auto &co : gstages) used += stage_depth(co);
+    p.l_lin = std::min(L - 1, 1 + used);
     p.l_d = p.l_lin - ceil_log2(degree);
     p.l_y = p.l_d - 1;
     p.l_u = p.l_y;
     for (auto &co : stages) p.l_u -= stage_depth(co);
-    const uint64_t n = C.N / 2;
-    p.ragged = records % n != 0;
     p.l_out = p.ragged ? p.l_u - 1 : p.l_u;
     TREQUIRE(p.l_out >= 1, TETRIS_ELEVEL, "circuit needs more levels: it would end at level " + std::to_string(p.l_out));
     const double R = (double)(norm_records ? norm_records : records);
@@ -109,6 +117,8 @@ QPlan make_plan(const Ctx &C, uint64_t records, int degree, const std::vector<st
         p.co.push_back(c);
     }
     p.step_const = 1.0 / (2.0 * R);
+    if (p.l_lin < L - 1)
+        p.w_factor = (C.S[p.l_lin] * (double)C.q[p.l_lin + 1]) / (C.S[p.l_lin + 1] * C.pt_scale);
     p.mask_scale = p.ragged ? (C.S[p.l_u - 1] * (double)C.q[p.l_u]) / C.S[p.l_u] : 0.0;
     p.degree = degree;
     poly_schedule(p, degree);
@@ -168,24 +178,24 @@ static CtH sign_stage(Rec &R, const CtH &u, const std::vector<double> &co) {
     return R.add(R.adjust(A, l - 4, 1.0), P);
 }
 
-static CtH eval_blocks(Rec &R, const Database &db, const QPlan &pl, int b0, int nb, const u64 *wbase,
+static CtH eval_blocks(Rec &R, const Database &db, const QPlan &pl, int b0, int nb, const CtH &w,
                        const std::vector<CtH> &ck, const CtH &tadj, int degree) {
     Ctx &C = R.C;
-    const int L = C.L();
+    const int tl = w.level;  // l_lin + 1
     const size_t N = C.N, nq = C.q.size();
-    // x = sum_j pt_j * Enc(w_j), then rescale
-    CtH x0 = R.new_ct(nb, 2, L);
+    // x = sum_j pt_j * Enc(w_j), then rescale (the plaintexts' first tl + 1 limbs)
+    CtH x0 = R.new_ct(nb, 2, tl);
     {
         // blocks innermost: the B jobs of one prime read the same w_j limbs back to back
         std::vector<LinJob> jobs;
-        for (int i = 0; i <= L; i++)
+        for (int i = 0; i <= tl; i++)
             for (int b = 0; b < nb; b++) {
                 LinJob j{};
                 j.pt = db.pts->ptr + (((size_t)(b0 + b) * db.attrs) * nq + i) * N;
                 j.pt_stride = nq * N;
-                j.w0 = wbase + (size_t)i * N;
-                j.w1 = wbase + (size_t)(L + 1) * N + (size_t)i * N;
-                j.w_stride = 2 * (size_t)(L + 1) * N;
+                j.w0 = w.limb(0, 0, i);
+                j.w1 = w.limb(0, 1, i);
+                j.w_stride = w.bstride;
                 j.d0 = x0.limb(b, 0, i);
                 j.d1 = x0.limb(b, 1, i);
                 j.prime = i;
@@ -195,7 +205,7 @@ static CtH eval_blocks(Rec &R, const Database &db, const QPlan &pl, int b0, int 
         R.lin(jobs);
     }
     CtH x = R.rescale(x0);
-    x.scale = C.S[L - 1];
+    x.scale = C.S[pl.l_lin];
     x0 = CtH();
     // powers x^k
     std::map<int, CtH> Pw;
@@ -298,7 +308,14 @@ std::unique_ptr<Program> record_query(Ctx &C, const Database &db, const QuerySpe
     std::vector<Rec::AdjustItem> items;
     for (int k = 0; k <= q.degree; k++) items.push_back({cin[k], pl.coef_level(k), 1.0});
     items.push_back({tin, pl.l_y, 1.0});
+    // the w_j (one batch of attrs ciphertexts) to level l_lin + 1
+    CtH w = R.view(wbuf, wbuf->ptr, q.attrs, 2, L, wwords, (L + 1) * N, C.S[L]);
+    if (pl.w_factor != 0) items.push_back({w, pl.l_lin + 1, pl.w_factor});
     std::vector<CtH> ck = R.adjust_many_coef(items);
+    if (pl.w_factor != 0) {
+        w = ck.back();
+        ck.pop_back();
+    }
     CtH tadj = ck.back();
     ck.pop_back();
     {
@@ -313,7 +330,7 @@ std::unique_ptr<Program> record_query(Ctx &C, const Database &db, const QuerySpe
                         jobs.push_back(j);
                     }
         };
-        for (int j = 0; j < q.attrs; j++) add_limbs(R.view(wbuf, wbuf->ptr + j * wwords, 1, 2, L, wwords, (L + 1) * N, 0));
+        add_limbs(w);
         for (auto &c : ck) add_limbs(c);
         add_limbs(tadj);
         R.ntt(false, jobs, LOAD_PLAIN, STORE_PLAIN);
@@ -325,7 +342,7 @@ std::unique_ptr<Program> record_query(Ctx &C, const Database &db, const QuerySpe
     bool have_full = false, have_last = false;
     for (int b0 = 0; b0 < B; b0 += bpl) {
         const int nb = std::min(bpl, B - b0);
-        CtH u = eval_blocks(R, db, pl, b0, nb, wbuf->ptr, ck, tadj, q.degree);
+        CtH u = eval_blocks(R, db, pl, b0, nb, w, ck, tadj, q.degree);
         int nfull = nb;
         if (pl.ragged && b0 + nb == B) {
             last = R.view(u.buf, u.limb(nb - 1, 0, 0), 1, u.comps, u.level, u.bstride, u.cstride, u.scale);

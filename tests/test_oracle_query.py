@@ -31,13 +31,21 @@ def run(par, vals, qv, stages, seed=1, alpha=1, base2=0):
 def test_plan_levels():
     par = chain_params(11)
     p = query.make_plan(par, query.QueryShape(2048, 8, 7, [query.F3]))
-    assert (p.l_lin, p.l_d, p.l_y, p.l_u, p.l_out) == (10, 7, 6, 3, 3)
+    # the circuit starts as low as its depth allows: it ends at level 1
+    assert (p.l_lin, p.l_d, p.l_y, p.l_u, p.l_out) == (8, 5, 4, 1, 1)
     q2 = rns.gen_primes(50, 20)
     par2 = ckks.Params(16, q2, rns.gen_primes(60, 3), 2.0 ** 50)
     p2 = query.make_plan(par2, query.QueryShape(131072, 16, 15, [query.F3] * 3))
-    assert (p2.l_lin, p2.l_d, p2.l_y, p2.l_u, p2.l_out) == (18, 14, 13, 4, 4)
+    assert (p2.l_lin, p2.l_d, p2.l_y, p2.l_u, p2.l_out) == (15, 11, 10, 1, 1)
     p3 = query.make_plan(par2, query.QueryShape(1 << 14, 16, 31, [query.F3] * 3))
-    assert p3.ragged and p3.l_out == 2
+    assert p3.ragged and (p3.l_lin, p3.l_u, p3.l_out) == (17, 2, 1)
+    # the factor that lands the rescaled linear combination on S[l_lin]
+    for pl in (p2, p3):
+        t = pl.l_lin + 1
+        assert abs(pl.w_factor * pl.S[t] * pl.pt_scale / (pl.S[pl.l_lin] * par2.q[t]) - 1) < 1e-15
+    # no spare levels: the circuit starts right below the top
+    p4 = query.make_plan(par2, query.QueryShape(131072, 16, 15, [query.F3] * 4))
+    assert (p4.l_lin, p4.l_out, p4.w_factor) == (18, 1, 0.0)
     with pytest.raises(ValueError):
         query.make_plan(par, query.QueryShape(2048, 8, 31, [query.F3] * 3))
     # exact standard scales: S[l-1] q_l = S[l]^2 up to one rounding
