@@ -83,6 +83,42 @@ const Key &find_key(const Ctx &c, uint32_t galois) {
 Program::~Program() {
     if (exec) cudaGraphExecDestroy(exec);
     if (graph) cudaGraphDestroy(graph);
+    if (exec_b) cudaGraphExecDestroy(exec_b);
+    if (graph_b) cudaGraphDestroy(graph_b);
+    if (side) {
+        cudaStreamSynchronize(side);
+        cudaStreamDestroy(side);
+    }
+    if (late_ev) cudaEventDestroy(late_ev);
+    if (early_ev) cudaEventDestroy(early_ev);
+}
+
+void Program::add_late_wait() {
+    TREQUIRE(late_slot <= in_slots.size(), TETRIS_EINVAL, "late inputs: no such slot");
+    TCHECK_CUDA(cudaEventCreateWithFlags(&late_ev, cudaEventDisableTiming));
+    TCHECK_CUDA(cudaEventCreateWithFlags(&early_ev, cudaEventDisableTiming));
+    TCHECK_CUDA(cudaStreamCreateWithFlags(&side, cudaStreamNonBlocking));
+    cudaEvent_t ev = late_ev;
+    Launch l;
+    l.fn = [ev](cudaStream_t s, const uint8_t *) { TCHECK_CUDA(cudaStreamWaitEvent(s, ev, 0)); };
+    l.kind = "wait_late_inputs";
+    l.kernel = false;
+    wait_at = launches.size();
+    launches.push_back(std::move(l));
+}
+
+void Program::copy_inputs(const std::vector<const void *> &srcs, cudaMemcpyKind kind, cudaStream_t s) {
+    TREQUIRE(srcs.size() == in_slots.size(), TETRIS_EINVAL, "inputs do not match the program");
+    const size_t split = late_ev ? std::min(late_slot, srcs.size()) : srcs.size();
+    for (size_t i = 0; i < split; i++)
+        TCHECK_CUDA(cudaMemcpyAsync(in_slots[i].first, srcs[i], in_slots[i].second * 8, kind, s));
+    if (!late_ev) return;
+    // the side stream starts after the early copies, which follow the previous run on s
+    TCHECK_CUDA(cudaEventRecord(early_ev, s));
+    TCHECK_CUDA(cudaStreamWaitEvent(side, early_ev, 0));
+    for (size_t i = split; i < srcs.size(); i++)
+        TCHECK_CUDA(cudaMemcpyAsync(in_slots[i].first, srcs[i], in_slots[i].second * 8, kind, side));
+    TCHECK_CUDA(cudaEventRecord(late_ev, side));
 }
 
 size_t Program::add_jobs(const void *p, size_t bytes) {
@@ -124,6 +160,7 @@ void Program::run_profiled(cudaStream_t s, std::map<std::string, KernelStat> &st
     TCHECK_CUDA(cudaGetLastError());
     double ks_ms = 0;
     for (size_t i = 0; i < launches.size(); i++) {
+        if (!launches[i].kernel) continue;
         float ms = 0;
         TCHECK_CUDA(cudaEventElapsedTime(&ms, ev[2 * i], ev[2 * i + 1]));
         KernelStat &k = stats[launches[i].kind];
@@ -142,19 +179,30 @@ void Program::run_profiled(cudaStream_t s, std::map<std::string, KernelStat> &st
     for (auto &e : ev) cudaEventDestroy(e);
 }
 
+// The launches captured as one CUDA graph, or as two around the wait for the
+// late inputs (a plain stream wait between the two graph launches).
 void Program::run_graph(cudaStream_t s) {
-    if (!exec) {
+    const size_t cut = wait_at < launches.size() ? wait_at : launches.size();
+    auto capture = [&](size_t i0, size_t i1, cudaGraph_t &g, cudaGraphExec_t &x) {
         cudaStream_t cs;
         TCHECK_CUDA(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
         TCHECK_CUDA(cudaStreamBeginCapture(cs, cudaStreamCaptureModeRelaxed));
         const uint8_t *a = reinterpret_cast<const uint8_t *>(arena_dev->ptr);
-        for (auto &l : launches) l.fn(cs, a);
-        cudaError_t e = cudaStreamEndCapture(cs, &graph);
+        for (size_t i = i0; i < i1; i++) launches[i].fn(cs, a);
+        cudaError_t e = cudaStreamEndCapture(cs, &g);
         cudaStreamDestroy(cs);
         TCHECK_CUDA(e);
-        TCHECK_CUDA(cudaGraphInstantiate(&exec, graph, 0));
+        TCHECK_CUDA(cudaGraphInstantiate(&x, g, 0));
+    };
+    if (!exec) {
+        capture(0, cut, graph, exec);
+        if (cut < launches.size()) capture(cut + 1, launches.size(), graph_b, exec_b);
     }
     TCHECK_CUDA(cudaGraphLaunch(exec, s));
+    if (exec_b) {
+        TCHECK_CUDA(cudaStreamWaitEvent(s, late_ev, 0));
+        TCHECK_CUDA(cudaGraphLaunch(exec_b, s));
+    }
 }
 
 // ---------------------------------------------------------------------------

@@ -94,6 +94,7 @@ struct Launch {
     std::string kind;
     double bytes = 0;
     double modmuls = 0;  // algorithmic modular multiplications (butterflies, conversion and key products)
+    bool kernel = true;  // false: a stream wait, neither timed nor counted
 };
 
 struct Program {
@@ -113,6 +114,15 @@ struct Program {
     double out_scale = 0;
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
+    // inputs in_slots[late_slot..] may arrive while the program runs: copy_inputs
+    // sends them on a side stream after the others and records late_ev, and the
+    // program waits for that event just before their first use
+    size_t late_slot = SIZE_MAX;
+    size_t wait_at = SIZE_MAX;  // index of the wait in launches
+    cudaEvent_t late_ev = nullptr, early_ev = nullptr;
+    cudaStream_t side = nullptr;
+    cudaGraph_t graph_b = nullptr;  // the launches after the wait
+    cudaGraphExec_t exec_b = nullptr;
     // counters
     int relins = 0, rescales = 0, rotations = 0;
     int ks_count = 0;
@@ -126,6 +136,10 @@ struct Program {
     void run_profiled(cudaStream_t s, std::map<std::string, KernelStat> &stats);
     void add_launch(std::function<void(cudaStream_t, const uint8_t *)> fn, const std::string &kind, double bytes,
                     double modmuls = 0);
+    // from here on the program may use in_slots[late_slot..]
+    void add_late_wait();
+    // copies srcs[i] into in_slots[i] (kind H2D or D2D), the late ones on the side stream
+    void copy_inputs(const std::vector<const void *> &srcs, cudaMemcpyKind kind, cudaStream_t s);
 };
 
 // A launch recorded but not yet emitted (batch schedules merge these): the

@@ -179,7 +179,7 @@ static CtH sign_stage(Rec &R, const CtH &u, const std::vector<double> &co) {
 }
 
 static CtH eval_blocks(Rec &R, const Database &db, const QPlan &pl, int b0, int nb, const CtH &w,
-                       const std::vector<CtH> &ck, const CtH &tadj, int degree) {
+                       const std::function<void()> &need_ck, const std::vector<CtH> &ck, const CtH &tadj, int degree) {
     Ctx &C = R.C;
     const int tl = w.level;  // l_lin + 1
     const size_t N = C.N, nq = C.q.size();
@@ -231,6 +231,7 @@ static CtH eval_blocks(Rec &R, const Database &db, const QPlan &pl, int b0, int 
     if (pl.g == 0) {
         for (int k = 2; k <= degree; k++) Pw[k] = power_rule(Pw, k, lvl);
         // y = sum_k c_k x^k with one relinearisation
+        need_ck();
         CtH T;
         for (int k = 1; k <= degree; k++) T = R.tensor_add(T, ck[k], lvl(k, pl.l_d));
         y = relin_rescale_to(R, T, pl.l_y);
@@ -250,6 +251,7 @@ static CtH eval_blocks(Rec &R, const Database &db, const QPlan &pl, int b0, int 
             return a;
         };
         for (int i = 2; i < m; i++) G[i] = power_rule(G, i, glvl);
+        need_ck();
         CtH T;
         for (int j = 1; j < g; j++) T = R.tensor_add(T, ck[j], lvl(j, l_f));  // s_0's terms at l_f
         for (int i = 1; i < m; i++) {
@@ -302,25 +304,12 @@ std::unique_ptr<Program> record_query(Ctx &C, const Database &db, const QuerySpe
         P->hold.push_back(t1in.buf);
         P->in_slots.push_back({t1in.base, t1in.bstride});
     }
-    // per-query: the coefficients and the threshold move to their levels while
-    // still in the coefficient domain (a rescale is per coefficient there), so
-    // only their remaining limbs are transformed, together with the w_j
-    std::vector<Rec::AdjustItem> items;
-    for (int k = 0; k <= q.degree; k++) items.push_back({cin[k], pl.coef_level(k), 1.0});
-    items.push_back({tin, pl.l_y, 1.0});
-    // the w_j (one batch of attrs ciphertexts) to level l_lin + 1
-    CtH w = R.view(wbuf, wbuf->ptr, q.attrs, 2, L, wwords, (L + 1) * N, C.S[L]);
-    if (pl.w_factor != 0) items.push_back({w, pl.l_lin + 1, pl.w_factor});
-    std::vector<CtH> ck = R.adjust_many_coef(items);
-    if (pl.w_factor != 0) {
-        w = ck.back();
-        ck.pop_back();
-    }
-    CtH tadj = ck.back();
-    ck.pop_back();
-    {
+    // per-query: the w_j (one batch of attrs ciphertexts) to level l_lin + 1,
+    // in the coefficient domain (a rescale is per coefficient there), then
+    // their remaining limbs to the NTT domain
+    auto ntt_inputs = [&](const std::vector<CtH> &cts) {
         std::vector<NttJob> jobs;
-        auto add_limbs = [&](const CtH &c) {
+        for (const CtH &c : cts)
             for (int b = 0; b < c.B; b++)
                 for (int k = 0; k < c.comps; k++)
                     for (int i = 0; i <= c.level; i++) {
@@ -329,12 +318,30 @@ std::unique_ptr<Program> record_query(Ctx &C, const Database &db, const QuerySpe
                         j.prime = i;
                         jobs.push_back(j);
                     }
-        };
-        add_limbs(w);
-        for (auto &c : ck) add_limbs(c);
-        add_limbs(tadj);
         R.ntt(false, jobs, LOAD_PLAIN, STORE_PLAIN);
-    }
+    };
+    CtH w = R.view(wbuf, wbuf->ptr, q.attrs, 2, L, wwords, (L + 1) * N, C.S[L]);
+    if (pl.w_factor != 0) w = R.adjust_many_coef({{w, pl.l_lin + 1, pl.w_factor}})[0];
+    ntt_inputs({w});
+    // the coefficients and the threshold (and t1) are late inputs: their copies
+    // overlap the linear combination and the first powers of x, and they are
+    // brought to their levels and transformed where first used
+    P->late_slot = (size_t)q.attrs;
+    std::vector<CtH> ck;
+    CtH tadj;
+    auto need_ck = [&]() {
+        if (!ck.empty()) return;
+        P->add_late_wait();
+        std::vector<Rec::AdjustItem> items;
+        for (int k = 0; k <= q.degree; k++) items.push_back({cin[k], pl.coef_level(k), 1.0});
+        items.push_back({tin, pl.l_y, 1.0});
+        ck = R.adjust_many_coef(items);
+        tadj = ck.back();
+        ck.pop_back();
+        std::vector<CtH> all = ck;
+        all.push_back(tadj);
+        ntt_inputs(all);
+    };
     // block groups
     const int B = db.blocks;
     const int bpl = q.bpl <= 0 ? B : std::min(q.bpl, B);
@@ -342,7 +349,7 @@ std::unique_ptr<Program> record_query(Ctx &C, const Database &db, const QuerySpe
     bool have_full = false, have_last = false;
     for (int b0 = 0; b0 < B; b0 += bpl) {
         const int nb = std::min(bpl, B - b0);
-        CtH u = eval_blocks(R, db, pl, b0, nb, w, ck, tadj, q.degree);
+        CtH u = eval_blocks(R, db, pl, b0, nb, w, need_ck, ck, tadj, q.degree);
         int nfull = nb;
         if (pl.ragged && b0 + nb == B) {
             last = R.view(u.buf, u.limb(nb - 1, 0, 0), 1, u.comps, u.level, u.bstride, u.cstride, u.scale);
@@ -505,8 +512,9 @@ void evaluate_query(Ctx &C, uint32_t dbh, const tetris_query *q, tetris_ct_out *
     const cudaMemcpyKind in_kind = device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
     const auto ins = query_inputs(q);
     TREQUIRE(ins.size() == P.in_slots.size(), TETRIS_EINVAL, "query: inputs do not match the program");
-    for (size_t slot = 0; slot < ins.size(); slot++)
-        TCHECK_CUDA(cudaMemcpyAsync(P.in_slots[slot].first, ins[slot]->data, P.in_slots[slot].second * 8, in_kind, s));
+    std::vector<const void *> srcs;
+    for (auto *c : ins) srcs.push_back(c->data);
+    P.copy_inputs(srcs, in_kind, s);
     if (C.profile) P.run_profiled(s, C.stats);
     else if (C.use_graph) P.run_graph(s);
     else P.run(s);
