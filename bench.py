@@ -761,7 +761,7 @@ def main():
         keyswitch = {"count_per_query": ks[0], "gbs": gbs_ks, "frac_of_hbm": gbs_ks / hbm, "ms_per_query": ks[1],
                      "share_of_query": ks[1] / tot_ms,
                      "bytes": "per keyswitch: input limbs + key limbs used + output limbs (the key read once per batched launch)"}
-    top = sorted(kern.items(), key=lambda kv: -kv[1][1])[:8]
+    top = sorted(kern.items(), key=lambda kv: -kv[1][1])
     kernels = [{"kind": k, "launches": v[0], "ms": round(v[1], 4), "share": round(v[1] / tot_ms, 4),
                 "alg_gbs": round(v[2] / (v[1] * 1e-3) / 1e9, 1),
                 "gmodmul_s": round(v[3] / (v[1] * 1e-3) / 1e9, 1)} for k, v in top]

@@ -158,6 +158,11 @@ class Plan:
     # plaintexts (scale pt_scale, encoded once for any query) land on S[l_lin]
     # and the circuit end at level 1; w_factor = 0 when l_lin = L - 1
     w_factor: float = 0.0
+    # factor each encrypted coefficient c_k carries after its arrival adjust (a
+    # reading, like the schedule): the power x^j it multiplies is only dropped
+    # (no rescale) to the product's level lt, so c_k carries S[lt] / S[level of
+    # x^j] and the degree-2 product lands on S[lt]^2; 1 where c_k is added
+    coef_factors: list = field(default_factory=list)
 
     def coef_level(self, k: int) -> int:
         """Level at which the encrypted coefficient c_k is used."""
@@ -222,13 +227,29 @@ def make_plan(par: Params, shape: QueryShape) -> Plan:
     if l_ret < 1:
         raise ValueError(f"global threshold needs more levels: ends at level {l_ret}")
     pt_scale = (S[L - 1] * float(par.q[L])) / S[L]
+    bsgs = poly_schedule(shape.degree)
+    lev = lambda k: l_lin - ceil_log2(k)              # level of the power x^k
+    cf = [1.0] * (shape.degree + 1)
+    for k in range(1, shape.degree + 1):
+        if bsgs is None:
+            cf[k] = S[l_d] / S[lev(k)]
+            continue
+        g, m, bb, df = bsgs
+        i, j = divmod(k, g)
+        l_b, l_f = l_lin - bb, l_lin - df
+        if i == 0:
+            cf[k] = S[l_f] / S[lev(j)]
+            continue
+        # s_i multiplies x^(g i) (level l_lin - b - ceil_log2(i), g = 2^b) dropped to l_f
+        fi = S[l_f] / S[l_lin - ceil_log2(g) - ceil_log2(i)]
+        cf[k] = fi * (S[l_b] / S[lev(j)]) if j >= 1 else fi
     w_factor = (S[l_lin] * float(par.q[l_lin + 1])) / (S[l_lin + 1] * pt_scale) if l_lin < L - 1 else 0.0
     return Plan(S=S, l_lin=l_lin, l_d=l_d, l_y=l_y, l_u=l_u, l_out=l_out, l_ret=l_ret, global_coeffs=gco,
                 records_norm=R, w_factor=w_factor,
                 pt_scale=pt_scale,
                 mask_scale=((S[l_u - 1] * float(par.q[l_u])) / S[l_u]) if ragged else 0.0,
                 ragged=ragged, stage_coeffs=stages, step_const=1.0 / (2.0 * R),
-                bsgs=poly_schedule(shape.degree), degree=shape.degree)
+                bsgs=bsgs, degree=shape.degree, coef_factors=cf)
 
 
 def adjust_const(plan: Plan, par: Params, lt: int, a: float, scale: float) -> int:
@@ -376,37 +397,47 @@ class Evaluator:
         out.scale = self.plan.S[level_out]
         return out
 
-    def odd7(self, a, u2: Ct, u2d: Ct, u4: Ct, l: int) -> Ct:
-        """a0 u + [(a1 u) u^2 + ((a3 u) u^2 + a2 u) u^4] from the adjusts
-        a = (a3 u at l-1, a2 u at l-2, a1 u at l-2, a0 u at l-3): the two
-        degree-2 products in brackets formed at level l-2 and relinearised
-        once; ends at level l-3."""
+    def fold(self, T: Ct, v: Ct, a: float) -> Ct:
+        """T + a v for a degree-2 accumulator T at level lt (plaintext scale
+        S[lt]^2) and a ciphertext v at level >= lt: v is dropped to lt and
+        multiplied by the integer round(a S[lt]^2 / scale(v)), no rescale (the
+        relinearisation's rescale that follows covers it).  A reading: the
+        paper does not say how the sign polynomial's terms are combined."""
+        par, lt = self.par, T.level
+        c = round_half_up(((a * self.plan.S[lt]) * self.plan.S[lt]) / v.scale)
+        m = ckks.mul_int(par, ckks.drop_to(v, lt), c)
+        mods = par.q[: lt + 1]
+        data = T.data.copy()
+        data[0] = ckks.rns_add(data[0], m.data[0], mods)
+        data[1] = ckks.rns_add(data[1], m.data[1], mods)
+        return Ct(data, lt, T.scale)
+
+    def odd7(self, a3u: Ct, a1u: Ct, c2: float, c0: float, u: Ct, u2: Ct, u2d: Ct, u4: Ct, l: int) -> Ct:
+        """c0 u + [(a1 u) u^2 + ((a3 u) u^2 + c2 u) u^4] from the adjusts
+        a3u (level l-1) and a1u (l-2): c2 u folded into (a3 u) u^2 before its
+        relinearisation at l-1, c0 u into the bracket's two degree-2 products
+        at l-2, which are relinearised once; ends at level l-3."""
         par = self.par
-        t7 = self.mul(a[0], u2)
-        inner = self.add(t7, a[1])
-        T = ckks.add(par, ckks.tensor(par, a[2], u2d), ckks.tensor(par, inner, u4))
-        return self.add(a[3], self.relin_rescale(T, l - 3))
+        inner = self.relin_rescale(self.fold(ckks.tensor(par, a3u, u2), u, c2), l - 2)
+        T = ckks.add(par, ckks.tensor(par, a1u, u2d), ckks.tensor(par, inner, u4))
+        return self.relin_rescale(self.fold(T, u, c0), l - 3)
 
     def sign_stage(self, u: Ct, co) -> Ct:
         """p(u) = sum_k a_k u^(2k+1).  Degree 7 (4 coefficients): depth 3,
         four relinearisations.  Degree 15 (8): depth 4 as A(u) + u^8 B(u),
         A and B the degree-7 parts of the low and high coefficients (u^2, u^4
-        shared), eight relinearisations."""
+        shared), eight relinearisations, A folded into u^8 B before its
+        relinearisation."""
         l = u.level
-        lv = [l - 1, l - 2, l - 2, l - 3]
-        a = [self.adjust(u, lv[i], co[3 - i]) for i in range(4)]
-        if len(co) == 8:
-            a += [self.adjust(u, lv[i], co[7 - i]) for i in range(4)]
         u2 = self.mul(u, u)
         u4 = self.mul(u2, u2)
         u2d = self.adjust(u2, l - 2)
-        A = self.odd7(a[:4], u2, u2d, u4, l)
+        A = self.odd7(self.adjust(u, l - 1, co[3]), self.adjust(u, l - 2, co[1]), co[2], co[0], u, u2, u2d, u4, l)
         if len(co) == 4:
             return A
         u8 = self.mul(u4, u4)
-        B = self.odd7(a[4:], u2, u2d, u4, l)
-        P = self.relin_rescale(ckks.tensor(self.par, u8, B), l - 4)
-        return self.add(self.adjust(A, l - 4), P)
+        B = self.odd7(self.adjust(u, l - 1, co[7]), self.adjust(u, l - 2, co[5]), co[6], co[4], u, u2, u2d, u4, l)
+        return self.relin_rescale(self.fold(ckks.tensor(self.par, u8, B), A, 1.0), l - 4)
 
     def per_query(self, q: EncQuery, degree: int):
         """Bring the encrypted coefficients and threshold to their levels (once per query)."""
@@ -416,7 +447,7 @@ class Evaluator:
                 raise ValueError("linear-combination coefficients must be fresh top-level ciphertexts")
         # the w_j at level l_lin + 1, where the linear combination is formed
         self.w_in = [self.adjust(w, p.l_lin + 1, p.w_factor) if p.w_factor else w for w in q.w]
-        ck = [self.adjust(q.c[k], p.coef_level(k)) for k in range(degree + 1)]
+        ck = [self.adjust(q.c[k], p.coef_level(k), p.coef_factors[k]) for k in range(degree + 1)]
         return ck, self.adjust(q.t, p.l_y)
 
     def block(self, pts: list, q: EncQuery, ck: list, tadj: Ct, degree: int) -> Ct:
@@ -453,7 +484,7 @@ class Evaluator:
             # y = sum_k c_k x^k: degree-2 products summed, one relinearisation
             T = None
             for k in range(1, degree + 1):
-                tk = ckks.tensor(par, ck[k], lvl(k, p.l_d))
+                tk = ckks.tensor(par, ck[k], ckks.drop_to(P[k], p.l_d))
                 T = tk if T is None else ckks.add(par, T, tk)
             y = self.relin_rescale(T, p.l_y)
         else:
@@ -476,21 +507,21 @@ class Evaluator:
             # s_i, i >= 1: sum_{j>=1} c_{gi+j} x^j at l_b, relinearised, plus c_{gi}
             T = None
             for j in range(1, g):          # s_0's terms at l_f
-                tk = ckks.tensor(par, ck[j], lvl(j, l_f))
+                tk = ckks.tensor(par, ck[j], ckks.drop_to(P[j], l_f))
                 T = tk if T is None else ckks.add(par, T, tk)
             for i in range(1, m):
                 Ti = None
                 for j in range(1, g):
                     if g * i + j > degree:
                         break
-                    tk = ckks.tensor(par, ck[g * i + j], lvl(j, l_b))
+                    tk = ckks.tensor(par, ck[g * i + j], ckks.drop_to(P[j], l_b))
                     Ti = tk if Ti is None else ckks.add(par, Ti, tk)
                 if Ti is None:
                     si = ck[g * i]
                 else:
                     si = ckks.add(par, self.relin_rescale(Ti, l_b - 1), ck[g * i])
                     si = self.adjust(si, l_f)
-                T = ckks.add(par, T, ckks.tensor(par, si, glvl(i, l_f)))
+                T = ckks.add(par, T, ckks.tensor(par, si, ckks.drop_to(G[i], l_f)))
             y = self.relin_rescale(T, l_f - 1)
             y = self.adjust(y, p.l_y)
         y = ckks.add(par, y, ck[0])

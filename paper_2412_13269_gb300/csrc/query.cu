@@ -36,6 +36,10 @@ struct QPlan {
     // w_j are adjusted from the top level to l_lin + 1 first, times w_factor
     // (the rescaled linear combination then lands on S[l_lin]); 0: no adjust
     double w_factor = 0;
+    // factor each c_k carries after its arrival adjust: the power it multiplies
+    // is dropped (not rescaled) to the product's level lt, so c_k carries
+    // S[lt] / S[level of the power] (and s_i's factor for x^(g i)); 1 where added
+    std::vector<double> cfac;
     int coef_level(int k) const;
 };
 
@@ -122,6 +126,25 @@ QPlan make_plan(const Ctx &C, uint64_t records, int degree, const std::vector<st
     p.mask_scale = p.ragged ? (C.S[p.l_u - 1] * (double)C.q[p.l_u]) / C.S[p.l_u] : 0.0;
     p.degree = degree;
     poly_schedule(p, degree);
+    {
+        const auto &S = C.S;
+        auto lev = [&](int k) { return p.l_lin - ceil_log2(k); };  // level of the power x^k
+        p.cfac.assign(degree + 1, 1.0);
+        for (int k = 1; k <= degree; k++) {
+            if (p.g == 0) {
+                p.cfac[k] = S[p.l_d] / S[lev(k)];
+                continue;
+            }
+            const int i = k / p.g, j = k % p.g, l_b = p.l_lin - p.bb, l_f = p.l_lin - p.df;
+            if (i == 0) {
+                p.cfac[k] = S[l_f] / S[lev(j)];
+                continue;
+            }
+            // s_i multiplies x^(g i) (level l_lin - log2 g - ceil_log2(i)) dropped to l_f
+            const double fi = S[l_f] / S[p.l_lin - ceil_log2(p.g) - ceil_log2(i)];
+            p.cfac[k] = j >= 1 ? fi * (S[l_b] / S[lev(j)]) : fi;
+        }
+    }
     // global threshold: step = (p + 1)/2 folded into the last stage
     p.records_norm = R;
     for (size_t s = 0; s < gstages.size(); s++) {
@@ -149,33 +172,66 @@ static CtH relin_rescale_to(Rec &R, const CtH &t, int level_out) {
 // at level l, from the adjusts a = (a3 u at l-1, a2 u at l-2, a1 u at l-2,
 // a0 u at l-3), u2 (l-1), u2d = u2 at l-2 and u4 (l-2): the two degree-2
 // products in brackets formed at level l-2 and relinearised once; ends at l-3.
-static CtH odd7(Rec &R, const CtH *a, const CtH &u2, const CtH &u2d, const CtH &u4, int l) {
-    CtH t7 = R.mul(a[0], u2);
-    CtH inner = R.add(t7, a[1]);
-    CtH T = R.tensor_add(R.tensor(a[2], u2d), inner, u4);
-    CtH t = relin_rescale_to(R, T, l - 3);
-    return R.add(a[3], t);
+// T + a v for a degree-2 accumulator T at level lt (plaintext scale S[lt]^2)
+// and a ciphertext v at level >= lt: v's first lt + 1 limbs times the integer
+// round(a S[lt]^2 / scale(v)) added to T's first two components, no rescale
+// (the relinearisation's rescale that follows covers it).  In place on T.
+static CtH fold(Rec &R, const CtH &T, const CtH &v, double a) {
+    Ctx &C = R.C;
+    const int lt = T.level;
+    TREQUIRE(T.comps == 3 && v.level >= lt && v.B == T.B, TETRIS_EINVAL, "fold: operands differ");
+    const int64_t c = round_half_up(((a * C.S[lt]) * C.S[lt]) / v.scale);
+    std::vector<EwJob> jobs;
+    for (int i = 0; i <= lt; i++) {
+        const u64 qi = C.q[i];
+        EwJob proto{};
+        proto.op = EW_ADD_MUL_CONST;
+        proto.prime = i;
+        proto.k = c >= 0 ? (u64)c % qi : qi - 1 - (u64)(-(c + 1)) % qi;
+        proto.k_sh = h_shoup(proto.k, qi);
+        for (int b = 0; b < T.B; b++)
+            for (int k = 0; k < 2; k++) {
+                EwJob j = proto;
+                j.a = v.limb(b, k, i);
+                j.b = j.dst = T.limb(b, k, i);
+                jobs.push_back(j);
+            }
+    }
+    R.ew(jobs);
+    return T;
+}
+
+// c0 u + [(a1 u) u^2 + ((a3 u) u^2 + c2 u) u^4] from the adjusts a3u (level
+// l-1) and a1u (l-2): c2 u folded into (a3 u) u^2 before its relinearisation,
+// c0 u into the bracket's two degree-2 products, relinearised once; ends at l-3.
+static CtH odd7(Rec &R, const CtH &a3u, const CtH &a1u, double c2, double c0, const CtH &u, const CtH &u2,
+                const CtH &u2d, const CtH &u4, int l) {
+    CtH inner = relin_rescale_to(R, fold(R, R.tensor(a3u, u2), u, c2), l - 2);
+    CtH T = R.tensor_add(R.tensor(a1u, u2d), inner, u4);
+    return relin_rescale_to(R, fold(R, T, u, c0), l - 3);
 }
 
 // One sign stage p(u) = sum_k a_k u^(2k+1): degree 7 in depth 3 with four
 // relinearisations; degree 15 in depth 4 as A(u) + u^8 B(u), A and B the
 // degree-7 parts of the low and high coefficients (u^2, u^4 shared), eight
-// relinearisations.  The adjusts of u are independent: one pair of transforms.
+// relinearisations, A folded into u^8 B.  The adjusts of u are independent:
+// one pair of transforms.
 static CtH sign_stage(Rec &R, const CtH &u, const std::vector<double> &co) {
     const int l = u.level;
-    std::vector<Rec::AdjustItem> items = {{u, l - 1, co[3]}, {u, l - 2, co[2]}, {u, l - 2, co[1]}, {u, l - 3, co[0]}};
-    if (co.size() == 8)
-        for (int h = 7; h >= 4; h--) items.push_back({u, h == 7 ? l - 1 : (h == 4 ? l - 3 : l - 2), co[h]});
+    std::vector<Rec::AdjustItem> items = {{u, l - 1, co[3]}, {u, l - 2, co[1]}};
+    if (co.size() == 8) {
+        items.push_back({u, l - 1, co[7]});
+        items.push_back({u, l - 2, co[5]});
+    }
     std::vector<CtH> a = R.adjust_many(items);
     CtH u2 = R.mul(u, u);
     CtH u4 = R.mul(u2, u2);
     CtH u2d = R.adjust(u2, l - 2, 1.0);
-    CtH A = odd7(R, a.data(), u2, u2d, u4, l);
+    CtH A = odd7(R, a[0], a[1], co[2], co[0], u, u2, u2d, u4, l);
     if (co.size() == 4) return A;
     CtH u8 = R.mul(u4, u4);
-    CtH B = odd7(R, a.data() + 4, u2, u2d, u4, l);
-    CtH P = relin_rescale_to(R, R.tensor(u8, B), l - 4);
-    return R.add(R.adjust(A, l - 4, 1.0), P);
+    CtH B = odd7(R, a[2], a[3], co[6], co[4], u, u2, u2d, u4, l);
+    return relin_rescale_to(R, fold(R, R.tensor(u8, B), A, 1.0), l - 4);
 }
 
 static CtH eval_blocks(Rec &R, const Database &db, const QPlan &pl, int b0, int nb, const CtH &w,
@@ -233,7 +289,7 @@ static CtH eval_blocks(Rec &R, const Database &db, const QPlan &pl, int b0, int 
         // y = sum_k c_k x^k with one relinearisation
         need_ck();
         CtH T;
-        for (int k = 1; k <= degree; k++) T = R.tensor_add(T, ck[k], lvl(k, pl.l_d));
+        for (int k = 1; k <= degree; k++) T = R.tensor_add(T, ck[k], R.drop(Pw[k], pl.l_d));
         y = relin_rescale_to(R, T, pl.l_y);
     } else {
         const int g = pl.g, m = pl.m, l_b = pl.l_lin - pl.bb, l_f = pl.l_lin - pl.df;
@@ -253,13 +309,13 @@ static CtH eval_blocks(Rec &R, const Database &db, const QPlan &pl, int b0, int 
         for (int i = 2; i < m; i++) G[i] = power_rule(G, i, glvl);
         need_ck();
         CtH T;
-        for (int j = 1; j < g; j++) T = R.tensor_add(T, ck[j], lvl(j, l_f));  // s_0's terms at l_f
+        for (int j = 1; j < g; j++) T = R.tensor_add(T, ck[j], R.drop(Pw[j], l_f));  // s_0's terms at l_f
         for (int i = 1; i < m; i++) {
             CtH Ti;
-            for (int j = 1; j < g && g * i + j <= degree; j++) Ti = R.tensor_add(Ti, ck[g * i + j], lvl(j, l_b));
+            for (int j = 1; j < g && g * i + j <= degree; j++) Ti = R.tensor_add(Ti, ck[g * i + j], R.drop(Pw[j], l_b));
             CtH si = ck[g * i];
             if (Ti.buf) si = R.adjust(R.add(relin_rescale_to(R, Ti, l_b - 1), ck[g * i]), l_f, 1.0);
-            T = R.tensor_add(T, si, glvl(i, l_f));
+            T = R.tensor_add(T, si, R.drop(G[i], l_f));
         }
         G.clear();
         gcache.clear();
@@ -333,7 +389,7 @@ std::unique_ptr<Program> record_query(Ctx &C, const Database &db, const QuerySpe
         if (!ck.empty()) return;
         P->add_late_wait();
         std::vector<Rec::AdjustItem> items;
-        for (int k = 0; k <= q.degree; k++) items.push_back({cin[k], pl.coef_level(k), 1.0});
+        for (int k = 0; k <= q.degree; k++) items.push_back({cin[k], pl.coef_level(k), pl.cfac[k]});
         items.push_back({tin, pl.l_y, 1.0});
         ck = R.adjust_many_coef(items);
         tadj = ck.back();
