@@ -228,21 +228,32 @@ def make_plan(par: Params, shape: QueryShape) -> Plan:
         raise ValueError(f"global threshold needs more levels: ends at level {l_ret}")
     pt_scale = (S[L - 1] * float(par.q[L])) / S[L]
     bsgs = poly_schedule(shape.degree)
-    lev = lambda k: l_lin - ceil_log2(k)              # level of the power x^k
     cf = [1.0] * (shape.degree + 1)
+    if bsgs is None:
+        sp, _ = power_scales(S[l_lin], l_lin, shape.degree, par.q)
+    else:
+        g, m, bb, df = bsgs
+        sp, lp = power_scales(S[l_lin], l_lin, max(g - 1, 1), par.q)
+        h = max(g // 2, 1)
+        sg, _ = power_scales((sp[h] * sp[h]) / float(par.q[lp[h]]), lp[h] - 1, max(m - 1, 1), par.q)
     for k in range(1, shape.degree + 1):
         if bsgs is None:
-            cf[k] = S[l_d] / S[lev(k)]
+            cf[k] = S[l_d] / sp[k]
             continue
-        g, m, bb, df = bsgs
         i, j = divmod(k, g)
         l_b, l_f = l_lin - bb, l_lin - df
         if i == 0:
-            cf[k] = S[l_f] / S[lev(j)]
+            cf[k] = S[l_f] / sp[j]
             continue
-        # s_i multiplies x^(g i) (level l_lin - b - ceil_log2(i), g = 2^b) dropped to l_f
-        fi = S[l_f] / S[l_lin - ceil_log2(g) - ceil_log2(i)]
-        cf[k] = fi * (S[l_b] / S[lev(j)]) if j >= 1 else fi
+        # s_i multiplies x^(g i) dropped to l_f, and is itself dropped there
+        # from l_b - 1 (its terms carry S[l_f] / S[l_b - 1] for that; c_d
+        # alone, at l_f, does not)
+        fi = S[l_f] / sg[i]
+        rb = S[l_f] / S[l_b - 1]
+        if j >= 1:
+            cf[k] = (fi * (S[l_b] / sp[j])) * rb
+        else:
+            cf[k] = fi * rb if k < shape.degree else fi
     w_factor = (S[l_lin] * float(par.q[l_lin + 1])) / (S[l_lin + 1] * pt_scale) if l_lin < L - 1 else 0.0
     return Plan(S=S, l_lin=l_lin, l_d=l_d, l_y=l_y, l_u=l_u, l_out=l_out, l_ret=l_ret, global_coeffs=gco,
                 records_norm=R, w_factor=w_factor,
@@ -250,6 +261,20 @@ def make_plan(par: Params, shape: QueryShape) -> Plan:
                 mask_scale=((S[l_u - 1] * float(par.q[l_u])) / S[l_u]) if ragged else 0.0,
                 ragged=ragged, stage_coeffs=stages, step_const=1.0 / (2.0 * R),
                 bsgs=bsgs, degree=shape.degree, coef_factors=cf)
+
+
+def power_scales(scale: float, level: int, n: int, q) -> tuple:
+    """Scales and levels of y^1..y^n formed from y (scale, level) by the power
+    rule y^k = y^a y^(k-a), a the largest power of two <= k (a power of two is
+    the square of its half), the lower factor dropped to the other's level and
+    the relinearisation's rescale removing that level's prime."""
+    sc, lv = {1: scale}, {1: level}
+    for k in range(2, n + 1):
+        a = 1 << (k.bit_length() - 1)
+        A, B = (k // 2, k // 2) if a == k else (a, k - a)
+        sc[k] = (sc[A] * sc[B]) / float(q[lv[A]])
+        lv[k] = lv[A] - 1
+    return sc, lv
 
 
 def adjust_const(plan: Plan, par: Params, lt: int, a: float, scale: float) -> int:
@@ -431,12 +456,14 @@ class Evaluator:
         l = u.level
         u2 = self.mul(u, u)
         u4 = self.mul(u2, u2)
-        u2d = self.adjust(u2, l - 2)
-        A = self.odd7(self.adjust(u, l - 1, co[3]), self.adjust(u, l - 2, co[1]), co[2], co[0], u, u2, u2d, u4, l)
+        # u^2 is dropped to l-2 (scale S[l-1]); a1 u carries S[l-2] / S[l-1]
+        u2d = ckks.drop_to(u2, l - 2)
+        r = self.plan.S[l - 2] / self.plan.S[l - 1]
+        A = self.odd7(self.adjust(u, l - 1, co[3]), self.adjust(u, l - 2, co[1] * r), co[2], co[0], u, u2, u2d, u4, l)
         if len(co) == 4:
             return A
         u8 = self.mul(u4, u4)
-        B = self.odd7(self.adjust(u, l - 1, co[7]), self.adjust(u, l - 2, co[5]), co[6], co[4], u, u2, u2d, u4, l)
+        B = self.odd7(self.adjust(u, l - 1, co[7]), self.adjust(u, l - 2, co[5] * r), co[6], co[4], u, u2, u2d, u4, l)
         return self.relin_rescale(self.fold(ckks.tensor(self.par, u8, B), A, 1.0), l - 4)
 
     def per_query(self, q: EncQuery, degree: int):
@@ -460,27 +487,22 @@ class Evaluator:
             acc = prod if acc is None else ckks.add(par, acc, prod)
         x = ckks.rescale(par, acc)
         x.scale = p.S[p.l_lin]
-        # powers x^k, k <= degree
+        # powers x^k, k <= degree; a factor of lower power is dropped (not
+        # adjusted) to the other's level, so a power's scale is the product of
+        # its factors' over the prime the relinearisation removes (power_scales)
         P = {1: x}
-        cache = {}
 
-        def lvl(k: int, lt: int) -> Ct:
-            if P[k].level == lt:
-                return P[k]
-            if (k, lt) not in cache:
-                cache[(k, lt)] = self.adjust(P[k], lt)
-            return cache[(k, lt)]
-
-        def power_rule(Q, k, at):
+        def power_rule(Q, k):
             # x^k = x^a x^(k-a), a the largest power of two <= k (depth ceil_log2(k))
             a = 1 << (k.bit_length() - 1)
-            if a == k:
-                return self.mul(Q[k // 2], Q[k // 2])
-            return self.mul(Q[a], at(k - a, Q[a].level))
+            A, B = (Q[k // 2], Q[k // 2]) if a == k else (Q[a], ckks.drop_to(Q[k - a], Q[a].level))
+            out = self.mul(A, B)
+            out.scale = (A.scale * B.scale) / float(par.q[A.level])
+            return out
 
         if p.bsgs is None:
             for k in range(2, degree + 1):
-                P[k] = power_rule(P, k, lvl)
+                P[k] = power_rule(P, k)
             # y = sum_k c_k x^k: degree-2 products summed, one relinearisation
             T = None
             for k in range(1, degree + 1):
@@ -491,19 +513,10 @@ class Evaluator:
             g, m, bb, df = p.bsgs
             l_b, l_f = p.l_lin - bb, p.l_lin - df
             for k in range(2, g):
-                P[k] = power_rule(P, k, lvl)
-            G = {1: self.mul(P[g // 2], P[g // 2])}     # giant powers x^(g i)
-            gcache = {}
-
-            def glvl(i: int, lt: int) -> Ct:
-                if G[i].level == lt:
-                    return G[i]
-                if (i, lt) not in gcache:
-                    gcache[(i, lt)] = self.adjust(G[i], lt)
-                return gcache[(i, lt)]
-
+                P[k] = power_rule(P, k)
+            G = {1: power_rule({1: P[g // 2]}, 2)}     # giant powers x^(g i)
             for i in range(2, m):
-                G[i] = power_rule(G, i, glvl)
+                G[i] = power_rule(G, i)
             # s_i, i >= 1: sum_{j>=1} c_{gi+j} x^j at l_b, relinearised, plus c_{gi}
             T = None
             for j in range(1, g):          # s_0's terms at l_f
@@ -519,8 +532,7 @@ class Evaluator:
                 if Ti is None:
                     si = ck[g * i]
                 else:
-                    si = ckks.add(par, self.relin_rescale(Ti, l_b - 1), ck[g * i])
-                    si = self.adjust(si, l_f)
+                    si = ckks.drop_to(ckks.add(par, self.relin_rescale(Ti, l_b - 1), ck[g * i]), l_f)
                 T = ckks.add(par, T, ckks.tensor(par, si, ckks.drop_to(G[i], l_f)))
             y = self.relin_rescale(T, l_f - 1)
             y = self.adjust(y, p.l_y)

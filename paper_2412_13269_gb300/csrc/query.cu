@@ -75,6 +75,24 @@ static void poly_schedule(QPlan &p, int d) {
     }
 }
 
+// Scales and levels of y^1..y^n formed from y (scale, level) by the power rule
+// y^k = y^a y^(k-a), a the largest power of two <= k (a power of two the square
+// of its half), the lower factor dropped to the other's level and the
+// relinearisation's rescale removing that level's prime.  Index k; [0] unused.
+static void power_scales(const Ctx &C, double scale, int level, int n, std::vector<double> &sc, std::vector<int> &lv) {
+    sc.assign(n + 1, 0.0);
+    lv.assign(n + 1, 0);
+    sc[1] = scale;
+    lv[1] = level;
+    for (int k = 2; k <= n; k++) {
+        int a = 1;
+        while (a * 2 <= k) a *= 2;
+        const int A = a == k ? k / 2 : a, B = a == k ? k / 2 : k - a;
+        sc[k] = (sc[A] * sc[B]) / (double)C.q[lv[A]];
+        lv[k] = lv[A] - 1;
+    }
+}
+
 // level at which the encrypted coefficient c_k is used
 int QPlan::coef_level(int k) const {
     if (k == 0) return l_y;
@@ -128,21 +146,33 @@ QPlan make_plan(const Ctx &C, uint64_t records, int degree, const std::vector<st
     poly_schedule(p, degree);
     {
         const auto &S = C.S;
-        auto lev = [&](int k) { return p.l_lin - ceil_log2(k); };  // level of the power x^k
+        std::vector<double> sp, sg;
+        std::vector<int> lp, lg;
         p.cfac.assign(degree + 1, 1.0);
+        if (p.g == 0) {
+            power_scales(C, S[p.l_lin], p.l_lin, degree, sp, lp);
+        } else {
+            power_scales(C, S[p.l_lin], p.l_lin, std::max(p.g - 1, 1), sp, lp);
+            const int h = std::max(p.g / 2, 1);
+            power_scales(C, (sp[h] * sp[h]) / (double)C.q[lp[h]], lp[h] - 1, std::max(p.m - 1, 1), sg, lg);
+        }
         for (int k = 1; k <= degree; k++) {
             if (p.g == 0) {
-                p.cfac[k] = S[p.l_d] / S[lev(k)];
+                p.cfac[k] = S[p.l_d] / sp[k];
                 continue;
             }
             const int i = k / p.g, j = k % p.g, l_b = p.l_lin - p.bb, l_f = p.l_lin - p.df;
             if (i == 0) {
-                p.cfac[k] = S[l_f] / S[lev(j)];
+                p.cfac[k] = S[l_f] / sp[j];
                 continue;
             }
-            // s_i multiplies x^(g i) (level l_lin - log2 g - ceil_log2(i)) dropped to l_f
-            const double fi = S[l_f] / S[p.l_lin - ceil_log2(p.g) - ceil_log2(i)];
-            p.cfac[k] = j >= 1 ? fi * (S[l_b] / S[lev(j)]) : fi;
+            // s_i multiplies x^(g i) dropped to l_f, and is itself dropped there
+            // from l_b - 1 (its terms carry S[l_f] / S[l_b - 1] for that; c_d
+            // alone, at l_f, does not)
+            const double fi = S[l_f] / sg[i];
+            const double rb = S[l_f] / S[l_b - 1];
+            if (j >= 1) p.cfac[k] = (fi * (S[l_b] / sp[j])) * rb;
+            else p.cfac[k] = k < degree ? fi * rb : fi;
         }
     }
     // global threshold: step = (p + 1)/2 folded into the last stage
@@ -215,18 +245,20 @@ static CtH odd7(Rec &R, const CtH &a3u, const CtH &a1u, double c2, double c0, co
 // relinearisations; degree 15 in depth 4 as A(u) + u^8 B(u), A and B the
 // degree-7 parts of the low and high coefficients (u^2, u^4 shared), eight
 // relinearisations, A folded into u^8 B.  The adjusts of u are independent:
-// one pair of transforms.
+// one pair of transforms; u^2 is only dropped.
 static CtH sign_stage(Rec &R, const CtH &u, const std::vector<double> &co) {
     const int l = u.level;
-    std::vector<Rec::AdjustItem> items = {{u, l - 1, co[3]}, {u, l - 2, co[1]}};
+    // u^2 is dropped to l-2 (scale S[l-1]); a1 u carries S[l-2] / S[l-1]
+    const double r = R.C.S[l - 2] / R.C.S[l - 1];
+    std::vector<Rec::AdjustItem> items = {{u, l - 1, co[3]}, {u, l - 2, co[1] * r}};
     if (co.size() == 8) {
         items.push_back({u, l - 1, co[7]});
-        items.push_back({u, l - 2, co[5]});
+        items.push_back({u, l - 2, co[5] * r});
     }
     std::vector<CtH> a = R.adjust_many(items);
     CtH u2 = R.mul(u, u);
     CtH u4 = R.mul(u2, u2);
-    CtH u2d = R.adjust(u2, l - 2, 1.0);
+    CtH u2d = R.drop(u2, l - 2);
     CtH A = odd7(R, a[0], a[1], co[2], co[0], u, u2, u2d, u4, l);
     if (co.size() == 4) return A;
     CtH u8 = R.mul(u4, u4);
@@ -263,29 +295,24 @@ static CtH eval_blocks(Rec &R, const Database &db, const QPlan &pl, int b0, int 
     CtH x = R.rescale(x0);
     x.scale = C.S[pl.l_lin];
     x0 = CtH();
-    // powers x^k
+    // powers x^k; a factor of lower power is dropped (not adjusted) to the
+    // other's level, so a power's scale is its factors' product over the prime
+    // the relinearisation removes (the planner's power_scales)
     std::map<int, CtH> Pw;
-    std::map<std::pair<int, int>, CtH> cache;
     Pw[1] = x;
-    auto lvl = [&](int k, int lt) -> CtH {
-        if (Pw[k].level == lt) return Pw[k];
-        auto key = std::make_pair(k, lt);
-        auto it = cache.find(key);
-        if (it != cache.end()) return it->second;
-        CtH a = R.adjust(Pw[k], lt, 1.0);
-        cache[key] = a;
-        return a;
-    };
     // x^k = x^a x^(k-a), a the largest power of two <= k (depth ceil_log2(k))
-    auto power_rule = [&](std::map<int, CtH> &Q, int k, const std::function<CtH(int, int)> &at) {
+    auto power_rule = [&](std::map<int, CtH> &Q, int k) {
         int a = 1;
         while (a * 2 <= k) a *= 2;
-        if (a == k) return R.mul(Q[k / 2], Q[k / 2]);
-        return R.mul(Q[a], at(k - a, Q[a].level));
+        const CtH A = a == k ? Q[k / 2] : Q[a];
+        const CtH B = a == k ? Q[k / 2] : R.drop(Q[k - a], A.level);
+        CtH o = R.mul(A, B);
+        o.scale = (A.scale * B.scale) / (double)C.q[A.level];
+        return o;
     };
     CtH y;
     if (pl.g == 0) {
-        for (int k = 2; k <= degree; k++) Pw[k] = power_rule(Pw, k, lvl);
+        for (int k = 2; k <= degree; k++) Pw[k] = power_rule(Pw, k);
         // y = sum_k c_k x^k with one relinearisation
         need_ck();
         CtH T;
@@ -293,20 +320,13 @@ static CtH eval_blocks(Rec &R, const Database &db, const QPlan &pl, int b0, int 
         y = relin_rescale_to(R, T, pl.l_y);
     } else {
         const int g = pl.g, m = pl.m, l_b = pl.l_lin - pl.bb, l_f = pl.l_lin - pl.df;
-        for (int k = 2; k < g; k++) Pw[k] = power_rule(Pw, k, lvl);
+        for (int k = 2; k < g; k++) Pw[k] = power_rule(Pw, k);
         std::map<int, CtH> G;  // giant powers x^(g i)
-        std::map<std::pair<int, int>, CtH> gcache;
-        G[1] = R.mul(Pw[g / 2], Pw[g / 2]);
-        auto glvl = [&](int i, int lt) -> CtH {
-            if (G[i].level == lt) return G[i];
-            auto key = std::make_pair(i, lt);
-            auto it = gcache.find(key);
-            if (it != gcache.end()) return it->second;
-            CtH a = R.adjust(G[i], lt, 1.0);
-            gcache[key] = a;
-            return a;
-        };
-        for (int i = 2; i < m; i++) G[i] = power_rule(G, i, glvl);
+        {
+            std::map<int, CtH> h = {{1, Pw[g / 2]}};
+            G[1] = power_rule(h, 2);
+        }
+        for (int i = 2; i < m; i++) G[i] = power_rule(G, i);
         need_ck();
         CtH T;
         for (int j = 1; j < g; j++) T = R.tensor_add(T, ck[j], R.drop(Pw[j], l_f));  // s_0's terms at l_f
@@ -314,15 +334,13 @@ static CtH eval_blocks(Rec &R, const Database &db, const QPlan &pl, int b0, int 
             CtH Ti;
             for (int j = 1; j < g && g * i + j <= degree; j++) Ti = R.tensor_add(Ti, ck[g * i + j], R.drop(Pw[j], l_b));
             CtH si = ck[g * i];
-            if (Ti.buf) si = R.adjust(R.add(relin_rescale_to(R, Ti, l_b - 1), ck[g * i]), l_f, 1.0);
+            if (Ti.buf) si = R.drop(R.add(relin_rescale_to(R, Ti, l_b - 1), ck[g * i]), l_f);
             T = R.tensor_add(T, si, R.drop(G[i], l_f));
         }
         G.clear();
-        gcache.clear();
         y = R.adjust(relin_rescale_to(R, T, l_f - 1), pl.l_y, 1.0);
     }
     Pw.clear();
-    cache.clear();
     y = R.add(y, ck[0]);
     CtH u = R.sub(y, tadj);
     for (auto &co : pl.co) u = sign_stage(R, u, co);
