@@ -7,7 +7,7 @@ coefficients, degree-15 polynomial with encrypted coefficients, encrypted
 threshold, three composite-sign stages, block sum, InnerSum, output back to
 the coefficient domain.  Workload: N = 2^16, twenty 50-bit ciphertext primes,
 three 60-bit special primes, Delta = 2^50, 131072 records x 16 attributes
-(four 32768-slot blocks), alpha = 3 (seven key digits at the top level).
+(four 32768-slot blocks), alpha = 4 (five key digits at the top level).
 
 Metric: amortised microseconds per record per query (lower is better),
 batched form (every launch covers all blocks, CUDA-graph replay) as `value`,
@@ -40,8 +40,8 @@ import synth  # noqa: E402
 
 METRIC = "amortized µs/record/query (batched vs plain on GB300); keyswitch GB/s vs HBM peak"
 WL = dict(log_n=16, n_q=20, q_bits=50, n_p=3, p_bits=60, scale=2.0 ** 50, records=131072, attrs=16, degree=15,
-          stages=3, alpha=3, dist="mixed", hw=192)
-WL_NAME = "query N=2^16 L=20x50b K=3x60b alpha=3; 131072 records x 16 attrs; f deg 15 enc coeffs; 3 x deg-7 sign; InnerSum"
+          stages=3, alpha=4, dist="mixed", hw=192)
+WL_NAME = "query N=2^16 L=20x50b K=3x60b alpha=4; 131072 records x 16 attrs; f deg 15 enc coeffs; 3 x deg-7 sign; InnerSum"
 F3 = (35.0 / 16.0, -35.0 / 16.0, 21.0 / 16.0, -5.0 / 16.0)
 
 
@@ -255,8 +255,8 @@ def run_micro_keyswitch(calls: int):
 def run_c3(args):
     """Batching workload: 524288 records x 32 attributes (16 blocks of 32768
     slots) at the benchmark parameters.  For each keyswitch digit size alpha in
-    {3, 2, 1} (dnum = 7, 10, 20 at 20 primes; larger digits need more special
-    primes than the three the parameters give), keys are generated and the
+    {4, 3, 2, 1} (dnum = 5, 7, 10, 20 at 20 primes; the kernels take at most
+    four primes per digit), keys are generated and the
     library's autotuner times the query under every schedule it knows (blocks
     per launch x NTT register-group width).  Reports the tuned best against
     the fixed plain schedule (one block per launch, radix-8 groups, alpha 3)."""
@@ -284,7 +284,7 @@ def run_c3(args):
     t = enc(qv.t, "t")
     qargs = (w, [(L, Delta)] * len(w), c, [(L, Delta)] * len(c), t, (L, Delta), np.array([F3] * WL["stages"]))
     per_alpha = []
-    for alpha in (3, 2, 1):
+    for alpha in (4, 3, 2, 1):
         dnum = -(-WL["n_q"] // alpha)
         d = synth.switch_key_draws(seed, f"relin.a{alpha}", dnum, q + p, N)
         ctx.keygen_relin(s, d.a, d.e, alpha)
@@ -311,6 +311,9 @@ def run_c3(args):
     ctx.close()
 
 
+C4_ALPHA = 3  # rotations run at every level here, where four-prime digits would exceed P
+
+
 def run_c4(args):
     """Uneven batch: 64 independent ciphertexts at ring degrees drawn from
     {2^14, 2^15, 2^16} and levels from [4, 19] (seeded), each through
@@ -329,12 +332,12 @@ def run_c4(args):
         N = 1 << log_n
         ctx = T.Ctx(log_n, q, p, Delta, device=local_rank)
         s = synth.ternary_secret(synth.stream(seed, f"secret{log_n}"), N, WL["hw"])
-        dnum = -(-WL["n_q"] // WL["alpha"])
+        dnum = -(-WL["n_q"] // C4_ALPHA)
         d = synth.switch_key_draws(seed, f"relin{log_n}", dnum, q + p, N)
-        ctx.keygen_relin(s, d.a, d.e, WL["alpha"])
+        ctx.keygen_relin(s, d.a, d.e, C4_ALPHA)
         for g in galois_elements(N):
             d = synth.switch_key_draws(seed, f"rot{g}.{log_n}", dnum, q + p, N)
-            ctx.keygen_rotation(g, s, d.a, d.e, WL["alpha"])
+            ctx.keygen_rotation(g, s, d.a, d.e, C4_ALPHA)
         ctxs[log_n] = ctx
     g = np.random.default_rng(seed)
     items = []

@@ -51,6 +51,14 @@ def wide():
     return Setup(12, q, rns.gen_primes(60, 3), 2.0 ** 50, 3, 22)
 
 
+@pytest.fixture(scope="module")
+def wide4():
+    """As `wide` with four-prime digits (alpha = 4 > K = 3), the benchmark's digit size."""
+    T.build()
+    q = rns.gen_primes(50, 8)
+    return Setup(12, q, rns.gen_primes(60, 3), 2.0 ** 50, 4, 24)
+
+
 def test_ntt_order_and_values(small):
     par, ctx = small.par, small.ctx
     a = rand_ct(par, 1, 3, 1)
@@ -62,7 +70,7 @@ def test_ntt_order_and_values(small):
         assert np.array_equal(got[0, i], x[perm]), i
 
 
-@pytest.mark.parametrize("fx", ["small", "wide"])
+@pytest.mark.parametrize("fx", ["small", "wide", "wide4"])
 def test_elementwise(fx, request):
     S = request.getfixturevalue(fx)
     par, ctx = S.par, S.ctx
@@ -84,7 +92,7 @@ def test_elementwise(fx, request):
     assert np.array_equal(got, ckks.mul_plain(par, A, pt[0], 1.0).data)
 
 
-@pytest.mark.parametrize("fx", ["small", "wide"])
+@pytest.mark.parametrize("fx", ["small", "wide", "wide4"])
 def test_rescale(fx, request):
     S = request.getfixturevalue(fx)
     par, ctx = S.par, S.ctx
@@ -96,7 +104,7 @@ def test_rescale(fx, request):
             assert lev == l - 1 and np.array_equal(got, want.data), (l, comps)
 
 
-@pytest.mark.parametrize("fx", ["small", "wide"])
+@pytest.mark.parametrize("fx", ["small", "wide", "wide4"])
 def test_keyswitch_relin_rotate(fx, request):
     S = request.getfixturevalue(fx)
     par, ctx, keys = S.par, S.ctx, S.keys
@@ -113,7 +121,7 @@ def test_keyswitch_relin_rotate(fx, request):
         assert np.array_equal(got, ckks.rotate(par, ckks.Ct(a, l, 1.0), g, keys.rot[g], S.alpha).data), l
 
 
-@pytest.mark.parametrize("fx", ["small", "wide"])
+@pytest.mark.parametrize("fx", ["small", "wide", "wide4"])
 def test_fused_relin_rescale_and_factor_rescale(fx, request):
     """The fused forms equal the oracle's compositions: rescale(relinearize(t))
     and rescale(mul_int(a, f)), including factors that are not invertible
@@ -143,7 +151,7 @@ def test_innersum(small):
     assert np.array_equal(got, acc.data)
 
 
-@pytest.mark.parametrize("fx", ["small", "wide"])
+@pytest.mark.parametrize("fx", ["small", "wide", "wide4"])
 def test_keygen_matches_oracle(fx, request):
     S = request.getfixturevalue(fx)
     par = S.par

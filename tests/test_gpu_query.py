@@ -202,16 +202,16 @@ def test_errors_leave_context_usable(chain):
 
 @pytest.fixture(scope="module")
 def full():
-    """The benchmark's parameters: N = 2^16, twenty 50-bit primes, three 60-bit special primes, Delta = 2^50, alpha = 3."""
+    """The benchmark's parameters: N = 2^16, twenty 50-bit primes, three 60-bit special primes, Delta = 2^50, alpha = 4."""
     T.build()
     q, p = rns.gen_primes(50, 20), rns.gen_primes(60, 3)
     par = ckks.Params(16, q, p, 2.0 ** 50)
     ctx = T.Ctx(16, q, p, 2.0 ** 50)
     s = query.secret(par, 8, 192)
-    keys = query.make_keys(par, s, 8, 3, query.innersum_galois(par))
-    ctx.load_relin_key(keys.rlk, 3)
+    keys = query.make_keys(par, s, 8, 4, query.innersum_galois(par))
+    ctx.load_relin_key(keys.rlk, 4)
     for g, k in keys.rot.items():
-        ctx.load_rotation_key(g, k, 3)
+        ctx.load_rotation_key(g, k, 4)
     return par, ctx, s, keys
 
 
