@@ -785,7 +785,7 @@ def main():
         "config": {"workload": WL_NAME, "records_per_gpu": WL["records"], "records_total": records_total,
                    "form": "batched: every launch covers all 4 blocks; CUDA graph replay; device-resident inputs"
                            + ("; per step: NCCL all-reduce of the ranks' result residues + reduction mod q" if world > 1 else ""),
-                   "l2": "inputs larger than L2 (2.6 GB of keys, 640 MiB database per query)",
+                   "l2": "inputs larger than L2 (1.8 GB of keys, 640 MiB database per query)",
                    "parallelism": f"records sharded over {world} GPU(s)"},
         "plain": plain,
         "e2e": {"value": e2e_ms * 1e3 / WL["records"], "unit": "us/record/query", "ms_per_step": e2e_ms,
