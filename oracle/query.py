@@ -429,7 +429,10 @@ class Evaluator:
         relinearisation's rescale that follows covers it).  A reading: the
         paper does not say how the sign polynomial's terms are combined."""
         par, lt = self.par, T.level
-        c = round_half_up(((a * self.plan.S[lt]) * self.plan.S[lt]) / v.scale)
+        cf = ((a * self.plan.S[lt]) * self.plan.S[lt]) / v.scale
+        if not abs(cf) < 2.0 ** 62:
+            raise ValueError("fold: coefficient too large for an integer multiple")
+        c = round_half_up(cf)
         m = ckks.mul_int(par, ckks.drop_to(v, lt), c)
         mods = par.q[: lt + 1]
         data = T.data.copy()

@@ -65,7 +65,10 @@ size_t Ctx::bytes_held() const {
     return b;
 }
 
-int64_t round_half_up(double x) { return (int64_t)std::floor(x + 0.5); }
+int64_t round_half_up(double x) {
+    TREQUIRE(std::fabs(x) < 0x1p62, TETRIS_EINVAL, "a scaled constant does not fit 62 bits");
+    return (int64_t)std::floor(x + 0.5);
+}
 
 const Key &find_key(const Ctx &c, uint32_t galois) {
     if (galois == 0) {

@@ -210,7 +210,9 @@ static CtH fold(Rec &R, const CtH &T, const CtH &v, double a) {
     Ctx &C = R.C;
     const int lt = T.level;
     TREQUIRE(T.comps == 3 && v.level >= lt && v.B == T.B, TETRIS_EINVAL, "fold: operands differ");
-    const int64_t c = round_half_up(((a * C.S[lt]) * C.S[lt]) / v.scale);
+    const double cf = ((a * C.S[lt]) * C.S[lt]) / v.scale;
+    TREQUIRE(std::fabs(cf) < 0x1p62, TETRIS_EINVAL, "fold: coefficient too large for an integer multiple");
+    const int64_t c = round_half_up(cf);
     std::vector<EwJob> jobs;
     for (int i = 0; i <= lt; i++) {
         const u64 qi = C.q[i];
