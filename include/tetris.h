@@ -84,6 +84,10 @@ int tetris_gen_primes(uint32_t bits, uint32_t count, uint32_t congruence_log2,
  * to device memory (converted to its internal NTT domain); loading a key for
  * an element that already has one replaces it.  All keys of a context share
  * one alpha: loading a key with a different alpha drops every loaded key.
+ * alpha is 1..4 (EINVAL otherwise).  A digit wider than P is accepted: its
+ * key-switch noise ~ (Q_j / P) sigma sqrt(N dnum) is harmless where the
+ * switched ciphertext's scale is far above it (relinearisation, at scale
+ * Delta^2; rotations at level 1), and the caller's choice elsewhere.
  * ------------------------------------------------------------------------- */
 int tetris_load_relin_key(tetris_ctx *ctx, const uint64_t *evk, size_t n_words, uint32_t alpha);
 int tetris_load_rotation_key(tetris_ctx *ctx, uint32_t galois_elt, const uint64_t *evk,
