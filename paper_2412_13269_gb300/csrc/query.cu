@@ -10,6 +10,12 @@
 // exactly onto S[l-1].  adjust() moves a ciphertext to a lower level t with
 // scale S[t] and applies a public factor a in one rescale: keep q_0..q_{t+1},
 // multiply by floor(a * S[t] * q_{t+1} / scale + 1/2), rescale by q_{t+1}.
+// Exceptions, kept exact by the planner: a power of x formed with a dropped
+// (not adjusted) factor carries its factors' product over the removed prime;
+// an encrypted coefficient multiplying a dropped power carries the ratio of
+// scales from its arrival adjust; a sign stage folds its additive terms into
+// the degree-2 sum before the relinearisation's rescale.  The circuit starts
+// at the lowest level its depth allows and ends at level 1.
 //
 // A block group of nb blocks is evaluated with every launch covering all nb
 // blocks (nb = all blocks: batched form; nb = 1: plain per-ciphertext form).
