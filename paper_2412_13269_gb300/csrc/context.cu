@@ -412,8 +412,11 @@ void Rec::ew(const std::vector<EwJob> &jobs) {
         rd.push_back(j.c2);
         writes += (j.op == EW_TENSOR || j.op == EW_TENSOR_ACC) ? 3 : 1;
     }
+    bool tensor = true;
+    for (auto &j : jobs) tensor = tensor && (j.op == EW_TENSOR || j.op == EW_TENSOR_ACC);
     P.add_launch([=](cudaStream_t s, const uint8_t *a) {
-        launch_ew(reinterpret_cast<const EwJob *>(a + off), n, logn, m, s);
+        if (tensor) launch_tensor(reinterpret_cast<const EwJob *>(a + off), n, logn, m, s);
+        else launch_ew(reinterpret_cast<const EwJob *>(a + off), n, logn, m, s);
     }, prefix + "ew_" + ew_name(jobs[0].op), distinct_bytes(rd, C.N) + writes * C.N * 8);
 }
 

@@ -155,6 +155,81 @@ __global__ void __launch_bounds__(kEwThreads) ew_kernel(const EwJob *jobs, int l
     }
 }
 
+// Tensor products (and tensor-accumulate) without the generic descriptor
+// staging: every thread reads the job's fields through the read-only cache,
+// handles two 16-byte pairs with all operand loads issued first, and forms
+// a0 b1 + a1 b0 as (a0 + a1)(b0 + b1) - a0 b0 - a1 b1 on 128-bit products
+// (three products instead of four; the same residues).
+__device__ __forceinline__ void mul128(u64 a, u64 b, u64 &hi, u64 &lo) {
+    lo = a * b;
+    hi = __umul64hi(a, b);
+}
+__global__ void __launch_bounds__(kEwThreads, 4) tensor_kernel(const EwJob *jobs, int log_n, const ModInfo *mods) {
+    const EwJob *jp = jobs + blockIdx.y;
+    const u64 *A0 = (const u64 *)__ldg((const unsigned long long *)&jp->a);
+    const u64 *A1 = (const u64 *)__ldg((const unsigned long long *)&jp->a1);
+    const u64 *B0 = (const u64 *)__ldg((const unsigned long long *)&jp->b);
+    const u64 *B1 = (const u64 *)__ldg((const unsigned long long *)&jp->b1);
+    u64 *D0 = (u64 *)__ldg((const unsigned long long *)&jp->dst);
+    u64 *D1 = (u64 *)__ldg((const unsigned long long *)&jp->d1);
+    u64 *D2 = (u64 *)__ldg((const unsigned long long *)&jp->d2);
+    const int op = __ldg(&jp->op);
+    const ModInfo m = mods[__ldg(&jp->prime)];
+    const u64 q = m.q;
+    const size_t n = (size_t)1 << log_n;
+    size_t p[2];
+    ulonglong2 a0[2], a1[2], b0[2], b1[2];
+#pragma unroll
+    for (int u = 0; u < 2; u++) {
+        p[u] = (((size_t)blockIdx.x * 2 + u) * kEwThreads + threadIdx.x) * 2;
+        if (p[u] < n) {
+            a0[u] = *reinterpret_cast<const ulonglong2 *>(A0 + p[u]);
+            a1[u] = *reinterpret_cast<const ulonglong2 *>(A1 + p[u]);
+            b0[u] = *reinterpret_cast<const ulonglong2 *>(B0 + p[u]);
+            b1[u] = *reinterpret_cast<const ulonglong2 *>(B1 + p[u]);
+        }
+    }
+    const u64 *C0 = nullptr, *C1 = nullptr, *C2 = nullptr;
+    if (op == EW_TENSOR_ACC) {
+        C0 = (const u64 *)__ldg((const unsigned long long *)&jp->c);
+        C1 = (const u64 *)__ldg((const unsigned long long *)&jp->c1);
+        C2 = (const u64 *)__ldg((const unsigned long long *)&jp->c2);
+    }
+#pragma unroll
+    for (int u = 0; u < 2; u++) {
+        if (p[u] >= n) break;
+        u64 r0[2], r1[2], r2[2];
+        const u64 x0[2] = {a0[u].x, a0[u].y}, x1[2] = {a1[u].x, a1[u].y};
+        const u64 y0[2] = {b0[u].x, b0[u].y}, y1[2] = {b1[u].x, b1[u].y};
+#pragma unroll
+        for (int e = 0; e < 2; e++) {
+            u64 h0, l0, h2, l2, ht, lt;
+            mul128(x0[e], y0[e], h0, l0);
+            mul128(x1[e], y1[e], h2, l2);
+            mul128(x0[e] + x1[e], y0[e] + y1[e], ht, lt);
+            // (t - p0 - p2) as a 128-bit difference (non-negative)
+            u64 l1 = lt - l0, h1 = ht - h0 - (lt < l0 ? 1 : 0);
+            const u64 l1b = l1;
+            l1 -= l2;
+            h1 = h1 - h2 - (l1b < l2 ? 1 : 0);
+            r0[e] = reduce128(h0, l0, m);
+            r1[e] = reduce128(h1, l1, m);
+            r2[e] = reduce128(h2, l2, m);
+        }
+        if (op == EW_TENSOR_ACC) {
+            const ulonglong2 c0 = *reinterpret_cast<const ulonglong2 *>(C0 + p[u]);
+            const ulonglong2 c1 = *reinterpret_cast<const ulonglong2 *>(C1 + p[u]);
+            const ulonglong2 c2 = *reinterpret_cast<const ulonglong2 *>(C2 + p[u]);
+            r0[0] = add_mod(r0[0], c0.x, q); r0[1] = add_mod(r0[1], c0.y, q);
+            r1[0] = add_mod(r1[0], c1.x, q); r1[1] = add_mod(r1[1], c1.y, q);
+            r2[0] = add_mod(r2[0], c2.x, q); r2[1] = add_mod(r2[1], c2.y, q);
+        }
+        *reinterpret_cast<ulonglong2 *>(D0 + p[u]) = make_ulonglong2(r0[0], r0[1]);
+        *reinterpret_cast<ulonglong2 *>(D1 + p[u]) = make_ulonglong2(r1[0], r1[1]);
+        *reinterpret_cast<ulonglong2 *>(D2 + p[u]) = make_ulonglong2(r2[0], r2[1]);
+    }
+}
+
 __global__ void __launch_bounds__(kEwThreads) aut_kernel(const AutJob *jobs, int njobs, int log_n, uint32_t g) {
     const size_t n = (size_t)1 << log_n;
     const size_t total = n * njobs;
@@ -263,6 +338,15 @@ void launch_ew(const EwJob *jobs, int njobs, int log_n, const ModInfo *mods, cud
     for (int j0 = 0; j0 < njobs; j0 += 65535) {
         dim3 grid(chunks, (unsigned)std::min(65535, njobs - j0));
         ew_kernel<<<grid, kEwThreads, 0, s>>>(jobs + j0, log_n, mods);
+    }
+}
+void launch_tensor(const EwJob *jobs, int njobs, int log_n, const ModInfo *mods, cudaStream_t s) {
+    if (njobs <= 0) return;
+    const size_t per_cta = 4 * (size_t)kEwThreads;
+    const unsigned chunks = (unsigned)((((size_t)1 << log_n) + per_cta - 1) / per_cta);
+    for (int j0 = 0; j0 < njobs; j0 += 65535) {
+        dim3 grid(chunks, (unsigned)std::min(65535, njobs - j0));
+        tensor_kernel<<<grid, kEwThreads, 0, s>>>(jobs + j0, log_n, mods);
     }
 }
 void launch_automorphism(const AutJob *jobs, int njobs, int log_n, uint32_t galois, cudaStream_t s) {

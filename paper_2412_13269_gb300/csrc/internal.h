@@ -158,6 +158,8 @@ struct EwJob {
     uint32_t prime2, pad2;
 };
 void launch_ew(const EwJob *jobs_dev, int njobs, int log_n, const ModInfo *mods, cudaStream_t s);
+// every job EW_TENSOR or EW_TENSOR_ACC
+void launch_tensor(const EwJob *jobs_dev, int njobs, int log_n, const ModInfo *mods, cudaStream_t s);
 
 // automorphism in the NTT domain: dst[k] = src[perm_g(k)]
 struct AutJob {
