@@ -570,11 +570,6 @@ CtH Rec::sub(const CtH &a, const CtH &b) {
     return o;
 }
 
-static u64 signed_mod(int64_t c, u64 q) {
-    if (c >= 0) return (u64)c % q;
-    u64 r = (u64)(-(c + 1)) % q;
-    return q - 1 - r;
-}
 
 CtH Rec::mul_int(const CtH &a, int64_t cst) {
     CtH o = new_ct(a.B, a.comps, a.level);

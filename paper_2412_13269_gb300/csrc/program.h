@@ -221,6 +221,8 @@ class Rec {
 };
 
 int64_t round_half_up(double x);
+// c mod q in [0, q) for a signed c
+inline u64 signed_mod(int64_t c, u64 q) { return c >= 0 ? (u64)c % q : q - 1 - (u64)(-(c + 1)) % q; }
 const Key &find_key(const Ctx &c, uint32_t galois);
 
 // Shape of a query: what a recorded program depends on.

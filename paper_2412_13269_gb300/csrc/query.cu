@@ -225,7 +225,7 @@ static CtH fold(Rec &R, const CtH &T, const CtH &v, double a) {
         EwJob proto{};
         proto.op = EW_ADD_MUL_CONST;
         proto.prime = i;
-        proto.k = c >= 0 ? (u64)c % qi : qi - 1 - (u64)(-(c + 1)) % qi;
+        proto.k = signed_mod(c, qi);
         proto.k_sh = h_shoup(proto.k, qi);
         for (int b = 0; b < T.B; b++)
             for (int k = 0; k < 2; k++) {
