@@ -153,11 +153,12 @@ class Plan:
     records_norm: float = 0.0
     # the circuit starts as low as its depth allows (a reading: Section 2.5
     # only says each rescale consumes a level, not where a circuit starts):
-    # the w_j are first adjusted from the top level L to l_lin + 1, carrying the
-    # factor w_factor that makes the rescaled product with the database
-    # plaintexts (scale pt_scale, encoded once for any query) land on S[l_lin]
-    # and the circuit end at level 1; w_factor = 0 when l_lin = L - 1
-    w_factor: float = 0.0
+    # the w_j (top level, scale Delta) are dropped to l_lin + 1, and the
+    # rescaled sum of their products with the database plaintexts (scale
+    # pt_scale, encoded once for any query) has scale
+    # x_scale = Delta pt_scale / q_{l_lin+1}, carried through the powers of x
+    # by power_scales; the circuit ends at level 1
+    x_scale: float = 0.0
     # factor each encrypted coefficient c_k carries after its arrival adjust (a
     # reading, like the schedule): the power x^j it multiplies is only dropped
     # (no rescale) to the product's level lt, so c_k carries S[lt] / S[level of
@@ -227,13 +228,14 @@ def make_plan(par: Params, shape: QueryShape) -> Plan:
     if l_ret < 1:
         raise ValueError(f"global threshold needs more levels: ends at level {l_ret}")
     pt_scale = (S[L - 1] * float(par.q[L])) / S[L]
+    x_scale = (S[L] * pt_scale) / float(par.q[l_lin + 1])
     bsgs = poly_schedule(shape.degree)
     cf = [1.0] * (shape.degree + 1)
     if bsgs is None:
-        sp, _ = power_scales(S[l_lin], l_lin, shape.degree, par.q)
+        sp, _ = power_scales(x_scale, l_lin, shape.degree, par.q)
     else:
         g, m, bb, df = bsgs
-        sp, lp = power_scales(S[l_lin], l_lin, max(g - 1, 1), par.q)
+        sp, lp = power_scales(x_scale, l_lin, max(g - 1, 1), par.q)
         h = max(g // 2, 1)
         sg, _ = power_scales((sp[h] * sp[h]) / float(par.q[lp[h]]), lp[h] - 1, max(m - 1, 1), par.q)
     for k in range(1, shape.degree + 1):
@@ -254,9 +256,8 @@ def make_plan(par: Params, shape: QueryShape) -> Plan:
             cf[k] = (fi * (S[l_b] / sp[j])) * rb
         else:
             cf[k] = fi * rb if k < shape.degree else fi
-    w_factor = (S[l_lin] * float(par.q[l_lin + 1])) / (S[l_lin + 1] * pt_scale) if l_lin < L - 1 else 0.0
     return Plan(S=S, l_lin=l_lin, l_d=l_d, l_y=l_y, l_u=l_u, l_out=l_out, l_ret=l_ret, global_coeffs=gco,
-                records_norm=R, w_factor=w_factor,
+                records_norm=R, x_scale=x_scale,
                 pt_scale=pt_scale,
                 mask_scale=((S[l_u - 1] * float(par.q[l_u])) / S[l_u]) if ragged else 0.0,
                 ragged=ragged, stage_coeffs=stages, step_const=1.0 / (2.0 * R),
@@ -476,7 +477,7 @@ class Evaluator:
             if w.level != self.par.L or w.scale != p.S[self.par.L]:
                 raise ValueError("linear-combination coefficients must be fresh top-level ciphertexts")
         # the w_j at level l_lin + 1, where the linear combination is formed
-        self.w_in = [self.adjust(w, p.l_lin + 1, p.w_factor) if p.w_factor else w for w in q.w]
+        self.w_in = [ckks.drop_to(w, p.l_lin + 1) for w in q.w]
         ck = [self.adjust(q.c[k], p.coef_level(k), p.coef_factors[k]) for k in range(degree + 1)]
         return ck, self.adjust(q.t, p.l_y)
 
@@ -489,7 +490,7 @@ class Evaluator:
             prod = ckks.mul_plain(par, w, rns.to_rns(pt, par.q[: p.l_lin + 2]), p.pt_scale)
             acc = prod if acc is None else ckks.add(par, acc, prod)
         x = ckks.rescale(par, acc)
-        x.scale = p.S[p.l_lin]
+        x.scale = p.x_scale
         # powers x^k, k <= degree; a factor of lower power is dropped (not
         # adjusted) to the other's level, so a power's scale is the product of
         # its factors' over the prime the relinearisation removes (power_scales)

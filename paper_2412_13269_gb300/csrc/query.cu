@@ -39,9 +39,10 @@ struct QPlan {
     std::vector<std::vector<double>> gco;
     double records_norm = 0;
     // the circuit starts as low as its depth allows and ends at level 1: the
-    // w_j are adjusted from the top level to l_lin + 1 first, times w_factor
-    // (the rescaled linear combination then lands on S[l_lin]); 0: no adjust
-    double w_factor = 0;
+    // w_j are dropped from the top level to l_lin + 1, and the rescaled linear
+    // combination has scale Delta pt_scale / q_{l_lin+1}, carried through the
+    // powers of x by power_scales
+    double x_scale = 0;
     // factor each c_k carries after its arrival adjust: the power it multiplies
     // is dropped (not rescaled) to the product's level lt, so c_k carries
     // S[lt] / S[level of the power] (and s_i's factor for x^(g i)); 1 where added
@@ -145,8 +146,7 @@ QPlan make_plan(const Ctx &C, uint64_t records, int degree, const std::vector<st
         p.co.push_back(c);
     }
     p.step_const = 1.0 / (2.0 * R);
-    if (p.l_lin < L - 1)
-        p.w_factor = (C.S[p.l_lin] * (double)C.q[p.l_lin + 1]) / (C.S[p.l_lin + 1] * C.pt_scale);
+    p.x_scale = (C.S[L] * C.pt_scale) / (double)C.q[p.l_lin + 1];
     p.mask_scale = p.ragged ? (C.S[p.l_u - 1] * (double)C.q[p.l_u]) / C.S[p.l_u] : 0.0;
     p.degree = degree;
     poly_schedule(p, degree);
@@ -156,9 +156,9 @@ QPlan make_plan(const Ctx &C, uint64_t records, int degree, const std::vector<st
         std::vector<int> lp, lg;
         p.cfac.assign(degree + 1, 1.0);
         if (p.g == 0) {
-            power_scales(C, S[p.l_lin], p.l_lin, degree, sp, lp);
+            power_scales(C, p.x_scale, p.l_lin, degree, sp, lp);
         } else {
-            power_scales(C, S[p.l_lin], p.l_lin, std::max(p.g - 1, 1), sp, lp);
+            power_scales(C, p.x_scale, p.l_lin, std::max(p.g - 1, 1), sp, lp);
             const int h = std::max(p.g / 2, 1);
             power_scales(C, (sp[h] * sp[h]) / (double)C.q[lp[h]], lp[h] - 1, std::max(p.m - 1, 1), sg, lg);
         }
@@ -301,7 +301,7 @@ static CtH eval_blocks(Rec &R, const Database &db, const QPlan &pl, int b0, int 
         R.lin(jobs);
     }
     CtH x = R.rescale(x0);
-    x.scale = C.S[pl.l_lin];
+    x.scale = pl.x_scale;
     x0 = CtH();
     // powers x^k; a factor of lower power is dropped (not adjusted) to the
     // other's level, so a power's scale is its factors' product over the prime
@@ -386,9 +386,8 @@ std::unique_ptr<Program> record_query(Ctx &C, const Database &db, const QuerySpe
         P->hold.push_back(t1in.buf);
         P->in_slots.push_back({t1in.base, t1in.bstride});
     }
-    // per-query: the w_j (one batch of attrs ciphertexts) to level l_lin + 1,
-    // in the coefficient domain (a rescale is per coefficient there), then
-    // their remaining limbs to the NTT domain
+    // per-query: the w_j (one batch of attrs ciphertexts) dropped to level
+    // l_lin + 1, their remaining limbs to the NTT domain
     auto ntt_inputs = [&](const std::vector<CtH> &cts) {
         std::vector<NttJob> jobs;
         for (const CtH &c : cts)
@@ -403,7 +402,7 @@ std::unique_ptr<Program> record_query(Ctx &C, const Database &db, const QuerySpe
         R.ntt(false, jobs, LOAD_PLAIN, STORE_PLAIN);
     };
     CtH w = R.view(wbuf, wbuf->ptr, q.attrs, 2, L, wwords, (L + 1) * N, C.S[L]);
-    if (pl.w_factor != 0) w = R.adjust_many_coef({{w, pl.l_lin + 1, pl.w_factor}})[0];
+    w = R.drop(w, pl.l_lin + 1);
     ntt_inputs({w});
     // the coefficients and the threshold (and t1) are late inputs: their copies
     // overlap the linear combination and the first powers of x, and they are

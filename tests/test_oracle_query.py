@@ -39,13 +39,14 @@ def test_plan_levels():
     assert (p2.l_lin, p2.l_d, p2.l_y, p2.l_u, p2.l_out) == (15, 11, 10, 1, 1)
     p3 = query.make_plan(par2, query.QueryShape(1 << 14, 16, 31, [query.F3] * 3))
     assert p3.ragged and (p3.l_lin, p3.l_u, p3.l_out) == (17, 2, 1)
-    # the factor that lands the rescaled linear combination on S[l_lin]
+    # the rescaled linear combination of dropped w_j: Delta pt_scale / q_{l_lin+1}, near S[l_lin]
     for pl in (p2, p3):
         t = pl.l_lin + 1
-        assert abs(pl.w_factor * pl.S[t] * pl.pt_scale / (pl.S[pl.l_lin] * par2.q[t]) - 1) < 1e-15
+        assert pl.x_scale == (pl.S[par2.L] * pl.pt_scale) / float(par2.q[t])
+        assert abs(pl.x_scale / pl.S[pl.l_lin] - 1) < 1e-3
     # no spare levels: the circuit starts right below the top
     p4 = query.make_plan(par2, query.QueryShape(131072, 16, 15, [query.F3] * 4))
-    assert (p4.l_lin, p4.l_out, p4.w_factor) == (18, 1, 0.0)
+    assert (p4.l_lin, p4.l_out) == (18, 1) and abs(p4.x_scale / p4.S[18] - 1) < 1e-12
     with pytest.raises(ValueError):
         query.make_plan(par, query.QueryShape(2048, 8, 31, [query.F3] * 3))
     # exact standard scales: S[l-1] q_l = S[l]^2 up to one rounding
