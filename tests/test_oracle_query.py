@@ -187,3 +187,49 @@ def test_global_threshold_bit(p_pos, t1_frac):
     assert ref.exact_bit == int(ref.exact >= t1) == (1 if p_pos > 0.5 else 0)
     assert np.max(np.abs(got - ref.exact_bit)) < 2.0 ** -12
     assert np.max(np.abs(got - ref.bit)) < 1e-6
+
+
+def _enc_slots(par, s, z, level, scale, seed):
+    m = ckks.encode_int(par.N, z, scale)
+    d = synth.encryption_draws(seed, f"v{seed}", par.q[: level + 1], par.N)
+    return ckks.encrypt(par, m, s, d.a, d.e, level, scale)
+
+
+def test_fold_adds_a_times_u_before_the_relinearisation():
+    """relin_rescale(tensor(a, b) + fold of c u) decrypts to a b + c u at the
+    standard scale of the level below, for u above the product's level (its
+    own scale) and positive, negative and tiny c."""
+    par = chain_params(6)
+    s = query.secret(par, 7, 2 * par.N // 3)
+    keys = query.make_keys(par, s, 7, 1)
+    S = query.standard_scales(par)
+    plan = query.Plan(S=S, l_lin=5, l_d=5, l_y=5, l_u=5, l_out=1, pt_scale=1.0, mask_scale=0.0, ragged=False)
+    ev = query.Evaluator(par, keys, plan)
+    g = np.random.default_rng(7)
+    lt = 4
+    za, zb, zu = (g.uniform(-1, 1, par.n_slots) for _ in range(3))
+    a = _enc_slots(par, s, za, lt, S[lt], 1)
+    b = _enc_slots(par, s, zb, lt, S[lt], 2)
+    u = _enc_slots(par, s, zu, 6, S[6], 3)
+    for c in (0.75, -2.5, 3e-5):
+        t = ev.relin_rescale(ev.fold(ckks.tensor(par, a, b), u, c), lt - 1)
+        got = ckks.decrypt_slots(par, t, s).real
+        assert np.max(np.abs(got - (za * zb + c * zu))) < 1e-6, c
+
+
+def test_power_scales_follow_the_power_rule():
+    """The planner's tracked scales equal the scales the evaluator's power
+    rule leaves on x^k (lower factor dropped, product over the removed prime)."""
+    par = chain_params(11)
+    S = query.standard_scales(par)
+    top = 9
+    sc, lv = query.power_scales(S[top] * 1.0001, top, 15, par.q)
+    # by hand for the first few powers
+    assert lv[2] == top - 1 and sc[2] == (sc[1] * sc[1]) / float(par.q[top])
+    assert lv[3] == top - 2 and sc[3] == (sc[2] * sc[1]) / float(par.q[top - 1])
+    assert lv[4] == top - 2 and sc[4] == (sc[2] * sc[2]) / float(par.q[top - 1])
+    assert lv[12] == top - 4 and sc[12] == (sc[8] * sc[4]) / float(par.q[lv[8]])
+    # a standard start keeps the powers of two standard
+    st, sl = query.power_scales(S[top], top, 8, par.q)
+    for k in (2, 4, 8):
+        assert st[k] == S[sl[k]]
