@@ -481,7 +481,13 @@ class Evaluator:
         ck = [self.adjust(q.c[k], p.coef_level(k), p.coef_factors[k]) for k in range(degree + 1)]
         return ck, self.adjust(q.t, p.l_y)
 
-    def block(self, pts: list, q: EncQuery, ck: list, tadj: Ct, degree: int) -> Ct:
+    def block(self, pts: list, q: EncQuery, ck: list, tadj: Ct, degree: int, record: dict | None = None) -> Ct:
+        """One block's circuit; returns the per-slot step values u / R (after
+        the sign stages and their affine map, before the block sum).  With a
+        dict ``record`` it also keeps the ciphertexts of the intermediate
+        stages: "x" the linear combination, "y" = f(x) (with c_0), "d" = y - t,
+        and "u" the result."""
+        keep = (lambda k, v: record.__setitem__(k, v)) if record is not None else (lambda k, v: None)
         par, p = self.par, self.plan
         L = par.L
         # linear combination: sum_j pt_j * Enc(w_j) at level l_lin + 1, rescale
@@ -491,6 +497,7 @@ class Evaluator:
             acc = prod if acc is None else ckks.add(par, acc, prod)
         x = ckks.rescale(par, acc)
         x.scale = p.x_scale
+        keep("x", x)
         # powers x^k, k <= degree; a factor of lower power is dropped (not
         # adjusted) to the other's level, so a power's scale is the product of
         # its factors' over the prime the relinearisation removes (power_scales)
@@ -541,11 +548,15 @@ class Evaluator:
             y = self.relin_rescale(T, l_f - 1)
             y = self.adjust(y, p.l_y)
         y = ckks.add(par, y, ck[0])
+        keep("y", y)
         # z = y - t (the 1/2 is folded into the first sign stage)
         u = ckks.sub(par, y, tadj)
+        keep("d", u)
         for co in p.stage_coeffs:
             u = self.sign_stage(u, co)
-        return ckks.add_int_const(par, u, round_half_up(p.step_const * p.S[u.level]))
+        u = ckks.add_int_const(par, u, round_half_up(p.step_const * p.S[u.level]))
+        keep("u", u)
+        return u
 
     def global_threshold(self, v: Ct, t1: Ct) -> Ct:
         """step((count - t1 + 1/2) / R) from v = count / R (Algorithm 2, last line)."""

@@ -2,8 +2,10 @@
 Python big integers against the statements they implement:
 
 * rescale = round-half-up of c / q_l (Section 2.5) on the CRT value;
-* fast base conversion = x + u*Q_D with 0 <= u < |D|;
-* ModDown = floor((c + floor(P/2)) / P) - u with 0 <= u < K (Section 2.4.1);
+* fast base conversion = x + u*Q_D with 0 <= u < |D|, and exactly its
+  integer definition sum_i [x_i (Q/q_i)^-1]_{q_i} (Q/q_i) reduced mod p;
+* ModDown = floor((c + floor(P/2)) / P) - u with 0 <= u < K (Section 2.4.1),
+  and exactly (c + floor(P/2) - V) / P with V that exact conversion;
 * automorphism = a(X^g) reduced modulo X^N + 1 (Section 2.2);
 * SwitchKeyGen: swk_j[0] + swk_j[1] s = e_j + w_j P s' exactly;
 * SwitchKey / relinearisation / rotation: decryption identities with small
@@ -62,6 +64,61 @@ def test_base_convert_excess_bound():
             got = int(out[t, k])
             ok = [u for u in range(len(src)) if (vals[k] + u * Qs) % p == got]
             assert ok, (t, k)
+
+
+def exact_conversion(x_cols, src):
+    """sum_i [x_i (Qs/q_i)^-1]_{q_i} (Qs/q_i) as one Python integer, for the
+    residues x_cols[i] of one coefficient (the conversion's definition,
+    without reduction by the target prime)."""
+    Qs = math.prod(src)
+    return sum(((int(x) * pow(Qs // qi, -1, qi)) % qi) * (Qs // qi) for x, qi in zip(x_cols, src))
+
+
+def test_base_convert_exact():
+    """The fast base conversion equals its integer definition reduced modulo
+    each target prime, for every coefficient; and that integer is x + u Qs with
+    the excess u in [0, |src|) determined coefficient by coefficient."""
+    rnd = random.Random(13)
+    for ns in (1, 2, 3, 4):
+        src = rns.gen_primes(50, ns)
+        dst = rns.gen_primes(60, 3) + rns.gen_primes(40, 2) + rns.gen_primes(50, 2, exclude=src)
+        n = 48
+        x = rand_rns(rnd, src, n)
+        out = np.empty((len(dst), n), dtype=np.uint64)
+        lib().or_base_convert(ptr(x), ptr(u64arr(src)), ns, ptr(u64arr(dst)), len(dst), n, ptr(out))
+        Qs = math.prod(src)
+        vals = rns.crt(x, src)
+        for k in range(n):
+            v = exact_conversion(x[:, k], src)
+            u, r = divmod(v - vals[k], Qs)
+            assert r == 0 and 0 <= u < ns
+            for t, p in enumerate(dst):
+                assert int(out[t, k]) == v % p, (ns, t, k)
+
+
+def test_moddown_exact():
+    """ModDown (Section 2.4.1's division by P with rounding) equals, modulo
+    each q_i, the integer (c + floor(P/2) - V) / P, c the CRT value over Q P
+    and V the exact fast conversion of the special residues of c + floor(P/2);
+    the division is exact."""
+    rnd = random.Random(14)
+    for K in (1, 2, 3):
+        qs = rns.gen_primes(50, 4)
+        ps = rns.gen_primes(60, K)
+        n = 40
+        mods = qs + ps
+        c = rand_rns(rnd, mods, n)
+        out = np.empty((len(qs), n), dtype=np.uint64)
+        lib().or_moddown(ptr(c), len(qs), K, ptr(u64arr(mods)), n, ptr(out))
+        P = math.prod(ps)
+        vals = rns.crt(c, mods)
+        for k in range(n):
+            shifted = [(int(c[len(qs) + j, k]) + P // 2) % pj for j, pj in enumerate(ps)]
+            V = exact_conversion(shifted, ps)
+            num = vals[k] + P // 2 - V
+            assert num % P == 0
+            for i, qi in enumerate(qs):
+                assert int(out[i, k]) == (num // P) % qi, (K, i, k)
 
 
 def test_moddown_is_rounded_division_up_to_K():
