@@ -219,6 +219,8 @@ typedef struct {
     double pt_scale, mask_scale;
     int32_t l_ret; /* level of the returned ciphertext: InnerSum runs after dropping to it */
     uint32_t pad;
+    uint64_t input_words; /* input words copied to the device per query (fresh inputs at the top
+                             level): only the limbs the circuit reads of each ciphertext */
 } tetris_plan_info;
 /* Levels and operation counts of the plan for a query shape on a database. */
 int tetris_plan(tetris_ctx *ctx, uint32_t db, uint32_t f_degree, uint32_t sign_stages,
@@ -248,11 +250,27 @@ enum {
     TETRIS_OPT_PROFILE = 4,            /* 1: run queries eagerly with a CUDA event pair around
                                           every launch, accumulating per-kernel statistics */
     TETRIS_OPT_NTT_GROUP = 5,          /* log2 of the NTT elements a thread holds: 3 or 4 */
-    TETRIS_OPT_KS_BASE2 = 6            /* w of the base-2^w decomposition of key-switch digits
+    TETRIS_OPT_KS_BASE2 = 6,           /* w of the base-2^w decomposition of key-switch digits
                                           (Table 1's base2), 0 for none, else 8..62; needs
                                           alpha 1; keys then carry (L+1) ceil(bits/w) digits,
                                           digit i B + b with P 2^(w b) on limb i.  Set before
                                           loading or generating keys: changing it drops them */
+    TETRIS_OPT_QUERY_STAGE = 7         /* 0 (default): queries return the InnerSum result.
+                                          1..4: queries stop after a stage of every block and
+                                          return its ciphertexts, block after block
+                                          ([blocks][2][level+1][N], out->ncomp = 2, out->level
+                                          and out->scale that stage's): 1 x (linear
+                                          combination), 2 y = f(x), 3 y - t, 4 the step values
+                                          u / records (before the block sum).  For checking the
+                                          stages slot by slot; a ragged last block's dead slots
+                                          carry whatever the circuit leaves there */
+};
+enum {
+    TETRIS_STAGE_FULL = 0,
+    TETRIS_STAGE_X = 1,
+    TETRIS_STAGE_Y = 2,
+    TETRIS_STAGE_D = 3,
+    TETRIS_STAGE_U = 4
 };
 int tetris_set_option(tetris_ctx *ctx, int option, int64_t value);
 int tetris_get_option(tetris_ctx *ctx, int option, int64_t *value);
@@ -348,7 +366,15 @@ int tetris_batch_run(const tetris_batch_item *items, uint32_t n_items, int sched
 typedef struct {
     uint64_t submitted, completed, rejected;
     double p50_ms, p99_ms;
-    size_t device_bytes, peak_device_bytes;
+    size_t device_bytes;       /* device bytes of the program instances kept now */
+    size_t peak_device_bytes;  /* most device bytes the server's programs held at once, measured
+                                  from their allocations right after each new instance
+                                  (released instances that are not freed yet included) */
+    uint64_t cancelled;        /* queries withdrawn by tetris_cancel before admission */
+    uint32_t max_admitted;  /* most requests admitted and not yet completed at one time */
+    uint32_t max_overlap;   /* most completed requests whose device work (CUDA events at the
+                               first copy in and after the copy out, on each request's
+                               stream) spans one instant: overlap on the device itself */
 } tetris_serve_stats;
 int tetris_serve_start(tetris_ctx *ctx, size_t memory_budget_bytes, uint32_t max_inflight);
 int tetris_submit(tetris_ctx *ctx, uint32_t db, const tetris_query *query, uint64_t *ticket);
@@ -356,6 +382,11 @@ int tetris_poll(tetris_ctx *ctx, uint64_t ticket, tetris_ct_out *out, uint32_t t
 /* Counters and submit-to-completion latency percentiles since the start (or
  * the last reset); reset != 0 clears them after reading. */
 int tetris_serve_stats_get(tetris_ctx *ctx, tetris_serve_stats *out, int reset);
+/* Withdraw a ticket.  A query still waiting for admission is removed before
+ * any of its work reaches the device; a finished query's result is dropped.
+ * Either way the ticket becomes unknown (TETRIS_ENOTFOUND afterwards).  A
+ * query already admitted cannot be stopped: TETRIS_EBUSY, poll it instead. */
+int tetris_cancel(tetris_ctx *ctx, uint64_t ticket);
 int tetris_serve_stop(tetris_ctx *ctx);
 
 /* ---------------------------------------------------------------------------
@@ -375,14 +406,17 @@ int tetris_serve_stop(tetris_ctx *ctx);
  *      (the order TETRIS_OP_NTT returns), 1 <= level <= n_q - 1, ncomp <= 3.
  * out: device pointer, [ncomp][level][N], same order; must not overlap in.
  * stream: cudaStream_t (NULL = legacy default stream); the call enqueues the
- *      work and returns; it may wait for earlier work in that stream while
- *      it copies its job tables from host memory.
+ *      work and returns without waiting for it.  Its job tables are written
+ *      on the device by a small kernel from that kernel's launch parameters,
+ *      so nothing in host memory is read after the call returns.
  * The first call on each device resolves the scratch array's address there
  * (with that device current).  All calls share the array and it keeps the
  * last call's contents (nothing in it needs to start at zero); calls whose
  * work overlaps on the GPU race on it, so callers serialise them.
- * Errors: TETRIS_EINVAL for sizes beyond the maximum, overlap or null
- * buffers, TETRIS_ELEVEL for a level outside [1, n_q - 1].
+ * Errors: TETRIS_EINVAL for sizes beyond the maximum, overlap, null buffers
+ * or buffers that are not device (or managed) memory of the context's device
+ * (checked before anything is launched), TETRIS_ELEVEL for a level outside
+ * [1, n_q - 1].
  * ------------------------------------------------------------------------- */
 int tetris_rescale_ntt_noalloc(tetris_ctx *ctx, const uint64_t *in, uint64_t *out, uint32_t level,
                                uint32_t ncomp, void *stream);

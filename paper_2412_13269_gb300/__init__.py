@@ -27,6 +27,8 @@ OP_ADD, OP_SUB, OP_TENSOR, OP_RELIN, OP_RESCALE, OP_MUL_INT, OP_ADD_INT = 1, 2, 
 OP_AUTOMORPHISM, OP_ROTATE, OP_KEYSWITCH, OP_MUL_PLAIN, OP_NTT, OP_INNERSUM, OP_DROP = 8, 9, 10, 11, 12, 13, 14
 OP_RELIN_RESCALE, OP_RESCALE_MUL_INT = 15, 16
 OPT_BLOCKS_PER_LAUNCH, OPT_USE_GRAPH, OPT_KS_ALPHA, OPT_PROFILE, OPT_NTT_GROUP, OPT_KS_BASE2 = 1, 2, 3, 4, 5, 6
+OPT_QUERY_STAGE = 7
+STAGE_FULL, STAGE_X, STAGE_Y, STAGE_D, STAGE_U = 0, 1, 2, 3, 4
 
 
 def build(force: bool = False) -> str:
@@ -66,12 +68,13 @@ class PlanInfo(C.Structure):
     _fields_ = [("l_lin", C.c_int32), ("l_d", C.c_int32), ("l_y", C.c_int32), ("l_u", C.c_int32),
                 ("l_out", C.c_int32), ("ragged", C.c_uint32), ("relins", C.c_uint32), ("rescales", C.c_uint32),
                 ("rotations", C.c_uint32), ("kernel_launches", C.c_uint32), ("pt_scale", C.c_double),
-                ("mask_scale", C.c_double), ("l_ret", C.c_int32), ("pad", C.c_uint32)]
+                ("mask_scale", C.c_double), ("l_ret", C.c_int32), ("pad", C.c_uint32), ("input_words", C.c_uint64)]
 
 
 class ServeStats(C.Structure):
     _fields_ = [("submitted", C.c_uint64), ("completed", C.c_uint64), ("rejected", C.c_uint64), ("p50_ms", C.c_double),
-                ("p99_ms", C.c_double), ("device_bytes", C.c_size_t), ("peak_device_bytes", C.c_size_t)]
+                ("p99_ms", C.c_double), ("device_bytes", C.c_size_t), ("peak_device_bytes", C.c_size_t),
+                ("cancelled", C.c_uint64), ("max_admitted", C.c_uint32), ("max_overlap", C.c_uint32)]
 
 
 class BatchItem(C.Structure):
@@ -145,6 +148,7 @@ SIGNATURES = {
     "tetris_submit": [_vp, _u32, C.POINTER(Query), C.POINTER(_u64)],
     "tetris_poll": [_vp, _u64, C.POINTER(CtOut), _u32],
     "tetris_serve_stats_get": [_vp, C.POINTER(ServeStats), C.c_int],
+    "tetris_cancel": [_vp, _u64],
     "tetris_serve_stop": [_vp],
     "tetris_noalloc_scratch_bytes": [],
     "tetris_repack": [_vp, _vp, _u32, _u32, _d, C.POINTER(CtOut)],
@@ -406,6 +410,22 @@ class Ctx:
         n = 2 * (o.level + 1) * self.N
         return out[:n].reshape(2, o.level + 1, self.N), o.level, o.scale
 
+    def query_stage(self, stage: int, blocks: int, db: int, w, w_meta, c, c_meta, t, t_meta, sign_coeffs,
+                    total_records=0):
+        """The ciphertexts of one stage of every block (TETRIS_OPT_QUERY_STAGE):
+        returns ([blocks][2][level+1][N] uint64, level, scale)."""
+        q, keep = self._query_struct(w, w_meta, c, c_meta, t, t_meta, sign_coeffs, total_records)
+        out = np.empty(blocks * 2 * (self.L + 1) * self.N, dtype=np.uint64)
+        o = CtOut(0, 0, 0.0, out.ctypes.data, out.size)
+        prev = self.get_option(OPT_QUERY_STAGE)
+        self.set_option(OPT_QUERY_STAGE, stage)
+        try:
+            check(lib().tetris_evaluate_query(self.h, db, C.byref(q), C.byref(o)))
+        finally:
+            self.set_option(OPT_QUERY_STAGE, prev)
+        n = blocks * 2 * (o.level + 1) * self.N
+        return out[:n].reshape(blocks, 2, o.level + 1, self.N), o.level, o.scale
+
     def evaluate_query_device(self, db: int, w, w_meta, c, c_meta, t, t_meta, sign_coeffs, out, stream: int,
                               total_records=0, glob=None):
         """torch CUDA tensors in and out; enqueued on ``stream`` (a cudaStream_t as int)."""
@@ -424,16 +444,20 @@ class Ctx:
         check(lib().tetris_submit(self.h, db, C.byref(q), C.byref(tk)))
         return tk.value
 
-    def poll(self, ticket: int, timeout_ms: int = 60000):
-        """Returns (out array, level, scale), or None if the ticket is still running."""
+    def poll(self, ticket: int, timeout_ms: int = 60000, cap_words: int | None = None):
+        """Returns (out array, level, scale), or None if the ticket is still running.
+        cap_words: the output capacity to announce (default: the whole buffer)."""
         out = np.empty(2 * (self.L + 1) * self.N, dtype=np.uint64)
-        o = CtOut(0, 0, 0.0, out.ctypes.data, out.size)
+        o = CtOut(0, 0, 0.0, out.ctypes.data, out.size if cap_words is None else min(cap_words, out.size))
         rc = lib().tetris_poll(self.h, ticket, C.byref(o), timeout_ms)
         if rc == -6:
             return None
         check(rc)
         n = 2 * (o.level + 1) * self.N
         return out[:n].reshape(2, o.level + 1, self.N), o.level, o.scale
+
+    def cancel(self, ticket: int):
+        check(lib().tetris_cancel(self.h, ticket))
 
     def serve_stats(self, reset: bool = False) -> ServeStats:
         st = ServeStats()

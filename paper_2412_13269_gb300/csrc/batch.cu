@@ -163,7 +163,7 @@ void batch_run(const tetris_batch_item *items, uint32_t n, int schedule, int *us
     TREQUIRE(items && n > 0, TETRIS_EINVAL, "empty batch");
     for (uint32_t i = 0; i < n; i++) {
         TREQUIRE(items[i].ctx, TETRIS_EINVAL, "batch item without a context");
-        cudaSetDevice(items[i].ctx->c.device);
+        TCHECK_CUDA(cudaSetDevice(items[i].ctx->c.device));
     }
     double ms;
     int chosen = schedule;

@@ -88,7 +88,8 @@ static void build_tables(Ctx &C) {
         e = e * 5 % (2 * N);
     }
     const size_t w = np * N;
-    const size_t mods_words = (np * sizeof(ModInfo) + 7) / 8;
+    // regions start on 256-byte boundaries: the encoder reads its table as double2
+    const size_t mods_words = (np * sizeof(ModInfo) + 255) / 256 * 32;
     const size_t enc_words = enc.size();
     C.tables = C.pool.alloc(4 * w + mods_words + enc_words);
     u64 *base = C.tables->ptr;
@@ -134,10 +135,24 @@ static void set_alpha(Ctx &C, uint32_t alpha) {
 }
 
 static Key load_key(Ctx &C, const uint64_t *evk, size_t n_words, uint32_t alpha) {
-    set_alpha(C, alpha);
+    // every check before set_alpha, which drops the loaded keys on a new digit size:
+    // a malformed key leaves the context as it was
+    TREQUIRE(alpha >= 1 && (int)alpha <= kMaxConvSrc, TETRIS_EINVAL, "alpha must be in [1, 4]");
     const int dnum = (C.L() + 1 + alpha - 1) / alpha * key_pieces(C), nqp = C.nqp();
     const size_t N = C.N;
-    TREQUIRE(evk && n_words == (size_t)dnum * 2 * nqp * N, TETRIS_EINVAL, "key: wrong size");
+    TREQUIRE(evk, TETRIS_EINVAL, "key: null buffer");
+    TREQUIRE(n_words == (size_t)dnum * 2 * nqp * N, TETRIS_EINVAL,
+             "key: wrong size (" + std::to_string(n_words) + " words for " + std::to_string(dnum) + " digits, " +
+                 std::to_string((size_t)dnum * 2 * nqp * N) + " expected)");
+    for (size_t row = 0; row < (size_t)dnum * 2 * nqp; row++) {  // residues of limb t below its prime
+        const u64 qt = C.all[row % nqp];
+        const uint64_t *r = evk + row * N;
+        u64 bad = 0;
+        for (size_t i = 0; i < N; i++) bad |= (u64)(r[i] >= qt);
+        TREQUIRE(!bad, TETRIS_EINVAL, "key: residue out of range in limb " + std::to_string(row % nqp) + " of row " +
+                                          std::to_string(row));
+    }
+    set_alpha(C, alpha);
     Key k;
     k.dnum = dnum;
     k.pieces = key_pieces(C);
@@ -179,11 +194,18 @@ static BufPtr secret_ntt(Ctx &C, Program &P, Rec &R, const int64_t *s, int nlimb
 // with the base-2^w decomposition (Table 1 base2) digit j = i B + b carries
 // P 2^(w b) s_from on limb i.
 static Key gen_key(Ctx &C, const int64_t *s, const uint64_t *a, const int64_t *e, uint32_t alpha, uint32_t galois) {
-    set_alpha(C, alpha);
+    TREQUIRE(alpha >= 1 && (int)alpha <= kMaxConvSrc, TETRIS_EINVAL, "alpha must be in [1, 4]");
+    TREQUIRE(s && a && e, TETRIS_EINVAL, "keygen: null input");
     const int B = key_pieces(C);
     const int dnum = (C.L() + 1 + alpha - 1) / alpha * B, nqp = C.nqp();
     const size_t N = C.N;
-    TREQUIRE(s && a && e, TETRIS_EINVAL, "keygen: null input");
+    for (size_t row = 0; row < (size_t)dnum * nqp; row++) {  // the uniform a: residues below their primes
+        const u64 qt = C.all[row % nqp];
+        u64 bad = 0;
+        for (size_t i = 0; i < N; i++) bad |= (u64)(a[row * N + i] >= qt);
+        TREQUIRE(!bad, TETRIS_EINVAL, "keygen: residue of a out of range in limb " + std::to_string(row % nqp));
+    }
+    set_alpha(C, alpha);
     Program P;
     Rec R(C, P);
     BufPtr sn = secret_ntt(C, P, R, s, nqp);
@@ -401,7 +423,7 @@ int tetris_standard_scale(const tetris_ctx *ctx, uint32_t level, double *out) {
 int tetris_load_relin_key(tetris_ctx *ctx, const uint64_t *evk, size_t n_words, uint32_t alpha) {
     return guarded([&] {
         TREQUIRE(ctx, TETRIS_EINVAL, "null context");
-        cudaSetDevice(ctx->c.device);
+        TCHECK_CUDA(cudaSetDevice(ctx->c.device));
         ctx->c.relin = load_key(ctx->c, evk, n_words, alpha);
         ctx->c.programs.clear();
     });
@@ -410,7 +432,7 @@ int tetris_load_relin_key(tetris_ctx *ctx, const uint64_t *evk, size_t n_words, 
 int tetris_load_rotation_key(tetris_ctx *ctx, uint32_t g, const uint64_t *evk, size_t n_words, uint32_t alpha) {
     return guarded([&] {
         TREQUIRE(ctx && (g & 1), TETRIS_EINVAL, "galois element must be odd");
-        cudaSetDevice(ctx->c.device);
+        TCHECK_CUDA(cudaSetDevice(ctx->c.device));
         ctx->c.rot[g & (uint32_t)(2 * ctx->c.N - 1)] = load_key(ctx->c, evk, n_words, alpha);
         ctx->c.programs.clear();
     });
@@ -419,7 +441,7 @@ int tetris_load_rotation_key(tetris_ctx *ctx, uint32_t g, const uint64_t *evk, s
 int tetris_keygen_relin(tetris_ctx *ctx, const int64_t *s, const uint64_t *a, const int64_t *e, uint32_t alpha) {
     return guarded([&] {
         TREQUIRE(ctx, TETRIS_EINVAL, "null context");
-        cudaSetDevice(ctx->c.device);
+        TCHECK_CUDA(cudaSetDevice(ctx->c.device));
         ctx->c.relin = gen_key(ctx->c, s, a, e, alpha, 0);
         ctx->c.programs.clear();
     });
@@ -428,7 +450,7 @@ int tetris_keygen_relin(tetris_ctx *ctx, const int64_t *s, const uint64_t *a, co
 int tetris_keygen_rotation(tetris_ctx *ctx, uint32_t g, const int64_t *s, const uint64_t *a, const int64_t *e, uint32_t alpha) {
     return guarded([&] {
         TREQUIRE(ctx && (g & 1), TETRIS_EINVAL, "galois element must be odd");
-        cudaSetDevice(ctx->c.device);
+        TCHECK_CUDA(cudaSetDevice(ctx->c.device));
         ctx->c.rot[g & (uint32_t)(2 * ctx->c.N - 1)] = gen_key(ctx->c, s, a, e, alpha, g);
         ctx->c.programs.clear();
     });
@@ -438,7 +460,7 @@ int tetris_get_key(tetris_ctx *ctx, uint32_t g, uint64_t *out, size_t cap) {
     return guarded([&] {
         TREQUIRE(ctx && out, TETRIS_EINVAL, "null pointer");
         Ctx &C = ctx->c;
-        cudaSetDevice(C.device);
+        TCHECK_CUDA(cudaSetDevice(C.device));
         const Key &k = find_key(C, g & (uint32_t)(2 * C.N - 1));
         const int nqp = C.nqp();
         const size_t words = (size_t)k.dnum * 2 * nqp * C.N;
@@ -465,7 +487,7 @@ int tetris_encrypt(tetris_ctx *ctx, const int64_t *m, const int64_t *s, const ui
     return guarded([&] {
         TREQUIRE(ctx && m && s && a && e, TETRIS_EINVAL, "null pointer");
         Ctx &C = ctx->c;
-        cudaSetDevice(C.device);
+        TCHECK_CUDA(cudaSetDevice(C.device));
         TREQUIRE((int)level <= C.L(), TETRIS_EINVAL, "level out of range");
         const int nl = level + 1;
         const size_t N = C.N;
@@ -531,7 +553,7 @@ int tetris_upload_database(tetris_ctx *ctx, const uint8_t *vals, uint64_t record
     return guarded([&] {
         TREQUIRE(ctx && vals && db_out && records > 0 && attrs > 0, TETRIS_EINVAL, "upload_database: bad arguments");
         Ctx &C = ctx->c;
-        cudaSetDevice(C.device);
+        TCHECK_CUDA(cudaSetDevice(C.device));
         TREQUIRE(C.L() >= 1, TETRIS_ELEVEL, "context has a single prime");
         const size_t N = C.N, n = N / 2, nq = C.q.size();
         Database db;
@@ -591,7 +613,7 @@ int tetris_upload_database_encoded(tetris_ctx *ctx, const int64_t *coeffs, const
     return guarded([&] {
         TREQUIRE(ctx && coeffs && db_out && records > 0 && attrs > 0, TETRIS_EINVAL, "upload_database_encoded: bad arguments");
         Ctx &C = ctx->c;
-        cudaSetDevice(C.device);
+        TCHECK_CUDA(cudaSetDevice(C.device));
         const size_t N = C.N, n = N / 2, nq = C.q.size();
         TREQUIRE((records % n == 0) == (mask_real == nullptr), TETRIS_EINVAL,
                  "mask_real is required exactly when the last block is partly filled");
@@ -632,7 +654,7 @@ int tetris_free_database(tetris_ctx *ctx, uint32_t db) {
         TREQUIRE(ctx, TETRIS_EINVAL, "null context");
         auto it = ctx->c.dbs.find(db);
         TREQUIRE(it != ctx->c.dbs.end(), TETRIS_ENOTFOUND, "unknown database handle");
-        cudaSetDevice(ctx->c.device);
+        TCHECK_CUDA(cudaSetDevice(ctx->c.device));
         cudaStreamSynchronize(ctx->c.stream);
         drop_programs_of_db(ctx->c, db);
         ctx->c.dbs.erase(it);
@@ -659,7 +681,7 @@ static void encode_common(Ctx &C, const double *slots, uint32_t nv, double *m_ho
 int tetris_encode(tetris_ctx *ctx, const double *slots, uint32_t nv, double scale, int64_t *coeffs) {
     return guarded([&] {
         TREQUIRE(ctx && coeffs, TETRIS_EINVAL, "null pointer");
-        cudaSetDevice(ctx->c.device);
+        TCHECK_CUDA(cudaSetDevice(ctx->c.device));
         encode_common(ctx->c, slots, nv, nullptr, coeffs, scale);
     });
 }
@@ -667,7 +689,7 @@ int tetris_encode(tetris_ctx *ctx, const double *slots, uint32_t nv, double scal
 int tetris_encode_real(tetris_ctx *ctx, const double *slots, uint32_t nv, double *m_out) {
     return guarded([&] {
         TREQUIRE(ctx && m_out, TETRIS_EINVAL, "null pointer");
-        cudaSetDevice(ctx->c.device);
+        TCHECK_CUDA(cudaSetDevice(ctx->c.device));
         encode_common(ctx->c, slots, nv, m_out, nullptr, 1.0);
     });
 }
@@ -675,7 +697,7 @@ int tetris_encode_real(tetris_ctx *ctx, const double *slots, uint32_t nv, double
 int tetris_evaluate_query(tetris_ctx *ctx, uint32_t db, const tetris_query *q, tetris_ct_out *out) {
     return guarded([&] {
         TREQUIRE(ctx, TETRIS_EINVAL, "null context");
-        cudaSetDevice(ctx->c.device);
+        TCHECK_CUDA(cudaSetDevice(ctx->c.device));
         evaluate_query(ctx->c, db, q, out, ctx->c.stream, false);
     });
 }
@@ -683,7 +705,7 @@ int tetris_evaluate_query(tetris_ctx *ctx, uint32_t db, const tetris_query *q, t
 int tetris_evaluate_query_device(tetris_ctx *ctx, uint32_t db, const tetris_query *q, tetris_ct_out *out, void *stream) {
     return guarded([&] {
         TREQUIRE(ctx, TETRIS_EINVAL, "null context");
-        cudaSetDevice(ctx->c.device);
+        TCHECK_CUDA(cudaSetDevice(ctx->c.device));
         evaluate_query(ctx->c, db, q, out, reinterpret_cast<cudaStream_t>(stream), true);
     });
 }
@@ -692,7 +714,7 @@ int tetris_autotune(tetris_ctx *ctx, uint32_t db, const tetris_query *q, uint32_
                     uint32_t cap, uint32_t *n_out) {
     return guarded([&] {
         TREQUIRE(ctx && n_out && (out || cap == 0), TETRIS_EINVAL, "null pointer");
-        cudaSetDevice(ctx->c.device);
+        TCHECK_CUDA(cudaSetDevice(ctx->c.device));
         std::vector<tetris_tune_entry> v;
         autotune(ctx->c, db, q, (int)std::max(1u, reps), v);
         *n_out = (uint32_t)std::min<size_t>(v.size(), cap);
@@ -703,7 +725,7 @@ int tetris_autotune(tetris_ctx *ctx, uint32_t db, const tetris_query *q, uint32_
 int tetris_reduce_sum_device(tetris_ctx *ctx, uint64_t *data, uint32_t level, uint32_t ncomp, void *stream) {
     return guarded([&] {
         TREQUIRE(ctx, TETRIS_EINVAL, "null context");
-        cudaSetDevice(ctx->c.device);
+        TCHECK_CUDA(cudaSetDevice(ctx->c.device));
         reduce_sum(ctx->c, data, (int)level, (int)ncomp, reinterpret_cast<cudaStream_t>(stream));
     });
 }
@@ -711,7 +733,7 @@ int tetris_reduce_sum_device(tetris_ctx *ctx, uint64_t *data, uint32_t level, ui
 int tetris_plan(tetris_ctx *ctx, uint32_t db, uint32_t f_degree, uint32_t sign_stages, tetris_plan_info *out) {
     return guarded([&] {
         TREQUIRE(ctx && out, TETRIS_EINVAL, "null pointer");
-        cudaSetDevice(ctx->c.device);
+        TCHECK_CUDA(cudaSetDevice(ctx->c.device));
         plan_info(ctx->c, db, f_degree, sign_stages, out);
     });
 }
@@ -743,6 +765,10 @@ int tetris_set_option(tetris_ctx *ctx, int option, int64_t value) {
                     C.alpha = 0;
                 }
                 break;
+            case TETRIS_OPT_QUERY_STAGE:
+                TREQUIRE(value >= TETRIS_STAGE_FULL && value <= TETRIS_STAGE_U, TETRIS_EINVAL, "query stage must be 0..4");
+                C.query_stage = (int)value;
+                break;
             default:
                 throw Error(TETRIS_EINVAL, "unknown or read-only option");
         }
@@ -760,6 +786,7 @@ int tetris_get_option(tetris_ctx *ctx, int option, int64_t *value) {
             case TETRIS_OPT_KS_BASE2: *value = C.base2; break;
             case TETRIS_OPT_PROFILE: *value = C.profile; break;
             case TETRIS_OPT_NTT_GROUP: *value = C.nt.loge; break;
+            case TETRIS_OPT_QUERY_STAGE: *value = C.query_stage; break;
             default: throw Error(TETRIS_EINVAL, "unknown option");
         }
     });
@@ -775,16 +802,23 @@ int tetris_batch_run(const tetris_batch_item *items, uint32_t n, int schedule, i
 int tetris_serve_start(tetris_ctx *ctx, size_t budget, uint32_t max_inflight) {
     return guarded([&] {
         TREQUIRE(ctx, TETRIS_EINVAL, "null context");
-        cudaSetDevice(ctx->c.device);
+        TCHECK_CUDA(cudaSetDevice(ctx->c.device));
         cudaStreamSynchronize(ctx->c.stream);
         serve_start(ctx->c, budget, max_inflight);
+    });
+}
+
+int tetris_cancel(tetris_ctx *ctx, uint64_t ticket) {
+    return guarded([&] {
+        TREQUIRE(ctx, TETRIS_EINVAL, "null context");
+        serve_cancel(ctx->c, ticket);
     });
 }
 
 int tetris_submit(tetris_ctx *ctx, uint32_t db, const tetris_query *q, uint64_t *ticket) {
     return guarded([&] {
         TREQUIRE(ctx && ticket, TETRIS_EINVAL, "null pointer");
-        cudaSetDevice(ctx->c.device);
+        TCHECK_CUDA(cudaSetDevice(ctx->c.device));
         *ticket = serve_submit(ctx->c, db, q);
     });
 }
@@ -809,7 +843,7 @@ int tetris_serve_stats_get(tetris_ctx *ctx, tetris_serve_stats *out, int reset) 
 int tetris_serve_stop(tetris_ctx *ctx) {
     return guarded([&] {
         TREQUIRE(ctx, TETRIS_EINVAL, "null context");
-        cudaSetDevice(ctx->c.device);
+        TCHECK_CUDA(cudaSetDevice(ctx->c.device));
         serve_stop(ctx->c);
     });
 }
@@ -818,7 +852,7 @@ int tetris_rescale_ntt_noalloc(tetris_ctx *ctx, const uint64_t *in, uint64_t *ou
                                void *stream) {
     return guarded([&] {
         TREQUIRE(ctx, TETRIS_EINVAL, "null context");
-        cudaSetDevice(ctx->c.device);
+        TCHECK_CUDA(cudaSetDevice(ctx->c.device));
         rescale_ntt_noalloc(ctx->c, in, out, (int)level, (int)ncomp, reinterpret_cast<cudaStream_t>(stream));
     });
 }
@@ -830,7 +864,7 @@ static int repack_call(tetris_ctx *ctx, const uint64_t *cts, uint32_t n, uint32_
     return guarded([&] {
         TREQUIRE(ctx && out && out->data, TETRIS_EINVAL, "repack: null pointer");
         Ctx &C = ctx->c;
-        cudaSetDevice(C.device);
+        TCHECK_CUDA(cudaSetDevice(C.device));
         TREQUIRE((int)level <= C.L(), TETRIS_ELEVEL, "repack: bad level");
         TREQUIRE(out->cap_words >= (size_t)2 * (level + 1) * C.N, TETRIS_EINVAL, "repack: output buffer too small");
         cudaStream_t s = device ? reinterpret_cast<cudaStream_t>(stream) : C.stream;
@@ -855,7 +889,7 @@ int tetris_pfe_scores_device(tetris_ctx *ctx, const uint64_t *u, uint32_t m, con
                              uint64_t *out, void *stream) {
     return guarded([&] {
         TREQUIRE(ctx, TETRIS_EINVAL, "null context");
-        cudaSetDevice(ctx->c.device);
+        TCHECK_CUDA(cudaSetDevice(ctx->c.device));
         pfe_scores(ctx->c, u, m, exps, p, out, reinterpret_cast<cudaStream_t>(stream));
     });
 }
@@ -866,7 +900,7 @@ int tetris_pfe_scores(tetris_ctx *ctx, const uint64_t *u, uint32_t m, const uint
         TREQUIRE(ctx && u && exps && out, TETRIS_EINVAL, "pfe: null pointer");
         TREQUIRE(m >= 1 && m <= 4096 && p >= 1 && p < (1ull << 30), TETRIS_EINVAL, "pfe: bad sizes");
         Ctx &C = ctx->c;
-        cudaSetDevice(C.device);
+        TCHECK_CUDA(cudaSetDevice(C.device));
         const size_t uw = (size_t)m * 2 * C.N, ow = (size_t)p * 2 * C.N, ew = (size_t)p * m;
         u64 *du = nullptr, *dout = nullptr;
         uint32_t *de = nullptr;
@@ -926,7 +960,7 @@ int tetris_op(tetris_ctx *ctx, int op, const tetris_ct_in *a, const tetris_ct_in
     return guarded([&] {
         TREQUIRE(ctx && a, TETRIS_EINVAL, "null pointer");
         Ctx &C = ctx->c;
-        cudaSetDevice(C.device);
+        TCHECK_CUDA(cudaSetDevice(C.device));
         Program P;
         Rec R(C, P);
         CtH x = upload_ct(C, P, R, *a, true);

@@ -110,17 +110,22 @@ void Program::add_late_wait() {
     launches.push_back(std::move(l));
 }
 
+void InSlot::copy_from(const void *src, cudaMemcpyKind kind, cudaStream_t s) const {
+    if (rows == 1 || src_pitch == row_words)
+        TCHECK_CUDA(cudaMemcpyAsync(dst, src, words() * 8, kind, s));
+    else
+        TCHECK_CUDA(cudaMemcpy2DAsync(dst, row_words * 8, src, src_pitch * 8, row_words * 8, rows, kind, s));
+}
+
 void Program::copy_inputs(const std::vector<const void *> &srcs, cudaMemcpyKind kind, cudaStream_t s) {
     TREQUIRE(srcs.size() == in_slots.size(), TETRIS_EINVAL, "inputs do not match the program");
     const size_t split = late_ev ? std::min(late_slot, srcs.size()) : srcs.size();
-    for (size_t i = 0; i < split; i++)
-        TCHECK_CUDA(cudaMemcpyAsync(in_slots[i].first, srcs[i], in_slots[i].second * 8, kind, s));
+    for (size_t i = 0; i < split; i++) in_slots[i].copy_from(srcs[i], kind, s);
     if (!late_ev) return;
     // the side stream starts after the early copies, which follow the previous run on s
     TCHECK_CUDA(cudaEventRecord(early_ev, s));
     TCHECK_CUDA(cudaStreamWaitEvent(side, early_ev, 0));
-    for (size_t i = split; i < srcs.size(); i++)
-        TCHECK_CUDA(cudaMemcpyAsync(in_slots[i].first, srcs[i], in_slots[i].second * 8, kind, side));
+    for (size_t i = split; i < srcs.size(); i++) in_slots[i].copy_from(srcs[i], kind, side);
     TCHECK_CUDA(cudaEventRecord(late_ev, side));
 }
 
@@ -322,9 +327,10 @@ static const char *store_name(int m) {
     return "plain";
 }
 
-void Rec::ntt(bool inverse, const std::vector<NttJob> &jobs, int load_mode, int store_mode, int split,
+void Rec::ntt(bool inverse, const std::vector<NttJob> &jobs_in, int load_mode, int store_mode, int split,
               int store_mode_b, int passes) {
-    if (jobs.empty()) return;
+    if (jobs_in.empty()) return;
+    const std::vector<NttJob> &jobs = jobs_in;
     TREQUIRE(split < 0 || !defer, TETRIS_EINVAL, "split transforms are not deferred");
     TREQUIRE(passes >= 1 && passes <= 3, TETRIS_EINVAL, "no transform pass selected");
     if (defer) {

@@ -9,16 +9,6 @@ namespace {
 
 constexpr int kEwThreads = 256;
 
-int sm_count() {
-    static int sms = 0;
-    if (!sms) {
-        int dev = 0;
-        cudaGetDevice(&dev);
-        if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms <= 0) sms = 148;
-    }
-    return sms;
-}
-
 // grid-stride kernels: a few resident CTAs per SM
 int grid_for(size_t work_items) {
     const int sms = sm_count();
@@ -307,6 +297,29 @@ __global__ void __launch_bounds__(kEwThreads) modmul_probe_kernel(u64 *sink, u64
 }
 
 }  // namespace
+
+int sm_count() {
+    constexpr int kDev = 64;
+    static std::atomic<int> sms[kDev];
+    int dev = 0;
+    TCHECK_CUDA(cudaGetDevice(&dev));
+    int v = (dev >= 0 && dev < kDev) ? sms[dev].load(std::memory_order_relaxed) : 0;
+    if (v <= 0) {
+        TCHECK_CUDA(cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev));
+        TREQUIRE(v > 0, -3, "device reports no SMs");
+        if (dev >= 0 && dev < kDev) sms[dev].store(v, std::memory_order_relaxed);
+    }
+    return v;
+}
+
+void opt_in_smem(const void *func, int bytes, std::atomic<uint64_t> &done) {
+    int dev = 0;
+    TCHECK_CUDA(cudaGetDevice(&dev));
+    const uint64_t bit = (dev >= 0 && dev < 64) ? 1ull << dev : 0;
+    if (bit && (done.load(std::memory_order_acquire) & bit)) return;
+    TCHECK_CUDA(cudaFuncSetAttribute(func, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes));
+    if (bit) done.fetch_or(bit, std::memory_order_release);
+}
 
 double modmul_peak_probe() {
     const u64 q = 1152921504606584833ull;  // a 60-bit prime = 1 mod 2^17

@@ -80,7 +80,7 @@ __global__ void round_kernel(const double *m, int64_t *out, size_t count, double
         out[it] = (int64_t)floor(__dadd_rn(__dmul_rn(scale, m[it]), 0.5));
 }
 
-int blocks_for(size_t n) { return (int)std::min<size_t>((n + 255) / 256, 152 * 16); }
+int blocks_for(size_t n) { return (int)std::min<size_t>((n + 255) / 256, (size_t)sm_count() * 16); }
 
 }  // namespace
 
@@ -89,6 +89,9 @@ int blocks_for(size_t n) { return (int)std::min<size_t>((n + 255) / 256, 152 * 1
 void encode_real_batch(const double *slots, double *m, int batch, int log_n, const double *twid_dev, double *work,
                        cudaStream_t s) {
     const size_t n = (size_t)1 << log_n;
+    // every buffer is read and written as double2: 16-byte alignment, checked here
+    TREQUIRE(((uintptr_t)twid_dev & 15) == 0 && ((uintptr_t)work & 15) == 0, -1,
+             "encoder: twiddle table or work buffer not 16-byte aligned");
     const double2 *tw = reinterpret_cast<const double2 *>(twid_dev);
     const double2 *twist = tw + n / 2;
     const int *u_of_j = reinterpret_cast<const int *>(twist + n);

@@ -2,6 +2,8 @@
 #pragma once
 #include <cuda_runtime.h>
 
+#include <atomic>
+
 #include <cstdint>
 #include <functional>
 #include <map>
@@ -210,6 +212,13 @@ void launch_reduce_i64(const RedJob *jobs_dev, int njobs, int log_n, const ModIn
 
 // measured lazy-Shoup modular multiplications per second (G/s) on the current device
 double modmul_peak_probe();
+
+// Dynamic shared memory above 48 KB needs an opt-in per kernel and device:
+// done once for the current device (a bit per device in done), safe to race
+// from several threads (they all set the same value).
+void opt_in_smem(const void *func, int bytes, std::atomic<uint64_t> &done);
+// the current device's SM count (queried once per device)
+int sm_count();
 
 // ---------------------------------------------------------------------------
 // FP64 encoder (encode.cu)

@@ -53,6 +53,55 @@ u64 *scratch_on(int device) {
     return g_scratch_addr[device];
 }
 
+// The job tables of one call, written on the device from the launch
+// parameters alone (nothing is read from host memory after the call returns).
+struct NoallocParams {
+    const u64 *in;
+    u64 *out, *top;
+    NttJob *jobs_inv, *jobs_fwd;
+    uint32_t N, level, ncomp, pad;
+    u64 top_mul, top_mul_sh, top_half;               // N^-1 mod q_l (Shoup pair), floor(q_l/2)
+    u64 half[kMaxPrimes], mul[kMaxPrimes], mul_sh[kMaxPrimes];  // per q_i, i < l
+};
+
+__global__ void noalloc_tables_kernel(NoallocParams p) {
+    const size_t N = p.N;
+    for (uint32_t c = threadIdx.x; c < p.ncomp; c += blockDim.x) {  // top limb -> coefficient domain
+        NttJob j{};
+        j.src = p.in + ((size_t)c * (p.level + 1) + p.level) * N;
+        j.dst = p.top + (size_t)c * N;
+        j.prime = p.level;
+        j.mul = p.top_mul;
+        j.mul_sh = p.top_mul_sh;
+        j.conv_sub = p.top_half;
+        p.jobs_inv[c] = j;
+    }
+    for (uint32_t t = threadIdx.x; t < p.level * p.ncomp; t += blockDim.x) {
+        const uint32_t i = t / p.ncomp, c = t % p.ncomp;
+        NttJob j{};
+        j.prime = i;
+        j.conv_sub = p.half[i];
+        j.mul = p.mul[i];
+        j.mul_sh = p.mul_sh[i];
+        j.src = p.top + (size_t)c * N;
+        j.base = p.in + ((size_t)c * (p.level + 1) + i) * N;
+        j.dst = p.out + ((size_t)c * p.level + i) * N;
+        p.jobs_fwd[t] = j;
+    }
+}
+
+// A caller buffer must be device (or managed) memory of the context's device.
+void require_device_buffer(const Ctx &C, const void *ptr, const char *what) {
+    cudaPointerAttributes a{};
+    cudaError_t e = cudaPointerGetAttributes(&a, ptr);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        throw Error(TETRIS_EINVAL, std::string("rescale_noalloc: ") + what + " is not a CUDA pointer");
+    }
+    TREQUIRE((a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged) && a.device == C.device, TETRIS_EINVAL,
+             std::string("rescale_noalloc: ") + what + " is not device memory of the context's device");
+}
+
 }  // namespace
 
 size_t noalloc_scratch_bytes() { return kScratchWords * 8; }
@@ -69,43 +118,33 @@ void rescale_ntt_noalloc(Ctx &C, const u64 *in, u64 *out, int level, int ncomp, 
     const size_t in_words = (size_t)ncomp * (level + 1) * N, out_words = (size_t)ncomp * level * N;
     const bool disjoint = out + out_words <= in || in + in_words <= out;
     TREQUIRE(disjoint, TETRIS_EINVAL, "rescale_noalloc: input and output overlap");
+    require_device_buffer(C, in, "input");
+    require_device_buffer(C, out, "output");
     u64 *base = scratch_on(C.device);
-    u64 *top = base;                                               // [ncomp][N] top limbs, coefficient domain
-    NttJob *jobs_inv = reinterpret_cast<NttJob *>(base + kLimbWords);
-    NttJob *jobs_fwd = jobs_inv + kNoAllocMaxJobs;
 
+    NoallocParams p{};
+    p.in = in;
+    p.out = out;
+    p.top = base;                                                  // [ncomp][N] top limbs, coefficient domain
+    p.jobs_inv = reinterpret_cast<NttJob *>(base + kLimbWords);
+    p.jobs_fwd = p.jobs_inv + kNoAllocMaxJobs;
+    p.N = (uint32_t)N;
+    p.level = (uint32_t)level;
+    p.ncomp = (uint32_t)ncomp;
     const u64 ql = C.q[level], half = (ql - 1) / 2;
-    std::vector<NttJob> ji, jf;
-    for (int c = 0; c < ncomp; c++) {  // top limb -> [a_l + floor(q_l/2)]_{q_l}, coefficient domain
-        NttJob j{};
-        j.src = in + ((size_t)c * (level + 1) + level) * N;
-        j.dst = top + (size_t)c * N;
-        j.prime = level;
-        j.mul = C.mods_host[level].ninv;
-        j.mul_sh = C.mods_host[level].ninv_sh;
-        j.conv_sub = half;
-        ji.push_back(j);
-    }
+    p.top_mul = C.mods_host[level].ninv;
+    p.top_mul_sh = C.mods_host[level].ninv_sh;
+    p.top_half = half;
     for (int i = 0; i < level; i++) {
         const u64 qi = C.q[i];
-        NttJob j{};
-        j.prime = i;
-        j.conv_sub = half % qi;
-        j.mul = h_invmod(ql % qi, qi);
-        j.mul_sh = h_shoup(j.mul, qi);
-        for (int c = 0; c < ncomp; c++) {
-            NttJob jc = j;
-            jc.src = top + (size_t)c * N;
-            jc.base = in + ((size_t)c * (level + 1) + i) * N;
-            jc.dst = out + ((size_t)c * level + i) * N;
-            jf.push_back(jc);
-        }
+        p.half[i] = half % qi;
+        p.mul[i] = h_invmod(ql % qi, qi);
+        p.mul_sh[i] = h_shoup(p.mul[i], qi);
     }
-    // job tables: copied from pageable host memory (staged before return)
-    TCHECK_CUDA(cudaMemcpyAsync(jobs_inv, ji.data(), ji.size() * sizeof(NttJob), cudaMemcpyHostToDevice, s));
-    TCHECK_CUDA(cudaMemcpyAsync(jobs_fwd, jf.data(), jf.size() * sizeof(NttJob), cudaMemcpyHostToDevice, s));
-    launch_ntt(true, C.log_n, C.nt, jobs_inv, (int)ji.size(), LOAD_PLAIN, STORE_SCALED, s);
-    launch_ntt(false, C.log_n, C.nt, jobs_fwd, (int)jf.size(), LOAD_REDUCE, STORE_COMBINE, s);
+    noalloc_tables_kernel<<<1, 128, 0, s>>>(p);
+    TCHECK_CUDA(cudaGetLastError());
+    launch_ntt(true, C.log_n, C.nt, p.jobs_inv, ncomp, LOAD_PLAIN, STORE_SCALED, s);
+    launch_ntt(false, C.log_n, C.nt, p.jobs_fwd, level * ncomp, LOAD_REDUCE, STORE_COMBINE, s);
     TCHECK_CUDA(cudaGetLastError());
 }
 

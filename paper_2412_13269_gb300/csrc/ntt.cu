@@ -432,7 +432,9 @@ template <int LOGM, int LOGEV>
 struct KsSmem {
     using GG = Geo<LOGM, false, false, LOGEV>;
     __host__ __device__ static size_t exch_words(int sub_cta) { return (size_t)sub_cta * (GG::M + GG::M / 16); }
-    __host__ __device__ static size_t bytes(int sub_cta) { return (exch_words(sub_cta) + 2 * (size_t)GG::E * kThreads) * 8; }
+    __host__ __device__ static size_t bytes(int sub_cta) {
+        return (exch_words(sub_cta) + 2 * (size_t)GG::E * kThreads) * 8;
+    }
 };
 
 // Bulk-copy (TMA) prefetch of a contiguous range into L2: no shared memory, no
@@ -535,12 +537,8 @@ void run_keyswitch_up(const PassParams &P, const KsJob *jobs, int njobs, cudaStr
     const int sub_cta = std::min(kThreads / GG::T, nsub);
     TREQUIRE(sub_cta * GG::T == kThreads, -1, "fused ModUp pass needs full CTAs");
     const size_t smem = KsSmem<LOGM, LOGEV>::bytes(sub_cta);
-    static bool opted = false;  // dynamic shared memory above 48 KB needs an opt-in per kernel
-    if (!opted) {
-        TCHECK_CUDA(cudaFuncSetAttribute(keyswitch_up_kernel<LOGM, LOGEV>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)KsSmem<LOGM, LOGEV>::bytes(kThreads / GG::T)));
-        opted = true;
-    }
+    static std::atomic<uint64_t> opted{0};
+    opt_in_smem((const void *)keyswitch_up_kernel<LOGM, LOGEV>, (int)KsSmem<LOGM, LOGEV>::bytes(kThreads / GG::T), opted);
     for (int j0 = 0; j0 < njobs; j0 += 65535) {
         dim3 grid(nsub / sub_cta, std::min(65535, njobs - j0));
         keyswitch_up_kernel<LOGM, LOGEV><<<grid, sub_cta * GG::T, smem, st>>>(P, jobs + j0);

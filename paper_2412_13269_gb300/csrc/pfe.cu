@@ -142,12 +142,8 @@ void run_pfe_staged(const u64 *u, const uint32_t *exps, uint32_t m, uint64_t p, 
                     cudaStream_t s) {
     const size_t stage_bytes = 4 * ((size_t)1 << LOGN) * 8;
     const size_t smem = stage_bytes + (size_t)kPfeGroups * m * 4;
-    static bool opted = false;  // dynamic shared memory above 48 KB needs an opt-in
-    if (!opted) {
-        TCHECK_CUDA(cudaFuncSetAttribute(pfe_staged_kernel<LOGN>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)(stage_bytes + (size_t)kPfeGroups * kPfeStagedMaxM * 4)));
-        opted = true;
-    }
+    static std::atomic<uint64_t> opted{0};
+    opt_in_smem((const void *)pfe_staged_kernel<LOGN>, (int)(stage_bytes + (size_t)kPfeGroups * kPfeStagedMaxM * 4), opted);
     dim3 grid((unsigned)((p + kPfeGroups - 1) / kPfeGroups), 2);
     pfe_staged_kernel<LOGN><<<grid, kPfeThreads * kPfeGroups, smem, s>>>(u, exps, m, p, mi.q, mi.one_sh, out);
 }

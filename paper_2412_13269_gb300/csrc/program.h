@@ -63,6 +63,7 @@ struct Ctx {
     int blocks_per_launch = 0;
     int use_graph = 1;
     int profile = 0;
+    int query_stage = 0;    // TETRIS_OPT_QUERY_STAGE: 0 the whole query, else the stage whose values are returned
     std::map<std::string, KernelStat> stats;
     void *server = nullptr;  // serve.cu
     std::map<std::string, std::unique_ptr<Program>> programs;
@@ -97,6 +98,18 @@ struct Launch {
     bool kernel = true;  // false: a stream wait, neither timed nor counted
 };
 
+// A device staging slot for one input: rows (ciphertext components) of
+// row_words words (the limbs the program uses), copied from a source whose
+// rows lie src_pitch words apart (the caller's [comps][level+1][N] layout,
+// of which only the first limbs of each component are read).
+struct InSlot {
+    u64 *dst = nullptr;
+    size_t rows = 1, row_words = 0, src_pitch = 0;
+    size_t words() const { return rows * row_words; }
+    // enqueue the copy of src into dst (host-to-device or device-to-device)
+    void copy_from(const void *src, cudaMemcpyKind kind, cudaStream_t s) const;
+};
+
 struct Program {
     Ctx *ctx = nullptr;
     Pool pool;
@@ -106,7 +119,7 @@ struct Program {
     int kernel_launches = 0;
     std::vector<BufPtr> hold;
     // query programs: input staging slots (device pointer, words) and output
-    std::vector<std::pair<u64 *, size_t>> in_slots;
+    std::vector<InSlot> in_slots;
     BufPtr out_buf;
     u64 *out_base = nullptr;
     size_t out_words = 0;
@@ -236,6 +249,7 @@ struct QuerySpec {
     int bpl = 0;
     int loge = 3;                // NTT register-group width (log2 elements per thread)
     uint64_t total_records = 0;  // 0: the database's own record count
+    int stage = 0;               // 0: the whole query; 1..4: stop after x, y, y - t or the step values
     // global threshold (none when gstages is empty): t1's level and scale
     int g_level = 0;
     double g_scale = 0;
@@ -243,7 +257,7 @@ struct QuerySpec {
     std::string key(uint32_t db) const {
         std::ostringstream o;
         o << "q" << db << ":" << attrs << ":" << degree << ":" << bpl << ":" << loge << ":" << t_level << ":"
-          << total_records << ":";
+          << total_records << ":" << stage << ":";
         auto bits = [&](double v) {
             uint64_t b;
             std::memcpy(&b, &v, 8);
@@ -270,6 +284,9 @@ struct QuerySpec {
 std::unique_ptr<Program> record_query(Ctx &C, const Database &db, const QuerySpec &q);
 QuerySpec spec_of(const Ctx &C, const Database &db, const tetris_query *q);
 std::vector<const tetris_ct_in *> query_inputs(const tetris_query *q);  // in input-slot order
+// the input slots a query program copies, in input-slot order (dst unset):
+// only the limbs the circuit reads of each input
+std::vector<InSlot> query_slot_shapes(const Ctx &C, const Database &db, const QuerySpec &q);
 void evaluate_query(Ctx &C, uint32_t db, const tetris_query *q, tetris_ct_out *out, cudaStream_t s, bool device);
 void plan_info(Ctx &C, uint32_t db, uint32_t degree, uint32_t stages, tetris_plan_info *out);
 void drop_programs_of_db(Ctx &C, uint32_t db);
@@ -281,6 +298,7 @@ void serve_start(Ctx &C, size_t budget, uint32_t max_inflight);
 uint64_t serve_submit(Ctx &C, uint32_t db, const tetris_query *q);
 int serve_poll(Ctx &C, uint64_t ticket, tetris_ct_out *out, uint32_t timeout_ms);
 void serve_stats(Ctx &C, tetris_serve_stats *st, bool reset);
+void serve_cancel(Ctx &C, uint64_t ticket);
 void serve_stop(Ctx &C);
 
 // batch.cu

@@ -274,8 +274,11 @@ static CtH sign_stage(Rec &R, const CtH &u, const std::vector<double> &co) {
     return relin_rescale_to(R, fold(R, R.tensor(u8, B), A, 1.0), l - 4);
 }
 
+// The circuit of nb blocks; stop (TETRIS_STAGE_*) ends it after a stage and
+// returns that stage's ciphertexts.
 static CtH eval_blocks(Rec &R, const Database &db, const QPlan &pl, int b0, int nb, const CtH &w,
-                       const std::function<void()> &need_ck, const std::vector<CtH> &ck, const CtH &tadj, int degree) {
+                       const std::function<void()> &need_ck, const std::vector<CtH> &ck, const CtH &tadj, int degree,
+                       int stop) {
     Ctx &C = R.C;
     const int tl = w.level;  // l_lin + 1
     const size_t N = C.N, nq = C.q.size();
@@ -303,6 +306,7 @@ static CtH eval_blocks(Rec &R, const Database &db, const QPlan &pl, int b0, int 
     CtH x = R.rescale(x0);
     x.scale = pl.x_scale;
     x0 = CtH();
+    if (stop == TETRIS_STAGE_X) return x;
     // powers x^k; a factor of lower power is dropped (not adjusted) to the
     // other's level, so a power's scale is its factors' product over the prime
     // the relinearisation removes (the planner's power_scales)
@@ -350,9 +354,37 @@ static CtH eval_blocks(Rec &R, const Database &db, const QPlan &pl, int b0, int 
     }
     Pw.clear();
     y = R.add(y, ck[0]);
+    if (stop == TETRIS_STAGE_Y) return y;
     CtH u = R.sub(y, tadj);
+    if (stop == TETRIS_STAGE_D) return u;
     for (auto &co : pl.co) u = sign_stage(R, u, co);
     return R.add_int(u, round_half_up(pl.step_const * C.S[u.level]));
+}
+
+// Limbs of an input at level `from` that an adjust to level lt reads: the
+// first lt + 2 (keep q_0..q_{lt+1}, rescale by q_{lt+1}), or lt + 1 when it
+// arrives at lt.  Dropping the others before the copy is exact.
+static int used_limbs(int from, int lt) {
+    TREQUIRE(from >= lt, TETRIS_ELEVEL, "input ciphertext level too low");
+    return from == lt ? lt + 1 : lt + 2;
+}
+
+std::vector<InSlot> query_slot_shapes(const Ctx &C, const Database &db, const QuerySpec &q) {
+    const QPlan pl = make_plan(C, db.records, q.degree, q.stages, q.total_records, q.gstages);
+    const size_t N = C.N;
+    std::vector<InSlot> v;
+    auto add = [&](int from, int m) {
+        InSlot s;
+        s.rows = 2;
+        s.row_words = (size_t)m * N;
+        s.src_pitch = (size_t)(from + 1) * N;
+        v.push_back(s);
+    };
+    for (int j = 0; j < q.attrs; j++) add(C.L(), pl.l_lin + 2);  // the w_j, dropped to l_lin + 1
+    for (int k = 0; k <= q.degree; k++) add(q.c_level[k], used_limbs(q.c_level[k], pl.coef_level(k)));
+    add(q.t_level, used_limbs(q.t_level, pl.l_y));
+    if (!q.gstages.empty()) add(q.g_level, used_limbs(q.g_level, pl.l_out));
+    return v;
 }
 
 std::unique_ptr<Program> record_query(Ctx &C, const Database &db, const QuerySpec &q) {
@@ -360,32 +392,29 @@ std::unique_ptr<Program> record_query(Ctx &C, const Database &db, const QuerySpe
     P->ctx = &C;
     Rec R(C, *P);
     const QPlan pl = make_plan(C, db.records, q.degree, q.stages, q.total_records, q.gstages);
-    const int L = C.L();
     const size_t N = C.N;
-    // staging buffers for the inputs (coefficient domain on arrival, NTT in place)
-    const size_t wwords = (size_t)2 * (L + 1) * N;
+    // staging buffers for the inputs (coefficient domain on arrival, NTT in
+    // place), holding only the limbs the circuit reads of each input
+    P->in_slots = query_slot_shapes(C, db, q);
+    const int lw = pl.l_lin + 1;  // the w_j's level after the drop
+    const size_t wwords = P->in_slots[0].words();
     BufPtr wbuf = P->pool.alloc(wwords * q.attrs);
     P->hold.push_back(wbuf);
-    for (int j = 0; j < q.attrs; j++) P->in_slots.push_back({wbuf->ptr + j * wwords, wwords});
-    std::vector<CtH> cin;
-    for (int k = 0; k <= q.degree; k++) {
-        CtH c = R.new_ct(1, 2, q.c_level[k]);
-        c.scale = q.c_scale[k];
+    for (int j = 0; j < q.attrs; j++) P->in_slots[j].dst = wbuf->ptr + j * wwords;
+    size_t slot = q.attrs;
+    auto input = [&](double scale) {
+        InSlot &sl = P->in_slots[slot++];
+        CtH c = R.new_ct(1, 2, (int)(sl.row_words / N) - 1);
+        c.scale = scale;
         P->hold.push_back(c.buf);
-        P->in_slots.push_back({c.base, c.bstride});
-        cin.push_back(c);
-    }
-    CtH tin = R.new_ct(1, 2, q.t_level);
-    tin.scale = q.t_scale;
-    P->hold.push_back(tin.buf);
-    P->in_slots.push_back({tin.base, tin.bstride});
+        sl.dst = c.base;
+        return c;
+    };
+    std::vector<CtH> cin;
+    for (int k = 0; k <= q.degree; k++) cin.push_back(input(q.c_scale[k]));
+    CtH tin = input(q.t_scale);
     CtH t1in;
-    if (!q.gstages.empty()) {
-        t1in = R.new_ct(1, 2, q.g_level);
-        t1in.scale = q.g_scale;
-        P->hold.push_back(t1in.buf);
-        P->in_slots.push_back({t1in.base, t1in.bstride});
-    }
+    if (!q.gstages.empty()) t1in = input(q.g_scale);
     // per-query: the w_j (one batch of attrs ciphertexts) dropped to level
     // l_lin + 1, their remaining limbs to the NTT domain
     auto ntt_inputs = [&](const std::vector<CtH> &cts) {
@@ -401,8 +430,7 @@ std::unique_ptr<Program> record_query(Ctx &C, const Database &db, const QuerySpe
                     }
         R.ntt(false, jobs, LOAD_PLAIN, STORE_PLAIN);
     };
-    CtH w = R.view(wbuf, wbuf->ptr, q.attrs, 2, L, wwords, (L + 1) * N, C.S[L]);
-    w = R.drop(w, pl.l_lin + 1);
+    CtH w = R.view(wbuf, wbuf->ptr, q.attrs, 2, lw, wwords, (size_t)(lw + 1) * N, C.S[C.L()]);
     ntt_inputs({w});
     // the coefficients and the threshold (and t1) are late inputs: their copies
     // overlap the linear combination and the first powers of x, and they are
@@ -428,9 +456,41 @@ std::unique_ptr<Program> record_query(Ctx &C, const Database &db, const QuerySpe
     const int bpl = q.bpl <= 0 ? B : std::min(q.bpl, B);
     CtH full, last;
     bool have_full = false, have_last = false;
+    if (q.stage != TETRIS_STAGE_FULL) {
+        // the stage's ciphertexts of every block, block after block, coefficient domain
+        BufPtr ob;
+        size_t bw = 0;
+        for (int b0 = 0; b0 < B; b0 += bpl) {
+            const int nb = std::min(bpl, B - b0);
+            CtH v = eval_blocks(R, db, pl, b0, nb, w, need_ck, ck, tadj, q.degree, q.stage);
+            if (!ob) {
+                bw = (size_t)2 * (v.level + 1) * N;
+                ob = P->pool.alloc(bw * B);
+                P->out_level = v.level;
+                P->out_scale = v.scale;
+            }
+            std::vector<NttJob> jobs;
+            for (int b = 0; b < nb; b++)
+                for (int c = 0; c < 2; c++)
+                    for (int i = 0; i <= v.level; i++) {
+                        NttJob j{};
+                        j.src = v.limb(b, c, i);
+                        j.dst = ob->ptr + (size_t)(b0 + b) * bw + ((size_t)c * (v.level + 1) + i) * N;
+                        j.prime = i;
+                        jobs.push_back(j);
+                    }
+            R.ntt(true, jobs, LOAD_PLAIN, STORE_PLAIN);
+        }
+        P->out_buf = ob;
+        P->out_base = ob->ptr;
+        P->out_words = bw * B;
+        P->out_comps = 2;
+        P->finalize();
+        return P;
+    }
     for (int b0 = 0; b0 < B; b0 += bpl) {
         const int nb = std::min(bpl, B - b0);
-        CtH u = eval_blocks(R, db, pl, b0, nb, w, need_ck, ck, tadj, q.degree);
+        CtH u = eval_blocks(R, db, pl, b0, nb, w, need_ck, ck, tadj, q.degree, TETRIS_STAGE_FULL);
         int nfull = nb;
         if (pl.ragged && b0 + nb == B) {
             last = R.view(u.buf, u.limb(nb - 1, 0, 0), 1, u.comps, u.level, u.bstride, u.cstride, u.scale);
@@ -538,6 +598,7 @@ QuerySpec spec_of(const Ctx &C, const Database &db, const tetris_query *q) {
         s.stages.push_back(std::vector<double>(q->sign_coeffs + st * nco, q->sign_coeffs + (st + 1) * nco));
     s.bpl = C.blocks_per_launch;
     s.loge = C.nt.loge;
+    s.stage = C.query_stage;
     TREQUIRE(q->total_records == 0 || q->total_records >= db.records, TETRIS_EINVAL,
              "query: total_records is smaller than the database");
     s.total_records = q->total_records;
@@ -651,8 +712,7 @@ void autotune(Ctx &C, uint32_t dbh, const tetris_query *q, int reps, std::vector
             Program &P = get_program(C, dbh, spec);
             const auto ins = query_inputs(q);
             for (size_t slot = 0; slot < ins.size(); slot++)
-                TCHECK_CUDA(cudaMemcpyAsync(P.in_slots[slot].first, ins[slot]->data, P.in_slots[slot].second * 8,
-                                            cudaMemcpyHostToDevice, C.stream));
+                P.in_slots[slot].copy_from(ins[slot]->data, cudaMemcpyHostToDevice, C.stream);
             P.run_graph(C.stream);
             TCHECK_CUDA(cudaEventRecord(e0, C.stream));
             for (int r = 0; r < reps; r++) P.run_graph(C.stream);
@@ -707,6 +767,8 @@ void plan_info(Ctx &C, uint32_t dbh, uint32_t degree, uint32_t stages, tetris_pl
     out->kernel_launches = P.kernel_launches;
     out->pt_scale = C.pt_scale;
     out->mask_scale = pl.mask_scale;
+    out->input_words = 0;
+    for (auto &sl : P.in_slots) out->input_words += sl.words();
 }
 
 }  // namespace tetris

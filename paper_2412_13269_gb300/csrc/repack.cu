@@ -35,7 +35,12 @@ std::unique_ptr<Program> record_repack(Ctx &C, uint32_t count, int level, double
     P->hold.push_back(x.buf);
     TCHECK_CUDA(cudaMemsetAsync(x.base, 0, x.bstride * n * 8, C.stream));
     TCHECK_CUDA(cudaStreamSynchronize(C.stream));
-    P->in_slots.push_back({x.base, x.bstride * count});
+    {
+        InSlot sl;
+        sl.dst = x.base;
+        sl.row_words = sl.src_pitch = x.bstride * count;
+        P->in_slots.push_back(sl);
+    }
     {
         std::vector<NttJob> jobs;
         for (uint32_t b = 0; b < count; b++)
@@ -127,7 +132,7 @@ void repack(Ctx &C, const u64 *cts, uint32_t count, int level, double scale, u64
     if (it == C.programs.end()) it = C.programs.emplace(key, record_repack(C, count, level, scale)).first;
     Program &P = *it->second;
     const cudaMemcpyKind in_kind = device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
-    TCHECK_CUDA(cudaMemcpyAsync(P.in_slots[0].first, cts, P.in_slots[0].second * 8, in_kind, s));
+    P.in_slots[0].copy_from(cts, in_kind, s);
     if (C.profile) P.run_profiled(s, C.stats);
     else if (C.use_graph) P.run_graph(s);
     else P.run(s);

@@ -56,6 +56,8 @@ struct Instance {
     std::string key;
     size_t bytes = 0;
     cudaStream_t stream = nullptr;
+    cudaEvent_t ev_start = nullptr, ev_end = nullptr;  // the running request's first and last device work
+    float t_start = 0, t_end = 0;                        // their times after the server's reference event (ms)
     u64 *pinned_out = nullptr;
     std::shared_ptr<Request> req;
     bool busy = false;
@@ -65,6 +67,8 @@ struct Instance {
             cudaStreamSynchronize(stream);
             cudaStreamDestroy(stream);
         }
+        if (ev_start) cudaEventDestroy(ev_start);
+        if (ev_end) cudaEventDestroy(ev_end);
         if (pinned_out) cudaFreeHost(pinned_out);
     }
 };
@@ -89,7 +93,12 @@ struct Server {
     bool stopping = false;
     size_t used = 0, peak = 0;
     std::vector<double> latencies_ms;
-    uint64_t submitted = 0, completed = 0, rejected = 0;
+    uint64_t submitted = 0, completed = 0, rejected = 0, cancelled = 0;
+    // overlap evidence: admitted requests in flight at once, and the device
+    // intervals [first work, last work] of completed requests (ms after ref)
+    cudaEvent_t ref = nullptr;
+    uint32_t max_admitted = 0;
+    std::vector<std::pair<double, double>> intervals;
 
     void loop();
     bool admit_one(std::unique_lock<std::mutex> &lk);
@@ -114,6 +123,7 @@ void CUDART_CB on_done(void *arg) {
 
 void Server::retire(Instance *in) {
     auto r = in->req;
+    if (in->t_end > 0) intervals.push_back({in->t_start, in->t_end});
     r->out.assign(in->pinned_out, in->pinned_out + in->prog->out_words);
     r->level = in->prog->out_level;
     r->ncomp = in->prog->out_comps;
@@ -183,7 +193,10 @@ bool Server::admit_one(std::unique_lock<std::mutex> &lk) {
         auto db_it = C->dbs.find(req->db);
         std::unique_ptr<Instance> ni(new Instance);
         ni->key = req->key;
+        std::vector<std::unique_ptr<Instance>> dead;
+        dead.swap(graveyard);
         lk.unlock();
+        dead.clear();  // evicted instances give their memory back before the new one allocates
         int code = TETRIS_OK;
         std::string msg;
         try {
@@ -191,6 +204,8 @@ bool Server::admit_one(std::unique_lock<std::mutex> &lk) {
             ni->prog = record_query(*C, db_it->second, req->spec);
             ni->bytes = ni->prog->pool.bytes_held();
             TCHECK_CUDA(cudaStreamCreateWithFlags(&ni->stream, cudaStreamNonBlocking));
+            TCHECK_CUDA(cudaEventCreate(&ni->ev_start));
+            TCHECK_CUDA(cudaEventCreate(&ni->ev_end));
             TCHECK_CUDA(cudaMallocHost(&ni->pinned_out, ni->prog->out_words * 8));
         } catch (const Error &e) {
             code = e.code;
@@ -209,24 +224,36 @@ bool Server::admit_one(std::unique_lock<std::mutex> &lk) {
             return true;
         }
         used += ni->bytes;
-        peak = std::max(peak, used);
         in = ni.get();
         instances.push_back(std::move(ni));
+        // the device bytes the server's programs hold right after an allocation
+        // (the high-water points): every instance and anything not yet freed
+        size_t held = 0;
+        for (auto &i : instances) held += i->prog ? i->prog->pool.bytes_held() : 0;
+        for (auto &i : graveyard) held += i->prog ? i->prog->pool.bytes_held() : 0;
+        peak = std::max(peak, held);
     }
     queue.pop_front();
     in->busy = true;
     in->req = req;
+    {
+        uint32_t n = 0;
+        for (auto &i : instances) n += i->busy;
+        max_admitted = std::max(max_admitted, n);
+    }
     Program &P = *in->prog;
     lk.unlock();
     try {
+        TCHECK_CUDA(cudaEventRecord(in->ev_start, in->stream));
         size_t off = 0;
-        for (size_t s = 0; s < P.in_slots.size(); s++) {
-            TCHECK_CUDA(cudaMemcpyAsync(P.in_slots[s].first, req->pinned_in + off, P.in_slots[s].second * 8,
+        for (size_t s = 0; s < P.in_slots.size(); s++) {  // the pinned copy holds each slot's rows back to back
+            TCHECK_CUDA(cudaMemcpyAsync(P.in_slots[s].dst, req->pinned_in + off, P.in_slots[s].words() * 8,
                                         cudaMemcpyHostToDevice, in->stream));
-            off += P.in_slots[s].second;
+            off += P.in_slots[s].words();
         }
         P.run_graph(in->stream);
         TCHECK_CUDA(cudaMemcpyAsync(in->pinned_out, P.out_base, P.out_words * 8, cudaMemcpyDeviceToHost, in->stream));
+        TCHECK_CUDA(cudaEventRecord(in->ev_end, in->stream));
         TCHECK_CUDA(cudaLaunchHostFunc(in->stream, on_done, new std::pair<Server *, Instance *>(this, in)));
     } catch (const Error &e) {
         lk.lock();
@@ -243,13 +270,24 @@ bool Server::admit_one(std::unique_lock<std::mutex> &lk) {
 }
 
 void Server::loop() {
+    // the device was made current and checked by serve_start on the same ordinal
     cudaSetDevice(C->device);
     std::unique_lock<std::mutex> lk(mu);
     bool blocked = false;  // the head of the queue waits for running queries (memory or sizing)
     for (;;) {
         if (!finished.empty()) {
-            for (Instance *in : finished) retire(in);
-            finished.clear();
+            std::vector<Instance *> fin;
+            fin.swap(finished);
+            lk.unlock();
+            for (Instance *in : fin) {  // both events have completed: the callback follows the stream's last work
+                if (cudaEventElapsedTime(&in->t_start, ref, in->ev_start) != cudaSuccess ||
+                    cudaEventElapsedTime(&in->t_end, ref, in->ev_end) != cudaSuccess) {
+                    cudaGetLastError();
+                    in->t_start = in->t_end = 0;
+                }
+            }
+            lk.lock();
+            for (Instance *in : fin) retire(in);
             blocked = false;
             cv_done.notify_all();
         }
@@ -290,6 +328,15 @@ void serve_start(Ctx &C, size_t budget, uint32_t max_inflight) {
     S->C = &C;
     S->budget = budget;
     S->max_inflight = max_inflight;
+    cudaError_t e = cudaEventCreate(&S->ref);
+    if (e == cudaSuccess) e = cudaEventRecord(S->ref, C.stream);
+    if (e == cudaSuccess) e = cudaEventSynchronize(S->ref);
+    if (e != cudaSuccess) {
+        if (S->ref) cudaEventDestroy(S->ref);
+        delete S;
+        cudaGetLastError();
+        throw Error(TETRIS_ECUDA, std::string("serve_start: ") + cudaGetErrorString(e));
+    }
     C.server = S;
     S->th = std::thread([S] { S->loop(); });
 }
@@ -304,12 +351,12 @@ uint64_t serve_submit(Ctx &C, uint32_t db, const tetris_query *q) {
     req->spec = spec_of(C, it->second, q);
     req->spec.bpl = 0;
     req->key = req->spec.key(db);
-    const size_t N = C.N;
-    auto words = [&](const tetris_ct_in &c) { return (size_t)2 * (c.level + 1) * N; };
     const std::vector<const tetris_ct_in *> ins = query_inputs(q);
-    for (auto c : ins) {
-        req->in_words.push_back(words(*c));
-        req->total_in += words(*c);
+    const std::vector<InSlot> shapes = query_slot_shapes(C, it->second, req->spec);  // only the limbs the circuit reads
+    TREQUIRE(shapes.size() == ins.size(), TETRIS_EINVAL, "query: inputs do not match the plan");
+    for (auto &sh : shapes) {
+        req->in_words.push_back(sh.words());
+        req->total_in += sh.words();
     }
     {
         std::lock_guard<std::mutex> lk(S->mu);
@@ -322,8 +369,11 @@ uint64_t serve_submit(Ctx &C, uint32_t db, const tetris_query *q) {
     if (!req->pinned_in) TCHECK_CUDA(cudaMallocHost(&req->pinned_in, req->total_in * 8));
     size_t off = 0;
     for (size_t i = 0; i < ins.size(); i++) {
-        std::memcpy(req->pinned_in + off, ins[i]->data, req->in_words[i] * 8);
-        off += req->in_words[i];
+        const InSlot &sh = shapes[i];
+        const u64 *src = static_cast<const u64 *>(ins[i]->data);
+        for (size_t r = 0; r < sh.rows; r++)
+            std::memcpy(req->pinned_in + off + r * sh.row_words, src + r * sh.src_pitch, sh.row_words * 8);
+        off += sh.words();
     }
     req->t_submit = Clock::now();
     {
@@ -346,14 +396,36 @@ int serve_poll(Ctx &C, uint64_t ticket, tetris_ct_out *out, uint32_t timeout_ms)
     auto req = it->second;
     if (!S->cv_done.wait_for(lk, std::chrono::milliseconds(timeout_ms), [&] { return req->done; }))
         return TETRIS_ETIMEOUT;
-    S->tickets.erase(it);
-    if (req->status != TETRIS_OK) throw Error(req->status, req->error);
+    if (req->status != TETRIS_OK) {
+        S->tickets.erase(it);
+        throw Error(req->status, req->error);
+    }
+    // a buffer too small keeps the ticket: the caller may poll again with a larger one
     TREQUIRE(out && out->data && out->cap_words >= req->out.size(), TETRIS_EINVAL, "output buffer too small");
+    S->tickets.erase(it);
     std::memcpy(out->data, req->out.data(), req->out.size() * 8);
     out->level = req->level;
     out->ncomp = req->ncomp;
     out->scale = req->scale;
     return TETRIS_OK;
+}
+
+void serve_cancel(Ctx &C, uint64_t ticket) {
+    Server *S = server_of(C);
+    TREQUIRE(S, TETRIS_EINVAL, "serving not started");
+    std::lock_guard<std::mutex> lk(S->mu);
+    auto it = S->tickets.find(ticket);
+    TREQUIRE(it != S->tickets.end(), TETRIS_ENOTFOUND, "unknown ticket");
+    auto req = it->second;
+    if (!req->done) {
+        auto q = std::find(S->queue.begin(), S->queue.end(), req);
+        TREQUIRE(q != S->queue.end(), TETRIS_EBUSY, "the query is running on the device; poll it");
+        S->queue.erase(q);
+        if (req->pinned_in) S->pinned_free.insert({req->total_in, req->pinned_in});
+        req->pinned_in = nullptr;
+        S->cancelled++;
+    }
+    S->tickets.erase(it);
 }
 
 void serve_stats(Ctx &C, tetris_serve_stats *st, bool reset) {
@@ -366,14 +438,28 @@ void serve_stats(Ctx &C, tetris_serve_stats *st, bool reset) {
     st->submitted = S->submitted;
     st->completed = S->completed;
     st->rejected = S->rejected;
+    st->cancelled = S->cancelled;
     st->p50_ms = pct(0.50);
     st->p99_ms = pct(0.99);
     st->device_bytes = S->used;
     st->peak_device_bytes = S->peak;
+    st->max_admitted = S->max_admitted;
+    // the most completed requests whose device intervals share one instant
+    std::vector<std::pair<double, int>> ev;
+    for (auto &iv : S->intervals) {
+        ev.push_back({iv.first, 1});
+        ev.push_back({iv.second, -1});
+    }
+    std::sort(ev.begin(), ev.end(), [](auto &a, auto &b) { return a.first < b.first || (a.first == b.first && a.second < b.second); });
+    int cur = 0, best = 0;
+    for (auto &e : ev) best = std::max(best, cur += e.second);
+    st->max_overlap = (uint32_t)best;
     if (reset) {
         S->latencies_ms.clear();
-        S->submitted = S->completed = S->rejected = 0;
+        S->intervals.clear();
+        S->submitted = S->completed = S->rejected = S->cancelled = 0;
         S->peak = S->used;
+        S->max_admitted = 0;
     }
 }
 
@@ -388,6 +474,7 @@ void serve_stop(Ctx &C) {
     S->th.join();
     S->instances.clear();
     S->graveyard.clear();
+    if (S->ref) cudaEventDestroy(S->ref);
     for (auto &kv : S->pinned_free) cudaFreeHost(kv.second);
     for (auto &kv : S->tickets)
         if (kv.second->pinned_in) cudaFreeHost(kv.second->pinned_in);

@@ -304,3 +304,67 @@ def test_degree15_minimax_stages_bit_exact(chain15):
     z = ckks.decrypt_slots(par, ckks.Ct(got.copy(), lev, sc), chain15.s).real
     assert int(np.rint(z[0] * R)) == int((vals[:, 0] > 128).sum())
     ctx.free_database(dbh)
+
+
+STAGES = [(1, "x"), (2, "y"), (3, "d"), (4, "u")]   # TETRIS_STAGE_X .. TETRIS_STAGE_U
+
+
+def check_stages(par, ctx, s, keys, vals, qv, stages, seed, bpls=(0,)):
+    """Every stage of every block (TETRIS_OPT_QUERY_STAGE): residues equal the
+    oracle's stage ciphertexts, and each slot decrypts to the FP64 pipeline's
+    value within 2^-12 (x, y = f(x), y - t, and the step values u, which
+    leave the block divided by the record count)."""
+    records, attrs = vals.shape
+    degree = len(qv.c) - 1
+    shape = query.QueryShape(records, attrs, degree, stages)
+    plan = query.make_plan(par, shape)
+    db = query.encode_database(par, plan, vals)
+    eq = query.encrypt_query(par, s, qv, seed)
+    ev = query.Evaluator(par, keys, plan)
+    ck, tadj = ev.per_query(eq, degree)
+    recs = []
+    for b in range(len(db.pts)):
+        rec = {}
+        ev.block(db.pts[b], eq, ck, tadj, degree, record=rec)
+        recs.append(rec)
+    ref = query.fp64_pipeline(vals, qv, stages)
+    want_vals = {"x": ref.x, "y": ref.y, "d": ref.y - qv.t, "u": ref.u}
+    dbh = upload_encoded(ctx, par, plan, db, records, attrs)
+    args = ([c.data for c in eq.w], [(c.level, c.scale) for c in eq.w], [c.data for c in eq.c],
+            [(c.level, c.scale) for c in eq.c], eq.t.data, (eq.t.level, eq.t.scale), np.array(stages))
+    n, B = par.n_slots, len(db.pts)
+    worst = {}
+    for bpl in bpls:
+        ctx.set_option(T.OPT_BLOCKS_PER_LAUNCH, bpl)
+        for stage, name in STAGES:
+            got, lev, sc = ctx.query_stage(stage, B, dbh, *args)
+            for b in range(B):
+                want = recs[b][name]
+                assert lev == want.level and sc == want.scale, (name, b)
+                assert np.array_equal(got[b], want.data), (bpl, name, b)
+                lo, hi = b * n, min(records, (b + 1) * n)
+                dec = ckks.decrypt_slots(par, ckks.Ct(got[b].copy(), lev, sc), s).real[: hi - lo]
+                if name == "u":
+                    dec = dec * plan.records_norm
+                err = float(np.max(np.abs(dec - want_vals[name][lo:hi])))
+                worst[name] = max(worst.get(name, 0.0), err)
+                assert err <= 2.0 ** -12, (name, b, err)
+    ctx.set_option(T.OPT_BLOCKS_PER_LAUNCH, 0)
+    ctx.free_database(dbh)
+    return worst
+
+
+@pytest.mark.parametrize("records,attrs,degree,nst", [(2048, 8, 7, 1), (3000, 3, 2, 1)])
+def test_stage_outputs_bit_exact_per_slot(chain, records, attrs, degree, nst):
+    vals = synth.database(synth.stream(50 + degree, "db"), records, attrs)
+    qv = synth.query_values(synth.stream(50 + degree, "qv"), attrs, degree)
+    check_stages(chain.par, chain.ctx, chain.s, chain.keys, vals, qv, [query.F3] * nst, 50 + degree, bpls=(0, 1))
+
+
+def test_full_size_stage_outputs_bit_exact_per_slot(full):
+    """One 32768-record block of the benchmark workload (degree 15, three f3
+    stages, alpha 4): every stage bit-exact and within 2^-12 per slot."""
+    par, ctx, s, keys = full
+    vals = synth.database(synth.stream(52, "db"), 32768, 16, "mixed")
+    qv = synth.query_values(synth.stream(52, "qv"), 16, 15)
+    check_stages(par, ctx, s, keys, vals, qv, [query.F3] * 3, 52)
