@@ -49,9 +49,11 @@ def dist_env():
     return int(os.environ.get("RANK", 0)), int(os.environ.get("WORLD_SIZE", 1)), int(os.environ.get("LOCAL_RANK", 0))
 
 
-def traffic_of(kind: str):
-    """DRAM bytes per launch of a kernel kind from the committed ncu summary,
-    if that capture was taken on the kernel source as it is now; else None."""
+def traffic_of(kind: str, jobs_per_launch: float):
+    """DRAM bytes per launch of a kernel kind: the committed one-kernel ncu
+    capture's DRAM bytes per limb job (profiles/traffic.json) times the limb
+    jobs of an average launch of this run, if that capture was taken on the
+    kernel source as it is now; else None."""
     import hashlib
     try:
         with open(os.path.join(ROOT, "profiles", "traffic.json")) as f:
@@ -59,7 +61,8 @@ def traffic_of(kind: str):
         src = open(os.path.join(ROOT, "paper_2412_13269_gb300", "csrc", "ntt.cu"), "rb").read()
         if t.get("ntt_source_sha256") != hashlib.sha256(src).hexdigest():
             return None
-        return t.get("dram_bytes_per_launch", {}).get(kind)
+        per_job = t.get("dram_bytes_per_job", {}).get(kind)
+        return None if per_job is None else per_job * jobs_per_launch
     except Exception:
         return None
 
@@ -284,6 +287,8 @@ def run_c3(args):
     t = enc(qv.t, "t")
     qargs = (w, [(L, Delta)] * len(w), c, [(L, Delta)] * len(c), t, (L, Delta), np.array([F3] * WL["stages"]))
     per_alpha = []
+    clocks = Clocks(local_rank)
+    clocks.start()
     for alpha in (4, 3, 2, 1):
         dnum = -(-WL["n_q"] // alpha)
         d = synth.switch_key_draws(seed, f"relin.a{alpha}", dnum, q + p, N)
@@ -298,6 +303,7 @@ def run_c3(args):
                           "table": [{"blocks_per_launch": b, "ntt_group_log2": g, "ms": round(m, 3)} for b, g, m in table]})
         if alpha == 3:
             fixed = next(m for b, g, m in table if b == 1 and g == 3)
+    clk = clocks.stop()  # sampled across key generation and every autotuner timing
     top = min(per_alpha, key=lambda r: r["best"]["ms"])
     ms = top["best"]["ms"]
     line = {"metric": METRIC, "workload": "c3", "value": ms * 1e3 / records, "unit": "us/record/query",
@@ -306,7 +312,7 @@ def run_c3(args):
                                    "f deg 15; 3 sign stages; autotuned", "tuned": top["best"], "alpha": top["alpha"]},
             "fixed_schedule": {"value": fixed * 1e3 / records, "ms_per_step": fixed,
                                "schedule": "one block per launch, radix-8 NTT groups, alpha 3"},
-            "per_alpha": per_alpha}
+            "per_alpha": per_alpha, "clocks": clk}
     print(json.dumps(line), flush=True)
     ctx.close()
 
@@ -350,15 +356,23 @@ def run_c4(args):
         pt = np.stack([g.integers(0, m, N, dtype=np.uint64) for m in q[: level + 1]])
         items.append((ctxs[log_n], level, ct, pt, rot))
     res = {}
-    for name, sched in (("per_item", T.SCHED_PER_ITEM), ("merged", T.SCHED_MERGED)):
+    clocks = Clocks(local_rank)
+    clocks.start()
+    for name, sched in (("per_item", T.SCHED_PER_ITEM), ("merged", T.SCHED_MERGED), ("fused", T.SCHED_FUSED)):
         T.batch_run(items, sched)  # warm-up (module loading, first allocations)
         times = [T.batch_run(items, sched)[2] for _ in range(max(3, args.steps // 4))]
         res[name] = statistics.median(times)
     outs, used, ms_auto = T.batch_run(items, T.SCHED_AUTO)
+    clk = clocks.stop()
+    names = {T.SCHED_PER_ITEM: "per_item", T.SCHED_MERGED: "merged", T.SCHED_FUSED: "fused"}
     line = {"metric": "uneven batch: device ms per batch of 64 ciphertexts", "workload": "c4", "unit": "ms",
             "higher_is_better": False, "value": min(res.values()), "fixed_schedule_ms": res["per_item"],
-            "merged_ms": res["merged"], "auto_choice": "merged" if used == T.SCHED_MERGED else "per_item",
-            "auto_ms": ms_auto, "dtype": "u64", "data": "synthetic (seeded uniform residues)",
+            "merged_ms": res["merged"], "fused_ms": res["fused"], "auto_choice": names[used],
+            "auto_ms": ms_auto, "clocks": clk, "dtype": "u64", "data": "synthetic (seeded uniform residues)",
+            "schedules": {"per_item": "each item's operations as their own launches",
+                          "merged": "k-th launches of the items of one ring degree merged; degrees on concurrent streams",
+                          "fused": "k-th launches of all items merged across ring degrees: one launch per stage, "
+                                   "persistent NTT and ModUp/key-inner-product kernels over the jobs' tiles"},
             "config": {"workload": "64 ciphertexts, N in {2^14, 2^15, 2^16}, levels 4..19, 1..16 rotations each, "
                                    "rescale(ct*pt) -> rotations -> relinearise(y*y); 20x50b + 3x60b primes, alpha 3",
                        "degrees": {str(k): sum(1 for it in items if it[0] is v) for k, v in ctxs.items()},
@@ -369,7 +383,7 @@ def run_c4(args):
 
 
 def run_pfe(args):
-    """PFE scoring step (Section 4.1.1) at the paper's Set I shape: N = 2^12,
+    """PFE scoring step (Section 5.4.1) at the paper's Set I shape: N = 2^12,
     one 55-bit modulus, m = 16 encrypted scoring functions, 131072 records
     whose attribute values (the paper's feature distribution for half the
     columns, uniform u8 for the rest) are placed in the exponent as
@@ -491,7 +505,7 @@ def run_repack(args):
     kern = {k: v for k, v in ctx.kernel_stats().items() if k != "keyswitch(total)"}
     tot = sum(v[1] for v in kern.values())
     dom = max(kern, key=lambda k: kern[k][1])
-    nl, dms, db, dmm = kern[dom]
+    nl, dms, db, dmm, _ = kern[dom]
     mm_peak = T.modmul_peak(local_rank)
     achieved = dmm / (dms * 1e-3) / 1e9
     # CPU oracle: a bounded sample of the rotations (each costs the same), scaled to all n - 1
@@ -566,6 +580,11 @@ def run_serve(args):
     ctx.serve_start(budget, 8)
     for key in shapes:  # size and capture every shape once before timing
         ctx.poll(ctx.submit(*shapes[key]), 600000)
+    alone = {}
+    for key in shapes:  # each shape alone on an idle server: its submit-to-completion latency
+        ctx.serve_stats(reset=True)
+        ctx.poll(ctx.submit(*shapes[key]), 600000)
+        alone[f"{SERVE_DBS[key[0]][0]}x{SERVE_DBS[key[0]][1]}/{SERVE_TYPES[key[1]][0]}"] = round(ctx.serve_stats().p50_ms, 2)
     ctx.serve_stats(reset=True)
     rnd = np.random.default_rng(seed)
     keys = list(shapes)
@@ -573,6 +592,8 @@ def run_serve(args):
         gaps = rnd.exponential(1.0 / rate, size=args.serve_queries)
         picks = [keys[i] for i in rnd.integers(0, len(keys), size=args.serve_queries)]
         tickets = []
+        clocks = Clocks(local_rank)
+        clocks.start()
         t0 = time.perf_counter()
         t_next = t0
         for gap, key in zip(gaps, picks):
@@ -584,13 +605,15 @@ def run_serve(args):
         for tk in tickets:
             ctx.poll(tk, 600000)
         elapsed = time.perf_counter() - t0
+        clk = clocks.stop()
         st = ctx.serve_stats(reset=True)
         rec = sum(SERVE_DBS[k[0]][0] for k in picks)
         print(json.dumps({"metric": "serving: queries/s and p50/p99 latency", "impl": "ours", "rate_qps": rate,
                           "queries": len(tickets), "qps": len(tickets) / elapsed, "records_per_s": rec / elapsed,
                           "p50_ms": st.p50_ms, "p99_ms": st.p99_ms, "completed": st.completed,
                           "rejected": st.rejected, "peak_device_gb": st.peak_device_bytes / 1e9,
-                          "budget_gb": budget / 1e9, "max_inflight": 8,
+                          "budget_gb": budget / 1e9, "max_inflight": 8, "max_admitted": st.max_admitted,
+                          "max_overlap_on_device": st.max_overlap, "alone_ms_by_shape": alone, "clocks": clk,
                           "config": {"workload": "N=2^16 L=20x50b K=3x60b; databases " + ", ".join(f"{r}x{a}" for r, a in SERVE_DBS)
                                      + "; types " + ", ".join(t for t, _ in SERVE_TYPES)}}), flush=True)
     ctx.serve_stop()
@@ -749,18 +772,18 @@ def main():
     kern = {k: v for k, v in stats.items() if k != "keyswitch(total)"}
     tot_ms = sum(v[1] for v in kern.values())
     dom = max(kern, key=lambda k: kern[k][1])
-    n_l, dom_ms, dom_b, dom_mm = kern[dom]
+    n_l, dom_ms, dom_b, dom_mm, dom_units = kern[dom]
     sec = dom_ms / n_l * 1e-3
     gbs = (dom_b / n_l) / sec / 1e9
     if "ntt_" in dom:  # transforms: 64-bit integer multiply chains bound them (ncu: DRAM mostly idle)
         achieved = (dom_mm / n_l) / sec / 1e9
         roofline = {"kernel": dom, "bound": "alu", "achieved": achieved, "peak": mm_peak, "unit": "Gmodmul/s",
-                    "frac": achieved / mm_peak, "traffic": traffic_of(dom), "share": dom_ms / tot_ms,
+                    "frac": achieved / mm_peak, "traffic": traffic_of(dom, dom_units / n_l), "share": dom_ms / tot_ms,
                     "launches_per_query": n_l, "avg_launch_us": sec * 1e6, "alg_gbs": gbs,
                     "peak_source": "measured: lazy Shoup modular products in registers (tetris_modmul_peak)"}
     else:
         roofline = {"kernel": dom, "bound": "hbm", "achieved": gbs, "peak": hbm, "unit": "GB/s", "frac": gbs / hbm,
-                    "traffic": traffic_of(dom), "share": dom_ms / tot_ms, "launches_per_query": n_l,
+                    "traffic": traffic_of(dom, dom_units / n_l), "share": dom_ms / tot_ms, "launches_per_query": n_l,
                     "avg_launch_us": sec * 1e6, "peak_source": f"{peak_kind} hbm_gbs"}
     ks = stats.get("keyswitch(total)")
     keyswitch = None
@@ -780,7 +803,8 @@ def main():
         cpu = {"value": v, "unit": "us/record/query", "cores": threads, "kind": "oracle", "sample": desc}
 
     line = {
-        "metric": METRIC, "value": value, "unit": "us/record/query", "n_gpus": world, "steps": args.steps,
+        "metric": METRIC, "value": value, "unit": "us/record/query", "roofline": roofline, "keyswitch": keyswitch,
+        "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": False, "scaling": "weak",
         "vs_baseline": None, "dtype": "u64",
         "data": "synthetic, seeded: u8 attributes, half uniform and half the paper's clipped-normal features",
@@ -794,11 +818,11 @@ def main():
                 "steps": k3, "ms_median": statistics.median(each), "ms_min": min(each), "ms_max": max(each),
                 "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
                 "api": "tetris_evaluate_query, pinned host buffers, copies and sync inside"},
-        "roofline": roofline, "keyswitch": keyswitch, "kernels": kernels,
         "cpu_baseline": cpu, "clocks": clk,
         "gpu_launches": info.kernel_launches * args.steps,
         "plan": {"relins": info.relins, "rescales": info.rescales, "rotations": info.rotations,
                  "launches_per_query": info.kernel_launches, "l_out": info.l_out, "l_ret": info.l_ret},
+        "kernels": kernels[:10],
     }
     if rank == 0:
         print(json.dumps(line), flush=True)

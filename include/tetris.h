@@ -184,11 +184,11 @@ typedef struct {
     uint64_t total_records;   /* the count is normalised by this many records (0: the
                                  database's own); set it to the total over the partitions
                                  when a database is split across GPUs or owners (the
-                                 horizontally partitioned database of Section 4.4): the
+                                 horizontally partitioned database of Section 5.6): the
                                  partitions' results then add up residue-wise */
     /* Optional global threshold (Algorithm 2, last line), NULL for none: the
      * result becomes step((count - t1 + 1/2) / records) in every slot, i.e. 1 iff
-     * at least t1 records pass (the 1/2 is Section 4.3.2's epsilon/2 shift for
+     * at least t1 records pass (the 1/2 is Section 5.4.2's epsilon/2 shift for
      * integer counts).  global_threshold encrypts t1 as a count (not normalised),
      * at a level above the step values'; global_stages odd stages of degree
      * sign_degree, global_coeffs their coefficients (laid out as sign_coeffs).
@@ -255,6 +255,11 @@ enum {
                                           alpha 1; keys then carry (L+1) ceil(bits/w) digits,
                                           digit i B + b with P 2^(w b) on limb i.  Set before
                                           loading or generating keys: changing it drops them */
+    TETRIS_OPT_DEBUG_CHECKS = 8,       /* 1: before a program is recorded, every device range each of
+                                          its kernel jobs will read or write is checked on the host
+                                          to lie inside a live allocation of the context, the program
+                                          or the batch item (TETRIS_EINVAL naming the job otherwise,
+                                          nothing launched); see tetris_debug_check */
     TETRIS_OPT_QUERY_STAGE = 7         /* 0 (default): queries return the InnerSum result.
                                           1..4: queries stop after a stage of every block and
                                           return its ciphertexts, block after block
@@ -273,6 +278,15 @@ enum {
     TETRIS_STAGE_U = 4
 };
 int tetris_set_option(tetris_ctx *ctx, int option, int64_t value);
+/* Debug: with the environment variable TETRIS_GUARD_WORDS set when a context
+ * (and its programs) allocate, every device buffer is framed by 32 words of a
+ * fixed pattern on each side.  This reads all of them back (context and
+ * recorded programs) and returns TETRIS_EINVAL naming the buffers whose guard
+ * words changed (a write past a buffer's end or before its start), else
+ * TETRIS_OK.  plant != 0 first overwrites one guard word (a test of the check
+ * itself).  *checked_ranges (may be NULL) receives the device ranges the
+ * TETRIS_OPT_DEBUG_CHECKS bounds check has verified so far. */
+int tetris_debug_check(tetris_ctx *ctx, int plant, uint64_t *checked_ranges);
 int tetris_get_option(tetris_ctx *ctx, int option, int64_t *value);
 
 /* Per-kernel statistics gathered while TETRIS_OPT_PROFILE is on: for each
@@ -285,6 +299,7 @@ typedef struct {
     double total_ms;
     double alg_bytes;
     double alg_modmuls;   /* modular multiplications: butterflies, conversion and key products */
+    double units;         /* limb jobs (N-word limbs) processed, summed over the launches */
 } tetris_kernel_stat;
 
 /* Measured throughput of lazy Shoup modular multiplications (the operation
@@ -332,7 +347,13 @@ int tetris_op(tetris_ctx *ctx, int opcode, const tetris_ct_in *a, const tetris_c
  *   TETRIS_SCHED_MERGED    the k-th launch of all items of one ring degree that
  *                          share kernel and mode is one launch (mixing levels);
  *                          ring degrees run as concurrent programs;
- *   TETRIS_SCHED_AUTO      times both, keeps the faster (*schedule_used).
+ *   TETRIS_SCHED_FUSED     the k-th launch of all items that share kernel and mode is
+ *                          one launch whatever their ring degree (log N in [14, 16], at
+ *                          most 4 contexts): each job reads its own context's tables,
+ *                          NTT passes and the ModUp row pass + key inner product run as
+ *                          persistent kernels (resident CTAs walking the jobs' tiles);
+ *   TETRIS_SCHED_AUTO      times them (fused only when every degree allows it), keeps
+ *                          the fastest (*schedule_used).
  * *device_ms receives the device time of the run (CUDA events). */
 typedef struct {
     tetris_ctx *ctx;
@@ -342,7 +363,7 @@ typedef struct {
     uint32_t rotations;
     uint64_t *out;
 } tetris_batch_item;
-enum { TETRIS_SCHED_PER_ITEM = 0, TETRIS_SCHED_MERGED = 1, TETRIS_SCHED_AUTO = 2 };
+enum { TETRIS_SCHED_PER_ITEM = 0, TETRIS_SCHED_MERGED = 1, TETRIS_SCHED_AUTO = 2, TETRIS_SCHED_FUSED = 3 };
 int tetris_batch_run(const tetris_batch_item *items, uint32_t n_items, int schedule, int *schedule_used,
                      double *device_ms);
 
@@ -423,7 +444,7 @@ int tetris_rescale_ntt_noalloc(tetris_ctx *ctx, const uint64_t *in, uint64_t *ou
 size_t tetris_noalloc_scratch_bytes(void);
 
 /* ---------------------------------------------------------------------------
- * PFE scoring step (Section 4.1.1; Algorithm 2, the loop building ct_i): for
+ * PFE scoring step (Section 5.4.1; Algorithm 2, the loop building ct_i): for
  * every record i,
  *   out[i] = sum_{j<m} X^{exps[i*m + j]} u[j]   in (Z_{q_0}[X] / (X^N + 1))^2,
  * where u[j] encrypts the scientist's scoring polynomial u_{f_j} (its value

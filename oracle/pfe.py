@@ -1,4 +1,4 @@
-"""Oracle for the private-function-evaluation scoring step (Section 4.1.1;
+"""Oracle for the private-function-evaluation scoring step (Section 5.4.1;
 Algorithm 2, the loop building ct_i).
 
 TEST INFRASTRUCTURE (see oracle/__init__.py).
@@ -6,7 +6,7 @@ TEST INFRASTRUCTURE (see oracle/__init__.py).
 The scientist encrypts, per attribute j, the polynomial u_{f_j} of a scoring
 function f_j: the value table v_j[k] = f_j(g^-1(k/N)) placed so that
 X^k * u_{f_j} has v_j[k] as its constant coefficient (u[0] = v[0],
-u[i] = -v[N - i] for i >= 1; Section 4.1.1, with Section 4.1's large-domain
+u[i] = -v[N - i] for i >= 1; Section 5.4.1, with Section 4.3's large-domain
 function method).  For each record i the server multiplies each U_j by the
 monomial X^{e_ij}, e_ij the record's discretised attribute value, and sums:
     ct_i = sum_j U_j * X^{e_ij}    in (Z_q[X] / (X^N + 1))^2.

@@ -8,8 +8,8 @@ The circuit is the server side of the paper's exploration (Algorithm 2, the
 local threshold and InnerSum): a linear combination of attribute columns with
 encrypted coefficients (attribute selection, Section 3.3), a private
 polynomial with encrypted coefficients, subtraction of an encrypted threshold
-(Section 4.3.2), a composite odd sign polynomial mapped to step(x) =
-(sign(x)+1)/2 (Section 4.3.2), a sum over ciphertext blocks and InnerSum by
+(Section 5.4.2), a composite odd sign polynomial mapped to step(x) =
+(sign(x)+1)/2 (Section 5.4.2), a sum over ciphertext blocks and InnerSum by
 rotations (Appendix A.1.2 rotation semantics).
 
 Scale discipline (a reading; the paper only says scales multiply and rescale
@@ -33,7 +33,7 @@ from .ckks import Ct, Params, round_half_up
 
 
 # ---------------------------------------------------------------------------
-# Sign polynomials (Section 4.3.2; the paper composes low-degree polynomials
+# Sign polynomials (Section 5.4.2; the paper composes low-degree polynomials
 # after Lee et al. but prints no coefficients).  Default stage: the odd
 # degree-7 polynomial f3 with f3(1) = 1 and f3'(x) = 35/16 (1-x^2)^3.
 # ---------------------------------------------------------------------------
@@ -74,7 +74,7 @@ class QueryShape:
     degree: int
     sign_stages: list            # list of (a0, a1, a2, a3) for x, x^3, x^5, x^7
     norm_records: int = 0        # records the count is normalised by (0: this database's own);
-                                 # the total over partitions for a horizontally split database (Section 4.4)
+                                 # the total over partitions for a horizontally split database (Section 5.6)
     global_stages: list = field(default_factory=list)   # stages of the global threshold (empty: none)
 
     def blocks(self, n_slots: int) -> int:

@@ -1,4 +1,4 @@
-"""Composite minimax approximations of sign(x) (Section 4.3.2, Table 2: the
+"""Composite minimax approximations of sign(x) (Section 5.4.2, Table 2: the
 paper composes low-degree minimax polynomials after LLNK20 but prints no
 coefficients).
 

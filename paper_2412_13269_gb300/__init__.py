@@ -27,7 +27,7 @@ OP_ADD, OP_SUB, OP_TENSOR, OP_RELIN, OP_RESCALE, OP_MUL_INT, OP_ADD_INT = 1, 2, 
 OP_AUTOMORPHISM, OP_ROTATE, OP_KEYSWITCH, OP_MUL_PLAIN, OP_NTT, OP_INNERSUM, OP_DROP = 8, 9, 10, 11, 12, 13, 14
 OP_RELIN_RESCALE, OP_RESCALE_MUL_INT = 15, 16
 OPT_BLOCKS_PER_LAUNCH, OPT_USE_GRAPH, OPT_KS_ALPHA, OPT_PROFILE, OPT_NTT_GROUP, OPT_KS_BASE2 = 1, 2, 3, 4, 5, 6
-OPT_QUERY_STAGE = 7
+OPT_QUERY_STAGE, OPT_DEBUG_CHECKS = 7, 8
 STAGE_FULL, STAGE_X, STAGE_Y, STAGE_D, STAGE_U = 0, 1, 2, 3, 4
 
 
@@ -82,7 +82,7 @@ class BatchItem(C.Structure):
                 ("rotations", C.c_uint32), ("out", C.c_void_p)]
 
 
-SCHED_PER_ITEM, SCHED_MERGED, SCHED_AUTO = 0, 1, 2
+SCHED_PER_ITEM, SCHED_MERGED, SCHED_AUTO, SCHED_FUSED = 0, 1, 2, 3
 
 
 def batch_run(items, schedule: int = SCHED_AUTO):
@@ -110,7 +110,7 @@ class TuneEntry(C.Structure):
 
 class KernelStat(C.Structure):
     _fields_ = [("kind", C.c_char * 48), ("launches", C.c_uint32), ("total_ms", C.c_double), ("alg_bytes", C.c_double),
-                ("alg_modmuls", C.c_double)]
+                ("alg_modmuls", C.c_double), ("units", C.c_double)]
 
 
 _vp, _u32, _u64, _i64, _sz, _d = C.c_void_p, C.c_uint32, C.c_uint64, C.c_int64, C.c_size_t, C.c_double
@@ -149,6 +149,7 @@ SIGNATURES = {
     "tetris_poll": [_vp, _u64, C.POINTER(CtOut), _u32],
     "tetris_serve_stats_get": [_vp, C.POINTER(ServeStats), C.c_int],
     "tetris_cancel": [_vp, _u64],
+    "tetris_debug_check": [_vp, C.c_int, C.POINTER(_u64)],
     "tetris_serve_stop": [_vp],
     "tetris_noalloc_scratch_bytes": [],
     "tetris_repack": [_vp, _vp, _u32, _u32, _d, C.POINTER(CtOut)],
@@ -317,12 +318,13 @@ class Ctx:
         return v.value
 
     def kernel_stats(self) -> dict:
-        """{kind: (launches, total_ms, alg_bytes)} gathered while OPT_PROFILE is on (clears them)."""
+        """{kind: (launches, total_ms, alg_bytes, alg_modmuls, limb jobs)} gathered while OPT_PROFILE is on
+        (clears them)."""
         buf = (KernelStat * 256)()
         n = C.c_uint32()
         check(lib().tetris_get_kernel_stats(self.h, buf, 256, C.byref(n)))
-        return {buf[i].kind.decode(): (buf[i].launches, buf[i].total_ms, buf[i].alg_bytes, buf[i].alg_modmuls)
-                for i in range(n.value)}
+        return {buf[i].kind.decode(): (buf[i].launches, buf[i].total_ms, buf[i].alg_bytes, buf[i].alg_modmuls,
+                                       buf[i].units) for i in range(n.value)}
 
     def repack(self, cts: np.ndarray, level: int, scale: float):
         """Ring repacking (Algorithm 1), host arrays: cts uint64 [n][2][level+1][N] ->
@@ -455,6 +457,13 @@ class Ctx:
         check(rc)
         n = 2 * (o.level + 1) * self.N
         return out[:n].reshape(2, o.level + 1, self.N), o.level, o.scale
+
+    def debug_check(self, plant: bool = False) -> int:
+        """Checks the guard words of every device buffer (TETRIS_GUARD_WORDS);
+        returns the ranges the TETRIS_OPT_DEBUG_CHECKS bounds check has verified."""
+        n = C.c_uint64()
+        check(lib().tetris_debug_check(self.h, 1 if plant else 0, C.byref(n)))
+        return n.value
 
     def cancel(self, ticket: int):
         check(lib().tetris_cancel(self.h, ticket))

@@ -769,6 +769,9 @@ int tetris_set_option(tetris_ctx *ctx, int option, int64_t value) {
                 TREQUIRE(value >= TETRIS_STAGE_FULL && value <= TETRIS_STAGE_U, TETRIS_EINVAL, "query stage must be 0..4");
                 C.query_stage = (int)value;
                 break;
+            case TETRIS_OPT_DEBUG_CHECKS:
+                C.debug_checks = value ? 1 : 0;
+                break;
             default:
                 throw Error(TETRIS_EINVAL, "unknown or read-only option");
         }
@@ -787,6 +790,7 @@ int tetris_get_option(tetris_ctx *ctx, int option, int64_t *value) {
             case TETRIS_OPT_PROFILE: *value = C.profile; break;
             case TETRIS_OPT_NTT_GROUP: *value = C.nt.loge; break;
             case TETRIS_OPT_QUERY_STAGE: *value = C.query_stage; break;
+            case TETRIS_OPT_DEBUG_CHECKS: *value = C.debug_checks; break;
             default: throw Error(TETRIS_EINVAL, "unknown option");
         }
     });
@@ -794,7 +798,7 @@ int tetris_get_option(tetris_ctx *ctx, int option, int64_t *value) {
 
 int tetris_batch_run(const tetris_batch_item *items, uint32_t n, int schedule, int *used, double *device_ms) {
     return guarded([&] {
-        TREQUIRE(schedule >= TETRIS_SCHED_PER_ITEM && schedule <= TETRIS_SCHED_AUTO, TETRIS_EINVAL, "unknown schedule");
+        TREQUIRE(schedule >= TETRIS_SCHED_PER_ITEM && schedule <= TETRIS_SCHED_FUSED, TETRIS_EINVAL, "unknown schedule");
         batch_run(items, n, schedule, used, device_ms);
     });
 }
@@ -935,6 +939,25 @@ int tetris_modmul_peak(int device, double *rate) {
     });
 }
 
+int tetris_debug_check(tetris_ctx *ctx, int plant, uint64_t *checked_ranges) {
+    return guarded([&] {
+        TREQUIRE(ctx, TETRIS_EINVAL, "null context");
+        Ctx &C = ctx->c;
+        TCHECK_CUDA(cudaSetDevice(C.device));
+        TCHECK_CUDA(cudaDeviceSynchronize());
+        if (checked_ranges) *checked_ranges = C.checked_ranges;
+        if (plant) C.pool.plant_guard_fault();
+        std::vector<std::string> bad = C.pool.check_guards();
+        for (auto &kv : C.programs)
+            for (auto &b : kv.second->pool.check_guards()) bad.push_back(b);
+        if (!bad.empty()) {
+            std::string m = "guard words overwritten: ";
+            for (size_t i = 0; i < bad.size() && i < 8; i++) m += (i ? ", " : "") + bad[i];
+            throw Error(TETRIS_EINVAL, m);
+        }
+    });
+}
+
 int tetris_get_kernel_stats(tetris_ctx *ctx, tetris_kernel_stat *out, uint32_t cap, uint32_t *n_out) {
     return guarded([&] {
         TREQUIRE(ctx && n_out && (out || cap == 0), TETRIS_EINVAL, "null pointer");
@@ -948,6 +971,7 @@ int tetris_get_kernel_stats(tetris_ctx *ctx, tetris_kernel_stat *out, uint32_t c
                 o.total_ms = kv.second.ms;
                 o.alg_bytes = kv.second.bytes;
                 o.alg_modmuls = kv.second.modmuls;
+                o.units = kv.second.units;
             }
             n++;
         }

@@ -2,6 +2,7 @@
 // recorder.  Paper references: Section 2.2 (ring), 2.4.1 (SwitchKey), 2.5
 // (rescale), Appendix A.2 (relinearisation, automorphism + key switch).
 #include <algorithm>
+#include <cstdlib>
 #include <cstring>
 #include <type_traits>
 
@@ -12,9 +13,11 @@ namespace tetris {
 // ---------------------------------------------------------------------------
 // Pool
 // ---------------------------------------------------------------------------
+Pool::Pool() : guard_(std::getenv("TETRIS_GUARD_WORDS") != nullptr) {}
+
 Pool::~Pool() {
     *alive_ = 0;
-    for (auto &a : all_) cudaFree(a.first);
+    for (auto &a : all_) cudaFree(a.first - (guard_ ? kGuardWords : 0));
 }
 
 BufPtr Pool::alloc(size_t words) {
@@ -25,18 +28,24 @@ BufPtr Pool::alloc(size_t words) {
         ptr = it->second;
         free_.erase(it);
     } else {
-        cudaError_t e = cudaMalloc(&ptr, words * 8);
+        const size_t g = guard_ ? kGuardWords : 0, total = words + 2 * g;
+        cudaError_t e = cudaMalloc(&ptr, total * 8);
         if (e != cudaSuccess) {
             cudaGetLastError();
             trim();
-            e = cudaMalloc(&ptr, words * 8);
+            e = cudaMalloc(&ptr, total * 8);
             if (e != cudaSuccess) {
                 cudaGetLastError();
-                throw Error(TETRIS_ENOMEM, "device allocation of " + std::to_string(words * 8) + " bytes failed");
+                throw Error(TETRIS_ENOMEM, "device allocation of " + std::to_string(total * 8) + " bytes failed");
             }
         }
+        if (g) {
+            TCHECK_CUDA(cudaMemset(ptr, kGuardByte, g * 8));
+            TCHECK_CUDA(cudaMemset(ptr + g + words, kGuardByte, g * 8));
+            ptr += g;
+        }
         all_.push_back({ptr, words});
-        held_ += words * 8;
+        held_ += total * 8;
     }
     std::weak_ptr<int> alive = alive_;
     auto *fl = &free_;
@@ -48,15 +57,49 @@ BufPtr Pool::alloc(size_t words) {
 }
 
 void Pool::trim() {
+    const size_t g = guard_ ? kGuardWords : 0;
     for (auto &f : free_) {
-        cudaFree(f.second);
+        cudaFree(f.second - g);
         auto it = std::find_if(all_.begin(), all_.end(), [&](auto &a) { return a.first == f.second; });
         if (it != all_.end()) {
-            held_ -= it->second * 8;
+            held_ -= (it->second + 2 * g) * 8;
             all_.erase(it);
         }
     }
     free_.clear();
+}
+
+bool Pool::contains(const void *p, size_t words) const {
+    const u64 *q = static_cast<const u64 *>(p);
+    for (auto &a : all_)
+        if (q >= a.first && q + words <= a.first + a.second) return true;
+    return false;
+}
+
+std::vector<std::string> Pool::check_guards() const {
+    std::vector<std::string> bad;
+    if (!guard_) return bad;
+    std::vector<u64> h(kGuardWords);
+    u64 pat;
+    std::memset(&pat, kGuardByte, 8);
+    for (auto &a : all_)
+        for (int side = 0; side < 2; side++) {
+            const u64 *g = side == 0 ? a.first - kGuardWords : a.first + a.second;
+            TCHECK_CUDA(cudaMemcpy(h.data(), g, kGuardWords * 8, cudaMemcpyDeviceToHost));
+            for (u64 w : h)
+                if (w != pat) {
+                    std::ostringstream o;
+                    o << a.first << (side == 0 ? ":before" : ":after");
+                    bad.push_back(o.str());
+                    break;
+                }
+        }
+    return bad;
+}
+
+void Pool::plant_guard_fault() {
+    TREQUIRE(guard_ && !all_.empty(), TETRIS_EINVAL, "no guarded buffer to plant a fault in");
+    TCHECK_CUDA(cudaMemset(all_.front().first + all_.front().second, 0, 8));  // the first word after the buffer
 }
 
 size_t Ctx::bytes_held() const {
@@ -143,8 +186,8 @@ void Program::finalize() {
 }
 
 void Program::add_launch(std::function<void(cudaStream_t, const uint8_t *)> fn, const std::string &kind, double bytes,
-                         double modmuls) {
-    launches.push_back({std::move(fn), kind, bytes, modmuls});
+                         double modmuls, double units) {
+    launches.push_back({std::move(fn), kind, bytes, modmuls, true, units});
     kernel_launches += 1;
 }
 
@@ -176,6 +219,7 @@ void Program::run_profiled(cudaStream_t s, std::map<std::string, KernelStat> &st
         k.ms += ms;
         k.bytes += launches[i].bytes;
         k.modmuls += launches[i].modmuls;
+        k.units += launches[i].units;
         if (launches[i].kind.compare(0, 3, "ks.") == 0) ks_ms += ms;
     }
     if (ks_count) {
@@ -294,9 +338,106 @@ static Deferred make_deferred(int type, const std::vector<J> &jobs, const std::s
     return d;
 }
 
+// ---------------------------------------------------------------------------
+// Debug checks: the device ranges of every job, checked on the host before the
+// job is recorded (nothing is launched with a range outside the allocations)
+// ---------------------------------------------------------------------------
+void Rec::check_range(const void *p, size_t words, const std::string &what) {
+    if (!p) return;
+    C.checked_ranges++;
+    if (C.pool.contains(p, words) || P.pool.contains(p, words) || (pool_override && pool_override->contains(p, words)))
+        return;
+    std::ostringstream o;
+    o << "debug check: " << what << " [" << p << ", +" << words << " words) lies outside every live allocation";
+    throw Error(TETRIS_EINVAL, o.str());
+}
+
+void Rec::check_prime(uint32_t prime, const std::string &what) {
+    TREQUIRE(prime < (uint32_t)C.nqp(), TETRIS_EINVAL, "debug check: " + what + " names prime " + std::to_string(prime));
+}
+
+void Rec::check(const std::vector<NttJob> &jobs, int load_mode, int store_mode) {
+    const size_t N = C.N;
+    for (size_t i = 0; i < jobs.size(); i++) {
+        const NttJob &j = jobs[i];
+        const std::string w = "NTT job " + std::to_string(i);
+        check_prime(j.prime, w);
+        const size_t ns = load_mode == LOAD_CONV_PRE ? j.nsrc : 1;
+        TREQUIRE(ns >= 1 && ns <= (size_t)kMaxConvSrc, TETRIS_EINVAL, "debug check: " + w + " has a bad source count");
+        check_range(j.src, (ns - 1) * j.src_stride + N, w + " source");
+        check_range(j.dst, N, w + " destination");
+        const size_t nb = (store_mode == STORE_SCALED_CONV && j.nsrc) ? j.nsrc : 1;
+        check_range(j.base, (nb - 1) * j.src_stride + N, w + " base");
+        check_range(j.extra, N, w + " extra");
+    }
+}
+
+void Rec::check(const std::vector<EwJob> &jobs) {
+    const size_t N = C.N;
+    for (size_t i = 0; i < jobs.size(); i++) {
+        const EwJob &j = jobs[i];
+        const std::string w = "elementwise job " + std::to_string(i);
+        check_prime(j.prime, w);
+        if (j.op == EW_RESCALE_COEF) check_prime(j.prime2, w);
+        for (const void *p : {(const void *)j.a, (const void *)j.b, (const void *)j.c, (const void *)j.dst,
+                              (const void *)j.a1, (const void *)j.b1, (const void *)j.d1, (const void *)j.d2,
+                              (const void *)j.c1, (const void *)j.c2})
+            check_range(p, N, w);
+    }
+}
+
+void Rec::check(const std::vector<AutJob> &jobs) {
+    for (size_t i = 0; i < jobs.size(); i++) {
+        check_range(jobs[i].src, C.N, "automorphism job " + std::to_string(i) + " source");
+        check_range(jobs[i].dst, C.N, "automorphism job " + std::to_string(i) + " destination");
+    }
+}
+
+void Rec::check(const std::vector<KsJob> &jobs) {
+    const size_t N = C.N;
+    for (size_t i = 0; i < jobs.size(); i++) {
+        const KsJob &j = jobs[i];
+        const std::string w = "key-switch job " + std::to_string(i);
+        check_prime(j.prime, w);
+        TREQUIRE(j.ndig >= 1 && j.ndig <= (uint32_t)kMaxKeyDigits, TETRIS_EINVAL, "debug check: " + w + " digits");
+        for (uint32_t d = 0; d < j.ndig; d++) {
+            check_range(j.src[d], N, w + " digit source");
+            check_range(j.key0[d], N, w + " key");
+            check_range(j.key1[d], N, w + " key");
+        }
+        for (const void *p : {(const void *)j.acc0, (const void *)j.acc1, (const void *)j.ex0, (const void *)j.ex1})
+            check_range(p, N, w);
+    }
+}
+
+void Rec::check(const std::vector<LinJob> &jobs) {
+    const size_t N = C.N;
+    for (size_t i = 0; i < jobs.size(); i++) {
+        const LinJob &j = jobs[i];
+        const std::string w = "linear-combination job " + std::to_string(i);
+        check_prime(j.prime, w);
+        for (uint32_t a = 0; a < j.nattr; a++) {
+            check_range(j.pt + a * j.pt_stride, N, w + " plaintext");
+            check_range(j.w0 + a * j.w_stride, N, w + " coefficient");
+            check_range(j.w1 + a * j.w_stride, N, w + " coefficient");
+        }
+        check_range(j.d0, N, w);
+        check_range(j.d1, N, w);
+    }
+}
+
+void Rec::check(const std::vector<RedJob> &jobs) {
+    for (size_t i = 0; i < jobs.size(); i++) {
+        check_prime(jobs[i].prime, "reduction job " + std::to_string(i));
+        check_range(jobs[i].src, C.N, "reduction job " + std::to_string(i));
+        check_range(jobs[i].dst, C.N, "reduction job " + std::to_string(i));
+    }
+}
+
 void Rec::emit(const Deferred &d) {
     auto *saved = defer;
     defer = nullptr;
+    emitting_ = true;  // checked when deferred (the item pools are not reachable from here)
     const size_t n = d.jobs.size() / d.job_size;
     auto as = [&](auto *tag) {
         using J = std::remove_pointer_t<decltype(tag)>;
@@ -316,6 +457,7 @@ void Rec::emit(const Deferred &d) {
     }
     prefix = saved_prefix;
     defer = saved;
+    emitting_ = false;
 }
 
 static const char *store_name(int m) {
@@ -333,6 +475,7 @@ void Rec::ntt(bool inverse, const std::vector<NttJob> &jobs_in, int load_mode, i
     const std::vector<NttJob> &jobs = jobs_in;
     TREQUIRE(split < 0 || !defer, TETRIS_EINVAL, "split transforms are not deferred");
     TREQUIRE(passes >= 1 && passes <= 3, TETRIS_EINVAL, "no transform pass selected");
+    if (checking()) check(jobs_in, load_mode, split >= 0 ? std::max(store_mode, store_mode_b) : store_mode);
     if (defer) {
         Deferred d = make_deferred(0, jobs, prefix, 0);
         d.inverse = inverse;
@@ -365,7 +508,7 @@ void Rec::ntt(bool inverse, const std::vector<NttJob> &jobs_in, int load_mode, i
     if (passes & 1)
         P.add_launch([=](cudaStream_t s, const uint8_t *a) {
             launch_ntt(inverse, logn, t, reinterpret_cast<const NttJob *>(a + off), n, load_mode, store_mode, s, 0);
-        }, prefix + dir + "_p1_" + load_name(load_mode), distinct_bytes(srcs, N) + w, mm1);
+        }, prefix + dir + "_p1_" + load_name(load_mode), distinct_bytes(srcs, N) + w, mm1, n);
     if (!(passes & 2)) return;
     // second pass: one launch per store segment
     auto second = [&](int j0, int j1, int mode) {
@@ -387,7 +530,7 @@ void Rec::ntt(bool inverse, const std::vector<NttJob> &jobs_in, int load_mode, i
         const size_t o2 = off + (size_t)j0 * sizeof(NttJob);
         P.add_launch([=](cudaStream_t s, const uint8_t *a) {
             launch_ntt(inverse, logn, t, reinterpret_cast<const NttJob *>(a + o2), m, load_mode, mode, s, 1);
-        }, prefix + dir + "_p2_" + store_name(mode), b2, mm2);
+        }, prefix + dir + "_p2_" + store_name(mode), b2, mm2, m);
     };
     if (split < 0 || split >= n) {
         second(0, n, store_mode);
@@ -399,6 +542,7 @@ void Rec::ntt(bool inverse, const std::vector<NttJob> &jobs_in, int load_mode, i
 
 void Rec::ew(const std::vector<EwJob> &jobs) {
     if (jobs.empty()) return;
+    if (checking()) check(jobs);
     if (defer) {
         defer->push_back(make_deferred(1, jobs, prefix + std::to_string(jobs[0].op), 0));
         return;
@@ -428,6 +572,7 @@ void Rec::ew(const std::vector<EwJob> &jobs) {
 
 void Rec::aut(const std::vector<AutJob> &jobs, uint32_t g) {
     if (jobs.empty()) return;
+    if (checking()) check(jobs);
     if (defer) {
         Deferred d = make_deferred(2, jobs, prefix, 0);
         d.galois = g;
@@ -443,6 +588,7 @@ void Rec::aut(const std::vector<AutJob> &jobs, uint32_t g) {
 
 void Rec::ksup(const std::vector<KsJob> &jobs) {
     if (jobs.empty()) return;
+    if (checking()) check(jobs);
     if (defer) {
         defer->push_back(make_deferred(3, jobs, prefix, 0));
         return;
@@ -467,11 +613,12 @@ void Rec::ksup(const std::vector<KsJob> &jobs) {
     const double mm = (transforms * (logn / 2) / 2.0 + prods) * C.N;
     P.add_launch([=](cudaStream_t s, const uint8_t *a) {
         launch_keyswitch_up(logn, t, reinterpret_cast<const KsJob *>(a + off), n, s);
-    }, prefix + "modup_keyip", distinct_bytes(rd, C.N) + 2.0 * n * C.N * 8, mm);
+    }, prefix + "modup_keyip", distinct_bytes(rd, C.N) + 2.0 * n * C.N * 8, mm, n);
 }
 
 void Rec::lin(const std::vector<LinJob> &jobs) {
     if (jobs.empty()) return;
+    if (checking()) check(jobs);
     if (defer) {
         defer->push_back(make_deferred(4, jobs, prefix, 0));
         return;
@@ -493,6 +640,7 @@ void Rec::lin(const std::vector<LinJob> &jobs) {
 
 void Rec::red(const std::vector<RedJob> &jobs) {
     if (jobs.empty()) return;
+    if (checking()) check(jobs);
     if (defer) {
         defer->push_back(make_deferred(5, jobs, prefix, 0));
         return;

@@ -19,7 +19,8 @@ int grid_for(size_t work_items) {
 
 // One CTA per (job, chunk of 2 * kEwThreads positions): the descriptor is
 // staged in shared memory once and each thread handles one 16-byte pair.
-__global__ void __launch_bounds__(kEwThreads) ew_kernel(const EwJob *jobs, int log_n, const ModInfo *mods) {
+__global__ void __launch_bounds__(kEwThreads) ew_kernel(const EwJob *jobs, int log_n, const ModInfo *mods,
+                                                         const TabEntry *tabs) {
     __shared__ EwJob J;
     {
         const u64 *gj = reinterpret_cast<const u64 *>(jobs + blockIdx.y);
@@ -27,6 +28,10 @@ __global__ void __launch_bounds__(kEwThreads) ew_kernel(const EwJob *jobs, int l
         for (int i = threadIdx.x; i < (int)(sizeof(EwJob) / 8); i += blockDim.x) dj[i] = gj[i];
     }
     __syncthreads();
+    if (tabs) {  // a job of one of several ring degrees: its own N and primes
+        log_n = tabs[J.tab].log_n;
+        mods = tabs[J.tab].t.mods;
+    }
     const size_t p = ((size_t)blockIdx.x * kEwThreads + threadIdx.x) * 2;
     if (p >= ((size_t)1 << log_n)) return;
     {
@@ -154,8 +159,14 @@ __device__ __forceinline__ void mul128(u64 a, u64 b, u64 &hi, u64 &lo) {
     lo = a * b;
     hi = __umul64hi(a, b);
 }
-__global__ void __launch_bounds__(kEwThreads, 4) tensor_kernel(const EwJob *jobs, int log_n, const ModInfo *mods) {
+__global__ void __launch_bounds__(kEwThreads, 4) tensor_kernel(const EwJob *jobs, int log_n, const ModInfo *mods,
+                                                                const TabEntry *tabs) {
     const EwJob *jp = jobs + blockIdx.y;
+    if (tabs) {  // a job of one of several ring degrees: its own N and primes
+        const uint32_t tb = __ldg(&jp->tab);
+        log_n = tabs[tb].log_n;
+        mods = tabs[tb].t.mods;
+    }
     const u64 *A0 = (const u64 *)__ldg((const unsigned long long *)&jp->a);
     const u64 *A1 = (const u64 *)__ldg((const unsigned long long *)&jp->a1);
     const u64 *B0 = (const u64 *)__ldg((const unsigned long long *)&jp->b);
@@ -233,6 +244,19 @@ __global__ void __launch_bounds__(kEwThreads) aut_kernel(const AutJob *jobs, int
         const uint32_t src = __brev((ge - 1) >> 1) >> (32 - log_n);
         jobs[j].dst[k] = jobs[j].src[src];
     }
+}
+
+// The automorphism of jobs at several ring degrees: one CTA per (job, chunk of
+// kEwThreads positions), each job with its own N and Galois element.
+__global__ void __launch_bounds__(kEwThreads) aut_multi_kernel(const AutJob *jobs, const TabEntry *tabs) {
+    const AutJob J = jobs[blockIdx.y];
+    const int log_n = tabs[J.tab].log_n;
+    const uint32_t k = blockIdx.x * kEwThreads + threadIdx.x;
+    if (k >= (1u << log_n)) return;
+    const uint32_t mask2n = (2u << log_n) - 1;
+    const uint32_t e = 2 * (__brev(k) >> (32 - log_n)) + 1;
+    const uint32_t ge = (uint32_t)(((uint64_t)J.g * e) & mask2n);
+    J.dst[k] = J.src[__brev((ge - 1) >> 1) >> (32 - log_n)];
 }
 
 // One CTA per (job, chunk of 2 * kEwThreads positions): the descriptor staged
@@ -344,22 +368,30 @@ double modmul_peak_probe() {
     return (double)blocks * kEwThreads * iters * 8 / (ms * 1e-3) / 1e9;
 }
 
-void launch_ew(const EwJob *jobs, int njobs, int log_n, const ModInfo *mods, cudaStream_t s) {
+void launch_ew(const EwJob *jobs, int njobs, int log_n, const ModInfo *mods, cudaStream_t s, const TabEntry *tabs) {
     if (njobs <= 0) return;
     const size_t per_cta = 2 * (size_t)kEwThreads;
     const unsigned chunks = (unsigned)((((size_t)1 << log_n) + per_cta - 1) / per_cta);
     for (int j0 = 0; j0 < njobs; j0 += 65535) {
         dim3 grid(chunks, (unsigned)std::min(65535, njobs - j0));
-        ew_kernel<<<grid, kEwThreads, 0, s>>>(jobs + j0, log_n, mods);
+        ew_kernel<<<grid, kEwThreads, 0, s>>>(jobs + j0, log_n, mods, tabs);
     }
 }
-void launch_tensor(const EwJob *jobs, int njobs, int log_n, const ModInfo *mods, cudaStream_t s) {
+void launch_tensor(const EwJob *jobs, int njobs, int log_n, const ModInfo *mods, cudaStream_t s, const TabEntry *tabs) {
     if (njobs <= 0) return;
     const size_t per_cta = 4 * (size_t)kEwThreads;
     const unsigned chunks = (unsigned)((((size_t)1 << log_n) + per_cta - 1) / per_cta);
     for (int j0 = 0; j0 < njobs; j0 += 65535) {
         dim3 grid(chunks, (unsigned)std::min(65535, njobs - j0));
-        tensor_kernel<<<grid, kEwThreads, 0, s>>>(jobs + j0, log_n, mods);
+        tensor_kernel<<<grid, kEwThreads, 0, s>>>(jobs + j0, log_n, mods, tabs);
+    }
+}
+void launch_automorphism_multi(const AutJob *jobs, int njobs, const TabEntry *tabs, int max_log_n, cudaStream_t s) {
+    if (njobs <= 0) return;
+    const unsigned chunks = (unsigned)((((size_t)1 << max_log_n) + kEwThreads - 1) / kEwThreads);
+    for (int j0 = 0; j0 < njobs; j0 += 65535) {
+        dim3 grid(chunks, (unsigned)std::min(65535, njobs - j0));
+        aut_multi_kernel<<<grid, kEwThreads, 0, s>>>(jobs + j0, tabs);
     }
 }
 void launch_automorphism(const AutJob *jobs, int njobs, int log_n, uint32_t galois, cudaStream_t s) {

@@ -61,17 +61,32 @@ struct DevBuf {
 };
 using BufPtr = std::shared_ptr<DevBuf>;
 
+// With the environment variable TETRIS_GUARD_WORDS set when a pool is made,
+// every buffer it allocates is framed by kGuardWords words of a known pattern
+// on each side; check_guards() reads them back.
+constexpr size_t kGuardWords = 32;
+constexpr unsigned char kGuardByte = 0xA5;
+
 class Pool {
   public:
+    Pool();
     ~Pool();
     BufPtr alloc(size_t words);
     size_t bytes_held() const { return held_; }
     void trim();
+    // true iff [p, p + words) lies inside one buffer of this pool
+    bool contains(const void *p, size_t words) const;
+    // buffers whose guard words were overwritten (each as "ptr:side"); empty without guards
+    std::vector<std::string> check_guards() const;
+    // overwrite one guard word of the first buffer (a self-test of check_guards)
+    void plant_guard_fault();
+    bool guarded() const { return guard_; }
 
   private:
     std::multimap<size_t, u64 *> free_;
-    std::vector<std::pair<u64 *, size_t>> all_;
+    std::vector<std::pair<u64 *, size_t>> all_;  // user pointer and words
     size_t held_ = 0;
+    bool guard_ = false;
     std::shared_ptr<int> alive_ = std::make_shared<int>(1);
 };
 
@@ -107,7 +122,8 @@ struct NttJob {
     u64 c2[kMaxConvSrc], c2_sh[kMaxConvSrc];  // c2_sh: Shoup companions of c2 modulo q_dst
     u64 conv_sub, mul, mul_sh;
     u64 piece_mask;                           // LOAD_PIECE
-    uint32_t piece_shift, pad;
+    uint32_t piece_shift;
+    uint32_t tab;                             // launches over several ring degrees: the job's table set
 };
 
 struct NttTables {
@@ -117,6 +133,16 @@ struct NttTables {
     const u64 *itw_sh;
     const ModInfo *mods;
     int loge = 3;       // log2 of the elements a thread holds (3 or 4)
+};
+
+// Launches whose jobs come from contexts of different ring degrees (batches
+// of uneven jobs): each job names its context's table set, an entry of a
+// device array of these.
+constexpr int kMaxTabs = 4;
+struct TabEntry {
+    NttTables t;
+    int log_n = 0;
+    int pad = 0;
 };
 
 // launchers (ntt.cu)
@@ -157,18 +183,27 @@ struct EwJob {
     const u64 *c1, *c2;
     // coefficient-domain rescale: second prime and constants
     u64 k2, k2_sh, k3, k3_sh, k4, k5;
-    uint32_t prime2, pad2;
+    uint32_t prime2;
+    uint32_t tab;  // launches over several ring degrees: the job's table set
 };
-void launch_ew(const EwJob *jobs_dev, int njobs, int log_n, const ModInfo *mods, cudaStream_t s);
+// tabs (device, may be null): jobs of several ring degrees, each reading its own
+// log N and primes from tabs[job.tab]; log_n is then the largest of them
+void launch_ew(const EwJob *jobs_dev, int njobs, int log_n, const ModInfo *mods, cudaStream_t s,
+               const TabEntry *tabs = nullptr);
 // every job EW_TENSOR or EW_TENSOR_ACC
-void launch_tensor(const EwJob *jobs_dev, int njobs, int log_n, const ModInfo *mods, cudaStream_t s);
+void launch_tensor(const EwJob *jobs_dev, int njobs, int log_n, const ModInfo *mods, cudaStream_t s,
+                   const TabEntry *tabs = nullptr);
 
 // automorphism in the NTT domain: dst[k] = src[perm_g(k)]
 struct AutJob {
     const u64 *src;
     u64 *dst;
+    uint32_t g;    // Galois element (launches over several ring degrees; else the launch's)
+    uint32_t tab;  // launches over several ring degrees: the job's table set
 };
 void launch_automorphism(const AutJob *jobs_dev, int njobs, int log_n, uint32_t galois, cudaStream_t s);
+// per-job Galois element and ring degree (tabs[job.tab].log_n); max_log_n the largest
+void launch_automorphism_multi(const AutJob *jobs_dev, int njobs, const TabEntry *tabs, int max_log_n, cudaStream_t s);
 
 // ModUp second pass fused with the key inner product (ntt.cu), one job per
 // (target limb t, block): for every digit j, x_j is the row pass of src[j] (the
@@ -186,9 +221,21 @@ struct KsJob {
     u64 qinv;              // q_t^-1 mod 2^64
     uint32_t prime, ndig;
     int32_t own;           // digit whose source is the NTT-domain input, -1 if none
-    uint32_t pad;
+    uint32_t tab;          // launches over several ring degrees: the job's table set
 };
 void launch_keyswitch_up(int log_n, const NttTables &t, const KsJob *jobs_dev, int njobs, cudaStream_t s);
+
+// Persistent launches over jobs of several ring degrees (log N in [14, 16]):
+// job j takes tiles [tile_start[j], tile_start[j+1]) of the pass (device array
+// of njobs + 1 entries); a grid of resident CTAs walks the tiles and each tile
+// reads its job's table set tabs[job.tab] (device).  One launch per pass.
+int ntt_pass_tiles(int log_n, bool col);  // tiles of one limb in a column or row pass
+void launch_ntt_pass_multi(bool inverse, int pass, const TabEntry *tabs, const NttJob *jobs_dev,
+                           const uint32_t *tile_start, int njobs, int total_tiles, int load_mode, int store_mode,
+                           cudaStream_t s);
+int keyswitch_up_tiles(int log_n);
+void launch_keyswitch_up_multi(const TabEntry *tabs, const KsJob *jobs_dev, const uint32_t *tile_start, int njobs,
+                               int total_tiles, cudaStream_t s);
 
 // linear combination: dst_c[limb] = sum_j pt_j[limb] * w_j[c][limb], c = 0,1
 struct LinJob {

@@ -121,12 +121,14 @@ struct Geo {
 
     int N1, N2, sub_cta, sub0, s, t;
     u64 o;
-    __device__ Geo(const PassParams &P) {
-        N1 = 1 << P.log1;
-        N2 = 1 << P.log2;
+    // log1, log2: the N1 x N2 split of the transform; tile: which group of
+    // sub_cta sub-problems this CTA takes
+    __device__ Geo(int log1, int log2, int tile) {
+        N1 = 1 << log1;
+        N2 = 1 << log2;
         const int nsub = COL ? N2 : N1;
         sub_cta = min(kThreads / T, nsub);
-        sub0 = blockIdx.x * sub_cta;
+        sub0 = tile * sub_cta;
         // consecutive threads take consecutive columns in the column pass and
         // consecutive lanes of a row in the row pass
         s = COL ? (int)threadIdx.x % sub_cta : (int)threadIdx.x / T;
@@ -212,14 +214,15 @@ __device__ __forceinline__ void run_stages(const Geo<LOGM, INV, COL, LOGEV> &g, 
 }
 
 template <int LOGM, bool INV, bool COL, int MODE, int LOGEV, bool OPEN>
-__device__ __forceinline__ void pass_body(const PassParams &P, const NttJob &J, u64 *sm, const ModInfo &mi) {
+__device__ __forceinline__ void pass_body(NttTables tb, int log1, int log2, int tile, const NttJob &J, u64 *sm,
+                                          const ModInfo &mi) {
     using GG = Geo<LOGM, INV, COL, LOGEV>;
     constexpr int E = GG::E;
-    const GG g(P);
+    const GG g(log1, log2, tile);
     const u64 q = mi.q, q2 = 2 * q;
     const size_t N = (size_t)g.N1 * g.N2;
-    const u64 *tw = (INV ? P.t.itw : P.t.tw) + (size_t)J.prime * N;
-    const u64 *twsh = (INV ? P.t.itw_sh : P.t.tw_sh) + (size_t)J.prime * N;
+    const u64 *tw = (INV ? tb.itw : tb.tw) + (size_t)J.prime * N;
+    const u64 *twsh = (INV ? tb.itw_sh : tb.tw_sh) + (size_t)J.prime * N;
 
     u64 x[E];
     // 1. load straight into the first group's registers, through the producer's load mode
@@ -332,6 +335,18 @@ __device__ __forceinline__ void pass_body(const PassParams &P, const NttJob &J, 
     }
 }
 
+// open butterflies for forward transforms modulo primes below 2^58, Harvey's otherwise
+template <int LOGM, bool INV, bool COL, int MODE, int LOGEV>
+__device__ __forceinline__ void pass_dispatch(NttTables tb, int log1, int log2, int tile, const NttJob &J,
+                                              u64 *sm, const ModInfo &mi) {
+    if constexpr (!INV) {
+        if (mi.q < kOpenBound) pass_body<LOGM, INV, COL, MODE, LOGEV, true>(tb, log1, log2, tile, J, sm, mi);
+        else pass_body<LOGM, INV, COL, MODE, LOGEV, false>(tb, log1, log2, tile, J, sm, mi);
+    } else {
+        pass_body<LOGM, INV, COL, MODE, LOGEV, false>(tb, log1, log2, tile, J, sm, mi);
+    }
+}
+
 template <int LOGM, bool INV, bool COL, int MODE, int LOGEV>
 __global__ void __launch_bounds__(kThreads, LOGEV >= 4 ? 3 : 4) ntt_pass_kernel(PassParams P) {
     extern __shared__ u64 sm[];
@@ -343,12 +358,7 @@ __global__ void __launch_bounds__(kThreads, LOGEV >= 4 ? 3 : 4) ntt_pass_kernel(
     }
     __syncthreads();
     const ModInfo mi = P.t.mods[J.prime];
-    if constexpr (!INV) {
-        if (mi.q < kOpenBound) pass_body<LOGM, INV, COL, MODE, LOGEV, true>(P, J, sm, mi);
-        else pass_body<LOGM, INV, COL, MODE, LOGEV, false>(P, J, sm, mi);
-    } else {
-        pass_body<LOGM, INV, COL, MODE, LOGEV, false>(P, J, sm, mi);
-    }
+    pass_dispatch<LOGM, INV, COL, MODE, LOGEV>(P.t, P.log1, P.log2, blockIdx.x, J, sm, mi);
 }
 
 template <int LOGM, bool INV, bool COL, int MODE, int LOGEV>
@@ -445,14 +455,15 @@ __device__ __forceinline__ void prefetch_l2_bulk(const void *p, uint32_t bytes) 
 }
 
 template <int LOGM, int LOGEV, bool OPEN>
-__device__ __forceinline__ void keyswitch_up_body(const PassParams &P, const KsJob &J, u64 *sm, const ModInfo &mi) {
+__device__ __forceinline__ void keyswitch_up_body(NttTables tb, int log1, int log2, int tile, const KsJob &J,
+                                                  u64 *sm, const ModInfo &mi) {
     using GG = Geo<LOGM, false, false, LOGEV>;
     constexpr int E = GG::E;
-    const GG g(P);
+    const GG g(log1, log2, tile);
     const u64 q = mi.q, q2 = 2 * q;
     const size_t N = (size_t)g.N1 * g.N2;
-    const u64 *tw = P.t.tw + (size_t)J.prime * N;
-    const u64 *twsh = P.t.tw_sh + (size_t)J.prime * N;
+    const u64 *tw = tb.tw + (size_t)J.prime * N;
+    const u64 *twsh = tb.tw_sh + (size_t)J.prime * N;
     const int nthr = blockDim.x, tid = threadIdx.x;
     u64 *acc = sm + KsSmem<LOGM, LOGEV>::exch_words(g.sub_cta);
     auto slot = [&](int c, int k) -> u64 & { return acc[(c * E + k) * nthr + tid]; };
@@ -526,8 +537,8 @@ __global__ void __launch_bounds__(kThreads, LOGEV >= 4 ? 2 : 4) keyswitch_up_ker
     }
     __syncthreads();
     const ModInfo mi = P.t.mods[J.prime];
-    if (mi.q < kOpenBound) keyswitch_up_body<LOGM, LOGEV, true>(P, J, sm, mi);
-    else keyswitch_up_body<LOGM, LOGEV, false>(P, J, sm, mi);
+    if (mi.q < kOpenBound) keyswitch_up_body<LOGM, LOGEV, true>(P.t, P.log1, P.log2, blockIdx.x, J, sm, mi);
+    else keyswitch_up_body<LOGM, LOGEV, false>(P.t, P.log1, P.log2, blockIdx.x, J, sm, mi);
 }
 
 template <int LOGM, int LOGEV>
@@ -556,7 +567,185 @@ void keyswitch_up_by_size(int logm, const PassParams &P, const KsJob *jobs, int 
     }
 }
 
+// ---------------------------------------------------------------------------
+// Persistent launches over jobs of several ring degrees.  Every pass of a
+// transform of log N in [14, 16] has sub-problems of 128 or 256 points, a
+// full CTA of 256 threads holds 256 / T of them and a tile is one such CTA's
+// share of a limb.  The grid is a few resident CTAs per SM; each walks the
+// tiles blockIdx.x, blockIdx.x + gridDim.x, ..., finds a tile's job in the
+// tile_start prefix table, stages the job and its table set in shared memory
+// when the job changes, and runs the job's pass body at the job's own size.
+// (Contiguous runs of tiles per CTA, one search each, measured slower: 70.9
+// against 63.3 ms for the 64-item batch.)
+// ---------------------------------------------------------------------------
+// Resident CTAs per SM of the persistent launches: a tile's geometry and
+// table pointers live in registers (the single-degree kernels read them as
+// kernel parameters), so these take up to 80 registers a thread.
+#ifndef MULTI_CTAS
+#define MULTI_CTAS 3
+#endif
+constexpr int kMultiCtas = MULTI_CTAS;
+constexpr int kMultiKsCtas = 2;  // the fused ModUp row pass + key inner product: up to 128 registers
+
+struct MultiParams {
+    const TabEntry *tabs;
+    const void *jobs;
+    const uint32_t *tile_start;
+    int njobs, total;
+};
+
+// the job a tile belongs to: the last j with tile_start[j] <= u
+__device__ __forceinline__ int find_job(const uint32_t *ts, int njobs, uint32_t u) {
+    int lo = 0, hi = njobs - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (__ldg(ts + mid) <= u) lo = mid;
+        else hi = mid - 1;
+    }
+    return lo;
+}
+
+// stage job j of a job array into shared memory (8-byte words)
+template <class JOB>
+__device__ __forceinline__ void stage_job(JOB &dst, const JOB *jobs, int j) {
+    const u64 *gj = reinterpret_cast<const u64 *>(jobs + j);
+    u64 *dj = reinterpret_cast<u64 *>(&dst);
+    for (int i = threadIdx.x; i < (int)(sizeof(JOB) / 8); i += blockDim.x) dj[i] = gj[i];
+}
+
+template <bool INV, bool COL, int MODE>
+__global__ void __launch_bounds__(kThreads, kMultiCtas) ntt_pass_multi_kernel(MultiParams P) {
+    extern __shared__ u64 sm[];
+    __shared__ NttJob J;
+    __shared__ TabEntry TE;  // the job's table set, read from shared memory where used
+    __shared__ int sj;
+    const NttJob *jobs = static_cast<const NttJob *>(P.jobs);
+    int jcur = -1;  // the staged job
+    uint32_t jbeg = 0;
+    for (uint32_t u = blockIdx.x; u < (uint32_t)P.total; u += gridDim.x) {
+        __syncthreads();  // the previous tile is done with the exchange buffer (and J)
+        if (threadIdx.x == 0) sj = find_job(P.tile_start, P.njobs, u);
+        __syncthreads();
+        if (sj != jcur) {  // uniform: stage the job and its table set when the job changes
+            jcur = sj;
+            stage_job(J, jobs, jcur);
+            __syncthreads();
+            stage_job(TE, P.tabs, (int)J.tab);
+            jbeg = __ldg(P.tile_start + jcur);
+            __syncthreads();
+        }
+        const NttTables &tb = TE.t;
+        const int log1 = (TE.log_n + 1) / 2, log2 = TE.log_n / 2;
+        const int tile = (int)(u - jbeg);
+        const ModInfo mi = tb.mods[J.prime];
+        switch (COL ? log1 : log2) {
+            case 7: pass_dispatch<7, INV, COL, MODE, 3>(tb, log1, log2, tile, J, sm, mi); break;
+            case 8: pass_dispatch<8, INV, COL, MODE, 3>(tb, log1, log2, tile, J, sm, mi); break;
+            default: break;  // refused on the host
+        }
+    }
+}
+
+__global__ void __launch_bounds__(kThreads, kMultiKsCtas) keyswitch_up_multi_kernel(MultiParams P) {
+    extern __shared__ u64 sm[];
+    __shared__ KsJob J;
+    __shared__ TabEntry TE;  // the job's table set, read from shared memory where used
+    __shared__ int sj;
+    const KsJob *jobs = static_cast<const KsJob *>(P.jobs);
+    int jcur = -1;  // the staged job
+    uint32_t jbeg = 0;
+    for (uint32_t u = blockIdx.x; u < (uint32_t)P.total; u += gridDim.x) {
+        __syncthreads();  // the previous tile is done with the exchange buffer (and J)
+        if (threadIdx.x == 0) sj = find_job(P.tile_start, P.njobs, u);
+        __syncthreads();
+        if (sj != jcur) {  // uniform: stage the job and its table set when the job changes
+            jcur = sj;
+            stage_job(J, jobs, jcur);
+            __syncthreads();
+            stage_job(TE, P.tabs, (int)J.tab);
+            jbeg = __ldg(P.tile_start + jcur);
+            __syncthreads();
+        }
+        const NttTables &tb = TE.t;
+        const int log1 = (TE.log_n + 1) / 2, log2 = TE.log_n / 2;
+        const int tile = (int)(u - jbeg);
+        const ModInfo mi = tb.mods[J.prime];
+        const bool open = mi.q < kOpenBound;
+        switch (log2) {
+            case 7:
+                if (open) keyswitch_up_body<7, 3, true>(tb, log1, log2, tile, J, sm, mi);
+                else keyswitch_up_body<7, 3, false>(tb, log1, log2, tile, J, sm, mi);
+                break;
+            case 8:
+                if (open) keyswitch_up_body<8, 3, true>(tb, log1, log2, tile, J, sm, mi);
+                else keyswitch_up_body<8, 3, false>(tb, log1, log2, tile, J, sm, mi);
+                break;
+            default: break;  // refused on the host
+        }
+    }
+}
+
+int persistent_grid(int total, int per_sm) { return std::max(1, std::min(total, sm_count() * per_sm)); }
+
+template <bool INV, bool COL, int MODE>
+void run_multi(const MultiParams &P, cudaStream_t st) {
+    // the exchange buffer is the same for 128- and 256-point sub-problems
+    constexpr size_t smem = COL ? (size_t)256 * 8 * 8 : (size_t)8 * (256 + 16) * 8;
+    ntt_pass_multi_kernel<INV, COL, MODE><<<persistent_grid(P.total, kMultiCtas), kThreads, smem, st>>>(P);
+}
+
 }  // namespace
+
+int ntt_pass_tiles(int log_n, bool col) {
+    TREQUIRE(log_n >= 14 && log_n <= 16, -1, "launches over several ring degrees take log N in [14, 16]");
+    const int log1 = (log_n + 1) / 2, log2 = log_n / 2;
+    const int logm = col ? log1 : log2, loge = std::min(3, logm);
+    const int T = 1 << (logm - loge), nsub = col ? (1 << log2) : (1 << log1);
+    const int sub_cta = std::min(kThreads / T, nsub);
+    TREQUIRE(sub_cta * T == kThreads, -1, "launches over several ring degrees need full CTAs");
+    return nsub / sub_cta;
+}
+
+int keyswitch_up_tiles(int log_n) { return ntt_pass_tiles(log_n, false); }
+
+void launch_ntt_pass_multi(bool inverse, int pass, const TabEntry *tabs, const NttJob *jobs_dev,
+                           const uint32_t *tile_start, int njobs, int total_tiles, int load_mode, int store_mode,
+                           cudaStream_t s) {
+    if (njobs <= 0 || total_tiles <= 0) return;
+    const MultiParams P{tabs, jobs_dev, tile_start, njobs, total_tiles};
+    if (pass == 0) {  // forward: column pass with the load mode; inverse: row pass, plain loads
+        if (inverse) {
+            TREQUIRE(load_mode == LOAD_PLAIN, -1, "inverse transforms load plain limbs");
+            run_multi<true, false, M_PLAIN>(P, s);
+        } else if (load_mode == LOAD_CONV_PRE) run_multi<false, true, M_CONVPRE>(P, s);
+        else if (load_mode == LOAD_REDUCE) run_multi<false, true, M_REDUCE>(P, s);
+        else if (load_mode == LOAD_INT64) run_multi<false, true, M_INT64>(P, s);
+        else if (load_mode == LOAD_PIECE) run_multi<false, true, M_PIECE>(P, s);
+        else if (load_mode == LOAD_PLAIN) run_multi<false, true, M_PLAIN>(P, s);
+        else throw Error(-1, "unsupported load mode");
+    } else {  // forward: row pass with the store mode; inverse: column pass
+        if (inverse) {
+            if (store_mode == STORE_SCALED) run_multi<true, true, M_SCALED>(P, s);
+            else if (store_mode == STORE_SCALED_CONV) run_multi<true, true, M_SCALED_CONV>(P, s);
+            else if (store_mode == STORE_PLAIN) run_multi<true, true, M_STORE>(P, s);
+            else throw Error(-1, "unsupported inverse store mode");
+        } else {
+            if (store_mode == STORE_COMBINE) run_multi<false, false, M_COMBINE>(P, s);
+            else if (store_mode == STORE_PLAIN) run_multi<false, false, M_STORE>(P, s);
+            else throw Error(-1, "unsupported forward store mode");
+        }
+    }
+}
+
+void launch_keyswitch_up_multi(const TabEntry *tabs, const KsJob *jobs_dev, const uint32_t *tile_start, int njobs,
+                               int total_tiles, cudaStream_t s) {
+    if (njobs <= 0 || total_tiles <= 0) return;
+    const MultiParams P{tabs, jobs_dev, tile_start, njobs, total_tiles};
+    const size_t smem = KsSmem<8, 3>::bytes(kThreads / Geo<8, false, false, 3>::T);  // the same at 128 points
+    static std::atomic<uint64_t> opted{0};
+    opt_in_smem((const void *)keyswitch_up_multi_kernel, (int)smem, opted);
+    keyswitch_up_multi_kernel<<<persistent_grid(total_tiles, kMultiKsCtas), kThreads, smem, s>>>(P);
+}
 
 void launch_keyswitch_up(int log_n, const NttTables &t, const KsJob *jobs_dev, int njobs, cudaStream_t s) {
     if (njobs <= 0) return;

@@ -1,4 +1,4 @@
-// Private-function-evaluation scoring step (Section 4.1.1; Algorithm 2, the
+// Private-function-evaluation scoring step (Section 5.4.1; Algorithm 2, the
 // loop building ct_i): for every record i,
 //   out[i] = sum_j X^{e_ij} U_j   in (Z_q[X] / (X^N + 1))^2, one modulus q,
 // where U_j encrypts the scientist's scoring polynomial u_{f_j} and e_ij is the

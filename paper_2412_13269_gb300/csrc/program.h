@@ -37,7 +37,7 @@ struct Program;
 
 struct KernelStat {
     uint32_t launches = 0;
-    double ms = 0, bytes = 0, modmuls = 0;
+    double ms = 0, bytes = 0, modmuls = 0, units = 0;
 };
 
 struct Ctx {
@@ -64,6 +64,8 @@ struct Ctx {
     int use_graph = 1;
     int profile = 0;
     int query_stage = 0;    // TETRIS_OPT_QUERY_STAGE: 0 the whole query, else the stage whose values are returned
+    int debug_checks = 0;   // TETRIS_OPT_DEBUG_CHECKS: bounds-check every recorded job on the host
+    uint64_t checked_ranges = 0;  // device ranges checked so far (debug)
     std::map<std::string, KernelStat> stats;
     void *server = nullptr;  // serve.cu
     std::map<std::string, std::unique_ptr<Program>> programs;
@@ -96,6 +98,7 @@ struct Launch {
     double bytes = 0;
     double modmuls = 0;  // algorithmic modular multiplications (butterflies, conversion and key products)
     bool kernel = true;  // false: a stream wait, neither timed nor counted
+    double units = 0;    // limb jobs (N-word limbs) the launch processes
 };
 
 // A device staging slot for one input: rows (ciphertext components) of
@@ -148,7 +151,7 @@ struct Program {
     void run_graph(cudaStream_t s);
     void run_profiled(cudaStream_t s, std::map<std::string, KernelStat> &stats);
     void add_launch(std::function<void(cudaStream_t, const uint8_t *)> fn, const std::string &kind, double bytes,
-                    double modmuls = 0);
+                    double modmuls = 0, double units = 0);
     // from here on the program may use in_slots[late_slot..]
     void add_late_wait();
     // copies srcs[i] into in_slots[i] (kind H2D or D2D), the late ones on the side stream
@@ -231,6 +234,18 @@ class Rec {
 
   private:
     NttJob conv_job(uint32_t dst_prime, const u64 *src, uint32_t first_src_prime, int nsrc);
+    // debug checks (TETRIS_OPT_DEBUG_CHECKS): every range a job reads or writes
+    // lies inside a live allocation of the context, the program or the item
+    bool emitting_ = false;  // jobs already checked when they were deferred
+    bool checking() const { return C.debug_checks && !emitting_; }
+    void check_range(const void *p, size_t words, const std::string &what);
+    void check_prime(uint32_t prime, const std::string &what);
+    void check(const std::vector<NttJob> &jobs, int load_mode, int store_mode);
+    void check(const std::vector<EwJob> &jobs);
+    void check(const std::vector<AutJob> &jobs);
+    void check(const std::vector<KsJob> &jobs);
+    void check(const std::vector<LinJob> &jobs);
+    void check(const std::vector<RedJob> &jobs);
 };
 
 int64_t round_half_up(double x);

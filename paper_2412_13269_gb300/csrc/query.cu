@@ -1,7 +1,7 @@
 // Query planner and executor: the server side of the paper's Algorithm 2
 // for the local threshold and InnerSum, with the attribute-selection product
 // (Section 3.3), a private polynomial with encrypted coefficients, the
-// encrypted threshold (Section 4.3.2), a composite odd sign polynomial mapped
+// encrypted threshold (Section 5.4.2), a composite odd sign polynomial mapped
 // to step(x) = (sign(x) + 1)/2, the block sum and InnerSum (Appendix A.1.2
 // rotations).
 //

@@ -168,7 +168,8 @@ bool Server::admit_one(std::unique_lock<std::mutex> &lk) {
             return true;
         };
         auto reject = [&](int code, const std::string &msg) {
-            queue.pop_front();
+            // the request may have been withdrawn while the lock was released
+            if (!queue.empty() && queue.front() == req) queue.pop_front();
             req->status = code;
             req->error = msg;
             req->done = true;
@@ -232,6 +233,11 @@ bool Server::admit_one(std::unique_lock<std::mutex> &lk) {
         for (auto &i : instances) held += i->prog ? i->prog->pool.bytes_held() : 0;
         for (auto &i : graveyard) held += i->prog ? i->prog->pool.bytes_held() : 0;
         peak = std::max(peak, held);
+        // withdrawn (tetris_cancel) while it was recorded: keep the instance idle
+        if (queue.empty() || queue.front() != req) {
+            in->last_use = ++use_clock;
+            return true;
+        }
     }
     queue.pop_front();
     in->busy = true;

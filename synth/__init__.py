@@ -17,7 +17,7 @@ from the workload definitions):
   * a: uniform residues in [0, q) for each modulus q;
   * database: u8 attribute values, either uniform on [0, 255] or the paper's
     synthetic feature distribution (normal, mean 1, sd 1, bounded to [0, 2),
-    Section 4.1.1) quantised as floor(128 * x).
+    Section 5.4.1) quantised as floor(128 * x).
 """
 from __future__ import annotations
 

@@ -1,4 +1,4 @@
-"""GPU parity for the PFE scoring step (Section 4.1.1): tetris_pfe_scores
+"""GPU parity for the PFE scoring step (Section 5.4.1): tetris_pfe_scores
 equals the oracle's negacyclic rotate-and-sum residue for residue, through
 host and device buffers, with exponents covering 0, N - 1, N, 2N - 1 and
 values beyond 2N (taken mod 2N)."""

@@ -127,7 +127,7 @@ def test_autotune_keeps_results(chain):
 
 def test_partition_normalisation_bit_exact(chain):
     """A partition of a larger database normalised by the total record count
-    (the horizontally partitioned database of Section 4.4)."""
+    (the horizontally partitioned database of Section 5.6)."""
     par, ctx = chain.par, chain.ctx
     vals = synth.database(synth.stream(41, "db"), 2048, 4)
     qv = synth.query_values(synth.stream(41, "qv"), 4, 3)

@@ -3,7 +3,7 @@ partition with the oracle, normalised by the total record count, and the
 ranks' result ciphertexts are summed residue by residue (an integer
 all-reduce followed by a reduction mod q).  The sum decrypts to the count
 over the whole database (the horizontally partitioned database of
-Section 4.4, where the partial counts are added before the final step)."""
+Section 5.6, where the partial counts are added before the final step)."""
 import os
 import socket
 

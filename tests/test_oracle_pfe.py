@@ -1,4 +1,4 @@
-"""Pins for the PFE scoring oracle (Section 4.1.1): the monomial product
+"""Pins for the PFE scoring oracle (Section 5.4.1): the monomial product
 against the schoolbook negacyclic product and against the oracle's NTT-based
 ring product; the constant-coefficient property of the function encoding,
 exhaustively; and the decrypted score of an encrypted query against the sum

@@ -1,7 +1,7 @@
 """Pins for the oracle's query circuit: the decrypted count matches the FP64
 plaintext pipeline (same polynomials, computed in floating point without
 encryption); with every record outside the sign margin (the epsilon shift of
-Section 4.3.2 keeps records off the threshold) the rounded count is the exact
+Section 5.4.2 keeps records off the threshold) the rounded count is the exact
 integer count; InnerSum leaves the total in every slot."""
 import numpy as np
 import pytest

@@ -1,4 +1,4 @@
-"""Pins for the sign/step approximation (Section 4.3.2; Table 2 defines the
+"""Pins for the sign/step approximation (Section 5.4.2; Table 2 defines the
 margin 2^-alpha and precision beta vocabulary): the default stage polynomial
 is derived here from its closed form, and the composite margin found by the
 oracle's grid search is checked against bisection on the monotone map."""

@@ -3,9 +3,9 @@ pipeline (the same polynomials evaluated in floating point without
 encryption), at the tolerance the method is held to: |error| <= 2^-12 on the
 normalised values.  Each stage of a block is decrypted slot by slot -- the
 linear combination x (attribute selection, Section 3.3), the private
-polynomial y = f(x), y - t (the encrypted threshold, Section 4.3.2) and the
+polynomial y = f(x), y - t (the encrypted threshold, Section 5.4.2) and the
 step values u (the composite sign mapped to step(z) = (sign(z) + 1)/2,
-Section 4.3.2) -- rather than only through the InnerSum, where per-slot
+Section 5.4.2) -- rather than only through the InnerSum, where per-slot
 errors of opposite sign could cancel.  Cases: N = 2^12 test chains (full,
 ragged, degree 15 with three stages) and one block of the benchmark
 workload (N = 2^16, twenty 50-bit primes, alpha = 4)."""
