@@ -24,8 +24,9 @@
 // per-coefficient constant.  The combine store fuses the consumer:
 // (extra) + (base - x) * mul; the inverse stores can scale, add a constant and
 // subtract a base conversion.  Butterflies are lazy: forward transforms modulo
-// primes below 2^58 run with no correction at all (values grow by at most 2q
-// per stage and stay below 41q), the others as Harvey's, in [0, 4q) (forward)
+// primes below 2^57 run with no correction at all (their products use a
+// Shoup quotient estimated from three partial products, < 4q; values grow by
+// at most 4q per stage and stay below 81q), the others as Harvey's, in [0, 4q) (forward)
 // or [0, 2q) (inverse) between stages and passes; the second pass reduces.
 #include "internal.h"
 
@@ -54,10 +55,20 @@ __device__ __forceinline__ void ct_bfly(u64 &x, u64 &y, u64 w, u64 wsh, u64 q, u
     x = X + T;
     y = X - T + q2;
 }
-// Forward butterfly without correction: the Shoup product is < 2q for any
-// 64-bit y, so each stage adds at most 2q to the bound of its inputs.
+// a * w mod q in [0, 4q) for any 64-bit a and w < q: the Shoup quotient
+// floor(a w' / 2^64) estimated from three of its four 32 x 32 partial
+// products, a1 w'1 + hi(a1 w'0) + hi(a0 w'1), which is at most 2 below it
+// (the dropped a0 w'0 and the two truncated high halves add less than 3)
+__device__ __forceinline__ u64 shoup_lazy4(u64 a, u64 w, u64 wsh, u64 q) {
+    const uint32_t a0 = (uint32_t)a, a1 = (uint32_t)(a >> 32), s0 = (uint32_t)wsh, s1 = (uint32_t)(wsh >> 32);
+    const u64 qt = (u64)a1 * s1 + __umulhi(a1, s0) + __umulhi(a0, s1);
+    return a * w - qt * q;
+}
+// Forward butterfly without correction: the estimated-quotient product is
+// < 4q for any 64-bit y, so each stage adds at most 4q to the bound of its
+// inputs (q4 = 4q keeps X - T + q4 non-negative).
 __device__ __forceinline__ void ct_bfly_open(u64 &x, u64 &y, u64 w, u64 wsh, u64 q, u64 q2) {
-    u64 T = shoup_lazy(y, w, wsh, q);
+    u64 T = shoup_lazy4(y, w, wsh, q);
     u64 X = x;
     x = X + T;
     y = X - T + q2;
@@ -70,12 +81,13 @@ __device__ __forceinline__ void gs_bfly(u64 &x, u64 &y, u64 w, u64 wsh, u64 q, u
     y = shoup_lazy(D, w, wsh, q);
 }
 
-// Forward transforms modulo q < 2^58 run "open" (no correction inside the two
-// passes): loads give values below (2 nsrc + 1) q <= 9q, sixteen stages add at
-// most 32q, so every intermediate stays below 41q < 2^64; the second pass's
-// store reduces once.  Larger primes (the 60-bit special primes) take
-// Harvey's corrected butterflies.
-constexpr u64 kOpenBound = 1ull << 58;
+// Forward transforms modulo q < 2^57 run "open" (no correction inside the two
+// passes): loads give values below q + 4 * 4q = 17q (a conversion from four
+// sources), sixteen stages add at most 64q, so every intermediate stays below
+// 81q < 2^64; the second pass's store reduces once.  Larger primes (the
+// 60-bit special primes) take Harvey's corrected butterflies with exact Shoup
+// products.
+constexpr u64 kOpenBound = 1ull << 57;
 
 // Register window of butterfly group g: the thread holds the E elements whose
 // row index differs only in bits [lo, lo + LOGE); stages run on bits [blo, bhi].
@@ -159,6 +171,8 @@ __device__ __forceinline__ void run_stages(const Geo<LOGM, INV, COL, LOGEV> &g, 
     using G = typename GG::G;
     constexpr int M = GG::M, E = GG::E, LOGE = GG::LOGE, NG = GG::NG;
     const u64 q2 = 2 * q;
+    // the open butterfly adds 4q, the bound of its estimated-quotient product
+    const u64 qb = OPEN ? 4 * q : q2;
     if (GG::IN_STAGE) {
 #pragma unroll
         for (int k = 0; k < E; k++) sm[g.smidx(g.lrow(k))] = x[k];
@@ -196,7 +210,7 @@ __device__ __forceinline__ void run_stages(const Geo<LOGM, INV, COL, LOGEV> &g, 
                     for (int j = 0; j < E; j++) {
                         if (j >= (1 << bb)) continue;
                         if (INV) gs_bfly(x[k + j], x[k + j + (1 << bb)], w, wsh, q, q2);
-                        else if (OPEN) ct_bfly_open(x[k + j], x[k + j + (1 << bb)], w, wsh, q, q2);
+                        else if (OPEN) ct_bfly_open(x[k + j], x[k + j + (1 << bb)], w, wsh, q, qb);
                         else ct_bfly(x[k + j], x[k + j + (1 << bb)], w, wsh, q, q2);
                     }
                 }
@@ -244,7 +258,8 @@ __device__ __forceinline__ void pass_body(NttTables tb, int log1, int log2, int 
             }
         }
     } else if (MODE == M_CONVPRE) {
-        // sum_s y_s * c2_s with lazy Shoup products: each term < 2q, the sum < 8q
+        // sum_s y_s * c2_s with lazy Shoup products: each term < 4q (open: estimated
+        // quotient) or < 2q, the sum < 16q
         const u64 *src = J.src;
         const u64 stride = J.src_stride;
         const int ns = (int)J.nsrc;
@@ -257,7 +272,8 @@ __device__ __forceinline__ void pass_body(NttTables tb, int log1, int log2, int 
                 const u64 c2 = J.c2[sidx], c2sh = J.c2_sh[sidx];
                 const u64 *sp = src + sidx * stride;
 #pragma unroll
-                for (int k = 0; k < E; k++) x[k] += shoup_lazy(sp[g.gidx(g.lrow(k))], c2, c2sh, q);
+                for (int k = 0; k < E; k++)
+                    x[k] += OPEN ? shoup_lazy4(sp[g.gidx(g.lrow(k))], c2, c2sh, q) : shoup_lazy(sp[g.gidx(g.lrow(k))], c2, c2sh, q);
             }
         }
         if (!OPEN) {
@@ -335,7 +351,7 @@ __device__ __forceinline__ void pass_body(NttTables tb, int log1, int log2, int 
     }
 }
 
-// open butterflies for forward transforms modulo primes below 2^58, Harvey's otherwise
+// open butterflies for forward transforms modulo primes below 2^57, Harvey's otherwise
 template <int LOGM, bool INV, bool COL, int MODE, int LOGEV>
 __device__ __forceinline__ void pass_dispatch(NttTables tb, int log1, int log2, int tile, const NttJob &J,
                                               u64 *sm, const ModInfo &mi) {
@@ -581,10 +597,7 @@ void keyswitch_up_by_size(int logm, const PassParams &P, const KsJob *jobs, int 
 // Resident CTAs per SM of the persistent launches: a tile's geometry and
 // table pointers live in registers (the single-degree kernels read them as
 // kernel parameters), so these take up to 80 registers a thread.
-#ifndef MULTI_CTAS
-#define MULTI_CTAS 3
-#endif
-constexpr int kMultiCtas = MULTI_CTAS;
+constexpr int kMultiCtas = 3;  // 4 measured the same (62.96 vs 63.14 ms for the 64-item batch)
 constexpr int kMultiKsCtas = 2;  // the fused ModUp row pass + key inner product: up to 128 registers
 
 struct MultiParams {
