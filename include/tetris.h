@@ -228,15 +228,18 @@ int tetris_plan(tetris_ctx *ctx, uint32_t db, uint32_t f_degree, uint32_t sign_s
 
 /* Autotuner: times the query's recorded program (device time, CUDA events,
  * reps replays after one warm-up) under each candidate schedule -- blocks per
- * launch in {all, 8, 4, 2, 1} (those below the database's block count) and
- * NTT register groups of 8 or 16 elements per thread -- keeps the fastest as
- * the context's options (TETRIS_OPT_BLOCKS_PER_LAUNCH, TETRIS_OPT_NTT_GROUP)
+ * launch in {all, 8, 4, 2, 1} (those below the database's block count) times
+ * NTT register groups of 8 or 16 elements per thread or, for log N in
+ * [14, 16], persistent launches -- keeps the fastest as the context's options
+ * (TETRIS_OPT_BLOCKS_PER_LAUNCH, TETRIS_OPT_NTT_GROUP, TETRIS_OPT_PERSISTENT)
  * and writes up to cap timings.  The keyswitch digit size is fixed by the
  * loaded keys (chosen by the client at key generation). */
 typedef struct {
     int32_t blocks_per_launch;  /* 0 = all */
     int32_t ntt_group_log2;     /* 3 or 4 */
     double ms;                  /* device time per query */
+    int32_t persistent;         /* 1: persistent launches (TETRIS_OPT_PERSISTENT) */
+    int32_t pad;
 } tetris_tune_entry;
 int tetris_autotune(tetris_ctx *ctx, uint32_t db, const tetris_query *query, uint32_t reps,
                     tetris_tune_entry *out, uint32_t cap, uint32_t *n_out);
@@ -255,6 +258,11 @@ enum {
                                           alpha 1; keys then carry (L+1) ceil(bits/w) digits,
                                           digit i B + b with P 2^(w b) on limb i.  Set before
                                           loading or generating keys: changing it drops them */
+    TETRIS_OPT_PERSISTENT = 9,         /* 1: queries record every NTT pass and every ModUp row pass +
+                                          key inner product as one persistent launch (resident CTAs
+                                          walking the tiles of all its limbs; log N in [14, 16]); 0
+                                          (default): one CTA per tile.  Same results; the autotuner
+                                          times both */
     TETRIS_OPT_DEBUG_CHECKS = 8,       /* 1: before a program is recorded, every device range each of
                                           its kernel jobs will read or write is checked on the host
                                           to lie inside a live allocation of the context, the program
@@ -371,9 +379,9 @@ int tetris_batch_run(const tetris_batch_item *items, uint32_t n_items, int sched
  * Serving.  tetris_serve_start starts a server thread that owns the GPU work
  * of the context until tetris_serve_stop; in between, only tetris_submit,
  * tetris_poll, tetris_serve_stats and tetris_serve_stop may be called on the
- * context (from any thread).  tetris_submit copies the query's inputs
- * (host buffers, as for tetris_evaluate_query) into pinned memory and returns
- * a ticket at once.  The server admits queued queries in arrival order while
+ * context (from any thread).  tetris_submit copies the limbs the circuit
+ * reads of the query's inputs (host buffers, as for tetris_evaluate_query)
+ * into pinned memory, split over up to 8 host threads, and returns a ticket.  The server admits queued queries in arrival order while
  * fewer than max_inflight are running and the device memory of the program
  * instance a query needs fits memory_budget_bytes (idle instances of other
  * query shapes are released first; the first instance of a shape is sized by

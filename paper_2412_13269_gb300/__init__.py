@@ -27,7 +27,7 @@ OP_ADD, OP_SUB, OP_TENSOR, OP_RELIN, OP_RESCALE, OP_MUL_INT, OP_ADD_INT = 1, 2, 
 OP_AUTOMORPHISM, OP_ROTATE, OP_KEYSWITCH, OP_MUL_PLAIN, OP_NTT, OP_INNERSUM, OP_DROP = 8, 9, 10, 11, 12, 13, 14
 OP_RELIN_RESCALE, OP_RESCALE_MUL_INT = 15, 16
 OPT_BLOCKS_PER_LAUNCH, OPT_USE_GRAPH, OPT_KS_ALPHA, OPT_PROFILE, OPT_NTT_GROUP, OPT_KS_BASE2 = 1, 2, 3, 4, 5, 6
-OPT_QUERY_STAGE, OPT_DEBUG_CHECKS = 7, 8
+OPT_QUERY_STAGE, OPT_DEBUG_CHECKS, OPT_PERSISTENT = 7, 8, 9
 STAGE_FULL, STAGE_X, STAGE_Y, STAGE_D, STAGE_U = 0, 1, 2, 3, 4
 
 
@@ -105,7 +105,8 @@ def batch_run(items, schedule: int = SCHED_AUTO):
 
 
 class TuneEntry(C.Structure):
-    _fields_ = [("blocks_per_launch", C.c_int32), ("ntt_group_log2", C.c_int32), ("ms", C.c_double)]
+    _fields_ = [("blocks_per_launch", C.c_int32), ("ntt_group_log2", C.c_int32), ("ms", C.c_double),
+                ("persistent", C.c_int32), ("pad", C.c_int32)]
 
 
 class KernelStat(C.Structure):
@@ -361,12 +362,12 @@ class Ctx:
 
     def autotune(self, db: int, w, w_meta, c, c_meta, t, t_meta, sign_coeffs, reps: int = 3):
         """Times the query under each candidate schedule, keeps the fastest;
-        returns [(blocks_per_launch, ntt_group_log2, ms)]."""
+        returns [(blocks_per_launch, ntt_group_log2, ms, persistent)]."""
         q, keep = self._query_struct(w, w_meta, c, c_meta, t, t_meta, sign_coeffs)
         buf = (TuneEntry * 32)()
         n = C.c_uint32()
         check(lib().tetris_autotune(self.h, db, C.byref(q), reps, buf, 32, C.byref(n)))
-        return [(buf[i].blocks_per_launch, buf[i].ntt_group_log2, buf[i].ms) for i in range(n.value)]
+        return [(buf[i].blocks_per_launch, buf[i].ntt_group_log2, buf[i].ms, buf[i].persistent) for i in range(n.value)]
 
     def reduce_sum_device(self, data, level: int, ncomp: int = 2, stream: int = 0):
         """In place: residue sums over partitions (torch CUDA int64 tensor) -> residues mod q_i."""

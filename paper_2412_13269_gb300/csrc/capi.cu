@@ -772,6 +772,10 @@ int tetris_set_option(tetris_ctx *ctx, int option, int64_t value) {
             case TETRIS_OPT_DEBUG_CHECKS:
                 C.debug_checks = value ? 1 : 0;
                 break;
+            case TETRIS_OPT_PERSISTENT:
+                if (value) ntt_pass_tiles(C.log_n, true);  // refuses ring degrees the persistent kernels do not take
+                C.persistent = value ? 1 : 0;
+                break;
             default:
                 throw Error(TETRIS_EINVAL, "unknown or read-only option");
         }
@@ -791,6 +795,7 @@ int tetris_get_option(tetris_ctx *ctx, int option, int64_t *value) {
             case TETRIS_OPT_NTT_GROUP: *value = C.nt.loge; break;
             case TETRIS_OPT_QUERY_STAGE: *value = C.query_stage; break;
             case TETRIS_OPT_DEBUG_CHECKS: *value = C.debug_checks; break;
+            case TETRIS_OPT_PERSISTENT: *value = C.persistent; break;
             default: throw Error(TETRIS_EINVAL, "unknown option");
         }
     });

@@ -342,6 +342,16 @@ static Deferred make_deferred(int type, const std::vector<J> &jobs, const std::s
 // Debug checks: the device ranges of every job, checked on the host before the
 // job is recorded (nothing is launched with a range outside the allocations)
 // ---------------------------------------------------------------------------
+size_t Rec::tab_offset() {
+    if (P.tab_off == SIZE_MAX) {
+        TabEntry te;
+        te.t = C.nt;
+        te.log_n = C.log_n;
+        P.tab_off = P.add_jobs(&te, sizeof te);
+    }
+    return P.tab_off;
+}
+
 void Rec::check_range(const void *p, size_t words, const std::string &what) {
     if (!p) return;
     C.checked_ranges++;
@@ -505,10 +515,28 @@ void Rec::ntt(bool inverse, const std::vector<NttJob> &jobs_in, int load_mode, i
     if (load_mode == LOAD_PIECE) conv = n;  // one Shoup product per element
     const double first_log = inverse ? log2 : log1, second_log = inverse ? log1 : log2;
     const double mm1 = (double)n * N * first_log / 2 + conv * N;
+    // one launch of pass `pass` over jobs [j0, j0 + m): a CTA per tile, or
+    // (persistent) resident CTAs walking the tiles
+    auto pass_fn = [&](int pass, size_t o, int m, int mode) -> std::function<void(cudaStream_t, const uint8_t *)> {
+        if (!persistent) {
+            return [=](cudaStream_t s, const uint8_t *a) {
+                launch_ntt(inverse, logn, t, reinterpret_cast<const NttJob *>(a + o), m, load_mode, mode, s, pass);
+            };
+        }
+        const uint32_t tiles = (uint32_t)ntt_pass_tiles(logn, inverse ? pass == 1 : pass == 0);
+        std::vector<uint32_t> ts(m + 1);
+        for (int k = 0; k <= m; k++) ts[k] = (uint32_t)k * tiles;
+        const size_t toff = P.add_jobs(ts.data(), ts.size() * sizeof(uint32_t)), tb = tab_offset();
+        const int total = (int)(m * tiles);
+        return [=](cudaStream_t s, const uint8_t *a) {
+            launch_ntt_pass_multi(inverse, pass, reinterpret_cast<const TabEntry *>(a + tb),
+                                  reinterpret_cast<const NttJob *>(a + o), reinterpret_cast<const uint32_t *>(a + toff), m,
+                                  total, load_mode, mode, s);
+        };
+    };
     if (passes & 1)
-        P.add_launch([=](cudaStream_t s, const uint8_t *a) {
-            launch_ntt(inverse, logn, t, reinterpret_cast<const NttJob *>(a + off), n, load_mode, store_mode, s, 0);
-        }, prefix + dir + "_p1_" + load_name(load_mode), distinct_bytes(srcs, N) + w, mm1, n);
+        P.add_launch(pass_fn(0, off, n, store_mode), prefix + dir + "_p1_" + load_name(load_mode),
+                     distinct_bytes(srcs, N) + w, mm1, n);
     if (!(passes & 2)) return;
     // second pass: one launch per store segment
     auto second = [&](int j0, int j1, int mode) {
@@ -528,9 +556,7 @@ void Rec::ntt(bool inverse, const std::vector<NttJob> &jobs_in, int load_mode, i
         b2 += distinct_bytes(rd, N);
         const double mm2 = (double)m * N * (second_log / 2 + ((mode != STORE_PLAIN || inverse) ? 1 : 0)) + extra_mm * N;
         const size_t o2 = off + (size_t)j0 * sizeof(NttJob);
-        P.add_launch([=](cudaStream_t s, const uint8_t *a) {
-            launch_ntt(inverse, logn, t, reinterpret_cast<const NttJob *>(a + o2), m, load_mode, mode, s, 1);
-        }, prefix + dir + "_p2_" + store_name(mode), b2, mm2, m);
+        P.add_launch(pass_fn(1, o2, m, mode), prefix + dir + "_p2_" + store_name(mode), b2, mm2, m);
     };
     if (split < 0 || split >= n) {
         second(0, n, store_mode);
@@ -611,9 +637,23 @@ void Rec::ksup(const std::vector<KsJob> &jobs) {
     }
     // the row pass of each transformed digit (log2(N2)/2 butterfly products per word) and the products above
     const double mm = (transforms * (logn / 2) / 2.0 + prods) * C.N;
-    P.add_launch([=](cudaStream_t s, const uint8_t *a) {
-        launch_keyswitch_up(logn, t, reinterpret_cast<const KsJob *>(a + off), n, s);
-    }, prefix + "modup_keyip", distinct_bytes(rd, C.N) + 2.0 * n * C.N * 8, mm, n);
+    std::function<void(cudaStream_t, const uint8_t *)> fn;
+    if (!persistent) {
+        fn = [=](cudaStream_t s, const uint8_t *a) {
+            launch_keyswitch_up(logn, t, reinterpret_cast<const KsJob *>(a + off), n, s);
+        };
+    } else {
+        const uint32_t tiles = (uint32_t)keyswitch_up_tiles(logn);
+        std::vector<uint32_t> ts(n + 1);
+        for (int k = 0; k <= n; k++) ts[k] = (uint32_t)k * tiles;
+        const size_t toff = P.add_jobs(ts.data(), ts.size() * sizeof(uint32_t)), tb = tab_offset();
+        const int total = (int)(n * tiles);
+        fn = [=](cudaStream_t s, const uint8_t *a) {
+            launch_keyswitch_up_multi(reinterpret_cast<const TabEntry *>(a + tb), reinterpret_cast<const KsJob *>(a + off),
+                                      reinterpret_cast<const uint32_t *>(a + toff), n, total, s);
+        };
+    }
+    P.add_launch(fn, prefix + "modup_keyip", distinct_bytes(rd, C.N) + 2.0 * n * C.N * 8, mm, n);
 }
 
 void Rec::lin(const std::vector<LinJob> &jobs) {

@@ -65,6 +65,7 @@ struct Ctx {
     int profile = 0;
     int query_stage = 0;    // TETRIS_OPT_QUERY_STAGE: 0 the whole query, else the stage whose values are returned
     int debug_checks = 0;   // TETRIS_OPT_DEBUG_CHECKS: bounds-check every recorded job on the host
+    int persistent = 0;     // TETRIS_OPT_PERSISTENT: NTT passes and fused row passes as persistent launches
     uint64_t checked_ranges = 0;  // device ranges checked so far (debug)
     std::map<std::string, KernelStat> stats;
     void *server = nullptr;  // serve.cu
@@ -142,6 +143,7 @@ struct Program {
     // counters
     int relins = 0, rescales = 0, rotations = 0;
     int ks_count = 0;
+    size_t tab_off = SIZE_MAX;  // the context's table set in the arena (persistent launches)
     double ks_bytes = 0;  // per keyswitch: input d + key limbs used + output, summed
 
     ~Program();
@@ -183,6 +185,7 @@ class Rec {
     std::string prefix;                     // prepended to the kind of every launch recorded (profiling scopes)
     std::vector<Deferred> *defer = nullptr; // when set, launches are collected here instead of emitted
     Pool *pool_override = nullptr;          // when set, buffers come from (and return to) this pool
+    bool persistent = false;                // NTT passes and fused row passes as persistent launches
     Pool &pool() { return pool_override ? *pool_override : P.pool; }
     void emit(const Deferred &d);           // turn a collected launch into a real one
 
@@ -234,6 +237,7 @@ class Rec {
 
   private:
     NttJob conv_job(uint32_t dst_prime, const u64 *src, uint32_t first_src_prime, int nsrc);
+    size_t tab_offset();  // the context's table set in the program arena (persistent launches)
     // debug checks (TETRIS_OPT_DEBUG_CHECKS): every range a job reads or writes
     // lies inside a live allocation of the context, the program or the item
     bool emitting_ = false;  // jobs already checked when they were deferred
@@ -265,6 +269,7 @@ struct QuerySpec {
     int loge = 3;                // NTT register-group width (log2 elements per thread)
     uint64_t total_records = 0;  // 0: the database's own record count
     int stage = 0;               // 0: the whole query; 1..4: stop after x, y, y - t or the step values
+    int persistent = 0;          // persistent NTT / fused row-pass launches
     // global threshold (none when gstages is empty): t1's level and scale
     int g_level = 0;
     double g_scale = 0;
@@ -272,7 +277,7 @@ struct QuerySpec {
     std::string key(uint32_t db) const {
         std::ostringstream o;
         o << "q" << db << ":" << attrs << ":" << degree << ":" << bpl << ":" << loge << ":" << t_level << ":"
-          << total_records << ":" << stage << ":";
+          << total_records << ":" << stage << ":" << persistent << ":";
         auto bits = [&](double v) {
             uint64_t b;
             std::memcpy(&b, &v, 8);

@@ -391,6 +391,7 @@ std::unique_ptr<Program> record_query(Ctx &C, const Database &db, const QuerySpe
     auto P = std::make_unique<Program>();
     P->ctx = &C;
     Rec R(C, *P);
+    R.persistent = q.persistent != 0;
     const QPlan pl = make_plan(C, db.records, q.degree, q.stages, q.total_records, q.gstages);
     const size_t N = C.N;
     // staging buffers for the inputs (coefficient domain on arrival, NTT in
@@ -599,6 +600,7 @@ QuerySpec spec_of(const Ctx &C, const Database &db, const tetris_query *q) {
     s.bpl = C.blocks_per_launch;
     s.loge = C.nt.loge;
     s.stage = C.query_stage;
+    s.persistent = C.persistent;
     TREQUIRE(q->total_records == 0 || q->total_records >= db.records, TETRIS_EINVAL,
              "query: total_records is smaller than the database");
     s.total_records = q->total_records;
@@ -696,17 +698,22 @@ void autotune(Ctx &C, uint32_t dbh, const tetris_query *q, int reps, std::vector
     std::vector<int> bpls = {0};
     for (int b : {8, 4, 2, 1})
         if (b < blocks) bpls.push_back(b);
-    const int saved_bpl = C.blocks_per_launch, saved_loge = C.nt.loge;
+    const int saved_bpl = C.blocks_per_launch, saved_loge = C.nt.loge, saved_pers = C.persistent;
     double best = 1e300;
-    int best_bpl = saved_bpl, best_loge = saved_loge;
+    int best_bpl = saved_bpl, best_loge = saved_loge, best_pers = saved_pers;
     std::string best_key;
     cudaEvent_t e0, e1;
     TCHECK_CUDA(cudaEventCreate(&e0));
     TCHECK_CUDA(cudaEventCreate(&e1));
-    for (int loge : {3, 4})
+    // (loge, persistent): radix-8 or radix-16 register groups, or persistent launches (radix 8)
+    std::vector<std::pair<int, int>> kinds = {{3, 0}, {4, 0}};
+    if (C.log_n >= 14 && C.log_n <= 16) kinds.push_back({3, 1});
+    for (auto kd : kinds)
         for (int bpl : bpls) {
+            const int loge = kd.first;
             C.blocks_per_launch = bpl;
             C.nt.loge = loge;
+            C.persistent = kd.second;
             QuerySpec spec = spec_of(C, it->second, q);
             const std::string key = spec.key(dbh);
             Program &P = get_program(C, dbh, spec);
@@ -720,12 +727,13 @@ void autotune(Ctx &C, uint32_t dbh, const tetris_query *q, int reps, std::vector
             TCHECK_CUDA(cudaEventSynchronize(e1));
             float ms = 0;
             TCHECK_CUDA(cudaEventElapsedTime(&ms, e0, e1));
-            out.push_back({bpl, loge, ms / reps});
+            out.push_back({bpl, loge, ms / reps, kd.second, 0});
             if (ms / reps < best) {
                 if (!best_key.empty()) C.programs.erase(best_key);
                 best = ms / reps;
                 best_bpl = bpl;
                 best_loge = loge;
+                best_pers = kd.second;
                 best_key = key;
             } else {
                 C.programs.erase(key);  // keep only the winner's buffers
@@ -735,6 +743,7 @@ void autotune(Ctx &C, uint32_t dbh, const tetris_query *q, int reps, std::vector
     cudaEventDestroy(e1);
     C.blocks_per_launch = best_bpl;
     C.nt.loge = best_loge;
+    C.persistent = best_pers;
 }
 
 void plan_info(Ctx &C, uint32_t dbh, uint32_t degree, uint32_t stages, tetris_plan_info *out) {

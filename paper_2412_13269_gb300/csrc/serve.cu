@@ -32,6 +32,8 @@ namespace tetris {
 namespace {
 
 using Clock = std::chrono::steady_clock;
+constexpr size_t kSubmitCopyThreads = 8;           // host threads copying a submission into pinned memory
+constexpr size_t kWordsPerCopyThread = 1u << 22;   // at least 32 MB each
 
 struct Request {
     uint64_t ticket = 0;
@@ -373,14 +375,32 @@ uint64_t serve_submit(Ctx &C, uint32_t db, const tetris_query *q) {
         }
     }
     if (!req->pinned_in) TCHECK_CUDA(cudaMallocHost(&req->pinned_in, req->total_in * 8));
+    // the rows to copy (one per ciphertext component), then split over a few
+    // host threads: a query's inputs reach a gigabyte
+    struct Row {
+        u64 *dst;
+        const u64 *src;
+        size_t words;
+    };
+    std::vector<Row> rows;
     size_t off = 0;
     for (size_t i = 0; i < ins.size(); i++) {
         const InSlot &sh = shapes[i];
         const u64 *src = static_cast<const u64 *>(ins[i]->data);
-        for (size_t r = 0; r < sh.rows; r++)
-            std::memcpy(req->pinned_in + off + r * sh.row_words, src + r * sh.src_pitch, sh.row_words * 8);
+        for (size_t r = 0; r < sh.rows; r++) rows.push_back({req->pinned_in + off + r * sh.row_words, src + r * sh.src_pitch, sh.row_words});
         off += sh.words();
     }
+    const size_t nthreads = std::min<size_t>(kSubmitCopyThreads, std::max<size_t>(1, req->total_in / kWordsPerCopyThread));
+    auto copy_part = [&](size_t t) {  // thread t copies the t-th share of every row
+        for (const Row &rw : rows) {
+            const size_t a = rw.words * t / nthreads, b = rw.words * (t + 1) / nthreads;
+            if (b > a) std::memcpy(rw.dst + a, rw.src + a, (b - a) * 8);
+        }
+    };
+    std::vector<std::thread> helpers;
+    for (size_t t = 1; t < nthreads; t++) helpers.emplace_back(copy_part, t);
+    copy_part(0);
+    for (auto &h : helpers) h.join();
     req->t_submit = Clock::now();
     {
         std::lock_guard<std::mutex> lk(S->mu);

@@ -236,3 +236,41 @@ def test_reduce_sum_device(small):
     for p_ in parts[1:]:
         acc = ckks.add(par, acc, ckks.Ct(p_, l, 1.0))
     assert np.array_equal(got, acc.data)
+
+
+def test_full_size_ntt_keyswitch_rotate_alpha4():
+    """The benchmark's parameters and digit size (N = 2^16, twenty 50-bit and
+    three 60-bit primes, alpha = 4): the forward NTT of every limb against the
+    oracle's transform in bit-reversed order, a top-level key switch and
+    rotations at the top level and at level 1 (where InnerSum runs), each
+    bit-exact against the oracle."""
+    T.build()
+    q, p = rns.gen_primes(50, 20), rns.gen_primes(60, 3)
+    par = ckks.Params(16, q, p, 2.0 ** 50)
+    ctx = T.Ctx(16, q, p, 2.0 ** 50)
+    s = query.secret(par, 19, 192)
+    alpha = 4
+    dnum = ckks.dnum_for(par.L, alpha)
+    d = synth.switch_key_draws(19, "relin", dnum, par.moduli, par.N)
+    ctx.keygen_relin(s, d.a, d.e, alpha)
+    rlk = ckks.relin_key(par, s, d.a, d.e, alpha)
+    g = ckks.galois_for_rotation(par.N, 1)
+    dr = synth.switch_key_draws(19, f"rot{g}", dnum, par.moduli, par.N)
+    ctx.keygen_rotation(g, s, dr.a, dr.e, alpha)
+    rk = ckks.rotation_key(par, g, s, dr.a, dr.e, alpha)
+    assert np.array_equal(ctx.get_key(g, dnum), rk)
+    l = par.L
+    a = rand_ct(par, 1, l, 7)
+    got = ctx.op(T.OP_NTT, a, l, out_comps=1)[0]
+    perm = np.array([brv(k, par.log_n) for k in range(par.N)])
+    for i in range(l + 1):
+        x = a[0, i].copy()
+        rns.lib().or_ntt(rns.ptr(x), par.N, par.q[i], par.psi[i])
+        assert np.array_equal(got[0, i], x[perm]), i
+    got = ctx.op(T.OP_KEYSWITCH, a, l, arg=0, out_comps=2)[0]
+    assert np.array_equal(got, ckks.keyswitch(par, a[0], l, rlk, alpha))
+    for lv in (l, 1):
+        c = rand_ct(par, 2, lv, 70 + lv)
+        got = ctx.op(T.OP_ROTATE, c, lv, arg=g, out_comps=2)[0]
+        assert np.array_equal(got, ckks.rotate(par, ckks.Ct(c, lv, 1.0), g, rk, alpha).data), lv
+    ctx.close()

@@ -114,7 +114,8 @@ def test_autotune_keeps_results(chain):
     a = ([c.data for c in eq.w], [(c.level, c.scale) for c in eq.w], [c.data for c in eq.c],
          [(c.level, c.scale) for c in eq.c], eq.t.data, (eq.t.level, eq.t.scale), np.array(stages))
     table = ctx.autotune(dbh, *a, reps=2)
-    assert sorted((b, g) for b, g, _ in table) == [(0, 3), (0, 4), (1, 3), (1, 4)]
+    assert sorted((b, g) for b, g, _, p in table) == [(0, 3), (0, 4), (1, 3), (1, 4)]
+    assert not any(p for *_, p in table)   # persistent launches take log N >= 14
     best = min(table, key=lambda e: e[2])
     assert (ctx.get_option(T.OPT_BLOCKS_PER_LAUNCH), ctx.get_option(T.OPT_NTT_GROUP)) == best[:2]
     for grp in (3, 4):
@@ -221,6 +222,11 @@ def test_full_size_one_block_bit_exact(full):
     want = query.evaluate_query(par, keys, shape, db, eq)
     dbh = upload_encoded(ctx, par, plan, db, 32768, 16)
     got, lev, sc = gpu_query(ctx, dbh, eq, stages)
+    assert lev == want.level and np.array_equal(got, want.data)
+    # persistent launches (resident CTAs walking every limb's tiles) give the same residues
+    ctx.set_option(T.OPT_PERSISTENT, 1)
+    got, lev, sc = gpu_query(ctx, dbh, eq, stages)
+    ctx.set_option(T.OPT_PERSISTENT, 0)
     assert lev == want.level and np.array_equal(got, want.data)
     ctx.free_database(dbh)
 
