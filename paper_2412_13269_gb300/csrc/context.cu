@@ -482,7 +482,28 @@ static const char *store_name(int m) {
 void Rec::ntt(bool inverse, const std::vector<NttJob> &jobs_in, int load_mode, int store_mode, int split,
               int store_mode_b, int passes) {
     if (jobs_in.empty()) return;
-    const std::vector<NttJob> &jobs = jobs_in;
+    // The column pass's outer stage has one twiddle, psi^(N/2) forward (its
+    // first stage) and psi^-(N/2) = -psi^(N/2) inverse (its last): a forward
+    // conversion load also forms the conversion times it for the upper half of
+    // every column, an inverse scaled store the scale times its inverse.
+    std::vector<NttJob> folded;
+    if ((load_mode == LOAD_CONV_PRE && !inverse) || inverse) {
+        folded = jobs_in;
+        for (auto &j : folded) {
+            const u64 q = C.all[j.prime], w1 = h_powmod(C.psi[j.prime], C.N / 2, q);
+            if (inverse) {
+                j.mul_w = h_mulmod(j.mul, q - w1, q);
+                j.mul_w_sh = h_shoup(j.mul_w, q);
+                continue;
+            }
+            for (uint32_t s = 0; s < j.nsrc; s++) {
+                j.c2w[s] = h_mulmod(j.c2[s], w1, q);
+                j.c2w_sh[s] = h_shoup(j.c2w[s], q);
+            }
+            j.conv_sub_w = h_mulmod(j.conv_sub, w1, q);
+        }
+    }
+    const std::vector<NttJob> &jobs = folded.empty() ? jobs_in : folded;
     TREQUIRE(split < 0 || !defer, TETRIS_EINVAL, "split transforms are not deferred");
     TREQUIRE(passes >= 1 && passes <= 3, TETRIS_EINVAL, "no transform pass selected");
     if (checking()) check(jobs_in, load_mode, split >= 0 ? std::max(store_mode, store_mode_b) : store_mode);

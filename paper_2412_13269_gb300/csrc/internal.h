@@ -120,7 +120,11 @@ struct NttJob {
     uint32_t nsrc;
     uint64_t src_stride;
     u64 c2[kMaxConvSrc], c2_sh[kMaxConvSrc];  // c2_sh: Shoup companions of c2 modulo q_dst
+    // forward conversion loads: c2 and conv_sub times the first butterfly
+    // stage's twiddle psi^(N/2) (filled in by the recorder)
+    u64 c2w[kMaxConvSrc], c2w_sh[kMaxConvSrc], conv_sub_w;
     u64 conv_sub, mul, mul_sh;
+    u64 mul_w, mul_w_sh;                      // inverse scaled stores: mul times the last stage's twiddle psi^-(N/2)
     u64 piece_mask;                           // LOAD_PIECE
     uint32_t piece_shift;
     uint32_t tab;                             // launches over several ring degrees: the job's table set

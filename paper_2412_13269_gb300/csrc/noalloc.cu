@@ -61,6 +61,7 @@ struct NoallocParams {
     NttJob *jobs_inv, *jobs_fwd;
     uint32_t N, level, ncomp, pad;
     u64 top_mul, top_mul_sh, top_half;               // N^-1 mod q_l (Shoup pair), floor(q_l/2)
+    u64 top_mul_w, top_mul_w_sh;                     // N^-1 psi^-(N/2) mod q_l (the upper half's scale)
     u64 half[kMaxPrimes], mul[kMaxPrimes], mul_sh[kMaxPrimes];  // per q_i, i < l
 };
 
@@ -73,6 +74,8 @@ __global__ void noalloc_tables_kernel(NoallocParams p) {
         j.prime = p.level;
         j.mul = p.top_mul;
         j.mul_sh = p.top_mul_sh;
+        j.mul_w = p.top_mul_w;
+        j.mul_w_sh = p.top_mul_w_sh;
         j.conv_sub = p.top_half;
         p.jobs_inv[c] = j;
     }
@@ -135,6 +138,8 @@ void rescale_ntt_noalloc(Ctx &C, const u64 *in, u64 *out, int level, int ncomp, 
     p.top_mul = C.mods_host[level].ninv;
     p.top_mul_sh = C.mods_host[level].ninv_sh;
     p.top_half = half;
+    p.top_mul_w = h_mulmod(p.top_mul, ql - h_powmod(C.psi[level], N / 2, ql), ql);
+    p.top_mul_w_sh = h_shoup(p.top_mul_w, ql);
     for (int i = 0; i < level; i++) {
         const u64 qi = C.q[i];
         p.half[i] = half % qi;

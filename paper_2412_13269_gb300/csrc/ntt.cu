@@ -26,7 +26,7 @@
 // subtract a base conversion.  Butterflies are lazy: forward transforms modulo
 // primes below 2^57 run with no correction at all (their products use a
 // Shoup quotient estimated from three partial products, < 4q; values grow by
-// at most 4q per stage and stay below 81q), the others as Harvey's, in [0, 4q) (forward)
+// at most 4q per stage and stay below 94q), the others as Harvey's, in [0, 4q) (forward)
 // or [0, 2q) (inverse) between stages and passes; the second pass reduces.
 #include "internal.h"
 
@@ -83,10 +83,12 @@ __device__ __forceinline__ void gs_bfly(u64 &x, u64 &y, u64 w, u64 wsh, u64 q, u
 
 // Forward transforms modulo q < 2^57 run "open" (no correction inside the two
 // passes): loads give values below q + 4 * 4q = 17q (a conversion from four
-// sources), sixteen stages add at most 64q, so every intermediate stays below
-// 81q < 2^64; the second pass's store reduces once.  Larger primes (the
-// 60-bit special primes) take Harvey's corrected butterflies with exact Shoup
-// products.
+// sources); the first stage of a conversion pass, whose upper inputs already
+// carry the twiddle, adds and subtracts them (< 34q); each later stage adds at
+// most 4q, so after seven more stages of the first pass and eight of the
+// second every intermediate stays below 34q + 60q = 94q < 2^64; the second
+// pass's store reduces once.  Larger primes (the 60-bit special primes) take
+// Harvey's corrected butterflies with exact Shoup products.
 constexpr u64 kOpenBound = 1ull << 57;
 
 // Register window of butterfly group g: the thread holds the E elements whose
@@ -164,7 +166,14 @@ struct Geo {
 // The butterfly stages of one pass on the thread's registers x (loaded at
 // lrow), leaving them at srow: shared-memory exchanges between groups and the
 // staging of non-coalesced ends.
-template <int LOGM, bool INV, bool COL, int LOGEV, bool OPEN>
+//
+// FOLD (column pass): the outer stage's one twiddle is folded into a job
+// constant.  Forward (open): the first stage's upper elements were loaded
+// already multiplied by it (a conversion load whose constants carry it), each
+// below 17q, so the stage only adds and subtracts.  Inverse: the last stage
+// leaves its differences x - y + 2q (< 4q) for the scaled store, whose
+// constant for the upper half carries the twiddle.
+template <int LOGM, bool INV, bool COL, int LOGEV, bool OPEN, bool FOLD = false>
 __device__ __forceinline__ void run_stages(const Geo<LOGM, INV, COL, LOGEV> &g, u64 (&x)[Geo<LOGM, INV, COL, LOGEV>::E],
                                            u64 *sm, const u64 *tw, const u64 *twsh, u64 q) {
     using GG = Geo<LOGM, INV, COL, LOGEV>;
@@ -198,6 +207,28 @@ __device__ __forceinline__ void run_stages(const Geo<LOGM, INV, COL, LOGEV> &g, 
             const int b = INV ? blo + st : bhi - st;
             if (b >= blo && b <= bhi) {
                 const int bb = b - lo;
+                if (INV && FOLD && b == LOGM - 1) {
+#pragma unroll
+                    for (int j = 0; j < E; j++) {
+                        if (j >= (1 << bb)) continue;
+                        const u64 X = x[j], Y = x[j + (1 << bb)];
+                        const u64 S = X + Y;
+                        x[j] = S >= q2 ? S - q2 : S;
+                        x[j + (1 << bb)] = X - Y + q2;
+                    }
+                    continue;
+                }
+                if (!INV && FOLD && gi == 0 && st == 0) {
+                    const u64 q17 = 17 * q;
+#pragma unroll
+                    for (int j = 0; j < E; j++) {
+                        if (j >= (1 << bb)) continue;
+                        const u64 X = x[j], T = x[j + (1 << bb)];
+                        x[j] = X + T;
+                        x[j + (1 << bb)] = X - T + q17;
+                    }
+                    continue;
+                }
 #pragma unroll
                 for (int k = 0; k < E; k++) {
                     if (k & (1 << bb)) continue;
@@ -259,21 +290,30 @@ __device__ __forceinline__ void pass_body(NttTables tb, int log1, int log2, int 
         }
     } else if (MODE == M_CONVPRE) {
         // sum_s y_s * c2_s with lazy Shoup products: each term < 4q (open: estimated
-        // quotient) or < 2q, the sum < 16q
+        // quotient) or < 2q, the sum < 16q.  Open (a forward column pass): the
+        // upper half of the first stage's pairs, k >= E/2, takes the constants
+        // times that stage's twiddle (c2w, conv_sub_w) and the stage no product.
         const u64 *src = J.src;
         const u64 stride = J.src_stride;
         const int ns = (int)J.nsrc;
         const u64 sub = J.conv_sub, q4 = 4 * q;
 #pragma unroll
-        for (int k = 0; k < E; k++) x[k] = OPEN ? q - sub : 0;
+        for (int k = 0; k < E; k++) x[k] = OPEN ? q - (k >= E / 2 ? J.conv_sub_w : sub) : 0;
 #pragma unroll
         for (int sidx = 0; sidx < kMaxConvSrc; sidx++) {
             if (sidx < ns) {
                 const u64 c2 = J.c2[sidx], c2sh = J.c2_sh[sidx];
                 const u64 *sp = src + sidx * stride;
+                if (OPEN) {
 #pragma unroll
-                for (int k = 0; k < E; k++)
-                    x[k] += OPEN ? shoup_lazy4(sp[g.gidx(g.lrow(k))], c2, c2sh, q) : shoup_lazy(sp[g.gidx(g.lrow(k))], c2, c2sh, q);
+                    for (int k = 0; k < E / 2; k++) x[k] += shoup_lazy4(sp[g.gidx(g.lrow(k))], c2, c2sh, q);
+                    const u64 c2w = J.c2w[sidx], c2wsh = J.c2w_sh[sidx];
+#pragma unroll
+                    for (int k = E / 2; k < E; k++) x[k] += shoup_lazy4(sp[g.gidx(g.lrow(k))], c2w, c2wsh, q);
+                } else {
+#pragma unroll
+                    for (int k = 0; k < E; k++) x[k] += shoup_lazy(sp[g.gidx(g.lrow(k))], c2, c2sh, q);
+                }
             }
         }
         if (!OPEN) {
@@ -307,7 +347,9 @@ __device__ __forceinline__ void pass_body(NttTables tb, int log1, int log2, int 
     }
 
     // 2. butterfly groups
-    run_stages<LOGM, INV, COL, LOGEV, OPEN>(g, x, sm, tw, twsh, q);
+    constexpr bool FOLD_INV = INV && COL && (MODE == M_SCALED || MODE == M_SCALED_CONV);
+    run_stages<LOGM, INV, COL, LOGEV, OPEN, (MODE == M_CONVPRE && OPEN && !INV && COL) || FOLD_INV>(g, x, sm, tw, twsh,
+                                                                                                  q);
 
     // 3. store straight from the last group's registers; the first pass keeps
     //    lazy values, the second reduces them and fuses the consumer
@@ -322,7 +364,11 @@ __device__ __forceinline__ void pass_body(NttTables tb, int log1, int log2, int 
         for (int k = 0; k < E; k++) {
             const size_t gi = g.gidx(g.srow(k));
             u64 v = x[k];
-            if (MODE == M_SCALED || MODE == M_SCALED_CONV) v = add_mod(shoup(v, mul, mulsh, q), addk, q);
+            if (MODE == M_SCALED || MODE == M_SCALED_CONV) {
+                // the upper half's constant carries the last stage's twiddle
+                const bool up = FOLD_INV && k >= E / 2;
+                v = add_mod(shoup(v, up ? J.mul_w : mul, up ? J.mul_w_sh : mulsh, q), addk, q);
+            }
             else if (INV) v = shoup(v, mi.ninv, mi.ninv_sh, q);
             else if (OPEN) {
                 v = v - __umul64hi(v, mi.one_sh) * q;  // Shoup product with w = 1: [0, 2q)
