@@ -752,7 +752,7 @@ def main():
     for _ in range(8):
         ctx.evaluate_query(dbh, hw, meta_w, hc, meta_c, ht, (L, Delta), sign, out=hout)
     barrier()
-    k3 = max(20, args.steps)
+    k3 = max(40, args.steps)
     each = []
     t0 = time.perf_counter()
     for _ in range(k3):
