@@ -43,7 +43,8 @@ static BufPtr upload(Pool &pool, const void *src, size_t bytes, cudaStream_t s) 
 
 static void build_tables(Ctx &C) {
     const size_t N = C.N, np = C.all.size();
-    std::vector<u64> tw(np * N), tws(np * N), itw(np * N), itws(np * N);
+    // [prime][N] pairs (psi^brv(k), its Shoup companion): one 16-byte load per twiddle
+    std::vector<u64> tw(2 * np * N), itw(2 * np * N);
     C.mods_host.resize(np);
     for (size_t t = 0; t < np; t++) {
         const u64 q = C.all[t], psi = C.psi[t], ipsi = h_invmod(psi, q);
@@ -55,10 +56,10 @@ static void build_tables(Ctx &C) {
         }
         for (size_t k = 0; k < N; k++) {
             const uint32_t r = bitrev((uint32_t)k, C.log_n);
-            tw[t * N + k] = pw[r];
-            tws[t * N + k] = h_shoup(pw[r], q);
-            itw[t * N + k] = ipw[r];
-            itws[t * N + k] = h_shoup(ipw[r], q);
+            tw[2 * (t * N + k)] = pw[r];
+            tw[2 * (t * N + k) + 1] = h_shoup(pw[r], q);
+            itw[2 * (t * N + k)] = ipw[r];
+            itw[2 * (t * N + k) + 1] = h_shoup(ipw[r], q);
         }
         ModInfo &m = C.mods_host[t];
         m.q = q;
@@ -93,16 +94,12 @@ static void build_tables(Ctx &C) {
     const size_t enc_words = enc.size();
     C.tables = C.pool.alloc(4 * w + mods_words + enc_words);
     u64 *base = C.tables->ptr;
-    TCHECK_CUDA(cudaMemcpy(base, tw.data(), w * 8, cudaMemcpyHostToDevice));
-    TCHECK_CUDA(cudaMemcpy(base + w, tws.data(), w * 8, cudaMemcpyHostToDevice));
-    TCHECK_CUDA(cudaMemcpy(base + 2 * w, itw.data(), w * 8, cudaMemcpyHostToDevice));
-    TCHECK_CUDA(cudaMemcpy(base + 3 * w, itws.data(), w * 8, cudaMemcpyHostToDevice));
+    TCHECK_CUDA(cudaMemcpy(base, tw.data(), 2 * w * 8, cudaMemcpyHostToDevice));
+    TCHECK_CUDA(cudaMemcpy(base + 2 * w, itw.data(), 2 * w * 8, cudaMemcpyHostToDevice));
     TCHECK_CUDA(cudaMemcpy(base + 4 * w, C.mods_host.data(), np * sizeof(ModInfo), cudaMemcpyHostToDevice));
     TCHECK_CUDA(cudaMemcpy(base + 4 * w + mods_words, enc.data(), enc_words * 8, cudaMemcpyHostToDevice));
     C.nt.tw = base;
-    C.nt.tw_sh = base + w;
     C.nt.itw = base + 2 * w;
-    C.nt.itw_sh = base + 3 * w;
     C.nt.mods = reinterpret_cast<const ModInfo *>(base + 4 * w);
     C.enc_tw = reinterpret_cast<const double *>(base + 4 * w + mods_words);
 }

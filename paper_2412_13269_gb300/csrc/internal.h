@@ -131,10 +131,8 @@ struct NttJob {
 };
 
 struct NttTables {
-    const u64 *tw;      // [nprimes][N] psi^brv(k)
-    const u64 *tw_sh;
-    const u64 *itw;     // [nprimes][N] psi^-brv(k)
-    const u64 *itw_sh;
+    const u64 *tw;      // [nprimes][N][2]: psi^brv(k) and its Shoup companion
+    const u64 *itw;     // [nprimes][N][2]: psi^-brv(k) and its Shoup companion
     const ModInfo *mods;
     int loge = 3;       // log2 of the elements a thread holds (3 or 4)
 };

@@ -17,7 +17,8 @@
 // (both coalesced across the warp), so a 256-point sub-problem needs two
 // shared-memory exchanges.  Stage bit b of a sub-problem of size
 // M uses twiddle index (M >> (b+1)) * o + (r >> (b+1)), with o = 1 in the
-// column pass and o = N1 + row in the row pass.
+// column pass and o = N1 + row in the row pass; the tables hold each twiddle
+// beside its Shoup companion, one 16-byte load per twiddle.
 //
 // Load modes fuse the producer: plain, int64 -> residue, or a fast base
 // conversion from up to four source limbs (ModUp / ModDown / rescale), less a
@@ -175,7 +176,7 @@ struct Geo {
 // constant for the upper half carries the twiddle.
 template <int LOGM, bool INV, bool COL, int LOGEV, bool OPEN, bool FOLD = false>
 __device__ __forceinline__ void run_stages(const Geo<LOGM, INV, COL, LOGEV> &g, u64 (&x)[Geo<LOGM, INV, COL, LOGEV>::E],
-                                           u64 *sm, const u64 *tw, const u64 *twsh, u64 q) {
+                                           u64 *sm, const u64 *tw, u64 q) {
     using GG = Geo<LOGM, INV, COL, LOGEV>;
     using G = typename GG::G;
     constexpr int M = GG::M, E = GG::E, LOGE = GG::LOGE, NG = GG::NG;
@@ -236,7 +237,8 @@ __device__ __forceinline__ void run_stages(const Geo<LOGM, INV, COL, LOGEV> &g, 
                     if (k & ((1 << bb) - 1)) continue;
                     const int r0 = tlow | (k << lo) | thigh;
                     const u64 widx = (u64)(M >> (b + 1)) * g.o + (u64)(r0 >> (b + 1));
-                    const u64 w = __ldg(tw + widx), wsh = __ldg(twsh + widx);
+                    const ulonglong2 wp = __ldg(reinterpret_cast<const ulonglong2 *>(tw) + widx);
+                    const u64 w = wp.x, wsh = wp.y;
 #pragma unroll
                     for (int j = 0; j < E; j++) {
                         if (j >= (1 << bb)) continue;
@@ -266,8 +268,7 @@ __device__ __forceinline__ void pass_body(NttTables tb, int log1, int log2, int 
     const GG g(log1, log2, tile);
     const u64 q = mi.q, q2 = 2 * q;
     const size_t N = (size_t)g.N1 * g.N2;
-    const u64 *tw = (INV ? tb.itw : tb.tw) + (size_t)J.prime * N;
-    const u64 *twsh = (INV ? tb.itw_sh : tb.tw_sh) + (size_t)J.prime * N;
+    const u64 *tw = (INV ? tb.itw : tb.tw) + (size_t)J.prime * 2 * N;  // (twiddle, companion) pairs
 
     u64 x[E];
     // 1. load straight into the first group's registers, through the producer's load mode
@@ -348,8 +349,7 @@ __device__ __forceinline__ void pass_body(NttTables tb, int log1, int log2, int 
 
     // 2. butterfly groups
     constexpr bool FOLD_INV = INV && COL && (MODE == M_SCALED || MODE == M_SCALED_CONV);
-    run_stages<LOGM, INV, COL, LOGEV, OPEN, (MODE == M_CONVPRE && OPEN && !INV && COL) || FOLD_INV>(g, x, sm, tw, twsh,
-                                                                                                  q);
+    run_stages<LOGM, INV, COL, LOGEV, OPEN, (MODE == M_CONVPRE && OPEN && !INV && COL) || FOLD_INV>(g, x, sm, tw, q);
 
     // 3. store straight from the last group's registers; the first pass keeps
     //    lazy values, the second reduces them and fuses the consumer
@@ -524,8 +524,7 @@ __device__ __forceinline__ void keyswitch_up_body(NttTables tb, int log1, int lo
     const GG g(log1, log2, tile);
     const u64 q = mi.q, q2 = 2 * q;
     const size_t N = (size_t)g.N1 * g.N2;
-    const u64 *tw = tb.tw + (size_t)J.prime * N;
-    const u64 *twsh = tb.tw_sh + (size_t)J.prime * N;
+    const u64 *tw = tb.tw + (size_t)J.prime * 2 * N;
     const int nthr = blockDim.x, tid = threadIdx.x;
     u64 *acc = sm + KsSmem<LOGM, LOGEV>::exch_words(g.sub_cta);
     auto slot = [&](int c, int k) -> u64 & { return acc[(c * E + k) * nthr + tid]; };
@@ -553,7 +552,7 @@ __device__ __forceinline__ void keyswitch_up_body(NttTables tb, int log1, int lo
         } else {
 #pragma unroll
             for (int k = 0; k < E; k++) x[k] = src[g.gidx(g.lrow(k))];
-            run_stages<LOGM, false, false, LOGEV, OPEN>(g, x, sm, tw, twsh, q);
+            run_stages<LOGM, false, false, LOGEV, OPEN>(g, x, sm, tw, q);
         }
         const u64 *k0 = J.key0[d], *k1 = J.key1[d];
 #pragma unroll
@@ -676,7 +675,10 @@ template <bool INV, bool COL, int MODE>
 __global__ void __launch_bounds__(kThreads, kMultiCtas) ntt_pass_multi_kernel(MultiParams P) {
     extern __shared__ u64 sm[];
     __shared__ NttJob J;
-    __shared__ TabEntry TE;  // the job's table set, read from shared memory where used
+    // the job's table set, read from shared memory where used (raw storage: TabEntry's
+    // default member initialisers cannot run for a __shared__ variable)
+    __shared__ __align__(16) unsigned char te_raw[sizeof(TabEntry)];
+    TabEntry &TE = *reinterpret_cast<TabEntry *>(te_raw);
     __shared__ int sj;
     const NttJob *jobs = static_cast<const NttJob *>(P.jobs);
     int jcur = -1;  // the staged job
@@ -708,7 +710,10 @@ __global__ void __launch_bounds__(kThreads, kMultiCtas) ntt_pass_multi_kernel(Mu
 __global__ void __launch_bounds__(kThreads, kMultiKsCtas) keyswitch_up_multi_kernel(MultiParams P) {
     extern __shared__ u64 sm[];
     __shared__ KsJob J;
-    __shared__ TabEntry TE;  // the job's table set, read from shared memory where used
+    // the job's table set, read from shared memory where used (raw storage: TabEntry's
+    // default member initialisers cannot run for a __shared__ variable)
+    __shared__ __align__(16) unsigned char te_raw[sizeof(TabEntry)];
+    TabEntry &TE = *reinterpret_cast<TabEntry *>(te_raw);
     __shared__ int sj;
     const KsJob *jobs = static_cast<const KsJob *>(P.jobs);
     int jcur = -1;  // the staged job

@@ -49,7 +49,7 @@ struct Ctx {
     std::vector<double> S;  // standard scales
     double pt_scale = 0;
     std::vector<ModInfo> mods_host;
-    BufPtr tables;          // tw, tw_sh, itw, itw_sh, mods, encoder tables
+    BufPtr tables;          // tw, itw (twiddle + companion pairs), mods, encoder tables
     NttTables nt{};
     const double *enc_tw = nullptr;
     Pool pool;
