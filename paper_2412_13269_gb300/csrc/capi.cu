@@ -131,6 +131,19 @@ static void set_alpha(Ctx &C, uint32_t alpha) {
     C.alpha = alpha;
 }
 
+// A key's device form: for each digit and prime, N (component 0, component 1)
+// pairs, so the key inner product reads both with one 16-byte load.
+static Key key_from_limbs(Ctx &C, u64 *limbs, int dnum) {
+    Key k;
+    k.dnum = dnum;
+    k.pieces = key_pieces(C);
+    k.buf = C.pool.alloc((size_t)dnum * 2 * C.nqp() * C.N);
+    launch_interleave_pairs(limbs, k.buf->ptr, dnum, C.nqp(), C.N, true, C.stream);
+    TCHECK_CUDA(cudaGetLastError());
+    TCHECK_CUDA(cudaStreamSynchronize(C.stream));
+    return k;
+}
+
 static Key load_key(Ctx &C, const uint64_t *evk, size_t n_words, uint32_t alpha) {
     // every check before set_alpha, which drops the loaded keys on a new digit size:
     // a malformed key leaves the context as it was
@@ -150,24 +163,22 @@ static Key load_key(Ctx &C, const uint64_t *evk, size_t n_words, uint32_t alpha)
                                           std::to_string(row));
     }
     set_alpha(C, alpha);
-    Key k;
-    k.dnum = dnum;
-    k.pieces = key_pieces(C);
-    k.buf = upload(C.pool, evk, n_words * 8, C.stream);
     Program P;
     Rec R(C, P);
+    BufPtr limbs = upload(P.pool, evk, n_words * 8, C.stream);  // [dnum][2][nqp][N], transformed in place
+    P.hold.push_back(limbs);
     std::vector<NttJob> jobs;
     for (int j = 0; j < dnum; j++)
         for (int c = 0; c < 2; c++)
             for (int t = 0; t < nqp; t++) {
                 NttJob jb{};
-                jb.src = jb.dst = k.buf->ptr + (((size_t)j * 2 + c) * nqp + t) * N;
+                jb.src = jb.dst = limbs->ptr + (((size_t)j * 2 + c) * nqp + t) * N;
                 jb.prime = t;
                 jobs.push_back(jb);
             }
     R.ntt(false, jobs, LOAD_PLAIN, STORE_PLAIN);
     run_now(C, P);
-    return k;
+    return key_from_limbs(C, limbs->ptr, dnum);
 }
 
 // s (int64, N) -> NTT-domain residues over every prime [nqp][N]
@@ -223,15 +234,13 @@ static Key gen_key(Ctx &C, const int64_t *s, const uint64_t *a, const int64_t *e
         for (int t = 0; t < nqp; t++) jobs.push_back({sn->ptr + (size_t)t * N, sf->ptr + (size_t)t * N});
         R.aut(jobs, galois & (uint32_t)(2 * N - 1));
     }
-    Key k;
-    k.dnum = dnum;
-    k.pieces = B;
-    k.buf = C.pool.alloc((size_t)dnum * 2 * nqp * N);
+    BufPtr kb = P.pool.alloc((size_t)dnum * 2 * nqp * N);  // [dnum][2][nqp][N]
+    P.hold.push_back(kb);
     BufPtr ad = upload(P.pool, a, (size_t)dnum * nqp * N * 8, C.stream);
     BufPtr ed = upload(P.pool, e, (size_t)dnum * N * 8, C.stream);
     P.hold.push_back(ad);
     P.hold.push_back(ed);
-    auto kl = [&](int j, int c, int t) { return k.buf->ptr + (((size_t)j * 2 + c) * nqp + t) * N; };
+    auto kl = [&](int j, int c, int t) { return kb->ptr + (((size_t)j * 2 + c) * nqp + t) * N; };
     std::vector<NttJob> ja, je;
     for (int j = 0; j < dnum; j++)
         for (int t = 0; t < nqp; t++) {
@@ -288,7 +297,7 @@ static Key gen_key(Ctx &C, const int64_t *s, const uint64_t *a, const int64_t *e
     R.ew(m2);
     R.ew(m3);
     run_now(C, P);
-    return k;
+    return key_from_limbs(C, kb->ptr, dnum);
 }
 
 // ---------------------------------------------------------------------------
@@ -464,11 +473,13 @@ int tetris_get_key(tetris_ctx *ctx, uint32_t g, uint64_t *out, size_t cap) {
         TREQUIRE(cap >= words, TETRIS_EINVAL, "output buffer too small");
         Program P;
         Rec R(C, P);
-        BufPtr o = P.pool.alloc(words);
+        BufPtr limbs = P.pool.alloc(words), o = P.pool.alloc(words);
+        launch_interleave_pairs(limbs->ptr, k.buf->ptr, k.dnum, nqp, C.N, false, C.stream);  // pairs -> limbs
+        TCHECK_CUDA(cudaGetLastError());
         std::vector<NttJob> jobs;
         for (size_t l = 0; l < (size_t)k.dnum * 2 * nqp; l++) {
             NttJob j{};
-            j.src = k.buf->ptr + l * C.N;
+            j.src = limbs->ptr + l * C.N;
             j.dst = o->ptr + l * C.N;
             j.prime = (uint32_t)(l % nqp);
             jobs.push_back(j);

@@ -412,8 +412,7 @@ void Rec::check(const std::vector<KsJob> &jobs) {
         TREQUIRE(j.ndig >= 1 && j.ndig <= (uint32_t)kMaxKeyDigits, TETRIS_EINVAL, "debug check: " + w + " digits");
         for (uint32_t d = 0; d < j.ndig; d++) {
             check_range(j.src[d], N, w + " digit source");
-            check_range(j.key0[d], N, w + " key");
-            check_range(j.key1[d], N, w + " key");
+            check_range(j.key[d], 2 * N, w + " key");
         }
         for (const void *p : {(const void *)j.acc0, (const void *)j.acc1, (const void *)j.ex0, (const void *)j.ex1})
             check_range(p, N, w);
@@ -648,8 +647,8 @@ void Rec::ksup(const std::vector<KsJob> &jobs) {
     for (auto &j : jobs) {
         for (uint32_t d = 0; d < j.ndig; d++) {
             rd.push_back(j.src[d]);
-            rd.push_back(j.key0[d]);
-            rd.push_back(j.key1[d]);
+            rd.push_back(j.key[d]);  // both components: 2N words
+            rd.push_back(j.key[d] + C.N);
             if ((int)d != j.own) transforms += 1;
         }
         rd.push_back(j.ex0);
@@ -1025,8 +1024,7 @@ CtH Rec::keyswitch(int B, int l, const std::function<const u64 *(int, int)> &d, 
                     const bool own = pieces == 1 && t >= lo && t < hi;
                     if (own) k.own = j;
                     k.src[j] = own ? d(b, t) : mul(b, j, t);
-                    k.key0[j] = key.buf->ptr + (((size_t)j * 2 + 0) * nQP + gp) * N;
-                    k.key1[j] = key.buf->ptr + (((size_t)j * 2 + 1) * nQP + gp) * N;
+                    k.key[j] = key.buf->ptr + ((size_t)j * nQP + gp) * 2 * N;
                 }
                 k.acc0 = accl(b, 0, t);
                 k.acc1 = accl(b, 1, t);

@@ -246,6 +246,25 @@ __global__ void __launch_bounds__(kEwThreads) aut_kernel(const AutJob *jobs, int
     }
 }
 
+// Pairs word (r, i, k) of the [rows][nl][n] pairs array with words (r, 0, i, k)
+// and (r, 1, i, k) of the [rows][2][nl][n] limbs array, in either direction.
+__global__ void __launch_bounds__(kEwThreads) interleave_kernel(u64 *limbs, u64 *pairs, size_t nl, size_t n,
+                                                                 size_t total, bool to_pairs) {
+    for (size_t it = blockIdx.x * (size_t)blockDim.x + threadIdx.x; it < total; it += (size_t)gridDim.x * blockDim.x) {
+        const size_t r = it / (nl * n), rest = it % (nl * n);
+        u64 *c0 = limbs + (2 * r) * nl * n + rest;
+        u64 *c1 = c0 + nl * n;
+        ulonglong2 *pp = reinterpret_cast<ulonglong2 *>(pairs) + it;
+        if (to_pairs) {
+            *pp = make_ulonglong2(*c0, *c1);
+        } else {
+            const ulonglong2 v = *pp;
+            *c0 = v.x;
+            *c1 = v.y;
+        }
+    }
+}
+
 // The automorphism of jobs at several ring degrees: one CTA per (job, chunk of
 // kEwThreads positions), each job with its own N and Galois element.
 __global__ void __launch_bounds__(kEwThreads) aut_multi_kernel(const AutJob *jobs, const TabEntry *tabs) {
@@ -393,6 +412,12 @@ void launch_automorphism_multi(const AutJob *jobs, int njobs, const TabEntry *ta
         dim3 grid(chunks, (unsigned)std::min(65535, njobs - j0));
         aut_multi_kernel<<<grid, kEwThreads, 0, s>>>(jobs + j0, tabs);
     }
+}
+void launch_interleave_pairs(u64 *limbs, u64 *pairs, size_t rows, size_t nl, size_t n, bool to_pairs,
+                             cudaStream_t s) {
+    const size_t total = rows * nl * n;
+    if (total == 0) return;
+    interleave_kernel<<<grid_for(total), kEwThreads, 0, s>>>(limbs, pairs, nl, n, total, to_pairs);
 }
 void launch_automorphism(const AutJob *jobs, int njobs, int log_n, uint32_t galois, cudaStream_t s) {
     if (njobs <= 0) return;

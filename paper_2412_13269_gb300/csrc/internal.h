@@ -204,6 +204,9 @@ struct AutJob {
     uint32_t tab;  // launches over several ring degrees: the job's table set
 };
 void launch_automorphism(const AutJob *jobs_dev, int njobs, int log_n, uint32_t galois, cudaStream_t s);
+// key layout conversion: [rows][2][nl][n] limbs <-> [rows][nl][n] pairs (component 0, component 1)
+void launch_interleave_pairs(u64 *limbs, u64 *pairs, size_t rows, size_t nl, size_t n, bool to_pairs,
+                             cudaStream_t s);
 // per-job Galois element and ring degree (tabs[job.tab].log_n); max_log_n the largest
 void launch_automorphism_multi(const AutJob *jobs_dev, int njobs, const TabEntry *tabs, int max_log_n, cudaStream_t s);
 
@@ -215,8 +218,7 @@ void launch_automorphism_multi(const AutJob *jobs_dev, int njobs, const TabEntry
 constexpr int kMaxKeyDigits = 64;
 struct KsJob {
     const u64 *src[kMaxKeyDigits];
-    const u64 *key0[kMaxKeyDigits];
-    const u64 *key1[kMaxKeyDigits];
+    const u64 *key[kMaxKeyDigits];  // digit j's key limb for prime t: N (component 0, component 1) pairs
     u64 *acc0, *acc1;
     const u64 *ex0, *ex1;  // optional: P e folded in (pm = [P]_{q_t}, Shoup companion pm_sh)
     u64 pm, pm_sh;

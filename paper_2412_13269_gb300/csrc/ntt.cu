@@ -536,8 +536,7 @@ __device__ __forceinline__ void keyswitch_up_body(NttTables tb, int log1, int lo
     const uint32_t tile_bytes = (uint32_t)g.sub_cta * (uint32_t)g.N2 * 8;
     auto prefetch_digit = [&](int d) {
         if (tid == 0 && d < nd && tile_bytes % 16 == 0) {
-            prefetch_l2_bulk(J.key0[d] + tile_off, tile_bytes);
-            prefetch_l2_bulk(J.key1[d] + tile_off, tile_bytes);
+            prefetch_l2_bulk(J.key[d] + 2 * (size_t)tile_off, 2 * tile_bytes);
             prefetch_l2_bulk(J.src[d] + tile_off, tile_bytes);
         }
     };
@@ -554,12 +553,13 @@ __device__ __forceinline__ void keyswitch_up_body(NttTables tb, int log1, int lo
             for (int k = 0; k < E; k++) x[k] = src[g.gidx(g.lrow(k))];
             run_stages<LOGM, false, false, LOGEV, OPEN>(g, x, sm, tw, q);
         }
-        const u64 *k0 = J.key0[d], *k1 = J.key1[d];
+        const ulonglong2 *kp = reinterpret_cast<const ulonglong2 *>(J.key[d]);  // (component 0, 1) pairs
 #pragma unroll
         for (int k = 0; k < E; k++) {
             const size_t gi = g.gidx(g.srow(k));
-            u64 v0 = mont_lazy(x[k], __ldg(k0 + gi), q, J.qinv);
-            u64 v1 = mont_lazy(x[k], __ldg(k1 + gi), q, J.qinv);
+            const ulonglong2 kk = __ldg(kp + gi);
+            u64 v0 = mont_lazy(x[k], kk.x, q, J.qinv);
+            u64 v1 = mont_lazy(x[k], kk.y, q, J.qinv);
             if (d > 0) {
                 v0 += slot(0, k);
                 v1 += slot(1, k);

@@ -20,7 +20,7 @@
 namespace tetris {
 
 struct Key {
-    BufPtr buf;      // NTT domain [dnum][2][nQP][N]
+    BufPtr buf;      // NTT domain [dnum][nQP][N][2]: both components of a word side by side
     int dnum = 0;    // key digits: CRT digits times base-2^w pieces
     int pieces = 1;  // base-2^w pieces per one-prime digit (1: no decomposition)
 };
