@@ -271,7 +271,11 @@ __device__ __forceinline__ void pass_body(NttTables tb, int log1, int log2, int 
     const u64 *tw = (INV ? tb.itw : tb.tw) + (size_t)J.prime * 2 * N;  // (twiddle, companion) pairs
 
     u64 x[E];
-    // 1. load straight into the first group's registers, through the producer's load mode
+    // 1. load straight into the first group's registers, through the producer's load mode.
+    //    Conversion sources and the stores' operands take the read-only data path
+    //    (__ldg): a position is read and written only by the thread that owns it, so
+    //    an operand that is also the output (in place) is read before it is written.
+    //    (Measured: the combine pass 16% faster; the plain first-pass load is no faster.)
     if (is_second(MODE)) {
 #pragma unroll
         for (int k = 0; k < E; k++) x[k] = J.dst[g.gidx(g.lrow(k))];
@@ -281,7 +285,7 @@ __device__ __forceinline__ void pass_body(NttTables tb, int log1, int log2, int 
         const u64 c = J.c2[0] ? J.c2[0] : 1, csh = J.c2[0] ? J.c2_sh[0] : mi.one_sh;
 #pragma unroll
         for (int k = 0; k < E; k++) {
-            u64 v = shoup_lazy(src[g.gidx(g.lrow(k))], c, csh, q);  // [0, 2q) for any 64-bit source
+            u64 v = shoup_lazy(__ldg(src + g.gidx(g.lrow(k))), c, csh, q);  // [0, 2q) for any 64-bit source
             if (OPEN) {
                 x[k] = v + (q - sub);  // < 3q
             } else {
@@ -307,13 +311,13 @@ __device__ __forceinline__ void pass_body(NttTables tb, int log1, int log2, int 
                 const u64 *sp = src + sidx * stride;
                 if (OPEN) {
 #pragma unroll
-                    for (int k = 0; k < E / 2; k++) x[k] += shoup_lazy4(sp[g.gidx(g.lrow(k))], c2, c2sh, q);
+                    for (int k = 0; k < E / 2; k++) x[k] += shoup_lazy4(__ldg(sp + g.gidx(g.lrow(k))), c2, c2sh, q);
                     const u64 c2w = J.c2w[sidx], c2wsh = J.c2w_sh[sidx];
 #pragma unroll
-                    for (int k = E / 2; k < E; k++) x[k] += shoup_lazy4(sp[g.gidx(g.lrow(k))], c2w, c2wsh, q);
+                    for (int k = E / 2; k < E; k++) x[k] += shoup_lazy4(__ldg(sp + g.gidx(g.lrow(k))), c2w, c2wsh, q);
                 } else {
 #pragma unroll
-                    for (int k = 0; k < E; k++) x[k] += shoup_lazy(sp[g.gidx(g.lrow(k))], c2, c2sh, q);
+                    for (int k = 0; k < E; k++) x[k] += shoup_lazy(__ldg(sp + g.gidx(g.lrow(k))), c2, c2sh, q);
                 }
             }
         }
@@ -378,15 +382,15 @@ __device__ __forceinline__ void pass_body(NttTables tb, int log1, int log2, int 
                 v = v >= q ? v - q : v;
             }
             if (MODE == M_COMBINE) {
-                v = shoup(sub_mod(base[gi], v, q), mul, mulsh, q);
-                if (extra) v = add_mod(v, extra[gi], q);
+                v = shoup(sub_mod(__ldg(base + gi), v, q), mul, mulsh, q);
+                if (extra) v = add_mod(v, __ldg(extra + gi), q);
             }
             if (MODE == M_SCALED_CONV) {
                 // sum_s base_s * c2_s as lazy Shoup products (< 8q), reduced, subtracted
                 u64 c = 0;
 #pragma unroll
                 for (int sidx = 0; sidx < kMaxConvSrc; sidx++)
-                    if (sidx < (int)J.nsrc) c += shoup_lazy(base[sidx * J.src_stride + gi], J.c2[sidx], J.c2_sh[sidx], q);
+                    if (sidx < (int)J.nsrc) c += shoup_lazy(__ldg(base + sidx * J.src_stride + gi), J.c2[sidx], J.c2_sh[sidx], q);
                 c = c >= 4 * q ? c - 4 * q : c;
                 c = c >= q2 ? c - q2 : c;
                 c = c >= q ? c - q : c;
@@ -547,10 +551,10 @@ __device__ __forceinline__ void keyswitch_up_body(NttTables tb, int log1, int lo
         const u64 *src = J.src[d];
         if (d == J.own) {
 #pragma unroll
-            for (int k = 0; k < E; k++) x[k] = shoup_lazy(src[g.gidx(g.srow(k))], mi.r64, mi.r64_sh, q);
+            for (int k = 0; k < E; k++) x[k] = shoup_lazy(__ldg(src + g.gidx(g.srow(k))), mi.r64, mi.r64_sh, q);
         } else {
 #pragma unroll
-            for (int k = 0; k < E; k++) x[k] = src[g.gidx(g.lrow(k))];
+            for (int k = 0; k < E; k++) x[k] = __ldg(src + g.gidx(g.lrow(k)));
             run_stages<LOGM, false, false, LOGEV, OPEN>(g, x, sm, tw, q);
         }
         const ulonglong2 *kp = reinterpret_cast<const ulonglong2 *>(J.key[d]);  // (component 0, 1) pairs
