@@ -68,7 +68,11 @@ def gpu_query(ctx, dbh, eq, stages):
 
 
 @pytest.mark.parametrize("records,attrs,degree,nst", [(2048, 8, 7, 1), (1500, 4, 3, 1), (3000, 3, 2, 1),
-                                                     (2048, 4, 12, 1), (2048, 4, 15, 1)])
+                                                     (2048, 4, 12, 1), (2048, 4, 15, 1),
+                                                     # degenerate shapes: one record and one attribute with a
+                                                     # linear f; a second block holding a single record; one
+                                                     # attribute filling exactly one block
+                                                     (1, 1, 1, 1), (2049, 2, 1, 2), (2048, 1, 2, 1)])
 def test_query_bit_exact(chain, records, attrs, degree, nst):
     par, ctx = chain.par, chain.ctx
     vals, qv, stages, shape, plan, db, eq = make_case(par, chain.s, records, attrs, degree, nst, records)
@@ -188,6 +192,11 @@ def test_plan_counts(chain):
     assert info.rotations == par.log_n - 1 and info.relins > 0 and info.kernel_launches > 0
     assert info.pt_scale == p.pt_scale
     ctx.free_database(dbh)
+
+
+def test_empty_database_refused(chain):
+    with pytest.raises(T.TetrisError):
+        chain.ctx.upload_database(np.zeros((0, 4), dtype=np.uint8))
 
 
 def test_errors_leave_context_usable(chain):
