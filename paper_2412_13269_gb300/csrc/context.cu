@@ -1204,6 +1204,37 @@ CtH Rec::relin_rescale(const CtH &t) {
     return o;
 }
 
+std::vector<CtH> Rec::relin_rescale_many(const std::vector<CtH> &ts) {
+    std::vector<CtH> outs;
+    if (ts.empty()) return outs;
+    bool same = true;
+    for (const CtH &t : ts) same = same && t.level == ts[0].level && t.comps == 3;
+    if (ts.size() == 1 || !same || defer || C.K() + 1 > kMaxConvSrc) {
+        for (const CtH &t : ts) outs.push_back(relin_rescale(t));
+        return outs;
+    }
+    TREQUIRE(ts[0].level >= 1, TETRIS_ELEVEL, "rescale at level 0");
+    // block b of the batch is block loc[b].second of ts[loc[b].first]
+    std::vector<std::pair<int, int>> loc;
+    for (size_t n = 0; n < ts.size(); n++)
+        for (int b = 0; b < ts[n].B; b++) loc.push_back({(int)n, b});
+    const Key &k = find_key(C, 0);
+    CtH o = keyswitch((int)loc.size(), ts[0].level,
+                      [&](int b, int i) { return (const u64 *)ts[loc[b].first].limb(loc[b].second, 2, i); }, k,
+                      [&](int b, int c, int i) { return (const u64 *)ts[loc[b].first].limb(loc[b].second, c, i); },
+                      true);
+    int b0 = 0;
+    for (const CtH &t : ts) {
+        CtH v = view(o.buf, o.base + (size_t)b0 * o.bstride, t.B, o.comps, o.level, o.bstride, o.cstride,
+                     t.scale / (double)C.q[t.level]);
+        outs.push_back(v);
+        b0 += t.B;
+        P.relins++;
+    }
+    P.rescales += (int)ts.size() - 1;  // the key switch counted one; one per ciphertext
+    return outs;
+}
+
 // Rescale (Section 2.5), per coefficient:
 //   out_i = (a_i + [floor(q_l/2)]_{q_i} - [[a_l + floor(q_l/2)]_{q_l}]_{q_i}) * q_l^-1;
 // the two constants are folded into the converted top limb before its NTT.

@@ -219,6 +219,9 @@ class Rec {
                   const std::function<const u64 *(int, int, int)> &extra, bool rescale_after = false);
     CtH relin(const CtH &t3);
     CtH relin_rescale(const CtH &t3);    // rescale(relin(t3)) in one pass over the targets
+    // independent degree-2 ciphertexts at one level, relinearised and rescaled by one
+    // batched key switch (their blocks side by side); each result as relin_rescale's
+    std::vector<CtH> relin_rescale_many(const std::vector<CtH> &ts);
     CtH rescale(const CtH &a, int64_t factor = 1);  // rescale(mul_int(a, factor))
     std::vector<CtH> rescale_many(const std::vector<std::pair<CtH, int64_t>> &items);
     CtH drop(const CtH &a, int level);

@@ -19,6 +19,7 @@
 //
 // A block group of nb blocks is evaluated with every launch covering all nb
 // blocks (nb = all blocks: batched form; nb = 1: plain per-ciphertext form).
+#include <algorithm>
 #include <cstring>
 #include <sstream>
 
@@ -239,21 +240,15 @@ static CtH fold(Rec &R, const CtH &T, const CtH &v, double a) {
     return T;
 }
 
+// One sign stage p(u) = sum_k a_k u^(2k+1): degree 7 in depth 3 as
 // c0 u + [(a1 u) u^2 + ((a3 u) u^2 + c2 u) u^4] from the adjusts a3u (level
-// l-1) and a1u (l-2): c2 u folded into (a3 u) u^2 before its relinearisation,
-// c0 u into the bracket's two degree-2 products, relinearised once; ends at l-3.
-static CtH odd7(Rec &R, const CtH &a3u, const CtH &a1u, double c2, double c0, const CtH &u, const CtH &u2,
-                const CtH &u2d, const CtH &u4, int l) {
-    CtH inner = relin_rescale_to(R, fold(R, R.tensor(a3u, u2), u, c2), l - 2);
-    CtH T = R.tensor_add(R.tensor(a1u, u2d), inner, u4);
-    return relin_rescale_to(R, fold(R, T, u, c0), l - 3);
-}
-
-// One sign stage p(u) = sum_k a_k u^(2k+1): degree 7 in depth 3 with four
-// relinearisations; degree 15 in depth 4 as A(u) + u^8 B(u), A and B the
-// degree-7 parts of the low and high coefficients (u^2, u^4 shared), eight
-// relinearisations, A folded into u^8 B.  The adjusts of u are independent:
-// one pair of transforms; u^2 is only dropped.
+// l-1) and a1u (l-2), c2 u folded into (a3 u) u^2 before its
+// relinearisation, c0 u into the bracket's two degree-2 products,
+// relinearised once (ends at l-3): four relinearisations; degree 15 in
+// depth 4 as A(u) + u^8 B(u), A and B the degree-7 parts of the low and
+// high coefficients (u^2, u^4 shared), eight relinearisations, A folded into
+// u^8 B.  The adjusts of u are independent: one pair of transforms; u^2 is
+// only dropped.
 static CtH sign_stage(Rec &R, const CtH &u, const std::vector<double> &co) {
     const int l = u.level;
     // u^2 is dropped to l-2 (scale S[l-1]); a1 u carries S[l-2] / S[l-1]
@@ -264,14 +259,28 @@ static CtH sign_stage(Rec &R, const CtH &u, const std::vector<double> &co) {
         items.push_back({u, l - 2, co[5] * r});
     }
     std::vector<CtH> a = R.adjust_many(items);
+    const bool deg15 = co.size() == 8;
     CtH u2 = R.mul(u, u);
-    CtH u4 = R.mul(u2, u2);
     CtH u2d = R.drop(u2, l - 2);
-    CtH A = odd7(R, a[0], a[1], co[2], co[0], u, u2, u2d, u4, l);
-    if (co.size() == 4) return A;
-    CtH u8 = R.mul(u4, u4);
-    CtH B = odd7(R, a[2], a[3], co[6], co[4], u, u2, u2d, u4, l);
-    return relin_rescale_to(R, fold(R, R.tensor(u8, B), A, 1.0), l - 4);
+    // the products of one depth are independent and share a level, so each
+    // depth's relinearisations are one batched key switch (the same arithmetic
+    // per ciphertext as odd7 and mul): at level l-1 u^4 and the inner products
+    // (a3 u) u^2 + a2 u of the degree-7 parts, at level l-2 their outer sums
+    // (and u^8)
+    std::vector<CtH> t1 = {R.tensor(u2, u2), fold(R, R.tensor(a[0], u2), u, co[2])};
+    if (deg15) t1.push_back(fold(R, R.tensor(a[2], u2), u, co[6]));
+    std::vector<CtH> r1 = R.relin_rescale_many(t1);
+    for (CtH &x : r1) x.scale = R.C.S[l - 2];
+    const CtH &u4 = r1[0];
+    std::vector<CtH> t2 = {fold(R, R.tensor_add(R.tensor(a[1], u2d), r1[1], u4), u, co[0])};
+    if (deg15) {
+        t2.push_back(fold(R, R.tensor_add(R.tensor(a[3], u2d), r1[2], u4), u, co[4]));
+        t2.push_back(R.tensor(u4, u4));
+    }
+    std::vector<CtH> r2 = R.relin_rescale_many(t2);
+    for (CtH &x : r2) x.scale = R.C.S[l - 3];
+    if (!deg15) return r2[0];
+    return relin_rescale_to(R, fold(R, R.tensor(r2[2], r2[1]), r2[0], 1.0), l - 4);
 }
 
 // The circuit of nb blocks; stop (TETRIS_STAGE_*) ends it after a stage and
@@ -332,21 +341,71 @@ static CtH eval_blocks(Rec &R, const Database &db, const QPlan &pl, int b0, int 
         y = relin_rescale_to(R, T, pl.l_y);
     } else {
         const int g = pl.g, m = pl.m, l_b = pl.l_lin - pl.bb, l_f = pl.l_lin - pl.df;
-        for (int k = 2; k < g; k++) Pw[k] = power_rule(Pw, k);
         std::map<int, CtH> G;  // giant powers x^(g i)
+        // the baby powers x^2 .. x^(g-1) and x^g = x^(g/2) x^(g/2), each by the power
+        // rule; the products whose factors are ready and share a level are
+        // relinearised by one batched key switch (the same arithmetic per power)
         {
-            std::map<int, CtH> h = {{1, Pw[g / 2]}};
-            G[1] = power_rule(h, 2);
+            std::vector<int> todo;  // k < g: x^k; k == g: the first giant power
+            for (int k = 2; k <= g; k++) todo.push_back(k);
+            while (!todo.empty()) {
+                std::map<int, std::vector<int>> by_level;  // ready powers by their factors' level
+                std::map<int, std::pair<CtH, CtH>> fac;
+                std::vector<int> rest;
+                for (int k : todo) {
+                    int a = 1;
+                    while (a * 2 <= k) a *= 2;
+                    const int ka = k == g ? g / 2 : (a == k ? k / 2 : a), kb = k == g ? g / 2 : (a == k ? k / 2 : k - a);
+                    if (!Pw.count(ka) || !Pw.count(kb)) {
+                        rest.push_back(k);
+                        continue;
+                    }
+                    const CtH A = Pw[ka];
+                    const CtH B = kb == ka ? A : R.drop(Pw[kb], A.level);
+                    fac[k] = {A, B};
+                    by_level[A.level].push_back(k);
+                }
+                TREQUIRE(!by_level.empty(), TETRIS_EINVAL, "power schedule: no power is ready");
+                for (auto &lv : by_level) {
+                    std::vector<CtH> ts;
+                    for (int k : lv.second) ts.push_back(R.tensor(fac[k].first, fac[k].second));
+                    std::vector<CtH> os = R.relin_rescale_many(ts);
+                    for (size_t n = 0; n < lv.second.size(); n++) {
+                        const int k = lv.second[n];
+                        const CtH &A = fac[k].first, &B = fac[k].second;
+                        os[n].scale = (A.scale * B.scale) / (double)C.q[A.level];
+                        if (k == g) G[1] = os[n];
+                        else Pw[k] = os[n];
+                    }
+                }
+                todo = rest;
+            }
         }
         for (int i = 2; i < m; i++) G[i] = power_rule(G, i);
         need_ck();
         CtH T;
         for (int j = 1; j < g; j++) T = R.tensor_add(T, ck[j], R.drop(Pw[j], l_f));  // s_0's terms at l_f
+        // the inner sums s_i = c_(g i) + sum_j c_(g i + j) x^j, independent of one
+        // another: their degree-2 sums relinearised by one batched key switch
+        std::vector<CtH> Ts;
+        std::vector<int> with_t;
         for (int i = 1; i < m; i++) {
             CtH Ti;
             for (int j = 1; j < g && g * i + j <= degree; j++) Ti = R.tensor_add(Ti, ck[g * i + j], R.drop(Pw[j], l_b));
+            if (Ti.buf) {
+                Ts.push_back(Ti);
+                with_t.push_back(i);
+            }
+        }
+        std::vector<CtH> rs = R.relin_rescale_many(Ts);
+        for (int i = 1; i < m; i++) {
             CtH si = ck[g * i];
-            if (Ti.buf) si = R.drop(R.add(relin_rescale_to(R, Ti, l_b - 1), ck[g * i]), l_f);
+            const auto it = std::find(with_t.begin(), with_t.end(), i);
+            if (it != with_t.end()) {
+                CtH r = rs[it - with_t.begin()];
+                r.scale = C.S[l_b - 1];
+                si = R.drop(R.add(r, ck[g * i]), l_f);
+            }
             T = R.tensor_add(T, si, R.drop(G[i], l_f));
         }
         G.clear();
