@@ -20,12 +20,15 @@ Pool::~Pool() {
     for (auto &a : all_) cudaFree(a.first - (guard_ ? kGuardWords : 0));
 }
 
-BufPtr Pool::alloc(size_t words) {
+BufPtr Pool::alloc(size_t words, bool fresh) {
     words = std::max<size_t>(words, 2);
     u64 *ptr = nullptr;
-    auto it = free_.find(words);
-    if (it != free_.end()) {
+    // best fit among the free buffers up to 4x the request (a buffer keeps its
+    // own size when it comes back), so requests of several sizes share buffers
+    auto it = fresh ? free_.end() : free_.lower_bound(words);
+    if (it != free_.end() && it->first <= 4 * words) {
         ptr = it->second;
+        words = it->first;
         free_.erase(it);
     } else {
         const size_t g = guard_ ? kGuardWords : 0, total = words + 2 * g;
@@ -181,7 +184,9 @@ size_t Program::add_jobs(const void *p, size_t bytes) {
 
 void Program::finalize() {
     if (arena.empty()) arena.resize(256);
-    arena_dev = pool.alloc((arena.size() + 7) / 8);
+    // a fresh buffer: one freed during recording may still be written by the
+    // program's own launches (reuse is safe in launch order, not after it)
+    arena_dev = pool.alloc((arena.size() + 7) / 8, true);
     TCHECK_CUDA(cudaMemcpy(arena_dev->ptr, arena.data(), arena.size(), cudaMemcpyHostToDevice));
 }
 
@@ -1204,6 +1209,11 @@ CtH Rec::relin_rescale(const CtH &t) {
     return o;
 }
 
+// A batched key switch's work buffers grow with its blocks (the ModUp output
+// alone is blocks x dnum x (l + 1 + K) limbs), and launches of this many
+// blocks already fill the GPU: batches stop there.
+constexpr int kRelinBatchBlocks = 12;
+
 std::vector<CtH> Rec::relin_rescale_many(const std::vector<CtH> &ts) {
     std::vector<CtH> outs;
     if (ts.empty()) return outs;
@@ -1211,6 +1221,24 @@ std::vector<CtH> Rec::relin_rescale_many(const std::vector<CtH> &ts) {
     for (const CtH &t : ts) same = same && t.level == ts[0].level && t.comps == 3;
     if (ts.size() == 1 || !same || defer || C.K() + 1 > kMaxConvSrc) {
         for (const CtH &t : ts) outs.push_back(relin_rescale(t));
+        return outs;
+    }
+    int total = 0;
+    for (const CtH &t : ts) total += t.B;
+    if (total > kRelinBatchBlocks) {  // consecutive groups of at most kRelinBatchBlocks blocks
+        std::vector<CtH> group;
+        int gb = 0;
+        auto flush = [&]() {
+            for (CtH &o : relin_rescale_many(group)) outs.push_back(o);
+            group.clear();
+            gb = 0;
+        };
+        for (const CtH &t : ts) {
+            if (!group.empty() && gb + t.B > kRelinBatchBlocks) flush();
+            group.push_back(t);
+            gb += t.B;
+        }
+        flush();
         return outs;
     }
     TREQUIRE(ts[0].level >= 1, TETRIS_ELEVEL, "rescale at level 0");

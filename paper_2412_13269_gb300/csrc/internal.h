@@ -71,7 +71,9 @@ class Pool {
   public:
     Pool();
     ~Pool();
-    BufPtr alloc(size_t words);
+    // fresh: a new device buffer, never one freed earlier (the job arena of a
+    // recorded program: buffers freed during recording are still used by its launches)
+    BufPtr alloc(size_t words, bool fresh = false);
     size_t bytes_held() const { return held_; }
     void trim();
     // true iff [p, p + words) lies inside one buffer of this pool
