@@ -132,28 +132,36 @@ const Key &find_key(const Ctx &c, uint32_t galois) {
 Program::~Program() {
     if (exec) cudaGraphExecDestroy(exec);
     if (graph) cudaGraphDestroy(graph);
-    if (exec_b) cudaGraphExecDestroy(exec_b);
-    if (graph_b) cudaGraphDestroy(graph_b);
     if (side) {
         cudaStreamSynchronize(side);
         cudaStreamDestroy(side);
     }
-    if (late_ev) cudaEventDestroy(late_ev);
+    for (auto &g : groups) {
+        if (g.exec) cudaGraphExecDestroy(g.exec);
+        if (g.graph) cudaGraphDestroy(g.graph);
+        if (g.ev) cudaEventDestroy(g.ev);
+    }
     if (early_ev) cudaEventDestroy(early_ev);
 }
 
-void Program::add_late_wait() {
-    TREQUIRE(late_slot <= in_slots.size(), TETRIS_EINVAL, "late inputs: no such slot");
-    TCHECK_CUDA(cudaEventCreateWithFlags(&late_ev, cudaEventDisableTiming));
-    TCHECK_CUDA(cudaEventCreateWithFlags(&early_ev, cudaEventDisableTiming));
-    TCHECK_CUDA(cudaStreamCreateWithFlags(&side, cudaStreamNonBlocking));
-    cudaEvent_t ev = late_ev;
+void Program::add_input_wait(size_t first) {
+    TREQUIRE(first <= in_slots.size() && (groups.empty() || first > groups.back().first), TETRIS_EINVAL,
+             "input groups: slots out of order");
+    if (!side) {
+        TCHECK_CUDA(cudaEventCreateWithFlags(&early_ev, cudaEventDisableTiming));
+        TCHECK_CUDA(cudaStreamCreateWithFlags(&side, cudaStreamNonBlocking));
+    }
+    InGroup g;
+    g.first = first;
+    TCHECK_CUDA(cudaEventCreateWithFlags(&g.ev, cudaEventDisableTiming));
+    cudaEvent_t ev = g.ev;
     Launch l;
     l.fn = [ev](cudaStream_t s, const uint8_t *) { TCHECK_CUDA(cudaStreamWaitEvent(s, ev, 0)); };
-    l.kind = "wait_late_inputs";
+    l.kind = "wait_inputs";
     l.kernel = false;
-    wait_at = launches.size();
+    g.wait_at = launches.size();
     launches.push_back(std::move(l));
+    groups.push_back(g);
 }
 
 void InSlot::copy_from(const void *src, cudaMemcpyKind kind, cudaStream_t s) const {
@@ -165,14 +173,17 @@ void InSlot::copy_from(const void *src, cudaMemcpyKind kind, cudaStream_t s) con
 
 void Program::copy_inputs(const std::vector<const void *> &srcs, cudaMemcpyKind kind, cudaStream_t s) {
     TREQUIRE(srcs.size() == in_slots.size(), TETRIS_EINVAL, "inputs do not match the program");
-    const size_t split = late_ev ? std::min(late_slot, srcs.size()) : srcs.size();
+    const size_t split = groups.empty() ? srcs.size() : std::min(groups[0].first, srcs.size());
     for (size_t i = 0; i < split; i++) in_slots[i].copy_from(srcs[i], kind, s);
-    if (!late_ev) return;
-    // the side stream starts after the early copies, which follow the previous run on s
+    if (groups.empty()) return;
+    // the side stream starts after the first group's copies, which follow the previous run on s
     TCHECK_CUDA(cudaEventRecord(early_ev, s));
     TCHECK_CUDA(cudaStreamWaitEvent(side, early_ev, 0));
-    for (size_t i = split; i < srcs.size(); i++) in_slots[i].copy_from(srcs[i], kind, side);
-    TCHECK_CUDA(cudaEventRecord(late_ev, side));
+    for (size_t k = 0; k < groups.size(); k++) {
+        const size_t end = k + 1 < groups.size() ? groups[k + 1].first : srcs.size();
+        for (size_t i = groups[k].first; i < end; i++) in_slots[i].copy_from(srcs[i], kind, side);
+        TCHECK_CUDA(cudaEventRecord(groups[k].ev, side));
+    }
 }
 
 size_t Program::add_jobs(const void *p, size_t bytes) {
@@ -236,10 +247,10 @@ void Program::run_profiled(cudaStream_t s, std::map<std::string, KernelStat> &st
     for (auto &e : ev) cudaEventDestroy(e);
 }
 
-// The launches captured as one CUDA graph, or as two around the wait for the
-// late inputs (a plain stream wait between the two graph launches).
+// The launches captured as one CUDA graph, or as one per segment between the
+// waits for input groups (a plain stream wait between two graph launches).
 void Program::run_graph(cudaStream_t s) {
-    const size_t cut = wait_at < launches.size() ? wait_at : launches.size();
+    const size_t cut = groups.empty() ? launches.size() : groups[0].wait_at;
     auto capture = [&](size_t i0, size_t i1, cudaGraph_t &g, cudaGraphExec_t &x) {
         cudaStream_t cs;
         TCHECK_CUDA(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
@@ -253,12 +264,15 @@ void Program::run_graph(cudaStream_t s) {
     };
     if (!exec) {
         capture(0, cut, graph, exec);
-        if (cut < launches.size()) capture(cut + 1, launches.size(), graph_b, exec_b);
+        for (size_t k = 0; k < groups.size(); k++) {
+            const size_t end = k + 1 < groups.size() ? groups[k + 1].wait_at : launches.size();
+            capture(groups[k].wait_at + 1, end, groups[k].graph, groups[k].exec);
+        }
     }
     TCHECK_CUDA(cudaGraphLaunch(exec, s));
-    if (exec_b) {
-        TCHECK_CUDA(cudaStreamWaitEvent(s, late_ev, 0));
-        TCHECK_CUDA(cudaGraphLaunch(exec_b, s));
+    for (auto &g : groups) {
+        TCHECK_CUDA(cudaStreamWaitEvent(s, g.ev, 0));
+        TCHECK_CUDA(cudaGraphLaunch(g.exec, s));
     }
 }
 

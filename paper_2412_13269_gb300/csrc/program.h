@@ -129,17 +129,23 @@ struct Program {
     size_t out_words = 0;
     int out_level = 0, out_comps = 0;
     double out_scale = 0;
-    cudaGraph_t graph = nullptr;
-    cudaGraphExec_t exec = nullptr;
-    // inputs in_slots[late_slot..] may arrive while the program runs: copy_inputs
-    // sends them on a side stream after the others and records late_ev, and the
-    // program waits for that event just before their first use
-    size_t late_slot = SIZE_MAX;
-    size_t wait_at = SIZE_MAX;  // index of the wait in launches
-    cudaEvent_t late_ev = nullptr, early_ev = nullptr;
+    // Inputs arrive in groups: in_slots[0, groups[0].first) are copied before the
+    // program runs; each later group may arrive while it runs (copy_inputs sends
+    // the groups in order on a side stream, recording each group's event), and
+    // the program waits for a group's event just before its first use.  A CUDA
+    // graph is captured per segment between two waits.
+    struct InGroup {
+        size_t first = 0;           // its first slot (it ends at the next group's)
+        size_t wait_at = 0;         // index of its wait in launches
+        cudaEvent_t ev = nullptr;
+        cudaGraph_t graph = nullptr;        // the launches after its wait
+        cudaGraphExec_t exec = nullptr;
+    };
+    std::vector<InGroup> groups;
+    cudaEvent_t early_ev = nullptr;
     cudaStream_t side = nullptr;
-    cudaGraph_t graph_b = nullptr;  // the launches after the wait
-    cudaGraphExec_t exec_b = nullptr;
+    cudaGraph_t graph = nullptr;  // the launches before the first wait
+    cudaGraphExec_t exec = nullptr;
     // counters
     int relins = 0, rescales = 0, rotations = 0;
     int ks_count = 0;
@@ -154,9 +160,9 @@ struct Program {
     void run_profiled(cudaStream_t s, std::map<std::string, KernelStat> &stats);
     void add_launch(std::function<void(cudaStream_t, const uint8_t *)> fn, const std::string &kind, double bytes,
                     double modmuls = 0, double units = 0);
-    // from here on the program may use in_slots[late_slot..]
-    void add_late_wait();
-    // copies srcs[i] into in_slots[i] (kind H2D or D2D), the late ones on the side stream
+    // from here on the program may use in_slots[first..] (groups in slot order)
+    void add_input_wait(size_t first);
+    // copies srcs[i] into in_slots[i] (kind H2D or D2D), the later groups on the side stream
     void copy_inputs(const std::vector<const void *> &srcs, cudaMemcpyKind kind, cudaStream_t s);
 };
 

@@ -27,6 +27,9 @@
 
 namespace tetris {
 
+// groups the w_j inputs are copied in (their transforms overlap the next group's copy)
+constexpr int kInputChunks = 4;
+
 struct QPlan {
     int l_lin, l_d, l_y, l_u, l_out;
     int l_ret = 1;  // the InnerSum and the returned ciphertext: drop to level 1 first
@@ -491,16 +494,23 @@ std::unique_ptr<Program> record_query(Ctx &C, const Database &db, const QuerySpe
         R.ntt(false, jobs, LOAD_PLAIN, STORE_PLAIN);
     };
     CtH w = R.view(wbuf, wbuf->ptr, q.attrs, 2, lw, wwords, (size_t)(lw + 1) * N, C.S[C.L()]);
-    ntt_inputs({w});
+    // the w_j arrive in up to kInputChunks groups: each group's transforms wait
+    // only for its own copy, so they overlap the next group's
+    const int chunks = std::min(q.attrs, kInputChunks), per = (q.attrs + chunks - 1) / chunks;
+    for (int j0 = 0; j0 < q.attrs; j0 += per) {
+        const int j1 = std::min(q.attrs, j0 + per);
+        if (j0 > 0) P->add_input_wait((size_t)j0);
+        ntt_inputs({R.view(wbuf, wbuf->ptr + (size_t)j0 * wwords, j1 - j0, 2, lw, wwords, (size_t)(lw + 1) * N,
+                           C.S[C.L()])});
+    }
     // the coefficients and the threshold (and t1) are late inputs: their copies
     // overlap the linear combination and the first powers of x, and they are
     // brought to their levels and transformed where first used
-    P->late_slot = (size_t)q.attrs;
     std::vector<CtH> ck;
     CtH tadj;
     auto need_ck = [&]() {
         if (!ck.empty()) return;
-        P->add_late_wait();
+        P->add_input_wait((size_t)q.attrs);
         std::vector<Rec::AdjustItem> items;
         for (int k = 0; k <= q.degree; k++) items.push_back({cin[k], pl.coef_level(k), pl.cfac[k]});
         items.push_back({tin, pl.l_y, 1.0});
