@@ -266,10 +266,10 @@ static CtH sign_stage(Rec &R, const CtH &u, const std::vector<double> &co) {
     CtH u2 = R.mul(u, u);
     CtH u2d = R.drop(u2, l - 2);
     // the products of one depth are independent and share a level, so each
-    // depth's relinearisations are one batched key switch (the same arithmetic
-    // per ciphertext as odd7 and mul): at level l-1 u^4 and the inner products
-    // (a3 u) u^2 + a2 u of the degree-7 parts, at level l-2 their outer sums
-    // (and u^8)
+    // depth's relinearisations are one batched key switch (each ciphertext's
+    // arithmetic as if relinearised alone): at level l-1 u^4 and the inner
+    // products (a3 u) u^2 + a2 u of the degree-7 parts, at level l-2 their
+    // outer sums (and u^8)
     std::vector<CtH> t1 = {R.tensor(u2, u2), fold(R, R.tensor(a[0], u2), u, co[2])};
     if (deg15) t1.push_back(fold(R, R.tensor(a[2], u2), u, co[6]));
     std::vector<CtH> r1 = R.relin_rescale_many(t1);
